@@ -1,0 +1,195 @@
+/*
+ * ibl.h - C ABI of the GB300 lattice-Boltzmann / dynamic-immersed-boundary
+ * solver (Coclite, de Tullio, Pascazio, Politi, "Characterization of
+ * micro-Capsules Deformation in Branching Channels").
+ *
+ * One call of ibl_step advances every lattice of a context by whole time steps
+ * of the coupled method:
+ *   - D3Q19 BGK collide + stream (Eq. evoleq, Eq. eqfunc) with the Guo forcing
+ *     term of the immersed-boundary force (Eq. forcing);
+ *   - Zou-He velocity / pressure conditions on the box faces (Eq. extbound);
+ *   - quadratic Bouzidi-Firdaouss-Lallemand bounce-back on fixed walls
+ *     (Eq. qbouzidi, Eq. bbouzidi);
+ *   - moving-least-squares interpolation / spreading between capsule mesh
+ *     vertices and the lattice (Eqs. uLag, l2norm, intKernel, bodyforce);
+ *   - spring-network membrane, volume penalty, probe-based hydrodynamic
+ *     stresses and inter-body repulsion (Eqs. strainPot .. collision);
+ *   - Verlet update of soft capsules (Eqs. verletPos .. verletPosC) and the
+ *     Newton-Euler update of rigid bodies (Eq. angularVelRig);
+ *   - the damage rule of Section "Transport of an elastic capsule": a mesh edge
+ *     at twice its rest length stops the run.
+ *
+ * Conventions
+ *   - Lattice units: dx = dt = 1, reference density 1, p = rho/3.
+ *   - Node index = x + nx*(y + ny*z) (x fastest).
+ *   - Direction numbering is the one of Eq. e_i.
+ *   - Faces: 0 = x-, 1 = x+, 2 = y-, 3 = y+, 4 = z-, 5 = z+.  A face array is
+ *     laid out with the lower remaining axis fastest (face 0/1: y + ny*z,
+ *     face 2/3: x + nx*z, face 4/5: x + nx*y).
+ *   - Ownership: the library copies every input; outputs go to caller
+ *     buffers.  A buffer flagged on_device is a device pointer that the
+ *     library reads/writes on the context's stream.
+ *   - Errors: every call returns an ibl_status; ibl_last_error gives the text.
+ *     No call throws across the ABI.  CUDA failures return IBL_ERR_CUDA.
+ *   - The library owns all device memory of a context (allocated with
+ *     cudaMalloc when the context is first stepped or read) and frees it in
+ *     ibl_destroy.
+ */
+#ifndef IBL_H
+#define IBL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibl_ctx ibl_ctx;
+
+typedef enum {
+    IBL_OK = 0,
+    IBL_ERR_ARG = -1,        /* invalid argument or inconsistent geometry      */
+    IBL_ERR_OOM = -2,        /* device or host allocation failed               */
+    IBL_ERR_CUDA = -3,       /* a CUDA runtime call failed                      */
+    IBL_ERR_DAMAGED = -4,    /* a capsule edge reached twice its rest length   */
+    IBL_ERR_NONFINITE = -5,  /* a vertex position became NaN/Inf               */
+    IBL_ERR_TIMEOUT = -6,    /* reserved: a bounded device wait gave up        */
+    IBL_ERR_STATE = -7       /* call not allowed in the context's current state */
+} ibl_status;
+
+/* storage of the distributions f_i - w_i (arithmetic is always FP32) */
+enum { IBL_STORAGE_F32 = 0, IBL_STORAGE_F16 = 1, IBL_STORAGE_BF16 = 2 };
+/* Dirichlet kind of a box face (Section "Dirichlet conditions ...") */
+enum { IBL_FACE_NONE = 0, IBL_FACE_VELOCITY = 1, IBL_FACE_PRESSURE = 2 };
+
+typedef struct {
+    int32_t nx, ny, nz;      /* lattice nodes per axis (each >= 3)               */
+    int32_t storage;         /* IBL_STORAGE_*                                    */
+    int32_t periodic[3];     /* nonzero: the axis wraps                          */
+    int32_t reserved;
+    double tau;              /* BGK relaxation time; nu = (tau - 1/2)/3 (> 0.5)  */
+    double body_force[3];    /* uniform force density added to f_ib              */
+    double u_max;            /* characteristic velocity of Eq. collision         */
+} ibl_lattice_desc;
+
+/* A fixed-wall link (Eq. qbouzidi): node + e_dir is solid and the wall cuts the
+ * link at fraction q in (0, 1] of its length, measured from node.  dq is the
+ * derivative of q with respect to the geometry parameter (kept for the
+ * gradient path; ignored by the forward step). */
+typedef struct {
+    uint32_t node;
+    uint32_t dir;
+    float q;
+    float dq;
+} ibl_wall_link;
+
+/* Capsule material (Section "Deforming bodies constitutive model"):
+ * k_s0 = rho nu u_ref / Ca, k_s,l = k_s0 (A_a + A_b) / l0^2,
+ * k_b = Eb k_s,l r^2 (r = radius of the rest volume), volume penalty kv,
+ * mass = density_ratio * rest volume.  rigid != 0: Newton-Euler body. */
+typedef struct {
+    double Ca, Eb, kv, density_ratio, u_ref;
+    int32_t rigid;
+    int32_t reserved;
+} ibl_capsule_params;
+
+/* FP64 capsule diagnostics at the current state. */
+typedef struct {
+    double centroid[3];      /* volume centroid                                   */
+    double volume, area;     /* enclosed volume, surface area                      */
+    double dS;               /* (S - S0)/S0, the relative stretching of Section 2 */
+    double taylor_D;         /* (a_max - a_min)/(a_max + a_min), equivalent ellipsoid */
+    double max_stretch;      /* max edge length / rest length                      */
+    double semi_axes[3];     /* ascending                                          */
+    double velocity[3];      /* mean vertex velocity                               */
+    int32_t damaged;
+    int32_t reserved;
+} ibl_capsule_stats;
+
+/* Create a context with one lattice.  cuda_stream: a cudaStream_t (NULL = the
+ * legacy default stream); every device operation of the context runs on it.
+ * Until the first ibl_step / ibl_read_* the context holds host data only. */
+ibl_status ibl_create(const ibl_lattice_desc* desc, void* cuda_stream, ibl_ctx** out);
+
+/* Fixed geometry (Section "No-Slip boundary conditions for stationary immersed
+ * boundaries"): cell_tag[nx*ny*nz] 0 = fluid, 1 = solid; links as above (only
+ * fluid nodes whose neighbour along dir is solid and inside the box).  Every
+ * fluid node on a non-periodic face must lie on exactly one face. */
+ibl_status ibl_set_geometry(ibl_ctx* ctx, const uint8_t* cell_tag,
+                            const ibl_wall_link* links, size_t n_links);
+
+/* Velocity face: u_xyz[3 * n_face] (face layout, x,y,z per node) is imposed
+ * on the fluid nodes of the face (Eq. extbound). */
+ibl_status ibl_set_inlet_velocity(ibl_ctx* ctx, int32_t face, const float* u_xyz);
+
+/* Pressure face: density rho_out with zero tangential velocity. */
+ibl_status ibl_set_outlet_pressure(ibl_ctx* ctx, int32_t face, double rho_out);
+
+/* Initial populations at equilibrium with rho[N] and u[3N] (x,y,z per node);
+ * either may be NULL (rho = 1, u = 0).  Default: rest state. */
+ibl_status ibl_init_equilibrium(ibl_ctx* ctx, const float* rho, const float* u);
+
+/* Add a closed triangular mesh (verts[3*nv] FP64, tris[3*nt] outward CCW)
+ * whose vertices are the Lagrangian markers.  vel0[3] may be NULL. */
+ibl_status ibl_add_capsule(ibl_ctx* ctx, const double* verts, int32_t nv,
+                           const int32_t* tris, int32_t nt, const double* vel0,
+                           const ibl_capsule_params* params, int32_t* id_out);
+
+/* Advance n_steps time steps.  steps_done (may be NULL) receives the steps
+ * member 0 completed.  Returns IBL_ERR_DAMAGED when a capsule broke (the state
+ * stays readable and the damaged lattice stops stepping), IBL_ERR_NONFINITE
+ * when a vertex left the finite range. */
+ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done);
+
+/* Macroscopic fields of member 0: rho[N], u[3N] (either may be NULL), with
+ * rho u = sum f e + F_body/2; solid nodes read 0. */
+ibl_status ibl_read_fields(ibl_ctx* ctx, float* rho, float* u, int32_t on_device);
+
+/* Populations f_i - w_i of member 0 in FP32, layout [19][N], as they stand
+ * before the next collision (wall and face values included). */
+ibl_status ibl_read_populations(ibl_ctx* ctx, float* g, int32_t on_device);
+
+/* Capsule id of member 0: FP64 diagnostics and (optional) vertices[3 nv]. */
+ibl_status ibl_read_capsule(ibl_ctx* ctx, int32_t id, ibl_capsule_stats* stats,
+                            double* verts_out);
+
+/* Per-vertex state of a capsule of member 0: positions x(t) and x(t-dt),
+ * velocity, and the total force of the last step (FP64, 3 per vertex, each
+ * pointer may be NULL). */
+ibl_status ibl_read_capsule_state(ibl_ctx* ctx, int32_t id, double* x, double* x_prev,
+                                  double* vel, double* force);
+
+/* Batched sweep: a new context holding copies of the (not yet stepped)
+ * members' set-up, stepped together in one launch per kernel.  All members
+ * must use the same storage. The member contexts stay valid. */
+ibl_status ibl_ensemble_create(ibl_ctx* const* members, int32_t n, void* cuda_stream,
+                               ibl_ctx** out);
+int32_t ibl_num_members(const ibl_ctx* ctx);
+ibl_status ibl_member_read_fields(ibl_ctx* ctx, int32_t member, float* rho, float* u,
+                                  int32_t on_device);
+ibl_status ibl_member_read_capsule(ibl_ctx* ctx, int32_t member, int32_t id,
+                                   ibl_capsule_stats* stats, double* verts_out);
+ibl_status ibl_member_steps(const ibl_ctx* ctx, int32_t member, int32_t* steps_done);
+
+/* Launch shape of the lattice kernel: threads per block (multiple of 32,
+ * <= 1024) and blocks per SM of the persistent grid (0 = one block per tile).
+ * Used by the autotuner; takes effect at the next step. */
+ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
+
+/* Device time of the last ibl_step's kernels by kind, in milliseconds, when
+ * timing was enabled with ibl_enable_timing (0 otherwise):
+ * out[0] lattice, out[1] walls, out[2] IB pre-pass, out[3] structure. */
+ibl_status ibl_enable_timing(ibl_ctx* ctx, int32_t on);
+ibl_status ibl_kernel_times(ibl_ctx* ctx, double* out4);
+
+/* Message of the last failed call on ctx (or of the last failed ibl_create /
+ * ibl_ensemble_create when ctx is NULL). */
+const char* ibl_last_error(const ibl_ctx* ctx);
+
+void ibl_destroy(ibl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBL_H */

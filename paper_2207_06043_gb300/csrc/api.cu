@@ -1,0 +1,987 @@
+// Host runtime of libibl: context and member set-up, mesh topology and rest
+// quantities, device buffers, the per-step launch sequence with CUDA-graph
+// replay, read-out and the C ABI of include/ibl.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ibl.h"
+#include "ibl_internal.cuh"
+
+using namespace ibl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct CapsuleHost {
+    std::vector<double> X;
+    std::vector<int> tris;
+    double vel0[3] = {0, 0, 0};
+    ibl_capsule_params p{};
+};
+
+struct MemberHost {
+    ibl_lattice_desc desc{};
+    std::vector<uint8_t> tag;
+    std::vector<ibl_wall_link> links;
+    int face_kind[6] = {0, 0, 0, 0, 0, 0};
+    double face_rho[6] = {1, 1, 1, 1, 1, 1};
+    std::vector<float> face_vel[6];
+    std::vector<float> init_rho, init_u;
+    std::vector<CapsuleHost> caps;
+};
+
+// Rest data of one capsule kept on the host for read-out.
+struct CapsuleRestHost {
+    int member, v_begin, nv, t_begin, nt, e_begin, ne;
+    double S0, V0;
+    std::vector<double> l0;
+    std::vector<int> edges;   // 2 per edge, local vertex ids
+    int rigid;
+};
+
+}  // namespace
+
+struct ibl_ctx {
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int storage = IBL_STORAGE_F32;
+    std::vector<MemberHost> members;
+    bool finalized = false;
+    long long t = 0;   // steps launched
+    DevState dev;
+    std::vector<MemberDev> hmem;
+    std::vector<CapsuleRestHost> rest;
+    std::vector<std::vector<int>> member_caps;   // global capsule ids per member
+    std::vector<void*> allocs;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool use_graphs = true;
+    int threads = 256;
+    int blocks_per_sm = 0;
+    int n_sm = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    double ktime[4] = {0, 0, 0, 0};
+    std::vector<int> h_counters;
+    std::vector<uint32_t> h_status;
+    std::string err;
+};
+
+namespace {
+
+ibl_status fail(ibl_ctx* ctx, ibl_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    else g_last_error = msg;
+    return st;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, IBL_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKS(call)                                   \
+    do {                                            \
+        ibl_status s_ = (call);                     \
+        if (s_ != IBL_OK) return s_;                \
+    } while (0)
+
+template <typename T>
+ibl_status dev_alloc(ibl_ctx* ctx, T*& p, size_t count) {
+    p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, IBL_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(sizeof(T) * count) +
+                                          " bytes failed: " + cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back((void*)p);
+    return IBL_OK;
+}
+
+template <typename T>
+ibl_status upload(ibl_ctx* ctx, T* dst, const std::vector<T>& src) {
+    if (src.empty()) return IBL_OK;
+    CK(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, ctx->work));
+    return IBL_OK;
+}
+
+inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------------------
+// mesh topology and rest quantities (Section "Deforming bodies constitutive
+// model"); independent host implementation
+// ---------------------------------------------------------------------------
+struct V3 { double x, y, z; };
+inline V3 vsub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 vcross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+inline double vdot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline double vnorm(V3 a) { return std::sqrt(vdot(a, a)); }
+
+// hinges: for every edge {p<q}: (wing of p->q, p, q, wing of q->p), sorted by (p, q)
+bool build_hinges(const std::vector<int>& tris, int nv, std::vector<int>& hinge, std::vector<int>& tri_a,
+                  std::vector<int>& tri_b, std::string& why) {
+    std::map<std::pair<int, int>, std::pair<int, int>> half;   // (u,v) -> (tri, wing)
+    const int nt = (int)tris.size() / 3;
+    for (int t = 0; t < nt; ++t) {
+        const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv || a == b || b == c || a == c) {
+            why = "triangle " + std::to_string(t) + " has an invalid vertex index";
+            return false;
+        }
+        const int uvw[3][3] = {{a, b, c}, {b, c, a}, {c, a, b}};
+        for (auto& r : uvw) {
+            auto key = std::make_pair(r[0], r[1]);
+            if (half.count(key)) { why = "edge used twice in the same direction (mesh not consistently oriented)"; return false; }
+            half[key] = std::make_pair(t, r[2]);
+        }
+    }
+    hinge.clear(); tri_a.clear(); tri_b.clear();
+    for (auto& kv : half) {
+        const int u = kv.first.first, v = kv.first.second;
+        if (u > v) continue;
+        auto it = half.find(std::make_pair(v, u));
+        if (it == half.end()) { why = "mesh is not closed"; return false; }
+        hinge.push_back(kv.second.second);
+        hinge.push_back(u);
+        hinge.push_back(v);
+        hinge.push_back(it->second.second);
+        tri_a.push_back(kv.second.first);
+        tri_b.push_back(it->second.first);
+    }
+    for (auto& kv : half) {
+        if (kv.first.first > kv.first.second && !half.count(std::make_pair(kv.first.second, kv.first.first))) {
+            why = "mesh is not closed";
+            return false;
+        }
+    }
+    return true;
+}
+
+double signed_dihedral(V3 v1, V3 v2, V3 v3, V3 v4) {
+    const V3 nA = vcross(vsub(v2, v1), vsub(v3, v1));
+    const V3 nB = vcross(vsub(v3, v4), vsub(v2, v4));
+    const V3 e = vsub(v3, v2);
+    const double L = vnorm(e);
+    const V3 eh = {e.x / L, e.y / L, e.z / L};
+    return std::atan2(vdot(vcross(nA, nB), eh), vdot(nA, nB));
+}
+
+struct MeshSums { double V, S; V3 cen; double M2[6]; };
+
+// volume, area, volume centroid and second moments about the centroid of a
+// closed mesh (tetrahedra fanned from the vertex mean)
+MeshSums mesh_sums(const double* X, int nv, const int* tris, int nt) {
+    V3 o = {0, 0, 0};
+    for (int v = 0; v < nv; ++v) { o.x += X[3 * v]; o.y += X[3 * v + 1]; o.z += X[3 * v + 2]; }
+    o.x /= nv; o.y /= nv; o.z /= nv;
+    MeshSums s{};
+    double cen[3] = {0, 0, 0};
+    for (int t = 0; t < nt; ++t) {
+        const int* T = tris + 3 * t;
+        const V3 a = vsub({X[3 * T[0]], X[3 * T[0] + 1], X[3 * T[0] + 2]}, o);
+        const V3 b = vsub({X[3 * T[1]], X[3 * T[1] + 1], X[3 * T[1] + 2]}, o);
+        const V3 c = vsub({X[3 * T[2]], X[3 * T[2] + 1], X[3 * T[2] + 2]}, o);
+        const double v = vdot(a, vcross(b, c)) / 6.0;
+        s.V += v;
+        s.S += 0.5 * vnorm(vcross(vsub(b, a), vsub(c, a)));
+        const V3 q = {a.x + b.x + c.x, a.y + b.y + c.y, a.z + b.z + c.z};
+        cen[0] += v * q.x / 4; cen[1] += v * q.y / 4; cen[2] += v * q.z / 4;
+        const double w = v / 20.0;
+        s.M2[0] += w * (a.x * a.x + b.x * b.x + c.x * c.x + q.x * q.x);
+        s.M2[1] += w * (a.y * a.y + b.y * b.y + c.y * c.y + q.y * q.y);
+        s.M2[2] += w * (a.z * a.z + b.z * b.z + c.z * c.z + q.z * q.z);
+        s.M2[3] += w * (a.x * a.y + b.x * b.y + c.x * c.y + q.x * q.y);
+        s.M2[4] += w * (a.x * a.z + b.x * b.z + c.x * c.z + q.x * q.z);
+        s.M2[5] += w * (a.y * a.z + b.y * b.z + c.y * c.z + q.y * q.z);
+    }
+    const V3 cr = {cen[0] / s.V, cen[1] / s.V, cen[2] / s.V};
+    s.M2[0] -= s.V * cr.x * cr.x; s.M2[1] -= s.V * cr.y * cr.y; s.M2[2] -= s.V * cr.z * cr.z;
+    s.M2[3] -= s.V * cr.x * cr.y; s.M2[4] -= s.V * cr.x * cr.z; s.M2[5] -= s.V * cr.y * cr.z;
+    s.cen = {o.x + cr.x, o.y + cr.y, o.z + cr.z};
+    return s;
+}
+
+// eigenvalues of a symmetric 3x3 matrix (cyclic Jacobi), ascending
+void sym3_eigen(const double M[6], double ev[3]) {
+    double a[3][3] = {{M[0], M[3], M[4]}, {M[3], M[1], M[5]}, {M[4], M[5], M[2]}};
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        if (off < 1e-300) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (std::fabs(a[p][q]) < 1e-300) continue;
+                const double th = 0.5 * std::atan2(2 * a[p][q], a[q][q] - a[p][p]);
+                const double c = std::cos(th), s = std::sin(th);
+                double b[3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) b[i][j] = a[i][j];
+                for (int k = 0; k < 3; ++k) {
+                    b[p][k] = c * a[p][k] - s * a[q][k];
+                    b[q][k] = s * a[p][k] + c * a[q][k];
+                }
+                for (int k = 0; k < 3; ++k) {
+                    a[k][p] = c * b[k][p] - s * b[k][q];
+                    a[k][q] = s * b[k][p] + c * b[k][q];
+                }
+                for (int k = 0; k < 3; ++k)
+                    if (k != p && k != q) { a[p][k] = b[p][k]; a[q][k] = b[q][k]; }
+                a[p][p] = c * c * b[p][p] - 2 * s * c * b[p][q] + s * s * b[q][q];
+                a[q][q] = s * s * b[p][p] + 2 * s * c * b[p][q] + c * c * b[q][q];
+                a[p][q] = a[q][p] = 0.0;
+            }
+    }
+    ev[0] = a[0][0]; ev[1] = a[1][1]; ev[2] = a[2][2];
+    std::sort(ev, ev + 3);
+}
+
+ibl_status enter(ibl_ctx* ctx) {
+    CK(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+    CK(cudaStreamWaitEvent(ctx->work, ctx->ev_in, 0));
+    return IBL_OK;
+}
+
+ibl_status leave(ibl_ctx* ctx) {
+    CK(cudaEventRecord(ctx->ev_out, ctx->work));
+    CK(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+    return IBL_OK;
+}
+
+void layout_tiles(ibl_ctx* ctx) {
+    int tiles = 0;
+    for (auto& m : ctx->hmem) {
+        m.tile_begin = tiles;
+        m.tile_count = (m.N + ctx->threads - 1) / ctx->threads;
+        tiles += m.tile_count;
+    }
+    ctx->dev.threads = ctx->threads;
+    ctx->dev.total_tiles = tiles;
+    ctx->dev.grid_lbm = ctx->blocks_per_sm > 0 ? std::min(tiles, ctx->blocks_per_sm * ctx->n_sm) : 0;
+}
+
+void drop_graphs(ibl_ctx* ctx) {
+    for (auto& g : ctx->graph)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+ibl_status validate_member(ibl_ctx* ctx, const MemberHost& M) {
+    const auto& d = M.desc;
+    const long long N = (long long)d.nx * d.ny * d.nz;
+    if ((long long)M.tag.size() != N) return fail(ctx, IBL_ERR_STATE, "geometry not set");
+    const int dims[3] = {d.nx, d.ny, d.nz};
+    for (long long n = 0; n < N; ++n) {
+        if (M.tag[n] != 0) continue;
+        const int c[3] = {(int)(n % d.nx), (int)((n / d.nx) % d.ny), (int)(n / ((long long)d.nx * d.ny))};
+        int nf = 0, face = -1;
+        for (int a = 0; a < 3; ++a) {
+            if (d.periodic[a]) continue;
+            if (c[a] == 0) { ++nf; face = 2 * a; }
+            if (c[a] == dims[a] - 1) { ++nf; face = 2 * a + 1; }
+        }
+        if (nf > 1)
+            return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on an edge of the box (two faces)");
+        if (nf == 1 && M.face_kind[face] == IBL_FACE_NONE)
+            return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on face " + std::to_string(face) +
+                                               " which has no velocity or pressure condition");
+    }
+    return IBL_OK;
+}
+
+ibl_status finalize(ibl_ctx* ctx) {
+    if (ctx->finalized) return IBL_OK;
+    int dev_id = 0;
+    CK(cudaGetDevice(&dev_id));
+    CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev_id));
+    const int nm = (int)ctx->members.size();
+    if (nm < 1 || nm > MAX_MEMBERS) return fail(ctx, IBL_ERR_ARG, "member count out of range");
+    for (auto& M : ctx->members) CKS(validate_member(ctx, M));
+
+    const size_t esize = ctx->storage == IBL_STORAGE_F32 ? 4 : 2;
+    DevState& D = ctx->dev;
+    D.storage = ctx->storage;
+    D.n_members = nm;
+    ctx->hmem.assign(nm, MemberDev{});
+    long long f_off = 0, node_off = 0, face_off = 0, cell_off = 0;
+    int link_off = 0, cap_off = 0, vert_off = 0;
+    std::vector<uint8_t> tag_all;
+    std::vector<float> face_all;
+    std::vector<uint32_t> l_node, l_meta;
+    std::vector<float> l_q;
+    // capsule arrays
+    std::vector<CapsuleDev> caps;
+    std::vector<int> v_cap, tri_all, hinge_all, e_cap;
+    std::vector<double> x_all, vel_all;
+    std::vector<float> l0_all, ks_all, th0_all, kb_all;
+    int max_nv = 0, tri_off = 0, edge_off = 0;
+    bool any_soft = false, any_rigid = false, any_cells = false;
+    ctx->member_caps.assign(nm, {});
+
+    for (int mi = 0; mi < nm; ++mi) {
+        const MemberHost& M = ctx->members[mi];
+        const auto& d = M.desc;
+        MemberDev& md = ctx->hmem[mi];
+        md.nx = d.nx; md.ny = d.ny; md.nz = d.nz;
+        md.px = d.periodic[0] ? 0 : 1; md.py = d.periodic[1] ? 0 : 1; md.pz = d.periodic[2] ? 0 : 1;
+        md.per = (d.periodic[0] ? 1 : 0) | (d.periodic[1] ? 2 : 0) | (d.periodic[2] ? 4 : 0);
+        md.NX = d.nx + 2 * md.px; md.NY = d.ny + 2 * md.py; md.NZ = d.nz + 2 * md.pz;
+        const long long Np = (long long)md.NX * md.NY * md.NZ;
+        if (Np * 19 >= (1LL << 31)) return fail(ctx, IBL_ERR_ARG, "lattice too large for one member");
+        md.N = (int)Np;
+        md.S = (int)round_up((size_t)Np, 64);
+        md.f_off = f_off;
+        md.node_off = node_off;
+        f_off += 19LL * md.S;
+        node_off += (long long)round_up((size_t)Np, 256);
+        md.omega = (float)(1.0 / d.tau);
+        md.guo = (float)(1.0 - 0.5 / d.tau);
+        md.nu = (float)((d.tau - 0.5) / 3.0);
+        md.umax = (float)d.u_max;
+        for (int a = 0; a < 3; ++a) md.F[a] = (float)d.body_force[a];
+        md.hasF = (d.body_force[0] != 0 || d.body_force[1] != 0 || d.body_force[2] != 0) ? 1 : 0;
+        md.st_scale = ctx->storage == IBL_STORAGE_F16 ? 4096.f : 1.f;
+        md.ld_scale = ctx->storage == IBL_STORAGE_F16 ? 1.f / 4096.f : 1.f;
+        for (int fc = 0; fc < 6; ++fc) {
+            md.face_kind[fc] = M.face_kind[fc];
+            md.face_rho[fc] = (float)M.face_rho[fc];
+            md.face_off[fc] = -1;
+            if (M.face_kind[fc] == IBL_FACE_VELOCITY) {
+                md.face_off[fc] = face_off;
+                face_all.insert(face_all.end(), M.face_vel[fc].begin(), M.face_vel[fc].end());
+                face_off += (long long)M.face_vel[fc].size() / 3;
+            }
+        }
+        // padded tags (ghost layer solid)
+        const size_t base = tag_all.size();
+        tag_all.resize(base + round_up((size_t)Np, 256), TAG_SOLID);
+        for (int z = 0; z < d.nz; ++z)
+            for (int y = 0; y < d.ny; ++y)
+                for (int x = 0; x < d.nx; ++x) {
+                    const long long un = x + (long long)d.nx * (y + (long long)d.ny * z);
+                    const long long pn = (x + md.px) + (long long)md.NX * ((y + md.py) + (long long)md.NY * (z + md.pz));
+                    tag_all[base + pn] = M.tag[un] ? TAG_SOLID : 0;
+                }
+        // links
+        md.link_begin = link_off;
+        const int dims[3] = {d.nx, d.ny, d.nz};
+        auto shift = [&](int c[3], int s, int k, int out[3]) -> bool {
+            const int e[3] = {ex(k), ey(k), ez(k)};
+            bool ok = true;
+            for (int a = 0; a < 3; ++a) {
+                int v = c[a] + s * e[a];
+                if (d.periodic[a]) v = ((v % dims[a]) + dims[a]) % dims[a];
+                else if (v < 0 || v >= dims[a]) ok = false;
+                out[a] = v;
+            }
+            return ok;
+        };
+        auto fluid_at = [&](int c[3]) { return M.tag[c[0] + (long long)d.nx * (c[1] + (long long)d.ny * c[2])] == 0; };
+        for (size_t li = 0; li < M.links.size(); ++li) {
+            const ibl_wall_link& L = M.links[li];
+            const long long Nu = (long long)d.nx * d.ny * d.nz;
+            if ((long long)L.node >= Nu || L.dir < 1 || L.dir > 18 || !(L.q > 0.f && L.q <= 1.f))
+                return fail(ctx, IBL_ERR_ARG, "wall link " + std::to_string(li) + " out of range");
+            int c[3] = {(int)(L.node % d.nx), (int)((L.node / d.nx) % d.ny), (int)(L.node / ((long long)d.nx * d.ny))};
+            int s0[3], m1[3], m2[3];
+            if (!fluid_at(c)) return fail(ctx, IBL_ERR_ARG, "wall link " + std::to_string(li) + " starts at a solid node");
+            if (!shift(c, 1, L.dir, s0) || fluid_at(s0))
+                return fail(ctx, IBL_ERR_ARG, "wall link " + std::to_string(li) + " does not end at a solid node inside the box");
+            const bool ok1 = shift(c, -1, L.dir, m1) && fluid_at(m1);
+            const bool ok2 = shift(c, -2, L.dir, m2) && fluid_at(m2);
+            const long long pn = (c[0] + md.px) + (long long)md.NX * ((c[1] + md.py) + (long long)md.NY * (c[2] + md.pz));
+            l_node.push_back((uint32_t)pn);
+            l_meta.push_back(L.dir | (ok1 ? 32u : 0u) | (ok2 ? 64u : 0u) | ((uint32_t)mi << 8));
+            l_q.push_back(L.q);
+        }
+        md.link_count = (int)M.links.size();
+        link_off += md.link_count;
+        // capsules
+        md.cap_begin = cap_off;
+        md.cap_count = (int)M.caps.size();
+        md.vert_begin = vert_off;
+        const double nu = (d.tau - 0.5) / 3.0;
+        for (const CapsuleHost& ch : M.caps) {
+            const int nv = (int)ch.X.size() / 3, nt = (int)ch.tris.size() / 3;
+            std::vector<int> hinge, ta, tb;
+            std::string why;
+            if (!build_hinges(ch.tris, nv, hinge, ta, tb, why)) return fail(ctx, IBL_ERR_ARG, "capsule mesh: " + why);
+            const int ne = (int)hinge.size() / 4;
+            const double* X = ch.X.data();
+            MeshSums ms = mesh_sums(X, nv, ch.tris.data(), nt);
+            if (!(ms.V > 0)) return fail(ctx, IBL_ERR_ARG, "capsule mesh encloses no volume (triangles must be outward CCW)");
+            std::vector<double> tri_area(nt);
+            for (int t = 0; t < nt; ++t) {
+                const int* T = &ch.tris[3 * t];
+                const V3 a = {X[3 * T[0]], X[3 * T[0] + 1], X[3 * T[0] + 2]};
+                const V3 b = {X[3 * T[1]], X[3 * T[1] + 1], X[3 * T[1] + 2]};
+                const V3 c = {X[3 * T[2]], X[3 * T[2] + 1], X[3 * T[2] + 2]};
+                tri_area[t] = 0.5 * vnorm(vcross(vsub(b, a), vsub(c, a)));
+            }
+            const double radius = std::cbrt(3.0 * ms.V / (4.0 * M_PI));
+            const double ks0 = ch.p.Ca > 0 ? nu * ch.p.u_ref / ch.p.Ca : 0.0;   // Ca = rho nu u_ref / k_s0
+            CapsuleDev cd{};
+            cd.member = mi;
+            cd.rigid = ch.p.rigid ? 1 : 0;
+            cd.v_begin = vert_off; cd.v_count = nv;
+            cd.t_begin = tri_off; cd.t_count = nt;
+            cd.e_begin = edge_off; cd.e_count = ne;
+            cd.kv = ch.p.kv; cd.V0 = ms.V; cd.S0 = ms.S;
+            cd.mass = ch.p.density_ratio * ms.V;
+            cd.mv = cd.mass / nv;
+            cd.inertia = 0.4 * cd.mass * radius * radius;
+            cd.xc[0] = ms.cen.x; cd.xc[1] = ms.cen.y; cd.xc[2] = ms.cen.z;
+            for (int a = 0; a < 3; ++a) { cd.u1[a] = cd.u2[a] = ch.vel0[a]; cd.w1[a] = cd.w2[a] = 0.0; }
+            CapsuleRestHost rh;
+            rh.member = mi; rh.v_begin = vert_off; rh.nv = nv; rh.t_begin = tri_off; rh.nt = nt;
+            rh.e_begin = edge_off; rh.ne = ne; rh.S0 = ms.S; rh.V0 = ms.V; rh.rigid = cd.rigid;
+            for (int e = 0; e < ne; ++e) {
+                const int* h = &hinge[4 * e];
+                const V3 p1 = {X[3 * h[0]], X[3 * h[0] + 1], X[3 * h[0] + 2]};
+                const V3 p2 = {X[3 * h[1]], X[3 * h[1] + 1], X[3 * h[1] + 2]};
+                const V3 p3 = {X[3 * h[2]], X[3 * h[2] + 1], X[3 * h[2] + 2]};
+                const V3 p4 = {X[3 * h[3]], X[3 * h[3] + 1], X[3 * h[3] + 2]};
+                const double l0 = vnorm(vsub(p3, p2));
+                const double ks = ks0 * (tri_area[ta[e]] + tri_area[tb[e]]) / (l0 * l0);   // T = 1
+                const double kb = ch.p.Eb * ks * radius * radius;                           // Eb = k_b/(k_s,l r^2)
+                for (int j = 0; j < 4; ++j) hinge_all.push_back(vert_off + h[j]);
+                l0_all.push_back((float)l0);
+                ks_all.push_back((float)ks);
+                kb_all.push_back((float)kb);
+                th0_all.push_back((float)signed_dihedral(p1, p2, p3, p4));
+                e_cap.push_back(cap_off);
+                rh.l0.push_back(l0);
+                rh.edges.push_back(h[1]);
+                rh.edges.push_back(h[2]);
+            }
+            for (int t = 0; t < nt; ++t)
+                for (int j = 0; j < 3; ++j) tri_all.push_back(vert_off + ch.tris[3 * t + j]);
+            for (int v = 0; v < nv; ++v) {
+                v_cap.push_back(cap_off);
+                for (int a = 0; a < 3; ++a) {
+                    x_all.push_back(X[3 * v + a]);
+                    vel_all.push_back(ch.vel0[a]);
+                }
+            }
+            caps.push_back(cd);
+            ctx->rest.push_back(rh);
+            ctx->member_caps[mi].push_back(cap_off);
+            max_nv = std::max(max_nv, nv);
+            any_soft |= !cd.rigid;
+            any_rigid |= (bool)cd.rigid;
+            ++cap_off;
+            vert_off += nv;
+            tri_off += nt;
+            edge_off += ne;
+        }
+        md.vert_count = vert_off - md.vert_begin;
+        md.has_cells = md.cap_count >= 2 ? 1 : 0;
+        md.cell_off = cell_off;
+        md.cnx = (d.nx + 1) / 2; md.cny = (d.ny + 1) / 2; md.cnz = (d.nz + 1) / 2;
+        if (md.has_cells) {
+            cell_off += (long long)md.cnx * md.cny * md.cnz;
+            any_cells = true;
+        }
+    }
+    if (max_nv > 12000) return fail(ctx, IBL_ERR_ARG, "a capsule has more than 12000 vertices");
+
+    layout_tiles(ctx);
+    // device buffers
+    CKS(dev_alloc(ctx, (uint8_t*&)D.f, (size_t)f_off * esize));
+    CKS(dev_alloc(ctx, D.tag, tag_all.size()));
+    CKS(dev_alloc(ctx, D.face_vel, std::max<size_t>(face_all.size(), 3)));
+    CKS(dev_alloc(ctx, D.status, nm));
+    CKS(dev_alloc(ctx, D.counters, nm));
+    D.n_links = link_off;
+    CKS(dev_alloc(ctx, D.l_node, l_node.size()));
+    CKS(dev_alloc(ctx, D.l_meta, l_meta.size()));
+    CKS(dev_alloc(ctx, D.l_q, l_q.size()));
+    CKS(upload(ctx, D.tag, tag_all));
+    CKS(upload(ctx, D.face_vel, face_all));
+    CKS(upload(ctx, D.l_node, l_node));
+    CKS(upload(ctx, D.l_meta, l_meta));
+    CKS(upload(ctx, D.l_q, l_q));
+    CK(cudaMemsetAsync(D.status, 0, sizeof(uint32_t) * nm, ctx->work));
+    CK(cudaMemsetAsync(D.counters, 0, sizeof(int) * nm, ctx->work));
+    D.n_caps = cap_off; D.n_verts = vert_off; D.n_tris = tri_off; D.n_edges = edge_off;
+    D.any_soft = any_soft; D.any_rigid = any_rigid; D.any_cells = any_cells; D.max_nv = max_nv;
+    if (cap_off > 0) {
+        CKS(dev_alloc(ctx, D.fib, 3 * (size_t)node_off));
+        CK(cudaMemsetAsync(D.fib, 0, sizeof(float) * 3 * (size_t)node_off, ctx->work));
+        CKS(dev_alloc(ctx, D.caps, caps.size()));
+        CKS(dev_alloc(ctx, D.sums, caps.size()));
+        CKS(dev_alloc(ctx, D.v_cap, v_cap.size()));
+        CKS(dev_alloc(ctx, D.x, x_all.size()));
+        CKS(dev_alloc(ctx, D.x_prev, x_all.size()));
+        CKS(dev_alloc(ctx, D.vel, vel_all.size()));
+        CKS(dev_alloc(ctx, D.force, x_all.size()));
+        CKS(dev_alloc(ctx, D.uv0, x_all.size()));
+        CKS(dev_alloc(ctx, D.nrm, x_all.size()));
+        CKS(dev_alloc(ctx, D.area, (size_t)vert_off));
+        CKS(dev_alloc(ctx, D.phi, 27 * (size_t)vert_off));
+        CKS(dev_alloc(ctx, D.tri, tri_all.size()));
+        CKS(dev_alloc(ctx, D.hinge, hinge_all.size()));
+        CKS(dev_alloc(ctx, D.l0, l0_all.size()));
+        CKS(dev_alloc(ctx, D.ks, ks_all.size()));
+        CKS(dev_alloc(ctx, D.th0, th0_all.size()));
+        CKS(dev_alloc(ctx, D.kb, kb_all.size()));
+        CKS(dev_alloc(ctx, D.e_cap, e_cap.size()));
+        CKS(upload(ctx, D.caps, caps));
+        CK(cudaMemsetAsync(D.sums, 0, sizeof(CapsuleSums) * caps.size(), ctx->work));
+        CKS(upload(ctx, D.v_cap, v_cap));
+        CKS(upload(ctx, D.x, x_all));
+        CKS(upload(ctx, D.x_prev, x_all));
+        CKS(upload(ctx, D.vel, vel_all));
+        CK(cudaMemsetAsync(D.force, 0, sizeof(float) * x_all.size(), ctx->work));
+        CK(cudaMemsetAsync(D.uv0, 0, sizeof(float) * x_all.size(), ctx->work));
+        CKS(upload(ctx, D.tri, tri_all));
+        CKS(upload(ctx, D.hinge, hinge_all));
+        CKS(upload(ctx, D.l0, l0_all));
+        CKS(upload(ctx, D.ks, ks_all));
+        CKS(upload(ctx, D.th0, th0_all));
+        CKS(upload(ctx, D.kb, kb_all));
+        CKS(upload(ctx, D.e_cap, e_cap));
+        if (any_cells) {
+            D.n_cells = cell_off;
+            CKS(dev_alloc(ctx, D.cell_count, (size_t)cell_off));
+            CKS(dev_alloc(ctx, D.cell_items, (size_t)cell_off * CELL_CAP));
+        }
+    }
+    D.h_mem = ctx->hmem.data();
+    lbm_set_members(ctx->hmem.data(), nm, ctx->work);
+    ib_set_members(ctx->hmem.data(), nm, ctx->work);
+    CK(cudaGetLastError());
+    // initial populations
+    for (int mi = 0; mi < nm; ++mi) {
+        const MemberHost& M = ctx->members[mi];
+        float* drho = nullptr;
+        float* du = nullptr;
+        if (!M.init_rho.empty()) { CK(cudaMalloc((void**)&drho, sizeof(float) * M.init_rho.size())); }
+        if (!M.init_u.empty()) { CK(cudaMalloc((void**)&du, sizeof(float) * M.init_u.size())); }
+        if (drho) CK(cudaMemcpyAsync(drho, M.init_rho.data(), sizeof(float) * M.init_rho.size(), cudaMemcpyHostToDevice, ctx->work));
+        if (du) CK(cudaMemcpyAsync(du, M.init_u.data(), sizeof(float) * M.init_u.size(), cudaMemcpyHostToDevice, ctx->work));
+        CK(launch_init_member(D, mi, drho, du, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        if (drho) cudaFree(drho);
+        if (du) cudaFree(du);
+    }
+    CK(launch_geometry(D, 0, ctx->work));
+    ctx->h_counters.assign(nm, 0);
+    ctx->h_status.assign(nm, 0);
+    CK(cudaStreamSynchronize(ctx->work));
+    ctx->finalized = true;
+    return IBL_OK;
+}
+
+enum { TK_LBM = 0, TK_BFL = 1, TK_IB = 2, TK_STRUCT = 3 };
+
+ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<std::pair<int, cudaEvent_t>>* marks) {
+    DevState& D = ctx->dev;
+    cudaStream_t s = ctx->work;
+    auto mark = [&](int kind) -> ibl_status {
+        if (!marks) return IBL_OK;
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        CK(cudaEventRecord(e, s));
+        marks->push_back(std::make_pair(kind, e));
+        return IBL_OK;
+    };
+    const bool caps = D.n_caps > 0;
+    if (caps) {
+        CKS(mark(TK_IB));
+        CK(launch_geometry(D, 0, s));
+        CK(launch_ib(D, parity, zh_on, s));
+    }
+    CKS(mark(TK_LBM));
+    CK(launch_lbm(D, parity, zh_on, s));
+    CKS(mark(TK_BFL));
+    CK(launch_bfl(D, parity, s));
+    CKS(mark(TK_STRUCT));
+    if (caps) {
+        CK(launch_post(D, 1 - parity, s));
+        CK(launch_edges(D, s));
+        CK(launch_repulsion(D, s));
+        CK(launch_update(D, s));
+    }
+    CKS(mark(-1));
+    return IBL_OK;
+}
+
+ibl_status capture_graph(ibl_ctx* ctx, int parity) {
+    if (ctx->graph[parity]) return IBL_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->work, cudaStreamCaptureModeThreadLocal));
+    ibl_status st = enqueue_step(ctx, parity, 1, nullptr);
+    cudaError_t e = cudaStreamEndCapture(ctx->work, &g);
+    if (st != IBL_OK) { if (g) cudaGraphDestroy(g); return st; }
+    CK(e);
+    e = cudaGraphInstantiate(&ctx->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return IBL_OK;
+}
+
+ibl_status sync_host_state(ibl_ctx* ctx) {
+    const int nm = ctx->dev.n_members;
+    CK(cudaMemcpyAsync(ctx->h_counters.data(), ctx->dev.counters, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaMemcpyAsync(ctx->h_status.data(), ctx->dev.status, sizeof(uint32_t) * nm, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    return IBL_OK;
+}
+
+MemberHost* member0(ibl_ctx* ctx) { return ctx->members.empty() ? nullptr : &ctx->members[0]; }
+
+ibl_status read_fields_member(ibl_ctx* ctx, int m, float* rho, float* u, float* g, int on_device) {
+    if (m < 0 || m >= (int)ctx->members.size()) return fail(ctx, IBL_ERR_ARG, "member out of range");
+    CKS(finalize(ctx));
+    CKS(enter(ctx));
+    const MemberDev& md = ctx->hmem[m];
+    const size_t Nu = (size_t)md.nx * md.ny * md.nz;
+    const int cnt = ctx->h_counters[m];
+    const int parity = cnt & 1, zh_on = cnt > 0 ? 1 : 0;
+    if (on_device) {
+        CK(launch_read(ctx->dev, m, parity, zh_on, rho, u, g, ctx->work));
+    } else {
+        float *dr = nullptr, *du = nullptr, *dg = nullptr;
+        if (rho) CK(cudaMalloc((void**)&dr, sizeof(float) * Nu));
+        if (u) CK(cudaMalloc((void**)&du, sizeof(float) * 3 * Nu));
+        if (g) CK(cudaMalloc((void**)&dg, sizeof(float) * 19 * Nu));
+        CK(launch_read(ctx->dev, m, parity, zh_on, dr, du, dg, ctx->work));
+        if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(float) * Nu, cudaMemcpyDeviceToHost, ctx->work));
+        if (u) CK(cudaMemcpyAsync(u, du, sizeof(float) * 3 * Nu, cudaMemcpyDeviceToHost, ctx->work));
+        if (g) CK(cudaMemcpyAsync(g, dg, sizeof(float) * 19 * Nu, cudaMemcpyDeviceToHost, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
+        if (dr) cudaFree(dr);
+        if (du) cudaFree(du);
+        if (dg) cudaFree(dg);
+    }
+    CKS(leave(ctx));
+    return IBL_OK;
+}
+
+ibl_status read_capsule_member(ibl_ctx* ctx, int m, int id, ibl_capsule_stats* st, double* verts_out) {
+    if (m < 0 || m >= (int)ctx->members.size()) return fail(ctx, IBL_ERR_ARG, "member out of range");
+    CKS(finalize(ctx));
+    if (id < 0 || id >= (int)ctx->member_caps[m].size()) return fail(ctx, IBL_ERR_ARG, "capsule id out of range");
+    const int cap = ctx->member_caps[m][id];
+    const CapsuleRestHost& R = ctx->rest[cap];
+    CKS(enter(ctx));
+    std::vector<double> X(3 * (size_t)R.nv), V(3 * (size_t)R.nv);
+    CK(cudaMemcpyAsync(X.data(), ctx->dev.x + 3 * (size_t)R.v_begin, sizeof(double) * X.size(), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaMemcpyAsync(V.data(), ctx->dev.vel + 3 * (size_t)R.v_begin, sizeof(double) * V.size(), cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    CKS(leave(ctx));
+    if (verts_out) std::memcpy(verts_out, X.data(), sizeof(double) * X.size());
+    if (st) {
+        const std::vector<int>& tris = ctx->members[m].caps[id].tris;
+        MeshSums ms = mesh_sums(X.data(), R.nv, tris.data(), R.nt);
+        std::memset(st, 0, sizeof(*st));
+        st->centroid[0] = ms.cen.x; st->centroid[1] = ms.cen.y; st->centroid[2] = ms.cen.z;
+        st->volume = ms.V;
+        st->area = ms.S;
+        st->dS = (ms.S - R.S0) / R.S0;
+        double ev[3];
+        sym3_eigen(ms.M2, ev);
+        for (int a = 0; a < 3; ++a) st->semi_axes[a] = std::sqrt(std::max(5.0 * ev[a] / ms.V, 0.0));
+        st->taylor_D = (st->semi_axes[2] - st->semi_axes[0]) / (st->semi_axes[2] + st->semi_axes[0]);
+        double mx = 0.0;
+        for (int e = 0; e < R.ne; ++e) {
+            const int a = R.edges[2 * e], b = R.edges[2 * e + 1];
+            const double dx = X[3 * a] - X[3 * b], dy = X[3 * a + 1] - X[3 * b + 1], dz = X[3 * a + 2] - X[3 * b + 2];
+            mx = std::max(mx, std::sqrt(dx * dx + dy * dy + dz * dz) / R.l0[e]);
+        }
+        st->max_stretch = R.rigid ? 1.0 : mx;
+        for (int v = 0; v < R.nv; ++v)
+            for (int a = 0; a < 3; ++a) st->velocity[a] += V[3 * v + a] / R.nv;
+        st->damaged = (ctx->h_status[m] & ST_DAMAGED) ? 1 : 0;
+    }
+    return IBL_OK;
+}
+
+ibl_status new_ctx(void* stream, ibl_ctx** out) {
+    ibl_ctx* ctx = new (std::nothrow) ibl_ctx();
+    if (!ctx) return fail(nullptr, IBL_ERR_OOM, "host allocation failed");
+    ctx->user_stream = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, IBL_ERR_CUDA, std::string("stream/event creation failed: ") + cudaGetErrorString(e));
+    }
+    *out = ctx;
+    return IBL_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+ibl_status ibl_create(const ibl_lattice_desc* desc, void* cuda_stream, ibl_ctx** out) {
+    if (!desc || !out) return fail(nullptr, IBL_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (desc->nx < 3 || desc->ny < 3 || desc->nz < 1 || (desc->nz < 3 && !desc->periodic[2]))
+        return fail(nullptr, IBL_ERR_ARG, "lattice dimensions too small (non-periodic axes need >= 3 nodes)");
+    if (desc->nx < 3 && !desc->periodic[0]) return fail(nullptr, IBL_ERR_ARG, "lattice dimensions too small");
+    if (!(desc->tau > 0.5)) return fail(nullptr, IBL_ERR_ARG, "tau must exceed 1/2");
+    if (desc->storage < 0 || desc->storage > 2) return fail(nullptr, IBL_ERR_ARG, "unknown storage");
+    ibl_ctx* ctx = nullptr;
+    ibl_status st = new_ctx(cuda_stream, &ctx);
+    if (st != IBL_OK) return st;
+    ctx->storage = desc->storage;
+    ctx->members.resize(1);
+    ctx->members[0].desc = *desc;
+    const size_t N = (size_t)desc->nx * desc->ny * desc->nz;
+    ctx->members[0].tag.assign(N, 0);
+    *out = ctx;
+    return IBL_OK;
+}
+
+ibl_status ibl_set_geometry(ibl_ctx* ctx, const uint8_t* cell_tag, const ibl_wall_link* links, size_t n_links) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (ctx->finalized) return fail(ctx, IBL_ERR_STATE, "geometry is fixed once the context has been stepped or read");
+    if (ctx->members.size() != 1) return fail(ctx, IBL_ERR_STATE, "an ensemble takes its geometry from its members");
+    MemberHost& M = ctx->members[0];
+    const size_t N = M.tag.size();
+    if (!cell_tag || (n_links && !links)) return fail(ctx, IBL_ERR_ARG, "null geometry array");
+    for (size_t n = 0; n < N; ++n)
+        if (cell_tag[n] > 1) return fail(ctx, IBL_ERR_ARG, "cell_tag values must be 0 (fluid) or 1 (solid)");
+    M.tag.assign(cell_tag, cell_tag + N);
+    M.links.assign(links, links + n_links);
+    return IBL_OK;
+}
+
+static size_t face_count(const ibl_lattice_desc& d, int face) {
+    return face < 2 ? (size_t)d.ny * d.nz : (face < 4 ? (size_t)d.nx * d.nz : (size_t)d.nx * d.ny);
+}
+
+ibl_status ibl_set_inlet_velocity(ibl_ctx* ctx, int32_t face, const float* u_xyz) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (ctx->finalized) return fail(ctx, IBL_ERR_STATE, "faces are fixed once the context has been stepped or read");
+    if (face < 0 || face > 5 || !u_xyz) return fail(ctx, IBL_ERR_ARG, "bad face or null velocity");
+    MemberHost* M = member0(ctx);
+    if (M->desc.periodic[face / 2]) return fail(ctx, IBL_ERR_ARG, "face lies on a periodic axis");
+    const size_t n = face_count(M->desc, face);
+    M->face_kind[face] = IBL_FACE_VELOCITY;
+    M->face_vel[face].assign(u_xyz, u_xyz + 3 * n);
+    return IBL_OK;
+}
+
+ibl_status ibl_set_outlet_pressure(ibl_ctx* ctx, int32_t face, double rho_out) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (ctx->finalized) return fail(ctx, IBL_ERR_STATE, "faces are fixed once the context has been stepped or read");
+    if (face < 0 || face > 5 || !(rho_out > 0)) return fail(ctx, IBL_ERR_ARG, "bad face or density");
+    MemberHost* M = member0(ctx);
+    if (M->desc.periodic[face / 2]) return fail(ctx, IBL_ERR_ARG, "face lies on a periodic axis");
+    M->face_kind[face] = IBL_FACE_PRESSURE;
+    M->face_rho[face] = rho_out;
+    M->face_vel[face].clear();
+    return IBL_OK;
+}
+
+ibl_status ibl_init_equilibrium(ibl_ctx* ctx, const float* rho, const float* u) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (ctx->finalized) return fail(ctx, IBL_ERR_STATE, "initial state is fixed once the context has been stepped or read");
+    MemberHost* M = member0(ctx);
+    const size_t N = M->tag.size();
+    if (rho) M->init_rho.assign(rho, rho + N); else M->init_rho.clear();
+    if (u) M->init_u.assign(u, u + 3 * N); else M->init_u.clear();
+    return IBL_OK;
+}
+
+ibl_status ibl_add_capsule(ibl_ctx* ctx, const double* verts, int32_t nv, const int32_t* tris, int32_t nt,
+                           const double* vel0, const ibl_capsule_params* params, int32_t* id_out) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (ctx->finalized) return fail(ctx, IBL_ERR_STATE, "capsules must be added before the first step or read");
+    if (!verts || !tris || !params || nv < 4 || nt < 4) return fail(ctx, IBL_ERR_ARG, "bad capsule arguments");
+    if (!params->rigid && !(params->Ca > 0)) return fail(ctx, IBL_ERR_ARG, "a soft capsule needs Ca > 0");
+    if (!(params->density_ratio > 0)) return fail(ctx, IBL_ERR_ARG, "density_ratio must be positive");
+    MemberHost* M = member0(ctx);
+    CapsuleHost ch;
+    ch.X.assign(verts, verts + 3 * (size_t)nv);
+    ch.tris.assign(tris, tris + 3 * (size_t)nt);
+    if (vel0) for (int a = 0; a < 3; ++a) ch.vel0[a] = vel0[a];
+    ch.p = *params;
+    std::vector<int> h, ta, tb;
+    std::string why;
+    if (!build_hinges(ch.tris, nv, h, ta, tb, why)) return fail(ctx, IBL_ERR_ARG, "capsule mesh: " + why);
+    M->caps.push_back(std::move(ch));
+    if (id_out) *id_out = (int32_t)M->caps.size() - 1;
+    return IBL_OK;
+}
+
+ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (n_steps < 0) return fail(ctx, IBL_ERR_ARG, "negative step count");
+    CKS(finalize(ctx));
+    const int before = ctx->h_counters[0];
+    CKS(enter(ctx));
+    std::vector<std::pair<int, cudaEvent_t>> marks;
+    for (int s = 0; s < n_steps; ++s) {
+        const int parity = (int)(ctx->t & 1);
+        const int zh_on = ctx->t > 0 ? 1 : 0;
+        if (ctx->timing) {
+            CKS(enqueue_step(ctx, parity, zh_on, &marks));
+        } else if (zh_on && ctx->use_graphs) {
+            CKS(capture_graph(ctx, parity));
+            CK(cudaGraphLaunch(ctx->graph[parity], ctx->work));
+        } else {
+            CKS(enqueue_step(ctx, parity, zh_on, nullptr));
+        }
+        ctx->t += 1;
+    }
+    CKS(sync_host_state(ctx));
+    CKS(leave(ctx));
+    if (ctx->timing) {
+        for (double& v : ctx->ktime) v = 0.0;
+        for (size_t i = 0; i + 1 < marks.size(); ++i) {
+            const int kind = marks[i].first;
+            if (kind < 0) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, marks[i].second, marks[i + 1].second);
+            ctx->ktime[kind] += ms;
+        }
+        for (auto& mk : marks) cudaEventDestroy(mk.second);
+    }
+    if (steps_done) *steps_done = ctx->h_counters[0] - before;
+    uint32_t any = 0;
+    for (uint32_t s : ctx->h_status) any |= s;
+    if (any & ST_NONFINITE) return fail(ctx, IBL_ERR_NONFINITE, "a capsule vertex became non-finite");
+    if (any & ST_DAMAGED) return fail(ctx, IBL_ERR_DAMAGED, "a capsule edge reached twice its rest length");
+    if (any & ST_OVERFLOW) return fail(ctx, IBL_ERR_ARG, "repulsion cell list overflow (markers too dense)");
+    return IBL_OK;
+}
+
+ibl_status ibl_read_fields(ibl_ctx* ctx, float* rho, float* u, int32_t on_device) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    return read_fields_member(ctx, 0, rho, u, nullptr, on_device);
+}
+
+ibl_status ibl_read_populations(ibl_ctx* ctx, float* g, int32_t on_device) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (!g) return fail(ctx, IBL_ERR_ARG, "null output");
+    return read_fields_member(ctx, 0, nullptr, nullptr, g, on_device);
+}
+
+ibl_status ibl_read_capsule(ibl_ctx* ctx, int32_t id, ibl_capsule_stats* stats, double* verts_out) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    return read_capsule_member(ctx, 0, id, stats, verts_out);
+}
+
+ibl_status ibl_read_capsule_state(ibl_ctx* ctx, int32_t id, double* x, double* x_prev, double* vel, double* force) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    CKS(finalize(ctx));
+    if (id < 0 || id >= (int)ctx->member_caps[0].size()) return fail(ctx, IBL_ERR_ARG, "capsule id out of range");
+    const CapsuleRestHost& R = ctx->rest[ctx->member_caps[0][id]];
+    const size_t n3 = 3 * (size_t)R.nv, off = 3 * (size_t)R.v_begin;
+    CKS(enter(ctx));
+    std::vector<float> F(n3);
+    if (x) CK(cudaMemcpyAsync(x, ctx->dev.x + off, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->work));
+    if (x_prev) CK(cudaMemcpyAsync(x_prev, ctx->dev.x_prev + off, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->work));
+    if (vel) CK(cudaMemcpyAsync(vel, ctx->dev.vel + off, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->work));
+    if (force) CK(cudaMemcpyAsync(F.data(), ctx->dev.force + off, sizeof(float) * n3, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    CKS(leave(ctx));
+    if (force) for (size_t i = 0; i < n3; ++i) force[i] = F[i];
+    return IBL_OK;
+}
+
+ibl_status ibl_ensemble_create(ibl_ctx* const* members, int32_t n, void* cuda_stream, ibl_ctx** out) {
+    if (!members || !out || n < 1 || n > MAX_MEMBERS) return fail(nullptr, IBL_ERR_ARG, "bad ensemble arguments");
+    *out = nullptr;
+    int storage = -1;
+    for (int i = 0; i < n; ++i) {
+        if (!members[i]) return fail(nullptr, IBL_ERR_ARG, "null member");
+        if (members[i]->finalized) return fail(nullptr, IBL_ERR_STATE, "ensemble members must not have been stepped or read");
+        if (storage >= 0 && members[i]->storage != storage) return fail(nullptr, IBL_ERR_ARG, "members use different storage");
+        storage = members[i]->storage;
+    }
+    ibl_ctx* ctx = nullptr;
+    ibl_status st = new_ctx(cuda_stream, &ctx);
+    if (st != IBL_OK) return st;
+    ctx->storage = storage;
+    for (int i = 0; i < n; ++i)
+        for (const MemberHost& M : members[i]->members) ctx->members.push_back(M);
+    if ((int)ctx->members.size() > MAX_MEMBERS) {
+        ibl_destroy(ctx);
+        return fail(nullptr, IBL_ERR_ARG, "too many members");
+    }
+    *out = ctx;
+    return IBL_OK;
+}
+
+int32_t ibl_num_members(const ibl_ctx* ctx) { return ctx ? (int32_t)ctx->members.size() : 0; }
+
+ibl_status ibl_member_read_fields(ibl_ctx* ctx, int32_t member, float* rho, float* u, int32_t on_device) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    return read_fields_member(ctx, member, rho, u, nullptr, on_device);
+}
+
+ibl_status ibl_member_read_capsule(ibl_ctx* ctx, int32_t member, int32_t id, ibl_capsule_stats* stats,
+                                   double* verts_out) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    return read_capsule_member(ctx, member, id, stats, verts_out);
+}
+
+ibl_status ibl_member_steps(const ibl_ctx* ctx, int32_t member, int32_t* steps_done) {
+    if (!ctx || !steps_done) return fail(nullptr, IBL_ERR_ARG, "null argument");
+    if (member < 0 || member >= (int)ctx->members.size()) return fail(nullptr, IBL_ERR_ARG, "member out of range");
+    *steps_done = ctx->finalized ? ctx->h_counters[member] : 0;
+    return IBL_OK;
+}
+
+ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (threads < 32 || threads > 1024 || threads % 32 || blocks_per_sm < 0 || blocks_per_sm > 64)
+        return fail(ctx, IBL_ERR_ARG, "threads must be a multiple of 32 in [32, 1024], blocks_per_sm in [0, 64]");
+    ctx->threads = threads;
+    ctx->blocks_per_sm = blocks_per_sm;
+    if (ctx->finalized) {
+        CK(cudaStreamSynchronize(ctx->work));
+        layout_tiles(ctx);
+        lbm_set_members(ctx->hmem.data(), (int)ctx->hmem.size(), ctx->work);
+        ib_set_members(ctx->hmem.data(), (int)ctx->hmem.size(), ctx->work);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(ctx->work));
+        drop_graphs(ctx);
+    }
+    return IBL_OK;
+}
+
+ibl_status ibl_enable_timing(ibl_ctx* ctx, int32_t on) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    ctx->timing = on != 0;
+    return IBL_OK;
+}
+
+ibl_status ibl_kernel_times(ibl_ctx* ctx, double* out4) {
+    if (!ctx || !out4) return fail(ctx, IBL_ERR_ARG, "null argument");
+    for (int i = 0; i < 4; ++i) out4[i] = ctx->ktime[i];
+    return IBL_OK;
+}
+
+const char* ibl_last_error(const ibl_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+void ibl_destroy(ibl_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->work) cudaStreamSynchronize(ctx->work);
+    drop_graphs(ctx);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->work) cudaStreamDestroy(ctx->work);
+    delete ctx;
+}
+
+}  // extern "C"

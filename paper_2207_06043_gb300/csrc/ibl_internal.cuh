@@ -1,0 +1,171 @@
+// Internal device/host definitions of libibl (not part of the C ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ibl {
+
+// ---------------------------------------------------------------------------
+// D3Q19 velocity set of Eq. e_i, packed two bits per direction so that both
+// compile-time (unrolled) and run-time (per-link) lookups are pure ALU work.
+// component(k) = ((CODE >> 2k) & 3) - 1
+// ---------------------------------------------------------------------------
+constexpr uint64_t EX_CODE = 0x15402a9549ull;
+constexpr uint64_t EY_CODE = 0x294949495ull;
+constexpr uint64_t EZ_CODE = 0x889494955ull;
+
+__host__ __device__ constexpr int ex(int k) { return int((EX_CODE >> (2 * k)) & 3ull) - 1; }
+__host__ __device__ constexpr int ey(int k) { return int((EY_CODE >> (2 * k)) & 3ull) - 1; }
+__host__ __device__ constexpr int ez(int k) { return int((EZ_CODE >> (2 * k)) & 3ull) - 1; }
+// opposite direction: pairs (1,2) (3,4) (5,6) (7,12) (8,11) (9,14) (10,13) (15,18) (16,17)
+__host__ __device__ constexpr int opp(int k) {
+    return k == 0 ? 0
+         : k <= 6 ? ((k & 1) ? k + 1 : k - 1)
+         : (k == 7 || k == 8 || k == 11 || k == 12) ? 19 - k
+         : k <= 14 ? 23 - k
+         : 33 - k;
+}
+__host__ __device__ constexpr float wgt(int k) {
+    return k == 0 ? (1.0f / 3.0f) : (k <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
+}
+
+constexpr int Q = 19;
+constexpr int MAX_MEMBERS = 128;
+
+enum : uint8_t { TAG_SOLID = 1, TAG_IB = 2 };
+enum : uint32_t { ST_DAMAGED = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
+enum { FACE_NONE = 0, FACE_VELOCITY = 1, FACE_PRESSURE = 2 };
+
+// Per-lattice descriptor (copied into each translation unit's constant bank).
+struct MemberDev {
+    int nx, ny, nz;          // user dims
+    int NX, NY, NZ;          // padded dims (non-periodic axes get a ghost layer)
+    int px, py, pz;          // padding per axis (0 periodic, 1 otherwise)
+    int per;                 // bit a set: axis a periodic
+    int N;                   // padded node count
+    int S;                   // plane stride in elements
+    long long f_off;         // element offset of plane 0 of this member
+    long long node_off;      // offset into per-node arrays (tag, f_ib)
+    float omega, guo, nu, umax;
+    float F[3];
+    int hasF;                // nonzero body force
+    float st_scale, ld_scale;
+    int face_kind[6];
+    float face_rho[6];
+    long long face_off[6];   // float3 record offset into the face velocity array
+    int tile_begin, tile_count;
+    int link_begin, link_count;
+    int cap_begin, cap_count;
+    int vert_begin, vert_count;
+    long long cell_off;
+    int cnx, cny, cnz, has_cells;
+};
+
+// Per-capsule descriptor (global memory).
+struct CapsuleDev {
+    int member;
+    int rigid;
+    int v_begin, v_count;
+    int t_begin, t_count;
+    int e_begin, e_count;
+    double kv, V0, S0, mass, mv, inertia;
+    double xc[3], u1[3], u2[3], w1[3], w2[3];
+};
+
+// Per-capsule FP64 sums written each step / on demand.
+struct CapsuleSums {
+    double V, S;
+    double cen[3];           // sum v (a+b+c)/4 relative to ref
+    double M2[6];            // xx yy zz xy xz yz relative to ref
+    double ref[3];
+    double max_stretch;
+};
+
+// ---------------------------------------------------------------------------
+// storage conversion
+// ---------------------------------------------------------------------------
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p, float) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p, float s) { return __half2float(*p) * s; }
+    static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, float) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v, float) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// host-side launch entry points (one per translation unit)
+// ---------------------------------------------------------------------------
+// Device buffers of a context (all members concatenated).
+struct DevState {
+    int storage = 0;                 // 0 f32, 1 f16, 2 bf16
+    int n_members = 0;
+    const MemberDev* h_mem = nullptr;
+    int threads = 256;               // lattice tile size (threads per block)
+    int total_tiles = 0;
+    int grid_lbm = 0;                // persistent grid (0: one block per tile)
+
+    void* f = nullptr;               // 19 planes per member, f - w
+    uint8_t* tag = nullptr;          // per padded node
+    float* fib = nullptr;            // 3 per padded node, zero outside the IB shell
+    float* face_vel = nullptr;       // float3 per face node of velocity faces
+    uint32_t* status = nullptr;      // per member
+    int* counters = nullptr;         // steps completed, per member
+
+    int n_links = 0;
+    uint32_t* l_node = nullptr;      // padded node of the link
+    uint32_t* l_meta = nullptr;      // dir | ok1 << 5 | ok2 << 6 | member << 8
+    float* l_q = nullptr;
+
+    int n_caps = 0, n_verts = 0, n_tris = 0, n_edges = 0;
+    int any_soft = 0, any_rigid = 0, any_cells = 0, max_nv = 0;
+    CapsuleDev* caps = nullptr;
+    CapsuleSums* sums = nullptr;
+    int* v_cap = nullptr;
+    double* x = nullptr;             // 3 per vertex
+    double* x_prev = nullptr;
+    double* vel = nullptr;
+    float* force = nullptr;          // 3 per vertex
+    float* uv0 = nullptr;            // 3 per vertex
+    float* nrm = nullptr;            // 3 per vertex
+    float* area = nullptr;           // per vertex
+    float* phi = nullptr;            // 27 per vertex
+    int* tri = nullptr;              // 3 per triangle (global vertex ids)
+    int* hinge = nullptr;            // 4 per edge: v1 v2 v3 v4 (edge = v2-v3)
+    float* l0 = nullptr;
+    float* ks = nullptr;
+    float* th0 = nullptr;
+    float* kb = nullptr;
+    int* e_cap = nullptr;
+    int* cell_count = nullptr;
+    int* cell_items = nullptr;
+    long long n_cells = 0;
+};
+constexpr int CELL_CAP = 32;
+
+void lbm_set_members(const MemberDev* m, int n, cudaStream_t s);
+void ib_set_members(const MemberDev* m, int n, cudaStream_t s);
+
+cudaError_t launch_lbm(const DevState& d, int parity, int zh_on, cudaStream_t s);
+cudaError_t launch_bfl(const DevState& d, int parity_done, cudaStream_t s);
+cudaError_t launch_init_member(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s);
+cudaError_t launch_read(const DevState& d, int member, int parity, int zh_on, float* rho, float* u,
+                        float* g, cudaStream_t s);
+
+cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s);
+cudaError_t launch_ib(const DevState& d, int parity, int zh_on, cudaStream_t s);
+cudaError_t launch_post(const DevState& d, int parity_next, cudaStream_t s);
+cudaError_t launch_edges(const DevState& d, cudaStream_t s);
+cudaError_t launch_repulsion(const DevState& d, cudaStream_t s);
+cudaError_t launch_update(const DevState& d, cudaStream_t s);
+
+}  // namespace ibl

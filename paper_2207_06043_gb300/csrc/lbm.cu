@@ -1,0 +1,254 @@
+// Lattice kernels: fused collide + stream (AA pattern, in place, Zou-He faces
+// fused), the sparse Bouzidi-Firdaouss-Lallemand fill pass, initialisation and
+// read-out.
+#include "lbm_device.cuh"
+
+namespace ibl {
+
+void lbm_set_members(const MemberDev* m, int n, cudaStream_t s) {
+    cudaMemcpyToSymbolAsync(c_mem, m, sizeof(MemberDev) * n, 0, cudaMemcpyHostToDevice, s);
+}
+
+// One time step of every fluid node of every member (Eq. evoleq): gather the
+// pre-collision populations (AA parity), apply the Zou-He face rule, add the
+// body force and the spread IB force (which is then cleared), collide, store.
+template <typename T>
+__global__ void __launch_bounds__(512) k_lbm(T* __restrict__ f, uint8_t* __restrict__ tag,
+                                              float* __restrict__ fib, const float* __restrict__ face_vel,
+                                              const uint32_t* __restrict__ status, int* __restrict__ counters,
+                                              int n_mem, int total_tiles, int parity, int zh_on) {
+    if (blockIdx.x == 0 && threadIdx.x < n_mem) {
+        if (!(status[threadIdx.x] & (ST_DAMAGED | ST_NONFINITE))) counters[threadIdx.x] += 1;
+    }
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        const int m = find_member_by_tile(n_mem, tile);
+        const MemberDev& d = c_mem[m];
+        if (status[m] & (ST_DAMAGED | ST_NONFINITE)) continue;
+        const int n = (tile - d.tile_begin) * blockDim.x + threadIdx.x;
+        if (n >= d.N) continue;
+        const long long gn = d.node_off + n;
+        const uint8_t tg = tag[gn];
+        if (tg & TAG_SOLID) continue;
+        int X, Y, Z;
+        node_coords(d, n, X, Y, Z);
+        T* fm = f + d.f_off;
+        float g[Q];
+        load_pre<T>(d, fm, n, X, Y, Z, parity, g);
+        if (zh_on) apply_face(d, X, Y, Z, face_vel, g);
+        float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
+        bool hasF = d.hasF != 0;
+        if (tg & TAG_IB) {
+            float* p = fib + 3 * gn;
+            Fx += p[0]; Fy += p[1]; Fz += p[2];
+            p[0] = 0.f; p[1] = 0.f; p[2] = 0.f;
+            tag[gn] = tg & (uint8_t)~TAG_IB;
+            hasF = true;
+        }
+        collide(g, d.omega, d.guo, Fx, Fy, Fz, hasF);
+        store_post<T>(d, fm, n, X, Y, Z, parity, g);
+    }
+}
+
+// Missing population of every wall link for the next step (Eq. bbouzidi, with
+// the q >= 1/2 branch re-derived by quadratic interpolation and the two-point
+// / halfway fall-backs when upstream nodes are not fluid).  Reads the
+// post-collision values of the step just done (parity pp) and writes the slot
+// the next step (parity 1 - pp) reads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bfl(T* __restrict__ f, const uint32_t* __restrict__ l_node,
+                                             const uint32_t* __restrict__ l_meta, const float* __restrict__ l_q,
+                                             const uint32_t* __restrict__ status, int n_links, int pp) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_links) return;
+    const uint32_t meta = l_meta[l];
+    const int m = (int)(meta >> 8);
+    if (status[m] & (ST_DAMAGED | ST_NONFINITE)) return;
+    const MemberDev& d = c_mem[m];
+    const int i = (int)(meta & 31u);
+    const bool ok1 = meta & 32u, ok2 = meta & 64u;
+    const int ib = opp(i);
+    const int xb = (int)l_node[l];
+    const float q = l_q[l];
+    int X, Y, Z;
+    node_coords(d, xb, X, Y, Z);
+    const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
+    const int exi = ex(i), eyi = ey(i), ezi = ez(i);
+    const int xsN = nbc(X, exi, d.NX, px) + d.NX * (nbc(Y, eyi, d.NY, py) + d.NY * nbc(Z, ezi, d.NZ, pz));
+    const int m1N = nbc(X, -exi, d.NX, px) + d.NX * (nbc(Y, -eyi, d.NY, py) + d.NY * nbc(Z, -ezi, d.NZ, pz));
+    const int X1 = nbc(X, -exi, d.NX, px), Y1 = nbc(Y, -eyi, d.NY, py), Z1 = nbc(Z, -ezi, d.NZ, pz);
+    const size_t S = (size_t)d.S;
+    const float ls = d.ld_scale;
+    T* fm = f + d.f_off;
+    float fi_b, fib_b, fi_1 = 0.f, fi_2 = 0.f, fib_1 = 0.f;
+    if (pp == 0) {
+        fi_b = Store<T>::ld(fm + ib * S + xb, ls);
+        fib_b = Store<T>::ld(fm + i * S + xb, ls);
+        if (ok1) {
+            fi_1 = Store<T>::ld(fm + ib * S + m1N, ls);
+            fib_1 = Store<T>::ld(fm + i * S + m1N, ls);
+            if (ok2) {
+                const int m2N = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
+                fi_2 = Store<T>::ld(fm + ib * S + m2N, ls);
+            }
+        }
+    } else {
+        fi_b = Store<T>::ld(fm + i * S + xsN, ls);
+        fib_b = Store<T>::ld(fm + ib * S + m1N, ls);
+        if (ok1) {
+            fi_1 = Store<T>::ld(fm + i * S + xb, ls);
+            const int m2N = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
+            fib_1 = Store<T>::ld(fm + ib * S + m2N, ls);
+            if (ok2) fi_2 = Store<T>::ld(fm + i * S + m1N, ls);
+        }
+    }
+    float v;
+    if (q < 0.5f) {
+        if (ok1 && ok2) v = q * (2.f * q + 1.f) * fi_b + (1.f - 4.f * q * q) * fi_1 - q * (1.f - 2.f * q) * fi_2;
+        else if (ok1) v = 2.f * q * fi_b + (1.f - 2.f * q) * fi_1;
+        else v = fi_b;
+    } else {
+        if (ok1) v = fi_b / (q * (2.f * q + 1.f)) + (2.f * q - 1.f) / q * fib_b + (1.f - 2.f * q) / (1.f + 2.f * q) * fib_1;
+        else v = fi_b / (2.f * q) + (2.f * q - 1.f) / (2.f * q) * fib_b;
+    }
+    if (pp == 0) Store<T>::st(fm + i * S + xsN, v, d.st_scale);   // next step odd: read from n - e_ib
+    else Store<T>::st(fm + ib * S + xb, v, d.st_scale);           // next step even: own slot
+}
+
+// Equilibrium initial state (parity 0 layout) from user-layout rho[N], u[3N].
+template <typename T>
+__global__ void k_init(T* __restrict__ f, const uint8_t* __restrict__ tag, int m, const float* __restrict__ rho,
+                       const float* __restrict__ u) {
+    const MemberDev& d = c_mem[m];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.N) return;
+    int X, Y, Z;
+    node_coords(d, n, X, Y, Z);
+    float g[Q];
+    const bool solid = tag[d.node_off + n] & TAG_SOLID;
+    const int x = X - d.px, y = Y - d.py, z = Z - d.pz;
+    float r = 1.f, ux = 0.f, uy = 0.f, uz = 0.f;
+    if (!solid) {
+        const long long un = x + (long long)d.nx * (y + (long long)d.ny * z);
+        if (rho) r = rho[un];
+        if (u) { ux = u[3 * un]; uy = u[3 * un + 1]; uz = u[3 * un + 2]; }
+    }
+    const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const float eu = ex(k) * ux + ey(k) * uy + ez(k) * uz;
+        g[k] = solid ? 0.f : wgt(k) * ((r - 1.f) + r * (3.f * eu + 4.5f * eu * eu - usq));
+    }
+    T* fm = f + d.f_off;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) Store<T>::st(fm + (size_t)k * d.S + n, g[k], d.st_scale);
+}
+
+// Macroscopic fields / populations of one member in user layout.
+template <typename T>
+__global__ void k_read(const T* __restrict__ f, const uint8_t* __restrict__ tag, const float* __restrict__ face_vel,
+                       int m, int parity, int zh_on, float* __restrict__ rho, float* __restrict__ u,
+                       float* __restrict__ gout) {
+    const MemberDev& d = c_mem[m];
+    const long long Nu = (long long)d.nx * d.ny * d.nz;
+    const long long un = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (un >= Nu) return;
+    const int x = (int)(un % d.nx), y = (int)((un / d.nx) % d.ny), z = (int)(un / ((long long)d.nx * d.ny));
+    const int X = x + d.px, Y = y + d.py, Z = z + d.pz;
+    const int n = X + d.NX * (Y + d.NY * Z);
+    float g[Q];
+    const bool solid = tag[d.node_off + n] & TAG_SOLID;
+    if (solid) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[k] = 0.f;
+    } else {
+        load_pre<T>(d, f + d.f_off, n, X, Y, Z, parity, g);
+        if (zh_on) apply_face(d, X, Y, Z, face_vel, g);
+    }
+    if (gout) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) gout[k * Nu + un] = g[k];
+    }
+    if (rho || u) {
+        float r = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
+        if (!solid) {
+            float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                drho += g[k]; jx += ex(k) * g[k]; jy += ey(k) * g[k]; jz += ez(k) * g[k];
+            }
+            r = 1.f + drho;
+            ux = (jx + 0.5f * d.F[0]) / r;
+            uy = (jy + 0.5f * d.F[1]) / r;
+            uz = (jz + 0.5f * d.F[2]) / r;
+        }
+        if (rho) rho[un] = r;
+        if (u) { u[3 * un] = ux; u[3 * un + 1] = uy; u[3 * un + 2] = uz; }
+    }
+}
+
+template <typename T>
+static cudaError_t lbm_t(const DevState& d, int parity, int zh_on, cudaStream_t s) {
+    const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.total_tiles;
+    k_lbm<T><<<grid, d.threads, 0, s>>>((T*)d.f, d.tag, d.fib, d.face_vel, d.status, d.counters, d.n_members,
+                                        d.total_tiles, parity, zh_on);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbm(const DevState& d, int parity, int zh_on, cudaStream_t s) {
+    switch (d.storage) {
+        case 1: return lbm_t<__half>(d, parity, zh_on, s);
+        case 2: return lbm_t<__nv_bfloat16>(d, parity, zh_on, s);
+        default: return lbm_t<float>(d, parity, zh_on, s);
+    }
+}
+
+template <typename T>
+static cudaError_t bfl_t(const DevState& d, int pp, cudaStream_t s) {
+    if (d.n_links == 0) return cudaSuccess;
+    k_bfl<T><<<(d.n_links + 255) / 256, 256, 0, s>>>((T*)d.f, d.l_node, d.l_meta, d.l_q, d.status, d.n_links, pp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfl(const DevState& d, int pp, cudaStream_t s) {
+    switch (d.storage) {
+        case 1: return bfl_t<__half>(d, pp, s);
+        case 2: return bfl_t<__nv_bfloat16>(d, pp, s);
+        default: return bfl_t<float>(d, pp, s);
+    }
+}
+
+template <typename T>
+static cudaError_t init_t(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s) {
+    const int N = d.h_mem[m].N;
+    k_init<T><<<(N + 255) / 256, 256, 0, s>>>((T*)d.f, d.tag, m, rho, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_member(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s) {
+    switch (d.storage) {
+        case 1: return init_t<__half>(d, m, rho, u, s);
+        case 2: return init_t<__nv_bfloat16>(d, m, rho, u, s);
+        default: return init_t<float>(d, m, rho, u, s);
+    }
+}
+
+template <typename T>
+static cudaError_t read_t(const DevState& d, int m, int parity, int zh_on, float* rho, float* u, float* g,
+                          cudaStream_t s) {
+    const MemberDev& md = d.h_mem[m];
+    const long long Nu = (long long)md.nx * md.ny * md.nz;
+    k_read<T><<<(unsigned)((Nu + 255) / 256), 256, 0, s>>>((const T*)d.f, d.tag, d.face_vel, m, parity, zh_on, rho,
+                                                           u, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read(const DevState& d, int m, int parity, int zh_on, float* rho, float* u, float* g,
+                        cudaStream_t s) {
+    switch (d.storage) {
+        case 1: return read_t<__half>(d, m, parity, zh_on, rho, u, g, s);
+        case 2: return read_t<__nv_bfloat16>(d, m, parity, zh_on, rho, u, g, s);
+        default: return read_t<float>(d, m, parity, zh_on, rho, u, g, s);
+    }
+}
+
+}  // namespace ibl

@@ -349,7 +349,7 @@ def _bifurcation_sdf(nx, ny, nz, D, half_angle_deg, r_j, x_junction, daughter_ra
             direc = np.array([math.cos(a), math.sin(a), 0.0])
             start = p - hw * np.array([math.cos(ang), math.sin(ang), 0.0])
             if lev + 1 < levels:
-                seg_len = 2.5 * (2 * hd)
+                seg_len = 1.5 * (2 * hd)
                 end = p + seg_len * direc
                 segs.append((start, end, hd))
                 pieces.append((end, a, hd, lev + 1))

@@ -1,0 +1,163 @@
+"""CUDA path against the FP64 oracle on the same seeded inputs (GPU).
+
+Tolerances: FP32 velocity relative L2 <= 1e-5 and capsule centroid <= 1e-4 lu
+(the stated targets); populations f - w within 1e-6 absolute (FP32 storage
+rounds each of them at ~6e-8 relative per step)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2207_06043_gb300 import geometry as G
+from paper_2207_06043_gb300 import meshes as Ms
+from paper_2207_06043_gb300 import workloads as W
+
+from helpers import case, gpu_for, oracle_for, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+VEL_TOL = 1e-5
+CEN_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.zeros(1, device="cuda")
+
+
+def _compare_fields(c, steps, tol=VEL_TOL, pop_tol=1e-6, f0=None):
+    lat, o = oracle_for(c, f0=f0)
+    s = gpu_for(c)
+    if f0 is not None:
+        rho0, u0 = lat.macroscopic(f0, include_body_force=False)
+        s.init_equilibrium(rho0.astype(np.float32), u0.astype(np.float32))
+    done, _ = s.step(steps)
+    assert done == steps
+    o.step(steps)
+    rho, u = s.read_fields()
+    _, uo = lat.macroscopic(o.f)
+    fl = lat.fluid
+    err = rel_l2(u, uo, fl)
+    g = s.read_populations()
+    gw = o.f - L_W()[:, None]
+    perr = np.abs(g[:, fl] - gw[:, fl]).max()
+    return err, perr, s, o, lat
+
+
+def L_W():
+    from oracle.lattice import W
+    return W
+
+
+def test_periodic_box_body_force():
+    g = G.periodic_box(12, 10, 8)
+    c = case(g, tau=0.9, body_force=(2e-6, -1e-6, 5e-7))
+    rng = np.random.default_rng(0)
+    from oracle import lattice as L
+    lat = L.Lattice(g.nx, g.ny, g.nz, 0.9, g.tag, g.links, g.faces, g.periodic)
+    f0 = lat.init_equilibrium(1 + 1e-3 * rng.standard_normal(lat.N), 1e-3 * rng.standard_normal((lat.N, 3)))
+    # the GPU starts from the same equilibrium, rounded to FP32 inputs
+    rho0, u0 = lat.macroscopic(f0, include_body_force=False)
+    f0 = lat.init_equilibrium(rho0.astype(np.float32).astype(np.float64), u0.astype(np.float32).astype(np.float64))
+    err, perr, *_ = _compare_fields(c, 60, f0=f0)
+    assert err <= VEL_TOL and perr <= 1e-6, (err, perr)
+
+
+def test_straight_duct_zou_he_and_bfl():
+    """Velocity inlet / pressure outlet, walls offset so q = 0.3 and 0.7."""
+    n = 14
+    yc = (n - 1) / 2 + 0.2
+    g = G.straight_duct(24, n, n, 10.0, u_max=0.02, centre=(yc, yc))
+    assert 0.3 in np.round(g.links["q"], 4)
+    err, perr, *_ = _compare_fields(case(g), 200)
+    assert err <= VEL_TOL and perr <= 1e-6, (err, perr)
+
+
+def test_inclined_periodic_channel_general_q():
+    g = G.inclined_channel(9)
+    c = case(g, tau=1.0, body_force=tuple(2e-6 * g.info["axis"]))
+    err, perr, *_ = _compare_fields(c, 150)
+    assert err <= VEL_TOL and perr <= 1e-6, (err, perr)
+
+
+def test_bifurcation_flow_without_capsules():
+    g = G.bifurcation(64, 28, 24, 16.0, 30.0, 3.0, u_max=0.02)
+    err, perr, *_ = _compare_fields(case(g), 120)
+    assert err <= VEL_TOL and perr <= 1e-6, (err, perr)
+
+
+def test_rigid_sphere_in_bifurcation_short():
+    g = G.bifurcation(48, 20, 20, 14.0, 45.0, 0.0, u_max=0.02)
+    V, T = Ms.sphere_mesh(162, 7.0, (10.0, g.info["yc"] + 1.0, g.info["zc"] - 0.5), Ms.SplitMix64(3))
+    c = case(g, capsules=[W._capsule(V, T, rigid=True, vel0=(0.01, 0.0, 0.0))])
+    err, perr, s, o, lat = _compare_fields(c, 80)
+    st = s.read_capsule(0)
+    dc = np.abs(st["centroid"] - o.stats(0)["centroid"]).max()
+    assert err <= VEL_TOL and dc <= CEN_TOL, (err, dc)
+
+
+def test_soft_capsule_in_duct():
+    g = G.straight_duct(40, 24, 24, 20.0, u_max=0.03)
+    V, T = Ms.sphere_mesh(642, 12.0, (11.0, g.info["yc"] + 0.7, g.info["zc"]), Ms.SplitMix64(5))
+    c = case(g, u_max=0.03, capsules=[W._capsule(V, T, Ca=0.05, Eb=0.01, u_ref=0.03)])
+    err, perr, s, o, lat = _compare_fields(c, 100)
+    st = s.read_capsule(0, with_verts=True)
+    so = o.stats(0)
+    dc = np.abs(st["centroid"] - so["centroid"]).max()
+    dx = np.abs(st["verts"] - o.bodies[0].x).max()
+    assert err <= VEL_TOL and dc <= CEN_TOL and dx <= 1e-3, (err, dc, dx)
+    assert abs(st["volume"] - so["volume"]) / so["volume"] < 1e-6
+    assert abs(st["taylor_D"] - so["taylor_D"]) < 1e-5
+
+
+def test_two_capsules_with_repulsion():
+    g = G.periodic_box(24, 20, 20)
+    Va, Ta = Ms.sphere_mesh(162, 8.0, (7.5, 10.0, 10.0), Ms.SplitMix64(7))
+    Vb, Tb = Ms.sphere_mesh(162, 8.0, (16.3, 10.4, 9.8), Ms.SplitMix64(8))
+    c = case(g, tau=0.9, capsules=[W._capsule(Va, Ta, Ca=0.05, vel0=(0.01, 0, 0)),
+                                   W._capsule(Vb, Tb, Ca=0.05, vel0=(-0.01, 0, 0))])
+    err, perr, s, o, lat = _compare_fields(c, 60)
+    for k in range(2):
+        st = s.read_capsule(k)
+        dc = np.abs(st["centroid"] - o.stats(k)["centroid"]).max()
+        assert dc <= CEN_TOL, (k, dc)
+    assert err <= VEL_TOL, err
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_reduced_storage_against_fp32(storage):
+    """16-bit storage of f - w with FP32 arithmetic against the FP32 path:
+    velocity relative L2 <= 1e-3."""
+    g = G.bifurcation(64, 28, 24, 16.0, 45.0, 2.0, u_max=0.02)
+    V, T = Ms.sphere_mesh(642, 10.0, (12.0, g.info["yc"], g.info["zc"] + 0.5), Ms.SplitMix64(9))
+    c = case(g, capsules=[W._capsule(V, T, Ca=0.02)])
+    a = gpu_for(c, "f32")
+    b = gpu_for(c, storage)
+    a.step(300)
+    b.step(300)
+    _, ua = a.read_fields()
+    _, ub = b.read_fields()
+    fl = g.tag == 0
+    assert rel_l2(ub, ua, fl) <= 1e-3
+
+
+def test_ensemble_matches_single_lattices_exactly():
+    """Batched lattices of uneven size give bit-identical fields to the same
+    lattices stepped alone (no capsules: no atomics, fixed arithmetic order)."""
+    from paper_2207_06043_gb300.binding import ensemble
+    geoms = [G.bifurcation(40, 20, 16, 10.0, 30.0, 0.0), G.straight_duct(33, 17, 15, 9.0),
+             G.bifurcation(56, 24, 20, 12.0, 60.0, 3.0)]
+    singles = [gpu_for(case(gm)) for gm in geoms]
+    members = [gpu_for(case(gm)) for gm in geoms]
+    ens = ensemble(members)
+    for s in singles:
+        s.step(70)
+    ens.step(70)
+    for m, (s, gm) in enumerate(zip(singles, geoms)):
+        _, u1 = s.read_fields()
+        _, u2 = ens.read_fields(member=m)
+        assert np.array_equal(u1, u2), m
+        assert ens.member_steps(m) == 70
