@@ -168,6 +168,7 @@ ibl_status ibl_ensemble_create(ibl_ctx* const* members, int32_t n, void* cuda_st
 int32_t ibl_num_members(const ibl_ctx* ctx);
 ibl_status ibl_member_read_fields(ibl_ctx* ctx, int32_t member, float* rho, float* u,
                                   int32_t on_device);
+ibl_status ibl_member_read_populations(ibl_ctx* ctx, int32_t member, float* g, int32_t on_device);
 ibl_status ibl_member_read_capsule(ibl_ctx* ctx, int32_t member, int32_t id,
                                    ibl_capsule_stats* stats, double* verts_out);
 ibl_status ibl_member_steps(const ibl_ctx* ctx, int32_t member, int32_t* steps_done);

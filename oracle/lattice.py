@@ -69,6 +69,22 @@ def collide(f, F, tau):
     return f - (f - feq) / tau + guo_forcing(u, F, tau)
 
 
+def bouzidi_value(q, fi_b, fi_1, fi_2, fib_b, fib_1, ok1, ok2):
+    """The returning population f_ib(x_b, t+1) of one wall link (Eq. bbouzidi
+    with the q >= 1/2 branch of Reading B and the fall-backs of Reading B'),
+    from the post-collision values f*_i at x_b, x_b - e_i, x_b - 2e_i and
+    f*_ib at x_b, x_b - e_i; ok1 / ok2 say whether x_b - e_i / x_b - 2e_i are
+    fluid."""
+    small = q < 0.5
+    quad_s = q * (2 * q + 1) * fi_b + (1 - 4 * q * q) * fi_1 - q * (1 - 2 * q) * fi_2
+    lin_s = 2 * q * fi_b + (1 - 2 * q) * fi_1
+    val_s = np.where(ok1 & ok2, quad_s, np.where(ok1, lin_s, fi_b))
+    quad_l = fi_b / (q * (2 * q + 1)) + (2 * q - 1) / q * fib_b + (1 - 2 * q) / (1 + 2 * q) * fib_1
+    lin_l = fi_b / (2 * q) + (2 * q - 1) / (2 * q) * fib_b
+    val_l = np.where(ok1, quad_l, lin_l)
+    return np.where(small, val_s, val_l)
+
+
 class Lattice:
     """Box lattice with fluid/solid tags, wall links and face conditions.
 
@@ -193,15 +209,7 @@ class Lattice:
         fi_1 = np.where(ok1, fstar[i, np.where(ok1, m1, 0)], 0.0)
         fi_2 = np.where(ok2, fstar[i, np.where(ok2, m2, 0)], 0.0)
         fib_1 = np.where(ok1, fstar[ib, np.where(ok1, m1, 0)], 0.0)
-
-        small = q < 0.5
-        quad_s = q * (2 * q + 1) * fi_b + (1 - 4 * q * q) * fi_1 - q * (1 - 2 * q) * fi_2
-        lin_s = 2 * q * fi_b + (1 - 2 * q) * fi_1
-        val_s = np.where(ok1 & ok2, quad_s, np.where(ok1, lin_s, fi_b))
-        quad_l = fi_b / (q * (2 * q + 1)) + (2 * q - 1) / q * fib_b + (1 - 2 * q) / (1 + 2 * q) * fib_1
-        lin_l = fi_b / (2 * q) + (2 * q - 1) / (2 * q) * fib_b
-        val_l = np.where(ok1, quad_l, lin_l)
-        fnew[ib, xb] = np.where(small, val_s, val_l)
+        fnew[ib, xb] = bouzidi_value(q, fi_b, fi_1, fi_2, fib_b, fib_1, ok1, ok2)
         return fnew
 
     def zou_he(self, fnew):

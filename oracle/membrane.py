@@ -201,9 +201,15 @@ def repulsion_forces(Xs, nrms, u_max, cutoff=2.0):
     over the partners j, n^- the inward normal of marker i."""
     out = [np.zeros_like(X) for X in Xs]
     c = u_max / (8.0 * math.sqrt(2.0))
+    lo = [X.min(axis=0) for X in Xs]
+    hi = [X.max(axis=0) for X in Xs]
     for a in range(len(Xs)):
         for b in range(len(Xs)):
             if a == b:
+                continue
+            # bodies whose bounding boxes are farther apart than the cutoff
+            # have no marker pair within it
+            if np.any(lo[a] - hi[b] >= cutoff) or np.any(lo[b] - hi[a] >= cutoff):
                 continue
             d = np.linalg.norm(Xs[a][:, None, :] - Xs[b][None, :, :], axis=2)
             with np.errstate(divide="ignore"):

@@ -1,11 +1,17 @@
 """FP64 oracle of the whole coupled time step, in the order
-  1. immersed-boundary pre-pass: MLS interpolation of u* at the markers,
-     F_l = (U_b - U_l)/dt, spreading to f_ib                (Eqs. uLag .. bodyforce)
-  2. collide, stream, BFL wall links, Zou-He faces          (Eqs. evoleq, extbound, bbouzidi)
-  3. structure forces at x(t) from the new field            (Eqs. strainFor .. collision)
-  4. Verlet (soft) or Newton-Euler (rigid) update           (Eqs. verletPos .. angularVelRig)
+  1. immersed-boundary pre-pass on the fluid solution at t: MLS interpolation
+     of u* at the markers, F_l = (U_b - U_l)/dt, spreading to f_ib
+                                                            (Eqs. uLag .. bodyforce)
+  2. structure forces F^tot(t) at x(t) from the same field  (Eqs. strainFor .. collision)
+  3. Verlet (soft) or Newton-Euler (rigid) update, with the tentative
+     velocity u_v,0 = U_l of step 1                         (Eqs. verletPos .. angularVelRig)
+  4. collide, stream, BFL wall links, Zou-He faces          (Eqs. evoleq, extbound, bbouzidi)
   5. damage check: an edge at twice its rest length stops the run
-(Reading T1 for the order, which the paper does not state).
+(Reading T1 for the order, which the paper does not state: every structure
+quantity of the step is taken from the fluid solution at time t, the field the
+IB pre-pass interpolates.  Interpolating u_v,0 and the probes from the field
+after the collision instead makes the explicit coupled scheme grow a
+period-2 tangential membrane mode at Re = 10-20.)
 
 TEST INFRASTRUCTURE (see the package docstring): never imported by the product.
 """
@@ -99,7 +105,8 @@ class Simulation:
         return f_ib, per
 
     def structure(self, fnew, per):
-        """Step 3: total force on each vertex at x(t), from the field at t+dt."""
+        """Step 2: total force F^tot(t) on each vertex at x(t); the probes read
+        the populations passed in (the solution at t)."""
         lat = self.lat
         Fs = []
         nrms = [p["nrm"] for p in per]
@@ -118,7 +125,7 @@ class Simulation:
         return Fs
 
     def update(self, fnew, per, Fs):
-        """Step 4: Eqs. verletPos, verletVel, verletPosC (soft) or the
+        """Step 3: Eqs. verletPos, verletVel, verletPosC (soft) or the
         Newton-Euler system with Eq. angularVelRig (rigid)."""
         for b, p, F in zip(self.bodies, per, Fs):
             if b.rigid:
@@ -138,8 +145,9 @@ class Simulation:
                 b.w2, b.w1 = b.w1, w
                 b.vel = b.boundary_velocity()
             else:
-                # u_v,0(t + dt): the new fluid velocity interpolated at x(t)
-                uv0 = ib.interpolate_velocity(fnew, p["stencil"])
+                # u_v,0(t + dt): the fluid velocity interpolated at x(t) by the
+                # IB pre-pass (Eq. uLag on the solution at t)
+                uv0 = p["U"]
                 p["uv0"] = uv0
                 x_new, u_new = verlet(b.x, b.x_prev, uv0, F, b.rest.mv)
                 b.x_prev = b.x
@@ -152,10 +160,9 @@ class Simulation:
             if self.damaged:
                 break
             f_ib, per = self.ib_force()
-            fnew = self.lat.step(self.f, f_ib if self.bodies else None)
-            Fs = self.structure(fnew, per)
-            self.update(fnew, per, Fs)
-            self.f = fnew
+            Fs = self.structure(self.f, per)
+            self.update(self.f, per, Fs)
+            self.f = self.lat.step(self.f, f_ib if self.bodies else None)
             self.t += 1
             done += 1
             self.last = dict(f_ib=f_ib, per=per)

@@ -81,6 +81,7 @@ def lib():
         "ibl_num_members": ([vp], i32),
         "ibl_member_read_fields": ([vp, i32, vp, vp, i32], i32),
         "ibl_member_read_capsule": ([vp, i32, i32, P(CapsuleStats), vp], i32),
+        "ibl_member_read_populations": ([vp, i32, vp, i32], i32),
         "ibl_member_steps": ([vp, i32, P(i32)], i32),
         "ibl_set_launch": ([vp, i32, i32], i32),
         "ibl_enable_timing": ([vp, i32], i32),
@@ -267,9 +268,12 @@ class Solver:
         s = self.member_shapes[member]
         return s[0] * s[1] * s[2]
 
-    def read_populations(self):
-        g = np.empty((19, self.n_nodes), dtype=np.float32)
-        self._check(self._L.ibl_read_populations(self._h, _ptr(g), 0))
+    def read_populations(self, member=None):
+        g = np.empty((19, self.member_nodes(member)), dtype=np.float32)
+        if member is None:
+            self._check(self._L.ibl_read_populations(self._h, _ptr(g), 0))
+        else:
+            self._check(self._L.ibl_member_read_populations(self._h, int(member), _ptr(g), 0))
         return g
 
     def read_capsule(self, cid, member=None, with_verts=False):

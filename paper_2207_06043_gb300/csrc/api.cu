@@ -52,6 +52,8 @@ struct ibl_ctx {
     cudaStream_t user_stream = nullptr;
     cudaStream_t work = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t work2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int storage = IBL_STORAGE_F32;
     std::vector<MemberHost> members;
     bool finalized = false;
@@ -212,36 +214,23 @@ MeshSums mesh_sums(const double* X, int nv, const int* tris, int nt) {
     return s;
 }
 
-// eigenvalues of a symmetric 3x3 matrix (cyclic Jacobi), ascending
+// eigenvalues of a symmetric 3x3 matrix (xx yy zz xy xz yz), ascending, by
+// the trigonometric solution of the characteristic cubic
 void sym3_eigen(const double M[6], double ev[3]) {
-    double a[3][3] = {{M[0], M[3], M[4]}, {M[3], M[1], M[5]}, {M[4], M[5], M[2]}};
-    for (int sweep = 0; sweep < 50; ++sweep) {
-        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
-        if (off < 1e-300) break;
-        for (int p = 0; p < 2; ++p)
-            for (int q = p + 1; q < 3; ++q) {
-                if (std::fabs(a[p][q]) < 1e-300) continue;
-                const double th = 0.5 * std::atan2(2 * a[p][q], a[q][q] - a[p][p]);
-                const double c = std::cos(th), s = std::sin(th);
-                double b[3][3];
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j) b[i][j] = a[i][j];
-                for (int k = 0; k < 3; ++k) {
-                    b[p][k] = c * a[p][k] - s * a[q][k];
-                    b[q][k] = s * a[p][k] + c * a[q][k];
-                }
-                for (int k = 0; k < 3; ++k) {
-                    a[k][p] = c * b[k][p] - s * b[k][q];
-                    a[k][q] = s * b[k][p] + c * b[k][q];
-                }
-                for (int k = 0; k < 3; ++k)
-                    if (k != p && k != q) { a[p][k] = b[p][k]; a[q][k] = b[q][k]; }
-                a[p][p] = c * c * b[p][p] - 2 * s * c * b[p][q] + s * s * b[q][q];
-                a[q][q] = s * s * b[p][p] + 2 * s * c * b[p][q] + c * c * b[q][q];
-                a[p][q] = a[q][p] = 0.0;
-            }
-    }
-    ev[0] = a[0][0]; ev[1] = a[1][1]; ev[2] = a[2][2];
+    const double a00 = M[0], a11 = M[1], a22 = M[2], a01 = M[3], a02 = M[4], a12 = M[5];
+    const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    const double q = (a00 + a11 + a22) / 3.0;
+    const double p2 = (a00 - q) * (a00 - q) + (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + 2.0 * p1;
+    if (p2 <= 0.0) { ev[0] = ev[1] = ev[2] = q; return; }
+    const double p = std::sqrt(p2 / 6.0);
+    const double b00 = (a00 - q) / p, b11 = (a11 - q) / p, b22 = (a22 - q) / p;
+    const double b01 = a01 / p, b02 = a02 / p, b12 = a12 / p;
+    const double det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+    const double r = std::min(1.0, std::max(-1.0, det / 2.0));
+    const double phi = std::acos(r) / 3.0;
+    const double e1 = q + 2.0 * p * std::cos(phi);
+    const double e3 = q + 2.0 * p * std::cos(phi + 2.0 * M_PI / 3.0);
+    ev[0] = e3; ev[1] = 3.0 * q - e1 - e3; ev[2] = e1;
     std::sort(ev, ev + 3);
 }
 
@@ -499,6 +488,7 @@ ibl_status finalize(ibl_ctx* ctx) {
     CKS(dev_alloc(ctx, D.tag, tag_all.size()));
     CKS(dev_alloc(ctx, D.face_vel, std::max<size_t>(face_all.size(), 3)));
     CKS(dev_alloc(ctx, D.status, nm));
+    CKS(dev_alloc(ctx, D.status_new, nm));
     CKS(dev_alloc(ctx, D.counters, nm));
     D.n_links = link_off;
     CKS(dev_alloc(ctx, D.l_node, l_node.size()));
@@ -510,6 +500,7 @@ ibl_status finalize(ibl_ctx* ctx) {
     CKS(upload(ctx, D.l_meta, l_meta));
     CKS(upload(ctx, D.l_q, l_q));
     CK(cudaMemsetAsync(D.status, 0, sizeof(uint32_t) * nm, ctx->work));
+    CK(cudaMemsetAsync(D.status_new, 0, sizeof(uint32_t) * nm, ctx->work));
     CK(cudaMemsetAsync(D.counters, 0, sizeof(int) * nm, ctx->work));
     D.n_caps = cap_off; D.n_verts = vert_off; D.n_tris = tri_off; D.n_edges = edge_off;
     D.any_soft = any_soft; D.any_rigid = any_rigid; D.any_cells = any_cells; D.max_nv = max_nv;
@@ -526,7 +517,7 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(dev_alloc(ctx, D.uv0, x_all.size()));
         CKS(dev_alloc(ctx, D.nrm, x_all.size()));
         CKS(dev_alloc(ctx, D.area, (size_t)vert_off));
-        CKS(dev_alloc(ctx, D.phi, 27 * (size_t)vert_off));
+        CKS(dev_alloc(ctx, D.macro, (size_t)node_off));
         CKS(dev_alloc(ctx, D.tri, tri_all.size()));
         CKS(dev_alloc(ctx, D.hinge, hinge_all.size()));
         CKS(dev_alloc(ctx, D.l0, l0_all.size()));
@@ -556,9 +547,8 @@ ibl_status finalize(ibl_ctx* ctx) {
         }
     }
     D.h_mem = ctx->hmem.data();
-    lbm_set_members(ctx->hmem.data(), nm, ctx->work);
-    ib_set_members(ctx->hmem.data(), nm, ctx->work);
-    CK(cudaGetLastError());
+    CKS(dev_alloc(ctx, D.mem, (size_t)nm));
+    CKS(upload(ctx, D.mem, ctx->hmem));
     // initial populations
     for (int mi = 0; mi < nm; ++mi) {
         const MemberHost& M = ctx->members[mi];
@@ -583,35 +573,58 @@ ibl_status finalize(ibl_ctx* ctx) {
 
 enum { TK_LBM = 0, TK_BFL = 1, TK_IB = 2, TK_STRUCT = 3 };
 
-ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<std::pair<int, cudaEvent_t>>* marks) {
+struct Mark {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+// One time step.  Stream `work`: step begin, geometry, IB pre-pass + marker
+// forces, then the lattice step and the wall fill.  Stream `work2` (forked
+// after the IB pass, joined at the end): hinge forces, repulsion and the
+// structure update, which touch no lattice data and overlap the lattice step.
+ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<Mark>* marks) {
     DevState& D = ctx->dev;
-    cudaStream_t s = ctx->work;
-    auto mark = [&](int kind) -> ibl_status {
+    cudaStream_t s = ctx->work, s2 = ctx->work2;
+    cudaEvent_t e0 = nullptr;
+    auto begin = [&](cudaStream_t st) -> ibl_status {
         if (!marks) return IBL_OK;
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e));
-        CK(cudaEventRecord(e, s));
-        marks->push_back(std::make_pair(kind, e));
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventRecord(e0, st));
         return IBL_OK;
     };
+    auto end = [&](int kind, cudaStream_t st) -> ibl_status {
+        if (!marks) return IBL_OK;
+        cudaEvent_t e1;
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e1, st));
+        marks->push_back(Mark{kind, e0, e1});
+        return IBL_OK;
+    };
+    CK(launch_step_begin(D, s));
     const bool caps = D.n_caps > 0;
     if (caps) {
-        CKS(mark(TK_IB));
+        CKS(begin(s));
         CK(launch_geometry(D, 0, s));
         CK(launch_ib(D, parity, zh_on, s));
+        CKS(end(TK_IB, s));
+        CK(cudaEventRecord(ctx->ev_fork, s));
+        CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
+        CKS(begin(s2));
+        CK(launch_edges(D, s2));
+        CK(launch_repulsion(D, s2));
+        CK(launch_update(D, s2));
+        CKS(end(TK_STRUCT, s2));
     }
-    CKS(mark(TK_LBM));
+    CKS(begin(s));
     CK(launch_lbm(D, parity, zh_on, s));
-    CKS(mark(TK_BFL));
+    CKS(end(TK_LBM, s));
+    CKS(begin(s));
     CK(launch_bfl(D, parity, s));
-    CKS(mark(TK_STRUCT));
+    CKS(end(TK_BFL, s));
     if (caps) {
-        CK(launch_post(D, 1 - parity, s));
-        CK(launch_edges(D, s));
-        CK(launch_repulsion(D, s));
-        CK(launch_update(D, s));
+        CK(cudaEventRecord(ctx->ev_join, s2));
+        CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     }
-    CKS(mark(-1));
     return IBL_OK;
 }
 
@@ -632,8 +645,11 @@ ibl_status capture_graph(ibl_ctx* ctx, int parity) {
 ibl_status sync_host_state(ibl_ctx* ctx) {
     const int nm = ctx->dev.n_members;
     CK(cudaMemcpyAsync(ctx->h_counters.data(), ctx->dev.counters, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->work));
+    std::vector<uint32_t> pending(nm);
     CK(cudaMemcpyAsync(ctx->h_status.data(), ctx->dev.status, sizeof(uint32_t) * nm, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaMemcpyAsync(pending.data(), ctx->dev.status_new, sizeof(uint32_t) * nm, cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
+    for (int m = 0; m < nm; ++m) ctx->h_status[m] |= pending[m];
     return IBL_OK;
 }
 
@@ -711,6 +727,9 @@ ibl_status new_ctx(void* stream, ibl_ctx** out) {
     if (!ctx) return fail(nullptr, IBL_ERR_OOM, "host allocation failed");
     ctx->user_stream = (cudaStream_t)stream;
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->work2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -827,7 +846,7 @@ ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done) {
     CKS(finalize(ctx));
     const int before = ctx->h_counters[0];
     CKS(enter(ctx));
-    std::vector<std::pair<int, cudaEvent_t>> marks;
+    std::vector<Mark> marks;
     for (int s = 0; s < n_steps; ++s) {
         const int parity = (int)(ctx->t & 1);
         const int zh_on = ctx->t > 0 ? 1 : 0;
@@ -845,14 +864,13 @@ ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done) {
     CKS(leave(ctx));
     if (ctx->timing) {
         for (double& v : ctx->ktime) v = 0.0;
-        for (size_t i = 0; i + 1 < marks.size(); ++i) {
-            const int kind = marks[i].first;
-            if (kind < 0) continue;
+        for (const Mark& mk : marks) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, marks[i].second, marks[i + 1].second);
-            ctx->ktime[kind] += ms;
+            cudaEventElapsedTime(&ms, mk.a, mk.b);
+            ctx->ktime[mk.kind] += ms;
+            cudaEventDestroy(mk.a);
+            cudaEventDestroy(mk.b);
         }
-        for (auto& mk : marks) cudaEventDestroy(mk.second);
     }
     if (steps_done) *steps_done = ctx->h_counters[0] - before;
     uint32_t any = 0;
@@ -928,6 +946,12 @@ ibl_status ibl_member_read_fields(ibl_ctx* ctx, int32_t member, float* rho, floa
     return read_fields_member(ctx, member, rho, u, nullptr, on_device);
 }
 
+ibl_status ibl_member_read_populations(ibl_ctx* ctx, int32_t member, float* g, int32_t on_device) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (!g) return fail(ctx, IBL_ERR_ARG, "null output");
+    return read_fields_member(ctx, member, nullptr, nullptr, g, on_device);
+}
+
 ibl_status ibl_member_read_capsule(ibl_ctx* ctx, int32_t member, int32_t id, ibl_capsule_stats* stats,
                                    double* verts_out) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
@@ -950,9 +974,7 @@ ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm) 
     if (ctx->finalized) {
         CK(cudaStreamSynchronize(ctx->work));
         layout_tiles(ctx);
-        lbm_set_members(ctx->hmem.data(), (int)ctx->hmem.size(), ctx->work);
-        ib_set_members(ctx->hmem.data(), (int)ctx->hmem.size(), ctx->work);
-        CK(cudaGetLastError());
+        CKS(upload(ctx, ctx->dev.mem, ctx->hmem));
         CK(cudaStreamSynchronize(ctx->work));
         drop_graphs(ctx);
     }
@@ -980,6 +1002,10 @@ void ibl_destroy(ibl_ctx* ctx) {
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->work2) cudaStreamSynchronize(ctx->work2);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->work2) cudaStreamDestroy(ctx->work2);
     if (ctx->work) cudaStreamDestroy(ctx->work);
     delete ctx;
 }

@@ -1,15 +1,14 @@
 // Immersed-boundary and structure kernels: per-capsule geometry, the MLS
-// interpolate/force/spread pre-pass (one warp per Lagrangian marker), the
-// post-step marker pass (u_v,0, pressure / viscous probes, volume penalty),
-// per-hinge stretching + bending, inter-body repulsion on a cell list, and the
-// Verlet / Newton-Euler update with the damage rule.
+// interpolate/force/spread pass with the probe stresses and volume penalty (one
+// thread per Lagrangian marker), per-hinge stretching + bending, inter-body
+// repulsion on a cell list, and the Verlet / Newton-Euler update with the
+// damage rule.
+#include <climits>
+
 #include "lbm_device.cuh"
 
 namespace ibl {
 
-void ib_set_members(const MemberDev* m, int n, cudaStream_t s) {
-    cudaMemcpyToSymbolAsync(c_mem, m, sizeof(MemberDev) * n, 0, cudaMemcpyHostToDevice, s);
-}
 
 constexpr float SUPPORT_SIDE = 2.6f;   // 2 r_w (Section "No-slip conditions for moving immersed boundaries")
 constexpr float ALPHA = 0.3f;          // Eq. intKernel
@@ -176,9 +175,28 @@ __global__ void __launch_bounds__(256) k_geometry(const CapsuleDev* __restrict__
     const CapsuleDev& C = caps[blockIdx.x];
     if (!full && (status[C.member] & STOP)) return;
     const int nv = C.v_count, vb = C.v_begin;
+    __shared__ int box[6];
+    if (threadIdx.x < 6) box[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
     for (int v = threadIdx.x; v < 4 * nv; v += blockDim.x) sh[v] = 0.f;
     const double rx0 = x[3 * vb], ry0 = x[3 * vb + 1], rz0 = x[3 * vb + 2];
     __syncthreads();
+    {
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double c = x[3 * v + a];
+                const int f = isfinite(c) ? (int)fmax(fmin(floor(c), 1e9), -1e9) : 0;
+                lo[a] = min(lo[a], f);
+                hi[a] = max(hi[a], f + 1);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&box[a], lo[a]);
+            atomicMax(&box[3 + a], hi[a]);
+        }
+    }
     double acc[11];
 #pragma unroll
     for (int i = 0; i < 11; ++i) acc[i] = 0.0;
@@ -232,6 +250,10 @@ __global__ void __launch_bounds__(256) k_geometry(const CapsuleDev* __restrict__
         sums[blockIdx.x].ref[0] = rx0; sums[blockIdx.x].ref[1] = ry0; sums[blockIdx.x].ref[2] = rz0;
     }
     __syncthreads();
+    if (threadIdx.x < 3) {
+        sums[blockIdx.x].box_lo[threadIdx.x] = box[threadIdx.x];
+        sums[blockIdx.x].box_hi[threadIdx.x] = box[3 + threadIdx.x];
+    }
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
         const float a = sh[4 * v], b = sh[4 * v + 1], c = sh[4 * v + 2];
         const float inv = rsqrtf(a * a + b * b + c * c);
@@ -243,127 +265,247 @@ __global__ void __launch_bounds__(256) k_geometry(const CapsuleDev* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// IB pre-pass (one warp per marker): Eq. uLag on u* = sum g e / rho of the
-// current populations, F_l = (U_b - U_l)/dt, Eq. bodyforce spreading with
-// c_l = A_l into the dense f_ib field (float atomics) and the node's IB flag.
+// IB pre-pass and marker forces (one thread per marker), all on the fluid
+// solution at t (the populations before this step's collision):
+//   Eq. uLag on u* = sum g e / rho, F_l = (U_b - U_l)/dt, Eq. bodyforce
+//   spreading with c_l = A_l into the dense f_ib field (float atomics) and the
+//   node's IB flag; u_v,0 = U_l (the tentative velocity of Eq. verletPos);
+//   probes at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u + grad u^T) from
+//   the MLS fit (Eqs. hydroForP, hydroForNu); the volume penalty
+//   k_v (1 - V/V0) n A (Eq. volFor, restoring sign) of soft capsules.
+// Writes force (overwrite; hinge and repulsion kernels add to it) and uv0.
 // ---------------------------------------------------------------------------
+
+// Moments (rho, u* = sum g e / rho) of the current populations at every fluid
+// node of each capsule's vertex bounding box grown by SHELL_MARGIN, which
+// holds every support node of the marker and probe stencils (probes sit
+// 1.2 dx off the surface, supports reach 1.5 dx further).  The IB kernel then
+// reads one float4 per support node instead of 19 scattered populations.
+// Overlapping boxes write identical values.
+constexpr int SHELL_MARGIN = 4;
+constexpr int SHELL_BLOCKS = 32;   // blocks per capsule
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_ib(const T* __restrict__ f, uint8_t* __restrict__ tag,
-                                            float* __restrict__ fib, const float* __restrict__ face_vel,
-                                            const uint32_t* __restrict__ status, const int* __restrict__ v_cap,
-                                            const CapsuleDev* __restrict__ caps, const double* __restrict__ x,
-                                            const double* __restrict__ vel, const float* __restrict__ area,
-                                            float* __restrict__ phi_out, int n_verts, int parity, int zh_on) {
-    const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (l >= n_verts) return;
-    const int m = caps[v_cap[l]].member;
-    if (status[m] & STOP) return;
-    const MemberDev& d = c_mem[m];
-    const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
-    int node;
-    float rx, ry, rz;
-    bool fluid;
-    support_node(d, tag, X, Y, Z, lane, node, rx, ry, rz, fluid);
-    const float W = mls_weight(fluid, rx, ry, rz);
-    float phi, gx, gy, gz;
-    mls_weights(W, rx, ry, rz, lane, false, phi, gx, gy, gz);
-    if (lane < 27) phi_out[27 * (size_t)l + lane] = phi;
-    float ux = 0.f, uy = 0.f, uz = 0.f;
-    if (phi != 0.f) {
-        float rho;
-        node_state<T>(d, f, face_vel, node, parity, zh_on, rho, ux, uy, uz);
+__global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
+                                               const uint8_t* __restrict__ tag, const float* __restrict__ face_vel,
+                                               const uint32_t* __restrict__ status, const CapsuleDev* __restrict__ caps,
+                                               const CapsuleSums* __restrict__ sums, float4* __restrict__ macro,
+                                               int parity, int zh_on) {
+    const int c = blockIdx.x / SHELL_BLOCKS;
+    const CapsuleDev& C = caps[c];
+    if (status[C.member] & STOP) return;
+    const MemberDev& d = mem[C.member];
+    const int dims[3] = {d.nx, d.ny, d.nz};
+    int lo[3], ext[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int l = sums[c].box_lo[a] - SHELL_MARGIN, h = sums[c].box_hi[a] + SHELL_MARGIN;
+        if ((d.per >> a) & 1) {
+            h = min(h, l + dims[a] - 1);
+        } else {
+            l = max(l, 0);
+            h = min(h, dims[a] - 1);
+        }
+        lo[a] = l;
+        ext[a] = h - l + 1;
     }
-    const float Ux = warp_sum(phi * ux), Uy = warp_sum(phi * uy), Uz = warp_sum(phi * uz);
-    const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
-    if (phi != 0.f) {
-        const float c = area[l] * phi;
-        const size_t gi = (size_t)d.node_off + node;
-        float* p = fib + 3 * gi;
-        atomicAdd(p, c * Fx);
-        atomicAdd(p + 1, c * Fy);
-        atomicAdd(p + 2, c * Fz);
-        atomicOr((unsigned int*)(tag + (gi & ~(size_t)3)), (unsigned int)TAG_IB << (8 * (gi & 3)));
+    if (ext[0] <= 0 || ext[1] <= 0 || ext[2] <= 0) return;
+    const long long total = (long long)ext[0] * ext[1] * ext[2];
+    for (long long i = (blockIdx.x % SHELL_BLOCKS) * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)SHELL_BLOCKS * blockDim.x) {
+        int cx = lo[0] + (int)(i % ext[0]);
+        int cy = lo[1] + (int)((i / ext[0]) % ext[1]);
+        int cz = lo[2] + (int)(i / ((long long)ext[0] * ext[1]));
+        if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx;
+        if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny;
+        if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz;
+        const int node = (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
+        if (tag[d.node_off + node] & TAG_SOLID) continue;
+        float rho, ux, uy, uz;
+        node_state<T>(d, f, face_vel, node, parity, zh_on, rho, ux, uy, uz);
+        macro[d.node_off + node] = make_float4(rho, ux, uy, uz);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Post-step marker pass (one warp per marker) on the new field:
-//   u_v,0 = sum phi u at x(t) (weights of the pre-pass, Eq. verletPos),
-//   probes at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u + grad u^T) from
-//   the MLS fit (Eqs. hydroForP, hydroForNu), and the volume penalty
-//   k_v (1 - V/V0) n A (Eq. volFor, restoring sign) of soft capsules.
-// Writes force (overwrite) and uv0.
-// ---------------------------------------------------------------------------
+// MLS operator of one point: weights W_k of the 27 support nodes (Eq.
+// intKernel) and the rows of A^{-1} (Eq. l2norm, basis [1, x-X, y-Y, z-Z]);
+// moments summed in FP32, the 4x4 system factorised in FP64.  fallback >= 0:
+// singular system, the whole point goes to support node `fallback`.
+struct Mls {
+    int bx, by, bz;
+    float ox, oy, oz;       // base node minus point
+    float W[27];
+    float inv[4][4];
+    int fallback;           // -1: regular; 0..26: nearest fluid node; 27: none
+};
+
+__device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy, int cz) {
+    if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx; else if (cx < 0 || cx >= d.nx) return -1;
+    if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny; else if (cy < 0 || cy >= d.ny) return -1;
+    if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz; else if (cz < 0 || cz >= d.nz) return -1;
+    return (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
+}
+
+__device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __restrict__ tag, double X, double Y,
+                                          double Z, Mls& M) {
+    M.bx = (int)floor(X + 0.5); M.by = (int)floor(Y + 0.5); M.bz = (int)floor(Z + 0.5);
+    M.ox = (float)((double)M.bx - X); M.oy = (float)((double)M.by - Y); M.oz = (float)((double)M.bz - Z);
+    float m0 = 0, m1 = 0, m2 = 0, m3 = 0, m11 = 0, m12 = 0, m13 = 0, m22 = 0, m23 = 0, m33 = 0;
+    float best = 0.f;
+    int bestk = 27;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+        const int node = support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
+        const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
+        const float rx = M.ox + dx, ry = M.oy + dy, rz = M.oz + dz;
+        const float w = mls_weight(fluid, rx, ry, rz);
+        M.W[k] = w;
+        if (w > best) { best = w; bestk = k; }
+        m0 += w; m1 += w * rx; m2 += w * ry; m3 += w * rz;
+        m11 += w * rx * rx; m12 += w * rx * ry; m13 += w * rx * rz;
+        m22 += w * ry * ry; m23 += w * ry * rz; m33 += w * rz * rz;
+    }
+    const double A[4][4] = {{m0, m1, m2, m3}, {m1, m11, m12, m13}, {m2, m12, m22, m23}, {m3, m13, m23, m33}};
+    // L D L^T in FP64
+    const double d0 = A[0][0];
+    const double s0 = d0 > 0.0 ? d0 : 1.0;
+    const double L10 = A[1][0] / s0, L20 = A[2][0] / s0, L30 = A[3][0] / s0;
+    const double d1 = A[1][1] - L10 * L10 * d0;
+    const double s1 = d1 != 0.0 ? d1 : 1.0;
+    const double L21 = (A[2][1] - L20 * L10 * d0) / s1;
+    const double L31 = (A[3][1] - L30 * L10 * d0) / s1;
+    const double d2 = A[2][2] - L20 * L20 * d0 - L21 * L21 * d1;
+    const double s2 = d2 != 0.0 ? d2 : 1.0;
+    const double L32 = (A[3][2] - L30 * L20 * d0 - L31 * L21 * d1) / s2;
+    const double d3 = A[3][3] - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
+    const double tol = PIVOT_TOL * s0;
+    const bool good = d0 > 0.0 && d1 > tol && d2 > tol && d3 > tol;
+    if (!good) {
+        M.fallback = best > 0.f ? bestk : 27;
+        return;
+    }
+    M.fallback = -1;
+    const double r0 = 1.0 / d0, r1 = 1.0 / d1, r2 = 1.0 / d2, r3 = 1.0 / d3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const double y0 = j == 0 ? 1.0 : 0.0;
+        const double y1 = (j == 1 ? 1.0 : 0.0) - L10 * y0;
+        const double y2 = (j == 2 ? 1.0 : 0.0) - L20 * y0 - L21 * y1;
+        const double y3 = (j == 3 ? 1.0 : 0.0) - L30 * y0 - L31 * y1 - L32 * y2;
+        const double c3 = y3 * r3;
+        const double c2 = y2 * r2 - L32 * c3;
+        const double c1 = y1 * r1 - L21 * c2 - L31 * c3;
+        const double c0 = y0 * r0 - L10 * c1 - L20 * c2 - L30 * c3;
+        M.inv[0][j] = (float)c0; M.inv[1][j] = (float)c1; M.inv[2][j] = (float)c2; M.inv[3][j] = (float)c3;
+    }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_post(const T* __restrict__ f, const uint8_t* __restrict__ tag,
-                                              const float* __restrict__ face_vel, const uint32_t* __restrict__ status,
-                                              const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
-                                              const CapsuleSums* __restrict__ sums, const double* __restrict__ x,
-                                              const float* __restrict__ nrm, const float* __restrict__ area,
-                                              const float* __restrict__ phi_in, float* __restrict__ force,
-                                              float* __restrict__ uv0, int n_verts, int pn) {
-    const int l = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, const T* __restrict__ f, uint8_t* __restrict__ tag,
+                                            float* __restrict__ fib, const float* __restrict__ face_vel,
+                                            const uint32_t* __restrict__ status, const int* __restrict__ v_cap,
+                                            const CapsuleDev* __restrict__ caps, const CapsuleSums* __restrict__ sums,
+                                            const double* __restrict__ x, const double* __restrict__ vel,
+                                            const float* __restrict__ nrm, const float* __restrict__ area,
+                                            float* __restrict__ force, float* __restrict__ uv0, int n_verts,
+                                            const float4* __restrict__ macro) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n_verts) return;
     const int cap = v_cap[l];
     const CapsuleDev& C = caps[cap];
     const int m = C.member;
     if (status[m] & STOP) return;
-    const MemberDev& d = c_mem[m];
+    const MemberDev& d = mem[m];
     const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
-    int node;
-    float rx, ry, rz;
-    bool fluid;
-    // (a) u_v,0 with the stored weights
-    support_node(d, tag, X, Y, Z, lane, node, rx, ry, rz, fluid);
-    const float phi0 = lane < 27 ? phi_in[27 * (size_t)l + lane] : 0.f;
-    float ux = 0.f, uy = 0.f, uz = 0.f, rho = 0.f;
-    if (phi0 != 0.f) node_state<T>(d, f, face_vel, node, pn, 1, rho, ux, uy, uz);
-    const float U0x = warp_sum(phi0 * ux), U0y = warp_sum(phi0 * uy), U0z = warp_sum(phi0 * uz);
-    // (b) probes
-    const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
     const float A = area[l];
-    float p[2], t[2][6];
-#pragma unroll
+    Mls M;
+    // --- interpolation at the marker (Eq. uLag) ---
+    mls_build(d, tag, X, Y, Z, M);
+    float Ux = 0.f, Uy = 0.f, Uz = 0.f;
+    float phi[27];
+#pragma unroll 1
+    for (int k = 0; k < 27; ++k) {
+        const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
+        float p = M.fallback < 0 ? M.W[k] * (M.inv[0][0] + M.inv[0][1] * rx + M.inv[0][2] * ry + M.inv[0][3] * rz)
+                                 : (M.fallback == k ? 1.f : 0.f);
+        phi[k] = p;
+        if (p != 0.f) {
+            const int node = support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
+            float rho, ux, uy, uz;
+            const float4 q = macro[d.node_off + node];
+            rho = q.x; ux = q.y; uy = q.z; uz = q.w;
+            Ux += p * ux; Uy += p * uy; Uz += p * uz;
+        }
+    }
+    // --- direct forcing and spreading (Eq. bodyforce) ---
+    const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
+#pragma unroll 1
+    for (int k = 0; k < 27; ++k) {
+        if (phi[k] != 0.f) {
+            const int node = support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
+            const float c = A * phi[k];
+            const size_t gi = (size_t)d.node_off + node;
+            float* p = fib + 3 * gi;
+            atomicAdd(p, c * Fx);
+            atomicAdd(p + 1, c * Fy);
+            atomicAdd(p + 2, c * Fz);
+            tag[gi] = TAG_IB;   // fluid node: its tag byte was 0 or TAG_IB
+        }
+    }
+    // --- probes at x +- 1.2 n (Eqs. hydroForP, hydroForNu) ---
+    const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
+    float dp = 0.f, dt0 = 0.f, dt1 = 0.f, dt2 = 0.f, dt3 = 0.f, dt4 = 0.f, dt5 = 0.f;
+#pragma unroll 1
     for (int s = 0; s < 2; ++s) {
         const double sg = s == 0 ? 1.2 : -1.2;
-        support_node(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, lane, node, rx, ry, rz, fluid);
-        const float W = mls_weight(fluid, rx, ry, rz);
-        float phi, gx, gy, gz;
-        mls_weights(W, rx, ry, rz, lane, true, phi, gx, gy, gz);
-        float r = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
-        if (W > 0.f) node_state<T>(d, f, face_vel, node, pn, 1, r, vx, vy, vz);
-        const float rP = warp_sum(phi * r);
-        const float Gxx = warp_sum(gx * vx), Gxy = warp_sum(gy * vx), Gxz = warp_sum(gz * vx);
-        const float Gyx = warp_sum(gx * vy), Gyy = warp_sum(gy * vy), Gyz = warp_sum(gz * vy);
-        const float Gzx = warp_sum(gx * vz), Gzy = warp_sum(gy * vz), Gzz = warp_sum(gz * vz);
-        const float mu = rP * d.nu;
-        p[s] = rP * (1.f / 3.f);
-        t[s][0] = mu * 2.f * Gxx;
-        t[s][1] = mu * 2.f * Gyy;
-        t[s][2] = mu * 2.f * Gzz;
-        t[s][3] = mu * (Gxy + Gyx);
-        t[s][4] = mu * (Gxz + Gzx);
-        t[s][5] = mu * (Gyz + Gzy);
-    }
-    if (lane == 0) {
-        const float dp = p[0] - p[1];
-        float dt[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) dt[i] = t[0][i] - t[1][i];
-        float Fx = -dp * A * nx + (dt[0] * nx + dt[3] * ny + dt[4] * nz) * A;
-        float Fy = -dp * A * ny + (dt[3] * nx + dt[1] * ny + dt[5] * nz) * A;
-        float Fz = -dp * A * nz + (dt[4] * nx + dt[5] * ny + dt[2] * nz) * A;
-        if (!C.rigid) {
-            const float kvol = (float)(C.kv * (1.0 - sums[cap].V / C.V0));
-            Fx += kvol * A * nx;
-            Fy += kvol * A * ny;
-            Fz += kvol * A * nz;
+        mls_build(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, M);
+        float rP = 0.f, G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll 1
+        for (int k = 0; k < 27; ++k) {
+            if (M.W[k] > 0.f) {
+                const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
+                float p, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+                if (M.fallback < 0) {
+                    const float w = M.W[k];
+                    p = w * (M.inv[0][0] + M.inv[0][1] * rx + M.inv[0][2] * ry + M.inv[0][3] * rz);
+                    g0 = w * (M.inv[1][0] + M.inv[1][1] * rx + M.inv[1][2] * ry + M.inv[1][3] * rz);
+                    g1 = w * (M.inv[2][0] + M.inv[2][1] * rx + M.inv[2][2] * ry + M.inv[2][3] * rz);
+                    g2 = w * (M.inv[3][0] + M.inv[3][1] * rx + M.inv[3][2] * ry + M.inv[3][3] * rz);
+                } else {
+                    p = M.fallback == k ? 1.f : 0.f;
+                }
+                const int node = support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
+                float r, vx, vy, vz;
+                const float4 q = macro[d.node_off + node];
+                r = q.x; vx = q.y; vy = q.z; vz = q.w;
+                rP += p * r;
+                G[0][0] += g0 * vx; G[0][1] += g1 * vx; G[0][2] += g2 * vx;
+                G[1][0] += g0 * vy; G[1][1] += g1 * vy; G[1][2] += g2 * vy;
+                G[2][0] += g0 * vz; G[2][1] += g1 * vz; G[2][2] += g2 * vz;
+            }
         }
-        force[3 * l] = Fx; force[3 * l + 1] = Fy; force[3 * l + 2] = Fz;
-        uv0[3 * l] = U0x; uv0[3 * l + 1] = U0y; uv0[3 * l + 2] = U0z;
+        const float mu = rP * d.nu;
+        const float sgn = s == 0 ? 1.f : -1.f;
+        dp += sgn * rP * (1.f / 3.f);
+        dt0 += sgn * mu * 2.f * G[0][0];
+        dt1 += sgn * mu * 2.f * G[1][1];
+        dt2 += sgn * mu * 2.f * G[2][2];
+        dt3 += sgn * mu * (G[0][1] + G[1][0]);
+        dt4 += sgn * mu * (G[0][2] + G[2][0]);
+        dt5 += sgn * mu * (G[1][2] + G[2][1]);
     }
+    float Hx = -dp * A * nx + (dt0 * nx + dt3 * ny + dt4 * nz) * A;
+    float Hy = -dp * A * ny + (dt3 * nx + dt1 * ny + dt5 * nz) * A;
+    float Hz = -dp * A * nz + (dt4 * nx + dt5 * ny + dt2 * nz) * A;
+    if (!C.rigid) {
+        const float kvol = (float)(C.kv * (1.0 - sums[cap].V / C.V0));
+        Hx += kvol * A * nx;
+        Hy += kvol * A * ny;
+        Hz += kvol * A * nz;
+    }
+    force[3 * l] = Hx; force[3 * l + 1] = Hy; force[3 * l + 2] = Hz;
+    uv0[3 * l] = Ux; uv0[3 * l + 1] = Uy; uv0[3 * l + 2] = Uz;
 }
 
 // ---------------------------------------------------------------------------
@@ -424,13 +566,14 @@ __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, co
 // Inter-body repulsion (Eq. collision) for markers of different capsules
 // closer than 2 dx, found on a uniform grid of 2 dx cells.
 // ---------------------------------------------------------------------------
-__global__ void k_cells_fill(const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
-                             uint32_t* __restrict__ status, const double* __restrict__ x, int* __restrict__ count,
-                             int* __restrict__ items, int n_verts) {
+__global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
+                             const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
+                             const double* __restrict__ x, int* __restrict__ count, int* __restrict__ items,
+                             int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_verts) return;
     const int m = caps[v_cap[v]].member;
-    const MemberDev& d = c_mem[m];
+    const MemberDev& d = mem[m];
     if (!d.has_cells || (status[m] & STOP)) return;
     const int cx = min(max((int)floor(x[3 * v] * 0.5), 0), d.cnx - 1);
     const int cy = min(max((int)floor(x[3 * v + 1] * 0.5), 0), d.cny - 1);
@@ -438,10 +581,10 @@ __global__ void k_cells_fill(const int* __restrict__ v_cap, const CapsuleDev* __
     const long long idx = d.cell_off + cx + (long long)d.cnx * (cy + (long long)d.cny * cz);
     const int slot = atomicAdd(count + idx, 1);
     if (slot < CELL_CAP) items[idx * CELL_CAP + slot] = v;
-    else atomicOr(status + m, ST_OVERFLOW);
+    else atomicOr(status_new + m, ST_OVERFLOW);
 }
 
-__global__ void k_repulsion(const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
+__global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
                             const uint32_t* __restrict__ status, const double* __restrict__ x,
                             const float* __restrict__ nrm, const int* __restrict__ count, const int* __restrict__ items,
                             float* __restrict__ force, int n_verts) {
@@ -449,7 +592,7 @@ __global__ void k_repulsion(const int* __restrict__ v_cap, const CapsuleDev* __r
     if (i >= n_verts) return;
     const int ci = v_cap[i];
     const int m = caps[ci].member;
-    const MemberDev& d = c_mem[m];
+    const MemberDev& d = mem[m];
     if (!d.has_cells || (status[m] & STOP)) return;
     const double X = x[3 * i], Y = x[3 * i + 1], Z = x[3 * i + 2];
     const int cx = min(max((int)floor(X * 0.5), 0), d.cnx - 1);
@@ -466,9 +609,13 @@ __global__ void k_repulsion(const int* __restrict__ v_cap, const CapsuleDev* __r
                 for (int s = 0; s < cnt; ++s) {
                     const int j = items[idx * CELL_CAP + s];
                     if (v_cap[j] == ci) continue;
-                    const float rx = (float)(X - x[3 * j]), ry = (float)(Y - x[3 * j + 1]), rz = (float)(Z - x[3 * j + 2]);
-                    const float dist = sqrtf(rx * rx + ry * ry + rz * rz);
-                    if (dist < 2.f) acc += 1.f / (dist * dist * sqrtf(dist));
+                    // the cutoff decides a discontinuous force: take it in FP64
+                    const double rx = X - x[3 * j], ry = Y - x[3 * j + 1], rz = Z - x[3 * j + 2];
+                    const double d2 = rx * rx + ry * ry + rz * rz;
+                    if (d2 < 4.0) {
+                        const float dist = sqrtf((float)d2);
+                        acc += 1.f / (dist * dist * sqrtf(dist));
+                    }
                 }
             }
     if (acc > 0.f) {
@@ -486,7 +633,8 @@ __global__ void k_repulsion(const int* __restrict__ v_cap, const CapsuleDev* __r
 // damage rule (an edge at twice its rest length) and a finiteness check.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_update(CapsuleDev* __restrict__ caps, CapsuleSums* __restrict__ sums,
-                                                uint32_t* __restrict__ status, double* __restrict__ x,
+                                                const uint32_t* __restrict__ status,
+                                                uint32_t* __restrict__ status_new, double* __restrict__ x,
                                                 double* __restrict__ x_prev, double* __restrict__ vel,
                                                 const float* __restrict__ force, const float* __restrict__ uv0,
                                                 const int* __restrict__ hinge, const float* __restrict__ l0) {
@@ -575,12 +723,19 @@ __global__ void __launch_bounds__(256) k_update(CapsuleDev* __restrict__ caps, C
     }
     __syncthreads();
     if (!C.rigid) {
+        // l >= 2 l0 decided on squared lengths in FP64 (no square root or
+        // division on the slow FP64 path); the reported stretch in FP32
         double mx = 0.0;
+        bool broken = false;
         for (int e = C.e_begin + threadIdx.x; e < C.e_begin + C.e_count; e += blockDim.x) {
             const int a = hinge[4 * e + 1], b = hinge[4 * e + 2];
             const double dx = x[3 * a] - x[3 * b], dy = x[3 * a + 1] - x[3 * b + 1], dz = x[3 * a + 2] - x[3 * b + 2];
-            mx = fmax(mx, sqrt(dx * dx + dy * dy + dz * dz) / (double)l0[e]);
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            const double l0e = (double)l0[e];
+            broken |= d2 >= 4.0 * l0e * l0e;
+            mx = fmax(mx, (double)(sqrtf((float)d2) / l0[e]));
         }
+        if (broken) mx = fmax(mx, 2.0);
 #pragma unroll
         for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
         __syncthreads();
@@ -590,11 +745,11 @@ __global__ void __launch_bounds__(256) k_update(CapsuleDev* __restrict__ caps, C
             double t = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
             sums[blockIdx.x].max_stretch = t;
-            if (t >= 2.0) atomicOr(status + m, ST_DAMAGED);
+            if (t >= 2.0) atomicOr(status_new + m, ST_DAMAGED);
         }
     }
     const int anybad = __syncthreads_or(bad ? 1 : 0);
-    if (anybad && threadIdx.x == 0) atomicOr(status + m, ST_NONFINITE);
+    if (anybad && threadIdx.x == 0) atomicOr(status_new + m, ST_NONFINITE);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,10 +770,11 @@ cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s) {
 
 template <typename T>
 static cudaError_t ib_t(const DevState& d, int parity, int zh_on, cudaStream_t s) {
-    const long long threads = 32LL * d.n_verts;
-    k_ib<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>((const T*)d.f, d.tag, d.fib, d.face_vel, d.status,
-                                                              d.v_cap, d.caps, d.x, d.vel, d.area, d.phi, d.n_verts,
-                                                              parity, zh_on);
+    k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.face_vel, d.status, d.caps,
+                                                       d.sums, d.macro, parity, zh_on);
+    k_ib<T><<<(unsigned)((d.n_verts + 127) / 128), 128, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.fib, d.face_vel, d.status,
+                                                              d.v_cap, d.caps, d.sums, d.x, d.vel, d.nrm, d.area,
+                                                              d.force, d.uv0, d.n_verts, d.macro);
     return cudaGetLastError();
 }
 
@@ -628,24 +784,6 @@ cudaError_t launch_ib(const DevState& d, int parity, int zh_on, cudaStream_t s) 
         case 1: return ib_t<__half>(d, parity, zh_on, s);
         case 2: return ib_t<__nv_bfloat16>(d, parity, zh_on, s);
         default: return ib_t<float>(d, parity, zh_on, s);
-    }
-}
-
-template <typename T>
-static cudaError_t post_t(const DevState& d, int pn, cudaStream_t s) {
-    const long long threads = 32LL * d.n_verts;
-    k_post<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>((const T*)d.f, d.tag, d.face_vel, d.status, d.v_cap,
-                                                                d.caps, d.sums, d.x, d.nrm, d.area, d.phi, d.force,
-                                                                d.uv0, d.n_verts, pn);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_post(const DevState& d, int pn, cudaStream_t s) {
-    if (d.n_verts == 0) return cudaSuccess;
-    switch (d.storage) {
-        case 1: return post_t<__half>(d, pn, s);
-        case 2: return post_t<__nv_bfloat16>(d, pn, s);
-        default: return post_t<float>(d, pn, s);
     }
 }
 
@@ -661,15 +799,17 @@ cudaError_t launch_repulsion(const DevState& d, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * d.n_cells, s);
     if (e != cudaSuccess) return e;
     const int blocks = (d.n_verts + 255) / 256;
-    k_cells_fill<<<blocks, 256, 0, s>>>(d.v_cap, d.caps, d.status, d.x, d.cell_count, d.cell_items, d.n_verts);
-    k_repulsion<<<blocks, 256, 0, s>>>(d.v_cap, d.caps, d.status, d.x, d.nrm, d.cell_count, d.cell_items, d.force,
+    k_cells_fill<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.status_new, d.x, d.cell_count, d.cell_items,
+                                        d.n_verts);
+    k_repulsion<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.x, d.nrm, d.cell_count, d.cell_items, d.force,
                                        d.n_verts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(const DevState& d, cudaStream_t s) {
     if (d.n_caps == 0) return cudaSuccess;
-    k_update<<<d.n_caps, 256, 0, s>>>(d.caps, d.sums, d.status, d.x, d.x_prev, d.vel, d.force, d.uv0, d.hinge, d.l0);
+    k_update<<<d.n_caps, 256, 0, s>>>(d.caps, d.sums, d.status, d.status_new, d.x, d.x_prev, d.vel, d.force, d.uv0,
+                                      d.hinge, d.l0);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ enum : uint8_t { TAG_SOLID = 1, TAG_IB = 2 };
 enum : uint32_t { ST_DAMAGED = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
 enum { FACE_NONE = 0, FACE_VELOCITY = 1, FACE_PRESSURE = 2 };
 
-// Per-lattice descriptor (copied into each translation unit's constant bank).
+// Per-lattice descriptor (a device array per context, passed to every kernel).
 struct MemberDev {
     int nx, ny, nz;          // user dims
     int NX, NY, NZ;          // padded dims (non-periodic axes get a ghost layer)
@@ -83,6 +83,7 @@ struct CapsuleSums {
     double M2[6];            // xx yy zz xy xz yz relative to ref
     double ref[3];
     double max_stretch;
+    int box_lo[3], box_hi[3];   // integer bounding box of the vertices (user coordinates)
 };
 
 // ---------------------------------------------------------------------------
@@ -110,6 +111,7 @@ struct DevState {
     int storage = 0;                 // 0 f32, 1 f16, 2 bf16
     int n_members = 0;
     const MemberDev* h_mem = nullptr;
+    MemberDev* mem = nullptr;         // device copy of the member table (one per context)
     int threads = 256;               // lattice tile size (threads per block)
     int total_tiles = 0;
     int grid_lbm = 0;                // persistent grid (0: one block per tile)
@@ -118,7 +120,8 @@ struct DevState {
     uint8_t* tag = nullptr;          // per padded node
     float* fib = nullptr;            // 3 per padded node, zero outside the IB shell
     float* face_vel = nullptr;       // float3 per face node of velocity faces
-    uint32_t* status = nullptr;      // per member
+    uint32_t* status = nullptr;      // per member, constant during a step
+    uint32_t* status_new = nullptr;  // flags raised during a step, merged at the next step begin
     int* counters = nullptr;         // steps completed, per member
 
     int n_links = 0;
@@ -138,7 +141,7 @@ struct DevState {
     float* uv0 = nullptr;            // 3 per vertex
     float* nrm = nullptr;            // 3 per vertex
     float* area = nullptr;           // per vertex
-    float* phi = nullptr;            // 27 per vertex
+    float4* macro = nullptr;         // (rho, u*) per padded node, written in capsule shells
     int* tri = nullptr;              // 3 per triangle (global vertex ids)
     int* hinge = nullptr;            // 4 per edge: v1 v2 v3 v4 (edge = v2-v3)
     float* l0 = nullptr;
@@ -152,8 +155,6 @@ struct DevState {
 };
 constexpr int CELL_CAP = 32;
 
-void lbm_set_members(const MemberDev* m, int n, cudaStream_t s);
-void ib_set_members(const MemberDev* m, int n, cudaStream_t s);
 
 cudaError_t launch_lbm(const DevState& d, int parity, int zh_on, cudaStream_t s);
 cudaError_t launch_bfl(const DevState& d, int parity_done, cudaStream_t s);
@@ -163,7 +164,7 @@ cudaError_t launch_read(const DevState& d, int member, int parity, int zh_on, fl
 
 cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s);
 cudaError_t launch_ib(const DevState& d, int parity, int zh_on, cudaStream_t s);
-cudaError_t launch_post(const DevState& d, int parity_next, cudaStream_t s);
+cudaError_t launch_step_begin(const DevState& d, cudaStream_t s);
 cudaError_t launch_edges(const DevState& d, cudaStream_t s);
 cudaError_t launch_repulsion(const DevState& d, cudaStream_t s);
 cudaError_t launch_update(const DevState& d, cudaStream_t s);

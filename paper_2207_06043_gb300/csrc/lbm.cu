@@ -3,26 +3,59 @@
 // read-out.
 #include "lbm_device.cuh"
 
+// launch bounds of the lattice kernel (threads per block, minimum resident
+// blocks per SM); the register budget is 64K / (threads * blocks)
+#ifndef LBM_THREADS
+#define LBM_THREADS 256
+#endif
+#ifndef LBM_MIN_BLOCKS
+#define LBM_MIN_BLOCKS 8
+#endif
+
 namespace ibl {
 
-void lbm_set_members(const MemberDev* m, int n, cudaStream_t s) {
-    cudaMemcpyToSymbolAsync(c_mem, m, sizeof(MemberDev) * n, 0, cudaMemcpyHostToDevice, s);
+
+// Start of a step: flags raised during the previous step take effect, and
+// every lattice still running counts one more step.
+__global__ void k_step_begin(uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
+                             int* __restrict__ counters, int n_mem) {
+    const int m = threadIdx.x;
+    if (m >= n_mem) return;
+    const uint32_t st = status[m] | status_new[m];
+    status[m] = st;
+    if (!(st & (ST_DAMAGED | ST_NONFINITE))) counters[m] += 1;
+}
+
+cudaError_t launch_step_begin(const DevState& d, cudaStream_t s) {
+    k_step_begin<<<1, MAX_MEMBERS, 0, s>>>(d.status, d.status_new, d.counters, d.n_members);
+    return cudaGetLastError();
+}
+
+// Zou-He face rule, out of line: only face nodes take this call, so its
+// registers stay out of the bulk path of the lattice kernel.
+struct G19 {
+    float v[Q];
+};
+
+__device__ __noinline__ G19 face_rule(const MemberDev* __restrict__ dp, int X, int Y, int Z,
+                                      const float* __restrict__ face_vel, G19 h) {
+    apply_face(*dp, X, Y, Z, face_vel, h.v);
+    return h;
 }
 
 // One time step of every fluid node of every member (Eq. evoleq): gather the
 // pre-collision populations (AA parity), apply the Zou-He face rule, add the
 // body force and the spread IB force (which is then cleared), collide, store.
-template <typename T>
-__global__ void __launch_bounds__(512) k_lbm(T* __restrict__ f, uint8_t* __restrict__ tag,
-                                              float* __restrict__ fib, const float* __restrict__ face_vel,
-                                              const uint32_t* __restrict__ status, int* __restrict__ counters,
-                                              int n_mem, int total_tiles, int parity, int zh_on) {
-    if (blockIdx.x == 0 && threadIdx.x < n_mem) {
-        if (!(status[threadIdx.x] & (ST_DAMAGED | ST_NONFINITE))) counters[threadIdx.x] += 1;
-    }
+// SINGLE: the context holds one lattice, whose descriptor arrives by value in
+// the kernel's parameter bank (its fields are then constant operands).
+template <typename T, bool SINGLE>
+__global__ void __launch_bounds__(LBM_THREADS, LBM_MIN_BLOCKS)
+k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T* __restrict__ f,
+      uint8_t* __restrict__ tag, float* __restrict__ fib, const float* __restrict__ face_vel,
+      const uint32_t* __restrict__ status, int n_mem, int total_tiles, int parity, int zh_on) {
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-        const int m = find_member_by_tile(n_mem, tile);
-        const MemberDev& d = c_mem[m];
+        const int m = SINGLE ? 0 : find_member_by_tile(mem, n_mem, tile);
+        const MemberDev& d = SINGLE ? d0 : mem[m];
         if (status[m] & (ST_DAMAGED | ST_NONFINITE)) continue;
         const int n = (tile - d.tile_begin) * blockDim.x + threadIdx.x;
         if (n >= d.N) continue;
@@ -34,7 +67,14 @@ __global__ void __launch_bounds__(512) k_lbm(T* __restrict__ f, uint8_t* __restr
         T* fm = f + d.f_off;
         float g[Q];
         load_pre<T>(d, fm, n, X, Y, Z, parity, g);
-        if (zh_on) apply_face(d, X, Y, Z, face_vel, g);
+        if (zh_on && face_of(d, X, Y, Z) >= 0) {
+            G19 h;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) h.v[k] = g[k];
+            h = face_rule(mem + m, X, Y, Z, face_vel, h);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) g[k] = h.v[k];
+        }
         float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
         bool hasF = d.hasF != 0;
         if (tg & TAG_IB) {
@@ -55,7 +95,7 @@ __global__ void __launch_bounds__(512) k_lbm(T* __restrict__ f, uint8_t* __restr
 // post-collision values of the step just done (parity pp) and writes the slot
 // the next step (parity 1 - pp) reads.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bfl(T* __restrict__ f, const uint32_t* __restrict__ l_node,
+__global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, T* __restrict__ f, const uint32_t* __restrict__ l_node,
                                              const uint32_t* __restrict__ l_meta, const float* __restrict__ l_q,
                                              const uint32_t* __restrict__ status, int n_links, int pp) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,7 +103,7 @@ __global__ void __launch_bounds__(256) k_bfl(T* __restrict__ f, const uint32_t* 
     const uint32_t meta = l_meta[l];
     const int m = (int)(meta >> 8);
     if (status[m] & (ST_DAMAGED | ST_NONFINITE)) return;
-    const MemberDev& d = c_mem[m];
+    const MemberDev& d = mem[m];
     const int i = (int)(meta & 31u);
     const bool ok1 = meta & 32u, ok2 = meta & 64u;
     const int ib = opp(i);
@@ -116,9 +156,9 @@ __global__ void __launch_bounds__(256) k_bfl(T* __restrict__ f, const uint32_t* 
 
 // Equilibrium initial state (parity 0 layout) from user-layout rho[N], u[3N].
 template <typename T>
-__global__ void k_init(T* __restrict__ f, const uint8_t* __restrict__ tag, int m, const float* __restrict__ rho,
+__global__ void k_init(const MemberDev* __restrict__ mem, T* __restrict__ f, const uint8_t* __restrict__ tag, int m, const float* __restrict__ rho,
                        const float* __restrict__ u) {
-    const MemberDev& d = c_mem[m];
+    const MemberDev& d = mem[m];
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= d.N) return;
     int X, Y, Z;
@@ -145,10 +185,10 @@ __global__ void k_init(T* __restrict__ f, const uint8_t* __restrict__ tag, int m
 
 // Macroscopic fields / populations of one member in user layout.
 template <typename T>
-__global__ void k_read(const T* __restrict__ f, const uint8_t* __restrict__ tag, const float* __restrict__ face_vel,
+__global__ void k_read(const MemberDev* __restrict__ mem, const T* __restrict__ f, const uint8_t* __restrict__ tag, const float* __restrict__ face_vel,
                        int m, int parity, int zh_on, float* __restrict__ rho, float* __restrict__ u,
                        float* __restrict__ gout) {
-    const MemberDev& d = c_mem[m];
+    const MemberDev& d = mem[m];
     const long long Nu = (long long)d.nx * d.ny * d.nz;
     const long long un = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (un >= Nu) return;
@@ -189,8 +229,12 @@ __global__ void k_read(const T* __restrict__ f, const uint8_t* __restrict__ tag,
 template <typename T>
 static cudaError_t lbm_t(const DevState& d, int parity, int zh_on, cudaStream_t s) {
     const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.total_tiles;
-    k_lbm<T><<<grid, d.threads, 0, s>>>((T*)d.f, d.tag, d.fib, d.face_vel, d.status, d.counters, d.n_members,
-                                        d.total_tiles, parity, zh_on);
+    if (d.n_members == 1)
+        k_lbm<T, true><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel, d.status,
+                                                  d.n_members, d.total_tiles, parity, zh_on);
+    else
+        k_lbm<T, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel, d.status,
+                                                   d.n_members, d.total_tiles, parity, zh_on);
     return cudaGetLastError();
 }
 
@@ -205,7 +249,7 @@ cudaError_t launch_lbm(const DevState& d, int parity, int zh_on, cudaStream_t s)
 template <typename T>
 static cudaError_t bfl_t(const DevState& d, int pp, cudaStream_t s) {
     if (d.n_links == 0) return cudaSuccess;
-    k_bfl<T><<<(d.n_links + 255) / 256, 256, 0, s>>>((T*)d.f, d.l_node, d.l_meta, d.l_q, d.status, d.n_links, pp);
+    k_bfl<T><<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.l_node, d.l_meta, d.l_q, d.status, d.n_links, pp);
     return cudaGetLastError();
 }
 
@@ -220,7 +264,7 @@ cudaError_t launch_bfl(const DevState& d, int pp, cudaStream_t s) {
 template <typename T>
 static cudaError_t init_t(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s) {
     const int N = d.h_mem[m].N;
-    k_init<T><<<(N + 255) / 256, 256, 0, s>>>((T*)d.f, d.tag, m, rho, u);
+    k_init<T><<<(N + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.tag, m, rho, u);
     return cudaGetLastError();
 }
 
@@ -237,7 +281,7 @@ static cudaError_t read_t(const DevState& d, int m, int parity, int zh_on, float
                           cudaStream_t s) {
     const MemberDev& md = d.h_mem[m];
     const long long Nu = (long long)md.nx * md.ny * md.nz;
-    k_read<T><<<(unsigned)((Nu + 255) / 256), 256, 0, s>>>((const T*)d.f, d.tag, d.face_vel, m, parity, zh_on, rho,
+    k_read<T><<<(unsigned)((Nu + 255) / 256), 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.face_vel, m, parity, zh_on, rho,
                                                            u, g);
     return cudaGetLastError();
 }

@@ -1,14 +1,11 @@
-// Device helpers shared by the lattice and immersed-boundary kernels: member
-// descriptors in constant memory, AA-pattern addressing, Zou-He faces,
-// BGK collision with Guo forcing.
+// Device helpers shared by the lattice and immersed-boundary kernels:
+// AA-pattern addressing, Zou-He faces, BGK collision with Guo forcing.
 #pragma once
 
 #include "ibl_internal.cuh"
 
 namespace ibl {
 
-// One copy per translation unit; each unit uploads it with its *_set_members.
-static __constant__ MemberDev c_mem[MAX_MEMBERS];
 
 __device__ __forceinline__ void node_coords(const MemberDev& d, int n, int& X, int& Y, int& Z) {
     X = n % d.NX;
@@ -206,11 +203,11 @@ __device__ __forceinline__ void moments_of(const float g[Q], float& rho, float& 
     ux = jx * inv; uy = jy * inv; uz = jz * inv;
 }
 
-__device__ __forceinline__ int find_member_by_tile(int n_mem, int tile) {
+__device__ __forceinline__ int find_member_by_tile(const MemberDev* __restrict__ mem, int n_mem, int tile) {
     int lo = 0, hi = n_mem - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (c_mem[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+        if (mem[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

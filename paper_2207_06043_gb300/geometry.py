@@ -102,13 +102,15 @@ def box_duct_sdf(p0, p1, half_width, half_height=None):
     centre = 0.5 * (p0 + p1)
 
     def f(P):
-        d = P - centre
-        s = np.abs(d @ a) - 0.5 * length
-        t = np.abs(d @ b) - half_width
-        w = np.abs(d @ c) - hh
-        q = np.stack([s, t, w], axis=-1)
-        outside = np.linalg.norm(np.maximum(q, 0.0), axis=-1)
-        inside = np.minimum(np.max(q, axis=-1), 0.0)
+        dx = P[:, 0] - centre[0]
+        dy = P[:, 1] - centre[1]
+        dz = P[:, 2] - centre[2]
+        s = np.abs(dx * a[0] + dy * a[1]) - 0.5 * length
+        t = np.abs(dx * b[0] + dy * b[1]) - half_width
+        w = np.abs(dz) - hh
+        so, to, wo = np.maximum(s, 0.0), np.maximum(t, 0.0), np.maximum(w, 0.0)
+        outside = np.sqrt(so * so + to * to + wo * wo)
+        inside = np.minimum(np.maximum(np.maximum(s, t), w), 0.0)
         return outside + inside
     return f
 
@@ -146,7 +148,7 @@ def _node_positions(nx, ny, nz):
     return np.stack([n % nx, (n // nx) % ny, n // (nx * ny)], axis=-1).astype(np.float64)
 
 
-def _bisect_root(sdf, a, b, iters=52):
+def _bisect_root(sdf, a, b, iters=40):
     """Root of sdf on the segments a->b (sdf(a) < 0 <= sdf(b)); returns the
     fraction along the segment."""
     lo = np.zeros(a.shape[0])
@@ -387,3 +389,38 @@ def bifurcation(nx, ny, nz, D, half_angle_deg=45.0, r_j=0.0, u_max=0.02, x_junct
     return Geometry(nx, ny, nz, periodic, tag, links, faces, sdf,
                     dict(kind="bifurcation", D=D, half_angle=half_angle_deg, r_j=r_j,
                          u_max=u_max, x_junction=x_junction, yc=yc, zc=zc, levels=levels))
+
+
+def crop_x(geom: Geometry, x1: int) -> Geometry:
+    """The slab 0 <= x < x1 of a geometry whose x axis is not periodic: wall
+    links that leave the slab are dropped and the fluid nodes of the cut plane
+    become a pressure face (density 1)."""
+    nx, ny, nz = geom.nx, geom.ny, geom.nz
+    t3 = geom.tag.reshape(nz, ny, nx)[:, :, :x1]
+    tag = np.ascontiguousarray(t3).reshape(-1).copy()
+    # nodes of the cut plane that also lie on another face become solid
+    X = np.arange(tag.size) % x1
+    Y = (np.arange(tag.size) // x1) % ny
+    Z = np.arange(tag.size) // (x1 * ny)
+    edge = (X == x1 - 1) & ((Y == 0) | (Y == ny - 1) | (Z == 0) | (Z == nz - 1))
+    tag[edge] = SOLID
+    lx = geom.links["node"] % nx
+    ly = (geom.links["node"] // nx) % ny
+    lz = geom.links["node"] // (nx * ny)
+    tx = lx + E19[geom.links["dir"].astype(np.int64), 0]
+    keep = (lx < x1) & (tx < x1) & (tx >= 0)
+    links = geom.links[keep].copy()
+    links["node"] = (lx[keep] + x1 * (ly[keep] + ny * lz[keep])).astype(np.uint32)
+    # drop links that start at nodes made solid above
+    links = links[tag[links["node"]] == FLUID]
+    faces = [Face(f.kind, f.rho, f.velocity) for f in geom.faces]
+    if faces[0].kind == FACE_VELOCITY:
+        faces[0] = Face(FACE_VELOCITY, 1.0, faces[0].velocity)
+    for f in (2, 3, 4, 5):
+        if faces[f].kind == FACE_VELOCITY:
+            raise ValueError("crop_x keeps only x- velocity faces")
+        faces[f] = Face(FACE_PRESSURE, 1.0, None) if face_node_mask(tag, x1, ny, nz, f).any() else Face()
+    faces[1] = Face(FACE_PRESSURE, 1.0, None)
+    info = dict(geom.info)
+    info["cropped_from"] = (nx, ny, nz)
+    return Geometry(x1, ny, nz, geom.periodic, tag, links, faces, None, info)
