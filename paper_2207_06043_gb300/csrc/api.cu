@@ -518,6 +518,10 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(dev_alloc(ctx, D.nrm, x_all.size()));
         CKS(dev_alloc(ctx, D.area, (size_t)vert_off));
         CKS(dev_alloc(ctx, D.macro, (size_t)node_off));
+        CKS(dev_alloc(ctx, D.probe, 16 * (size_t)vert_off));
+        CKS(dev_alloc(ctx, D.vacc, (size_t)vert_off));
+        CK(cudaMemsetAsync(D.vacc, 0, sizeof(float4) * (size_t)vert_off, ctx->work));
+        CK(cudaMemsetAsync(D.probe, 0, sizeof(float) * 16 * (size_t)vert_off, ctx->work));
         CKS(dev_alloc(ctx, D.tri, tri_all.size()));
         CKS(dev_alloc(ctx, D.hinge, hinge_all.size()));
         CKS(dev_alloc(ctx, D.l0, l0_all.size()));
@@ -563,7 +567,6 @@ ibl_status finalize(ibl_ctx* ctx) {
         if (drho) cudaFree(drho);
         if (du) cudaFree(du);
     }
-    CK(launch_geometry(D, 0, ctx->work));
     ctx->h_counters.assign(nm, 0);
     ctx->h_status.assign(nm, 0);
     CK(cudaStreamSynchronize(ctx->work));

@@ -146,10 +146,16 @@ __device__ __forceinline__ void node_state(const MemberDev& d, const T* __restri
 }
 
 // ---------------------------------------------------------------------------
-// per-capsule geometry at x(t): vertex areas A_v = 1/3 sum of adjacent triangle
-// areas, vertex normals = normalised area-weighted triangle normals, and the
-// FP64 enclosed volume (full = 1 adds area, centroid and second moments)
+// Per-capsule geometry at x(t), spread over GEO_BLOCKS blocks per capsule:
+// per triangle, the area-weighted normal and a third of the area go to its
+// vertices (float atomics into vacc); the enclosed volume (divergence theorem,
+// tetrahedra fanned from the capsule's first vertex) is summed in FP64.  Then
+// per vertex: A_v = 1/3 sum of adjacent triangle areas, n_v = normalised
+// area-weighted sum of adjacent normals, the integer bounding box, and vacc
+// is cleared for the next step.  V and the box are reset at the step begin.
 // ---------------------------------------------------------------------------
+constexpr int GEO_BLOCKS = 4;
+
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -166,115 +172,64 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
     return t;   // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) k_geometry(const CapsuleDev* __restrict__ caps, CapsuleSums* __restrict__ sums,
+__global__ void __launch_bounds__(256) k_geom_tri(const CapsuleDev* __restrict__ caps, CapsuleSums* __restrict__ sums,
                                                   const uint32_t* __restrict__ status, const double* __restrict__ x,
-                                                  const int* __restrict__ tri, float* __restrict__ nrm,
-                                                  float* __restrict__ area, int full) {
-    extern __shared__ float sh[];
+                                                  const int* __restrict__ tri, float4* __restrict__ vacc) {
     __shared__ double red[32];
-    const CapsuleDev& C = caps[blockIdx.x];
-    if (!full && (status[C.member] & STOP)) return;
-    const int nv = C.v_count, vb = C.v_begin;
-    __shared__ int box[6];
-    if (threadIdx.x < 6) box[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
-    for (int v = threadIdx.x; v < 4 * nv; v += blockDim.x) sh[v] = 0.f;
+    const int c = blockIdx.x / GEO_BLOCKS, part = blockIdx.x % GEO_BLOCKS;
+    const CapsuleDev& C = caps[c];
+    if (status[C.member] & STOP) return;
+    const int vb = C.v_begin;
     const double rx0 = x[3 * vb], ry0 = x[3 * vb + 1], rz0 = x[3 * vb + 2];
-    __syncthreads();
-    {
-        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-        for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double c = x[3 * v + a];
-                const int f = isfinite(c) ? (int)fmax(fmin(floor(c), 1e9), -1e9) : 0;
-                lo[a] = min(lo[a], f);
-                hi[a] = max(hi[a], f + 1);
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            atomicMin(&box[a], lo[a]);
-            atomicMax(&box[3 + a], hi[a]);
-        }
-    }
-    double acc[11];
-#pragma unroll
-    for (int i = 0; i < 11; ++i) acc[i] = 0.0;
-    for (int t = C.t_begin + threadIdx.x; t < C.t_begin + C.t_count; t += blockDim.x) {
+    double vol = 0.0;
+    for (int t = C.t_begin + part * blockDim.x + threadIdx.x; t < C.t_begin + C.t_count;
+         t += GEO_BLOCKS * blockDim.x) {
         const int ia = tri[3 * t], ib = tri[3 * t + 1], ic = tri[3 * t + 2];
         const double ax = x[3 * ia] - rx0, ay = x[3 * ia + 1] - ry0, az = x[3 * ia + 2] - rz0;
         const double bx = x[3 * ib] - rx0, by = x[3 * ib + 1] - ry0, bz = x[3 * ib + 2] - rz0;
         const double cx = x[3 * ic] - rx0, cy = x[3 * ic + 1] - ry0, cz = x[3 * ic + 2] - rz0;
-        const double ux = bx - ax, uy = by - ay, uz = bz - az;
-        const double vx = cx - ax, vy = cy - ay, vz = cz - az;
-        const double Nx = uy * vz - uz * vy, Ny = uz * vx - ux * vz, Nz = ux * vy - uy * vx;
-        const double ar = 0.5 * sqrt(Nx * Nx + Ny * Ny + Nz * Nz);
-        const int ids[3] = {ia - vb, ib - vb, ic - vb};
+        vol += (ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx)) * (1.0 / 6.0);
+        const float ux = (float)(bx - ax), uy = (float)(by - ay), uz = (float)(bz - az);
+        const float vx = (float)(cx - ax), vy = (float)(cy - ay), vz = (float)(cz - az);
+        const float Nx = uy * vz - uz * vy, Ny = uz * vx - ux * vz, Nz = ux * vy - uy * vx;
+        const float a3 = sqrtf(Nx * Nx + Ny * Ny + Nz * Nz) * (1.f / 6.f);
+        const int ids[3] = {ia, ib, ic};
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            float* p = sh + 4 * ids[j];
-            atomicAdd(p, (float)(0.5 * Nx));
-            atomicAdd(p + 1, (float)(0.5 * Ny));
-            atomicAdd(p + 2, (float)(0.5 * Nz));
-            atomicAdd(p + 3, (float)(ar / 3.0));
-        }
-        const double vol = (ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx)) / 6.0;
-        acc[0] += vol;
-        if (full) {
-            acc[1] += ar;
-            const double sx = ax + bx + cx, sy = ay + by + cy, sz = az + bz + cz;
-            acc[2] += vol * sx * 0.25; acc[3] += vol * sy * 0.25; acc[4] += vol * sz * 0.25;
-            const double c20 = vol / 20.0;
-            acc[5] += c20 * (ax * ax + bx * bx + cx * cx + sx * sx);
-            acc[6] += c20 * (ay * ay + by * by + cy * cy + sy * sy);
-            acc[7] += c20 * (az * az + bz * bz + cz * cz + sz * sz);
-            acc[8] += c20 * (ax * ay + bx * by + cx * cy + sx * sy);
-            acc[9] += c20 * (ax * az + bx * bz + cx * cz + sx * sz);
-            acc[10] += c20 * (ay * az + by * bz + cy * cz + sy * sz);
+            float* p = (float*)(vacc + ids[j]);
+            atomicAdd(p, 0.5f * Nx);
+            atomicAdd(p + 1, 0.5f * Ny);
+            atomicAdd(p + 2, 0.5f * Nz);
+            atomicAdd(p + 3, a3);
         }
     }
-    const int nacc = full ? 11 : 1;
-    for (int i = 0; i < nacc; ++i) {
-        const double s = block_sum_d(acc[i], red);
-        if (threadIdx.x == 0) {
-            CapsuleSums& S = sums[blockIdx.x];
-            switch (i) {
-                case 0: S.V = s; break;
-                case 1: S.S = s; break;
-                case 2: case 3: case 4: S.cen[i - 2] = s; break;
-                default: S.M2[i - 5] = s; break;
-            }
-        }
-    }
-    if (threadIdx.x == 0 && full) {
-        sums[blockIdx.x].ref[0] = rx0; sums[blockIdx.x].ref[1] = ry0; sums[blockIdx.x].ref[2] = rz0;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        sums[blockIdx.x].box_lo[threadIdx.x] = box[threadIdx.x];
-        sums[blockIdx.x].box_hi[threadIdx.x] = box[3 + threadIdx.x];
-    }
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-        const float a = sh[4 * v], b = sh[4 * v + 1], c = sh[4 * v + 2];
-        const float inv = rsqrtf(a * a + b * b + c * c);
-        nrm[3 * (vb + v)] = a * inv;
-        nrm[3 * (vb + v) + 1] = b * inv;
-        nrm[3 * (vb + v) + 2] = c * inv;
-        area[vb + v] = sh[4 * v + 3];
-    }
+    const double s = block_sum_d(vol, red);
+    if (threadIdx.x == 0) atomicAdd(&sums[c].V, s);
 }
 
-// ---------------------------------------------------------------------------
-// IB pre-pass and marker forces (one thread per marker), all on the fluid
-// solution at t (the populations before this step's collision):
-//   Eq. uLag on u* = sum g e / rho, F_l = (U_b - U_l)/dt, Eq. bodyforce
-//   spreading with c_l = A_l into the dense f_ib field (float atomics) and the
-//   node's IB flag; u_v,0 = U_l (the tentative velocity of Eq. verletPos);
-//   probes at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u + grad u^T) from
-//   the MLS fit (Eqs. hydroForP, hydroForNu); the volume penalty
-//   k_v (1 - V/V0) n A (Eq. volFor, restoring sign) of soft capsules.
-// Writes force (overwrite; hinge and repulsion kernels add to it) and uv0.
-// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__ caps, const int* __restrict__ v_cap,
+                                                  CapsuleSums* __restrict__ sums, const uint32_t* __restrict__ status,
+                                                  const double* __restrict__ x, float4* __restrict__ vacc,
+                                                  float* __restrict__ nrm, float* __restrict__ area, int n_verts) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_verts) return;
+    const int c = v_cap[v];
+    if (status[caps[c].member] & STOP) return;
+    const float4 a = vacc[v];
+    const float inv = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+    nrm[3 * v] = a.x * inv;
+    nrm[3 * v + 1] = a.y * inv;
+    nrm[3 * v + 2] = a.z * inv;
+    area[v] = a.w;
+    vacc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double q = x[3 * v + k];
+        const int f = isfinite(q) ? (int)fmax(fmin(floor(q), 1e9), -1e9) : 0;
+        atomicMin(&sums[c].box_lo[k], f);
+        atomicMax(&sums[c].box_hi[k], f + 1);
+    }
+}
 
 // Moments (rho, u* = sum g e / rho) of the current populations at every fluid
 // node of each capsule's vertex bounding box grown by SHELL_MARGIN, which
@@ -328,8 +283,9 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
 }
 
 // MLS operator of one point: weights W_k of the 27 support nodes (Eq.
-// intKernel) and the rows of A^{-1} (Eq. l2norm, basis [1, x-X, y-Y, z-Z]);
-// moments summed in FP32, the 4x4 system factorised in FP64.  fallback >= 0:
+// intKernel) and the first ROWS rows of A^{-1} (Eq. l2norm, basis
+// [1, x-X, y-Y, z-Z]; A is symmetric, so row j is A^{-1} e_j); moments summed
+// in FP32, the 4x4 system factorised and solved in FP64.  fallback >= 0:
 // singular system, the whole point goes to support node `fallback`.
 struct Mls {
     int bx, by, bz;
@@ -346,6 +302,7 @@ __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy,
     return (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
 }
 
+template <int ROWS>
 __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __restrict__ tag, double X, double Y,
                                           double Z, Mls& M) {
     M.bx = (int)floor(X + 0.5); M.by = (int)floor(Y + 0.5); M.bz = (int)floor(Z + 0.5);
@@ -366,19 +323,20 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
         m11 += w * rx * rx; m12 += w * rx * ry; m13 += w * rx * rz;
         m22 += w * ry * ry; m23 += w * ry * rz; m33 += w * rz * rz;
     }
-    const double A[4][4] = {{m0, m1, m2, m3}, {m1, m11, m12, m13}, {m2, m12, m22, m23}, {m3, m13, m23, m33}};
     // L D L^T in FP64
-    const double d0 = A[0][0];
+    const double a00 = m0, a10 = m1, a20 = m2, a30 = m3, a11 = m11, a21 = m12, a31 = m13, a22 = m22, a32 = m23,
+                 a33 = m33;
+    const double d0 = a00;
     const double s0 = d0 > 0.0 ? d0 : 1.0;
-    const double L10 = A[1][0] / s0, L20 = A[2][0] / s0, L30 = A[3][0] / s0;
-    const double d1 = A[1][1] - L10 * L10 * d0;
+    const double L10 = a10 / s0, L20 = a20 / s0, L30 = a30 / s0;
+    const double d1 = a11 - L10 * L10 * d0;
     const double s1 = d1 != 0.0 ? d1 : 1.0;
-    const double L21 = (A[2][1] - L20 * L10 * d0) / s1;
-    const double L31 = (A[3][1] - L30 * L10 * d0) / s1;
-    const double d2 = A[2][2] - L20 * L20 * d0 - L21 * L21 * d1;
+    const double L21 = (a21 - L20 * L10 * d0) / s1;
+    const double L31 = (a31 - L30 * L10 * d0) / s1;
+    const double d2 = a22 - L20 * L20 * d0 - L21 * L21 * d1;
     const double s2 = d2 != 0.0 ? d2 : 1.0;
-    const double L32 = (A[3][2] - L30 * L20 * d0 - L31 * L21 * d1) / s2;
-    const double d3 = A[3][3] - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
+    const double L32 = (a32 - L30 * L20 * d0 - L31 * L21 * d1) / s2;
+    const double d3 = a33 - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
     const double tol = PIVOT_TOL * s0;
     const bool good = d0 > 0.0 && d1 > tol && d2 > tol && d3 > tol;
     if (!good) {
@@ -388,7 +346,7 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
     M.fallback = -1;
     const double r0 = 1.0 / d0, r1 = 1.0 / d1, r2 = 1.0 / d2, r3 = 1.0 / d3;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < ROWS; ++j) {
         const double y0 = j == 0 ? 1.0 : 0.0;
         const double y1 = (j == 1 ? 1.0 : 0.0) - L10 * y0;
         const double y2 = (j == 2 ? 1.0 : 0.0) - L20 * y0 - L21 * y1;
@@ -397,20 +355,47 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
         const double c2 = y2 * r2 - L32 * c3;
         const double c1 = y1 * r1 - L21 * c2 - L31 * c3;
         const double c0 = y0 * r0 - L10 * c1 - L20 * c2 - L30 * c3;
-        M.inv[0][j] = (float)c0; M.inv[1][j] = (float)c1; M.inv[2][j] = (float)c2; M.inv[3][j] = (float)c3;
+        M.inv[j][0] = (float)c0; M.inv[j][1] = (float)c1; M.inv[j][2] = (float)c2; M.inv[j][3] = (float)c3;
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, const T* __restrict__ f, uint8_t* __restrict__ tag,
-                                            float* __restrict__ fib, const float* __restrict__ face_vel,
-                                            const uint32_t* __restrict__ status, const int* __restrict__ v_cap,
-                                            const CapsuleDev* __restrict__ caps, const CapsuleSums* __restrict__ sums,
-                                            const double* __restrict__ x, const double* __restrict__ vel,
-                                            const float* __restrict__ nrm, const float* __restrict__ area,
-                                            float* __restrict__ force, float* __restrict__ uv0, int n_verts,
+__device__ __forceinline__ float mls_row(const Mls& M, int j, int k) {
+    const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
+    return M.W[k] * (M.inv[j][0] + M.inv[j][1] * rx + M.inv[j][2] * ry + M.inv[j][3] * rz);
+}
+
+__device__ __forceinline__ int mls_node(const MemberDev& d, const Mls& M, int k) {
+    return support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
+}
+
+// ---------------------------------------------------------------------------
+// IB pre-pass and marker stencils, three threads per marker, all on the fluid
+// solution at t (moments of the current populations from the shell pass):
+//  s = 0: Eq. uLag on u*, F_l = (U_b - U_l)/dt, Eq. bodyforce spreading with
+//         c_l = A_l into the dense f_ib field (float atomics) and the node's IB
+//         flag; u_v,0 = U_l (the tentative velocity of Eq. verletPos); the
+//         force accumulator starts at the volume penalty k_v (1 - V/V0) n A
+//         (Eq. volFor, restoring sign) of soft capsules (0 for rigid ones);
+//  s = 1, 2: the probe at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u +
+//         grad u^T) from the MLS fit (Eqs. hydroForP, hydroForNu), stored for
+//         the update kernels, which add F_p + F_tau.
+// Gathers are issued nine at a time so that their latencies overlap.
+// ---------------------------------------------------------------------------
+constexpr int PROBE_STRIDE = 8;   // floats per probe record: p, tau xx yy zz xy xz yz, pad
+
+__global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag,
+                                            float* __restrict__ fib, const uint32_t* __restrict__ status,
+                                            const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
+                                            const CapsuleSums* __restrict__ sums, const double* __restrict__ x,
+                                            const double* __restrict__ vel, const float* __restrict__ nrm,
+                                            const float* __restrict__ area, float* __restrict__ force,
+                                            float* __restrict__ uv0, float* __restrict__ probe, int n_verts,
                                             const float4* __restrict__ macro) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    // threads [0, M) take the marker stencils, [M, 3M) the probes, so that
+    // whole warps follow one code path
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = t < n_verts ? t : (t - n_verts) >> 1;
+    const int s = t < n_verts ? 0 : 1 + ((t - n_verts) & 1);
     if (l >= n_verts) return;
     const int cap = v_cap[l];
     const CapsuleDev& C = caps[cap];
@@ -418,94 +403,98 @@ __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, c
     if (status[m] & STOP) return;
     const MemberDev& d = mem[m];
     const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
-    const float A = area[l];
-    Mls M;
-    // --- interpolation at the marker (Eq. uLag) ---
-    mls_build(d, tag, X, Y, Z, M);
-    float Ux = 0.f, Uy = 0.f, Uz = 0.f;
-    float phi[27];
-#pragma unroll 1
-    for (int k = 0; k < 27; ++k) {
-        const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
-        float p = M.fallback < 0 ? M.W[k] * (M.inv[0][0] + M.inv[0][1] * rx + M.inv[0][2] * ry + M.inv[0][3] * rz)
-                                 : (M.fallback == k ? 1.f : 0.f);
-        phi[k] = p;
-        if (p != 0.f) {
-            const int node = support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
-            float rho, ux, uy, uz;
-            const float4 q = macro[d.node_off + node];
-            rho = q.x; ux = q.y; uy = q.z; uz = q.w;
-            Ux += p * ux; Uy += p * uy; Uz += p * uz;
-        }
-    }
-    // --- direct forcing and spreading (Eq. bodyforce) ---
-    const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
-#pragma unroll 1
-    for (int k = 0; k < 27; ++k) {
-        if (phi[k] != 0.f) {
-            const int node = support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
-            const float c = A * phi[k];
-            const size_t gi = (size_t)d.node_off + node;
-            float* p = fib + 3 * gi;
-            atomicAdd(p, c * Fx);
-            atomicAdd(p + 1, c * Fy);
-            atomicAdd(p + 2, c * Fz);
-            tag[gi] = TAG_IB;   // fluid node: its tag byte was 0 or TAG_IB
-        }
-    }
-    // --- probes at x +- 1.2 n (Eqs. hydroForP, hydroForNu) ---
     const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
-    float dp = 0.f, dt0 = 0.f, dt1 = 0.f, dt2 = 0.f, dt3 = 0.f, dt4 = 0.f, dt5 = 0.f;
+    Mls M;
+    if (s == 0) {
+        mls_build<1>(d, tag, X, Y, Z, M);
+        float Ux = 0.f, Uy = 0.f, Uz = 0.f;
 #pragma unroll 1
-    for (int s = 0; s < 2; ++s) {
-        const double sg = s == 0 ? 1.2 : -1.2;
-        mls_build(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, M);
-        float rP = 0.f, G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int c = 0; c < 3; ++c) {
+            float p[9];
+            float4 q[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int k = 9 * c + j;
+                p[j] = M.fallback < 0 ? mls_row(M, 0, k) : (M.fallback == k ? 1.f : 0.f);
+                q[j] = p[j] != 0.f ? macro[d.node_off + mls_node(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                Ux += p[j] * q[j].y; Uy += p[j] * q[j].z; Uz += p[j] * q[j].w;
+            }
+        }
+        const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
+        const float A = area[l];
 #pragma unroll 1
         for (int k = 0; k < 27; ++k) {
-            if (M.W[k] > 0.f) {
-                const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
-                float p, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+            const float p = M.fallback < 0 ? mls_row(M, 0, k) : (M.fallback == k ? 1.f : 0.f);
+            if (p != 0.f) {
+                const float c = A * p;
+                const size_t gi = (size_t)d.node_off + mls_node(d, M, k);
+                float* f3 = fib + 3 * gi;
+                atomicAdd(f3, c * Fx);
+                atomicAdd(f3 + 1, c * Fy);
+                atomicAdd(f3 + 2, c * Fz);
+                tag[gi] = TAG_IB;   // fluid node: its tag byte was 0 or TAG_IB
+            }
+        }
+        uv0[3 * l] = Ux; uv0[3 * l + 1] = Uy; uv0[3 * l + 2] = Uz;
+        float kvol = 0.f;
+        if (!C.rigid) kvol = (float)(C.kv * (1.0 - sums[cap].V / C.V0)) * A;
+        force[3 * l] = kvol * nx; force[3 * l + 1] = kvol * ny; force[3 * l + 2] = kvol * nz;
+    } else {
+        const double sg = s == 1 ? 1.2 : -1.2;
+        mls_build<4>(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, M);
+        float rP = 0.f, G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            float4 q[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int k = 9 * c + j;
+                q[j] = M.W[k] > 0.f ? macro[d.node_off + mls_node(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const int k = 9 * c + j;
                 if (M.fallback < 0) {
-                    const float w = M.W[k];
-                    p = w * (M.inv[0][0] + M.inv[0][1] * rx + M.inv[0][2] * ry + M.inv[0][3] * rz);
-                    g0 = w * (M.inv[1][0] + M.inv[1][1] * rx + M.inv[1][2] * ry + M.inv[1][3] * rz);
-                    g1 = w * (M.inv[2][0] + M.inv[2][1] * rx + M.inv[2][2] * ry + M.inv[2][3] * rz);
-                    g2 = w * (M.inv[3][0] + M.inv[3][1] * rx + M.inv[3][2] * ry + M.inv[3][3] * rz);
-                } else {
-                    p = M.fallback == k ? 1.f : 0.f;
+                    const float p = mls_row(M, 0, k), g0 = mls_row(M, 1, k), g1 = mls_row(M, 2, k),
+                                g2 = mls_row(M, 3, k);
+                    rP += p * q[j].x;
+                    G[0][0] += g0 * q[j].y; G[0][1] += g1 * q[j].y; G[0][2] += g2 * q[j].y;
+                    G[1][0] += g0 * q[j].z; G[1][1] += g1 * q[j].z; G[1][2] += g2 * q[j].z;
+                    G[2][0] += g0 * q[j].w; G[2][1] += g1 * q[j].w; G[2][2] += g2 * q[j].w;
+                } else if (M.fallback == k) {
+                    rP += q[j].x;
                 }
-                const int node = support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
-                float r, vx, vy, vz;
-                const float4 q = macro[d.node_off + node];
-                r = q.x; vx = q.y; vy = q.z; vz = q.w;
-                rP += p * r;
-                G[0][0] += g0 * vx; G[0][1] += g1 * vx; G[0][2] += g2 * vx;
-                G[1][0] += g0 * vy; G[1][1] += g1 * vy; G[1][2] += g2 * vy;
-                G[2][0] += g0 * vz; G[2][1] += g1 * vz; G[2][2] += g2 * vz;
             }
         }
         const float mu = rP * d.nu;
-        const float sgn = s == 0 ? 1.f : -1.f;
-        dp += sgn * rP * (1.f / 3.f);
-        dt0 += sgn * mu * 2.f * G[0][0];
-        dt1 += sgn * mu * 2.f * G[1][1];
-        dt2 += sgn * mu * 2.f * G[2][2];
-        dt3 += sgn * mu * (G[0][1] + G[1][0]);
-        dt4 += sgn * mu * (G[0][2] + G[2][0]);
-        dt5 += sgn * mu * (G[1][2] + G[2][1]);
+        float* rec = probe + ((size_t)2 * l + (s - 1)) * PROBE_STRIDE;
+        rec[0] = rP * (1.f / 3.f);
+        rec[1] = mu * 2.f * G[0][0];
+        rec[2] = mu * 2.f * G[1][1];
+        rec[3] = mu * 2.f * G[2][2];
+        rec[4] = mu * (G[0][1] + G[1][0]);
+        rec[5] = mu * (G[0][2] + G[2][0]);
+        rec[6] = mu * (G[1][2] + G[2][1]);
     }
-    float Hx = -dp * A * nx + (dt0 * nx + dt3 * ny + dt4 * nz) * A;
-    float Hy = -dp * A * ny + (dt3 * nx + dt1 * ny + dt5 * nz) * A;
-    float Hz = -dp * A * nz + (dt4 * nx + dt5 * ny + dt2 * nz) * A;
-    if (!C.rigid) {
-        const float kvol = (float)(C.kv * (1.0 - sums[cap].V / C.V0));
-        Hx += kvol * A * nx;
-        Hy += kvol * A * ny;
-        Hz += kvol * A * nz;
-    }
-    force[3 * l] = Hx; force[3 * l + 1] = Hy; force[3 * l + 2] = Hz;
-    uv0[3 * l] = Ux; uv0[3 * l + 1] = Uy; uv0[3 * l + 2] = Uz;
+}
+
+// F_p + F_tau of vertex v from its two probe records (Eqs. hydroForP,
+// hydroForNu): -(p+ - p-) n A + (tau+ - tau-) . n A.
+__device__ __forceinline__ void hydro_force(const float* __restrict__ probe, const float* __restrict__ nrm,
+                                            const float* __restrict__ area, int v, float& Hx, float& Hy,
+                                            float& Hz) {
+    const float* a = probe + (size_t)2 * v * PROBE_STRIDE;
+    const float* b = a + PROBE_STRIDE;
+    const float nx = nrm[3 * v], ny = nrm[3 * v + 1], nz = nrm[3 * v + 2], A = area[v];
+    const float dp = a[0] - b[0];
+    const float t0 = a[1] - b[1], t1 = a[2] - b[2], t2 = a[3] - b[3], t3 = a[4] - b[4], t4 = a[5] - b[5],
+                t5 = a[6] - b[6];
+    Hx = (-dp * nx + t0 * nx + t3 * ny + t4 * nz) * A;
+    Hy = (-dp * ny + t3 * nx + t1 * ny + t5 * nz) * A;
+    Hz = (-dp * nz + t4 * nx + t5 * ny + t2 * nz) * A;
 }
 
 // ---------------------------------------------------------------------------
@@ -568,11 +557,12 @@ __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, co
 // ---------------------------------------------------------------------------
 __global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
                              const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
-                             const double* __restrict__ x, int* __restrict__ count, int* __restrict__ items,
+                             const double* __restrict__ x, int* __restrict__ count, float4* __restrict__ items,
                              int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_verts) return;
-    const int m = caps[v_cap[v]].member;
+    const int cap = v_cap[v];
+    const int m = caps[cap].member;
     const MemberDev& d = mem[m];
     if (!d.has_cells || (status[m] & STOP)) return;
     const int cx = min(max((int)floor(x[3 * v] * 0.5), 0), d.cnx - 1);
@@ -580,14 +570,17 @@ __global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __res
     const int cz = min(max((int)floor(x[3 * v + 2] * 0.5), 0), d.cnz - 1);
     const long long idx = d.cell_off + cx + (long long)d.cnx * (cy + (long long)d.cny * cz);
     const int slot = atomicAdd(count + idx, 1);
-    if (slot < CELL_CAP) items[idx * CELL_CAP + slot] = v;
+    // item: FP32 position (prefilter) and the vertex id; its capsule is v_cap
+    if (slot < CELL_CAP)
+        items[idx * CELL_CAP + slot] = make_float4((float)x[3 * v], (float)x[3 * v + 1], (float)x[3 * v + 2],
+                                                   __int_as_float(v));
     else atomicOr(status_new + m, ST_OVERFLOW);
 }
 
 __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
                             const uint32_t* __restrict__ status, const double* __restrict__ x,
-                            const float* __restrict__ nrm, const int* __restrict__ count, const int* __restrict__ items,
-                            float* __restrict__ force, int n_verts) {
+                            const float* __restrict__ nrm, const int* __restrict__ count,
+                            const float4* __restrict__ items, float* __restrict__ force, int n_verts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_verts) return;
     const int ci = v_cap[i];
@@ -595,6 +588,7 @@ __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __rest
     const MemberDev& d = mem[m];
     if (!d.has_cells || (status[m] & STOP)) return;
     const double X = x[3 * i], Y = x[3 * i + 1], Z = x[3 * i + 2];
+    const float Xf = (float)X, Yf = (float)Y, Zf = (float)Z;
     const int cx = min(max((int)floor(X * 0.5), 0), d.cnx - 1);
     const int cy = min(max((int)floor(Y * 0.5), 0), d.cny - 1);
     const int cz = min(max((int)floor(Z * 0.5), 0), d.cnz - 1);
@@ -607,7 +601,12 @@ __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __rest
                 const long long idx = d.cell_off + qx + (long long)d.cnx * (qy + (long long)d.cny * qz);
                 const int cnt = min(count[idx], CELL_CAP);
                 for (int s = 0; s < cnt; ++s) {
-                    const int j = items[idx * CELL_CAP + s];
+                    const float4 it = items[idx * CELL_CAP + s];
+                    // FP32 prefilter (coordinates below 1e4 lu round by < 1e-3,
+                    // far inside the 0.01 margin on d^2)
+                    const float fx = Xf - it.x, fy = Yf - it.y, fz = Zf - it.z;
+                    if (fx * fx + fy * fy + fz * fz > 4.01f) continue;
+                    const int j = __float_as_int(it.w);
                     if (v_cap[j] == ci) continue;
                     // the cutoff decides a discontinuous force: take it in FP64
                     const double rx = X - x[3 * j], ry = Y - x[3 * j + 1], rz = Z - x[3 * j + 2];
@@ -627,144 +626,143 @@ __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Structure update (one block per capsule): Verlet predictor / velocity /
-// corrector for soft capsules (Eqs. verletPos, verletVel, verletPosC), or the
-// Newton-Euler system with Eq. angularVelRig for rigid bodies; then the
-// damage rule (an edge at twice its rest length) and a finiteness check.
+// Structure update.  Soft capsules, one thread per vertex: the Verlet
+// predictor / velocity / corrector (Eqs. verletPos, verletVel, verletPosC) in
+// FP64 on F^tot = hinge + repulsion + volume (accumulated in `force`) +
+// hydrodynamic (probe records).  Rigid bodies, one block each: the
+// Newton-Euler system with Eq. angularVelRig.  Then, one thread per edge, the
+// damage rule (an edge at twice its rest length).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_update(CapsuleDev* __restrict__ caps, CapsuleSums* __restrict__ sums,
-                                                const uint32_t* __restrict__ status,
-                                                uint32_t* __restrict__ status_new, double* __restrict__ x,
-                                                double* __restrict__ x_prev, double* __restrict__ vel,
-                                                const float* __restrict__ force, const float* __restrict__ uv0,
-                                                const int* __restrict__ hinge, const float* __restrict__ l0) {
+__global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ caps, const int* __restrict__ v_cap,
+                                                const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
+                                                double* __restrict__ x, double* __restrict__ x_prev,
+                                                double* __restrict__ vel, const float* __restrict__ force,
+                                                const float* __restrict__ uv0, const float* __restrict__ probe,
+                                                const float* __restrict__ nrm, const float* __restrict__ area,
+                                                int n_verts) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_verts) return;
+    const CapsuleDev& C = caps[v_cap[v]];
+    if (C.rigid || (status[C.member] & STOP)) return;
+    float H[3];
+    hydro_force(probe, nrm, area, v, H[0], H[1], H[2]);
+    const double half_inv_m = 0.5 / C.mv;
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double acc = ((double)force[3 * v + a] + (double)H[a]) * half_inv_m;
+        const double xt = x[3 * v + a];
+        const double xp = xt + (double)uv0[3 * v + a] + acc;
+        const double un = 1.5 * xp - 2.0 * xt + 0.5 * x_prev[3 * v + a];
+        const double xn = xt + un + acc;
+        x_prev[3 * v + a] = xt;
+        x[3 * v + a] = xn;
+        vel[3 * v + a] = un;
+        bad |= !isfinite(xn);
+    }
+    if (bad) atomicOr(status_new + C.member, ST_NONFINITE);
+}
+
+__global__ void __launch_bounds__(256) k_rigid(CapsuleDev* __restrict__ caps, const uint32_t* __restrict__ status,
+                                               uint32_t* __restrict__ status_new, double* __restrict__ x,
+                                               double* __restrict__ x_prev, double* __restrict__ vel,
+                                               const float* __restrict__ force, const float* __restrict__ probe,
+                                               const float* __restrict__ nrm, const float* __restrict__ area) {
     __shared__ double red[32];
     __shared__ double sh_rig[16];
     CapsuleDev& C = caps[blockIdx.x];
-    const int m = C.member;
-    if (status[m] & STOP) return;
+    if (!C.rigid || (status[C.member] & STOP)) return;
     const int vb = C.v_begin, nv = C.v_count;
-    bool bad = false;
-    if (!C.rigid) {
-        const double mv = C.mv;
-        for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double acc = 0.5 * (double)force[3 * v + a] / mv;
-                const double xt = x[3 * v + a];
-                const double xp = xt + (double)uv0[3 * v + a] + acc;
-                const double un = 1.5 * xp - 2.0 * xt + 0.5 * x_prev[3 * v + a];
-                const double xn = xt + un + acc;
-                x_prev[3 * v + a] = xt;
-                x[3 * v + a] = xn;
-                vel[3 * v + a] = un;
-                bad |= !isfinite(xn);
-            }
-        }
-    } else {
-        const double xc0 = C.xc[0], xc1 = C.xc[1], xc2 = C.xc[2];
-        double s[6] = {0, 0, 0, 0, 0, 0};
-        for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
-            const double fx = force[3 * v], fy = force[3 * v + 1], fz = force[3 * v + 2];
-            const double rx = x[3 * v] - xc0, ry = x[3 * v + 1] - xc1, rz = x[3 * v + 2] - xc2;
-            s[0] += fx; s[1] += fy; s[2] += fz;
-            s[3] += ry * fz - rz * fy; s[4] += rz * fx - rx * fz; s[5] += rx * fy - ry * fx;
-        }
-        for (int i = 0; i < 6; ++i) {
-            const double t = block_sum_d(s[i], red);
-            if (threadIdx.x == 0) sh_rig[i] = t;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double u[3], w[3];
-            for (int a = 0; a < 3; ++a) {
-                u[a] = (2.0 / 3.0) * (2.0 * C.u1[a] - 0.5 * C.u2[a] + sh_rig[a] / C.mass);
-                w[a] = (2.0 / 3.0) * (2.0 * C.w1[a] - 0.5 * C.w2[a] + sh_rig[3 + a] / C.inertia);
-            }
-            // Rodrigues rotation by the angle vector w (dt = 1)
-            const double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-            double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-            if (th > 0.0) {
-                const double kx = w[0] / th, ky = w[1] / th, kz = w[2] / th;
-                const double sn = sin(th), cs1 = 1.0 - cos(th);
-                const double K[9] = {0, -kz, ky, kz, 0, -kx, -ky, kx, 0};
-                double K2[9];
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j)
-                        K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
-                for (int i = 0; i < 9; ++i) R[i] += sn * K[i] + cs1 * K2[i];
-            }
-            for (int i = 0; i < 9; ++i) sh_rig[i] = R[i];
-            for (int a = 0; a < 3; ++a) {
-                sh_rig[9 + a] = u[a];
-                C.u2[a] = C.u1[a]; C.u1[a] = u[a];
-                C.w2[a] = C.w1[a]; C.w1[a] = w[a];
-            }
-            sh_rig[12] = w[0]; sh_rig[13] = w[1]; sh_rig[14] = w[2];
-        }
-        __syncthreads();
-        const double ncx = xc0 + sh_rig[9], ncy = xc1 + sh_rig[10], ncz = xc2 + sh_rig[11];
-        const double* R = sh_rig;
-        for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
-            const double rx = x[3 * v] - xc0, ry = x[3 * v + 1] - xc1, rz = x[3 * v + 2] - xc2;
-            const double qx = R[0] * rx + R[1] * ry + R[2] * rz;
-            const double qy = R[3] * rx + R[4] * ry + R[5] * rz;
-            const double qz = R[6] * rx + R[7] * ry + R[8] * rz;
-            x_prev[3 * v] = x[3 * v]; x_prev[3 * v + 1] = x[3 * v + 1]; x_prev[3 * v + 2] = x[3 * v + 2];
-            x[3 * v] = ncx + qx; x[3 * v + 1] = ncy + qy; x[3 * v + 2] = ncz + qz;
-            const double wx = sh_rig[12], wy = sh_rig[13], wz = sh_rig[14];
-            vel[3 * v] = sh_rig[9] + (wy * qz - wz * qy);
-            vel[3 * v + 1] = sh_rig[10] + (wz * qx - wx * qz);
-            vel[3 * v + 2] = sh_rig[11] + (wx * qy - wy * qx);
-            bad |= !(isfinite(x[3 * v]) && isfinite(x[3 * v + 1]) && isfinite(x[3 * v + 2]));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) { C.xc[0] = ncx; C.xc[1] = ncy; C.xc[2] = ncz; }
+    const double xc0 = C.xc[0], xc1 = C.xc[1], xc2 = C.xc[2];
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
+        float H[3];
+        hydro_force(probe, nrm, area, v, H[0], H[1], H[2]);
+        const double fx = (double)force[3 * v] + H[0], fy = (double)force[3 * v + 1] + H[1],
+                     fz = (double)force[3 * v + 2] + H[2];
+        const double rx = x[3 * v] - xc0, ry = x[3 * v + 1] - xc1, rz = x[3 * v + 2] - xc2;
+        s[0] += fx; s[1] += fy; s[2] += fz;
+        s[3] += ry * fz - rz * fy; s[4] += rz * fx - rx * fz; s[5] += rx * fy - ry * fx;
+    }
+    for (int i = 0; i < 6; ++i) {
+        const double t = block_sum_d(s[i], red);
+        if (threadIdx.x == 0) sh_rig[i] = t;
     }
     __syncthreads();
-    if (!C.rigid) {
-        // l >= 2 l0 decided on squared lengths in FP64 (no square root or
-        // division on the slow FP64 path); the reported stretch in FP32
-        double mx = 0.0;
-        bool broken = false;
-        for (int e = C.e_begin + threadIdx.x; e < C.e_begin + C.e_count; e += blockDim.x) {
-            const int a = hinge[4 * e + 1], b = hinge[4 * e + 2];
-            const double dx = x[3 * a] - x[3 * b], dy = x[3 * a + 1] - x[3 * b + 1], dz = x[3 * a + 2] - x[3 * b + 2];
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            const double l0e = (double)l0[e];
-            broken |= d2 >= 4.0 * l0e * l0e;
-            mx = fmax(mx, (double)(sqrtf((float)d2) / l0[e]));
+    if (threadIdx.x == 0) {
+        double u[3], w[3];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = (2.0 / 3.0) * (2.0 * C.u1[a] - 0.5 * C.u2[a] + sh_rig[a] / C.mass);
+            w[a] = (2.0 / 3.0) * (2.0 * C.w1[a] - 0.5 * C.w2[a] + sh_rig[3 + a] / C.inertia);
         }
-        if (broken) mx = fmax(mx, 2.0);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
-            sums[blockIdx.x].max_stretch = t;
-            if (t >= 2.0) atomicOr(status_new + m, ST_DAMAGED);
+        // Rodrigues rotation by the angle vector w (dt = 1)
+        const double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        if (th > 0.0) {
+            const double kx = w[0] / th, ky = w[1] / th, kz = w[2] / th;
+            const double sn = sin(th), cs1 = 1.0 - cos(th);
+            const double K[9] = {0, -kz, ky, kz, 0, -kx, -ky, kx, 0};
+            double K2[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+            for (int i = 0; i < 9; ++i) R[i] += sn * K[i] + cs1 * K2[i];
         }
+        for (int i = 0; i < 9; ++i) sh_rig[i] = R[i];
+        for (int a = 0; a < 3; ++a) {
+            sh_rig[9 + a] = u[a];
+            C.u2[a] = C.u1[a]; C.u1[a] = u[a];
+            C.w2[a] = C.w1[a]; C.w1[a] = w[a];
+        }
+        sh_rig[12] = w[0]; sh_rig[13] = w[1]; sh_rig[14] = w[2];
     }
+    __syncthreads();
+    const double ncx = xc0 + sh_rig[9], ncy = xc1 + sh_rig[10], ncz = xc2 + sh_rig[11];
+    const double* R = sh_rig;
+    bool bad = false;
+    for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
+        const double rx = x[3 * v] - xc0, ry = x[3 * v + 1] - xc1, rz = x[3 * v + 2] - xc2;
+        const double qx = R[0] * rx + R[1] * ry + R[2] * rz;
+        const double qy = R[3] * rx + R[4] * ry + R[5] * rz;
+        const double qz = R[6] * rx + R[7] * ry + R[8] * rz;
+        x_prev[3 * v] = x[3 * v]; x_prev[3 * v + 1] = x[3 * v + 1]; x_prev[3 * v + 2] = x[3 * v + 2];
+        x[3 * v] = ncx + qx; x[3 * v + 1] = ncy + qy; x[3 * v + 2] = ncz + qz;
+        const double wx = sh_rig[12], wy = sh_rig[13], wz = sh_rig[14];
+        vel[3 * v] = sh_rig[9] + (wy * qz - wz * qy);
+        vel[3 * v + 1] = sh_rig[10] + (wz * qx - wx * qz);
+        vel[3 * v + 2] = sh_rig[11] + (wx * qy - wy * qx);
+        bad |= !(isfinite(x[3 * v]) && isfinite(x[3 * v + 1]) && isfinite(x[3 * v + 2]));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { C.xc[0] = ncx; C.xc[1] = ncy; C.xc[2] = ncz; }
     const int anybad = __syncthreads_or(bad ? 1 : 0);
-    if (anybad && threadIdx.x == 0) atomicOr(status_new + m, ST_NONFINITE);
+    if (anybad && threadIdx.x == 0) atomicOr(status_new + C.member, ST_NONFINITE);
+}
+
+// l >= 2 l0 decided on squared lengths in FP64 (no square root or division
+// on the slow FP64 path).
+__global__ void __launch_bounds__(256) k_damage(const CapsuleDev* __restrict__ caps, const int* __restrict__ e_cap,
+                                                const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
+                                                const double* __restrict__ x, const int* __restrict__ hinge,
+                                                const float* __restrict__ l0, int n_edges) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_edges) return;
+    const CapsuleDev& C = caps[e_cap[e]];
+    if (C.rigid || (status[C.member] & STOP)) return;
+    const int a = hinge[4 * e + 1], b = hinge[4 * e + 2];
+    const double dx = x[3 * a] - x[3 * b], dy = x[3 * a + 1] - x[3 * b + 1], dz = x[3 * a + 2] - x[3 * b + 2];
+    const double l0e = (double)l0[e];
+    if (dx * dx + dy * dy + dz * dz >= 4.0 * l0e * l0e) atomicOr(status_new + C.member, ST_DAMAGED);
 }
 
 // ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
-cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s) {
+cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) {
     if (d.n_caps == 0) return cudaSuccess;
-    const size_t smem = 16 * (size_t)d.max_nv;
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_geometry, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    k_geometry<<<d.n_caps, 256, smem, s>>>(d.caps, d.sums, d.status, d.x, d.tri, d.nrm, d.area, full);
+    k_geom_tri<<<d.n_caps * GEO_BLOCKS, 256, 0, s>>>(d.caps, d.sums, d.status, d.x, d.tri, d.vacc);
+    k_geom_vtx<<<(d.n_verts + 255) / 256, 256, 0, s>>>(d.caps, d.v_cap, d.sums, d.status, d.x, d.vacc, d.nrm, d.area,
+                                                       d.n_verts);
     return cudaGetLastError();
 }
 
@@ -772,9 +770,10 @@ template <typename T>
 static cudaError_t ib_t(const DevState& d, int parity, int zh_on, cudaStream_t s) {
     k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.face_vel, d.status, d.caps,
                                                        d.sums, d.macro, parity, zh_on);
-    k_ib<T><<<(unsigned)((d.n_verts + 127) / 128), 128, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.fib, d.face_vel, d.status,
-                                                              d.v_cap, d.caps, d.sums, d.x, d.vel, d.nrm, d.area,
-                                                              d.force, d.uv0, d.n_verts, d.macro);
+    const long long threads = 3LL * d.n_verts;
+    k_ib<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d.mem, d.tag, d.fib, d.status, d.v_cap, d.caps, d.sums, d.x,
+                                                           d.vel, d.nrm, d.area, d.force, d.uv0, d.probe, d.n_verts,
+                                                           d.macro);
     return cudaGetLastError();
 }
 
@@ -808,8 +807,15 @@ cudaError_t launch_repulsion(const DevState& d, cudaStream_t s) {
 
 cudaError_t launch_update(const DevState& d, cudaStream_t s) {
     if (d.n_caps == 0) return cudaSuccess;
-    k_update<<<d.n_caps, 256, 0, s>>>(d.caps, d.sums, d.status, d.status_new, d.x, d.x_prev, d.vel, d.force, d.uv0,
-                                      d.hinge, d.l0);
+    if (d.any_soft)
+        k_verlet<<<(d.n_verts + 255) / 256, 256, 0, s>>>(d.caps, d.v_cap, d.status, d.status_new, d.x, d.x_prev, d.vel,
+                                                         d.force, d.uv0, d.probe, d.nrm, d.area, d.n_verts);
+    if (d.any_rigid)
+        k_rigid<<<d.n_caps, 256, 0, s>>>(d.caps, d.status, d.status_new, d.x, d.x_prev, d.vel, d.force, d.probe, d.nrm,
+                                         d.area);
+    if (d.any_soft && d.n_edges > 0)
+        k_damage<<<(d.n_edges + 255) / 256, 256, 0, s>>>(d.caps, d.e_cap, d.status, d.status_new, d.x, d.hinge, d.l0,
+                                                         d.n_edges);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,8 @@ struct DevState {
     float* nrm = nullptr;            // 3 per vertex
     float* area = nullptr;           // per vertex
     float4* macro = nullptr;         // (rho, u*) per padded node, written in capsule shells
+    float* probe = nullptr;          // 2 probe records (8 floats) per vertex
+    float4* vacc = nullptr;          // per-vertex normal / area accumulator, zero between steps
     int* tri = nullptr;              // 3 per triangle (global vertex ids)
     int* hinge = nullptr;            // 4 per edge: v1 v2 v3 v4 (edge = v2-v3)
     float* l0 = nullptr;
@@ -150,7 +152,7 @@ struct DevState {
     float* kb = nullptr;
     int* e_cap = nullptr;
     int* cell_count = nullptr;
-    int* cell_items = nullptr;
+    float4* cell_items = nullptr;    // (x, y, z, vertex id bits) per slot
     long long n_cells = 0;
 };
 constexpr int CELL_CAP = 32;

@@ -17,17 +17,26 @@ namespace ibl {
 
 // Start of a step: flags raised during the previous step take effect, and
 // every lattice still running counts one more step.
+// The capsules' volume sums and bounding boxes restart from zero / empty.
 __global__ void k_step_begin(uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
-                             int* __restrict__ counters, int n_mem) {
+                             int* __restrict__ counters, int n_mem, CapsuleSums* __restrict__ sums, int n_caps) {
     const int m = threadIdx.x;
-    if (m >= n_mem) return;
-    const uint32_t st = status[m] | status_new[m];
-    status[m] = st;
-    if (!(st & (ST_DAMAGED | ST_NONFINITE))) counters[m] += 1;
+    if (m < n_mem) {
+        const uint32_t st = status[m] | status_new[m];
+        status[m] = st;
+        if (!(st & (ST_DAMAGED | ST_NONFINITE))) counters[m] += 1;
+    }
+    for (int c = threadIdx.x; c < n_caps; c += blockDim.x) {
+        sums[c].V = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            sums[c].box_lo[a] = 0x7fffffff;
+            sums[c].box_hi[a] = -0x7fffffff - 1;
+        }
+    }
 }
 
 cudaError_t launch_step_begin(const DevState& d, cudaStream_t s) {
-    k_step_begin<<<1, MAX_MEMBERS, 0, s>>>(d.status, d.status_new, d.counters, d.n_members);
+    k_step_begin<<<1, MAX_MEMBERS, 0, s>>>(d.status, d.status_new, d.counters, d.n_members, d.sums, d.n_caps);
     return cudaGetLastError();
 }
 
