@@ -33,7 +33,7 @@ WORKLOADS = {
     # the throughput configuration (12.6 M nodes, 64 capsules)
     "throughput": dict(),
     # a smaller instance of the same family for profiler captures (~4 M nodes)
-    "small": dict(n_capsules=16, nx=320, ny=128, nz=96, D=64.0, d=16.0, nv=642),
+    "small": dict(n_capsules=32, nx=320, ny=128, nz=96, D=64.0, d=16.0, nv=2562),
 }
 
 

@@ -53,7 +53,7 @@ struct ibl_ctx {
     cudaStream_t work = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaStream_t work2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_ib = nullptr;
     int storage = IBL_STORAGE_F32;
     std::vector<MemberHost> members;
     bool finalized = false;
@@ -423,7 +423,7 @@ ibl_status finalize(ibl_ctx* ctx) {
             cd.v_begin = vert_off; cd.v_count = nv;
             cd.t_begin = tri_off; cd.t_count = nt;
             cd.e_begin = edge_off; cd.e_count = ne;
-            cd.kv = ch.p.kv; cd.V0 = ms.V; cd.S0 = ms.S;
+            cd.kv = ch.p.kv; cd.V0 = ms.V; cd.inv_V0 = 1.0 / ms.V; cd.S0 = ms.S;
             cd.mass = ch.p.density_ratio * ms.V;
             cd.mv = cd.mass / nv;
             cd.inertia = 0.4 * cd.mass * radius * radius;
@@ -581,10 +581,11 @@ struct Mark {
     cudaEvent_t a, b;
 };
 
-// One time step.  Stream `work`: step begin, geometry, IB pre-pass + marker
-// forces, then the lattice step and the wall fill.  Stream `work2` (forked
-// after the IB pass, joined at the end): hinge forces, repulsion and the
-// structure update, which touch no lattice data and overlap the lattice step.
+// One time step.  Stream `work`: step begin, geometry, shell moments and the
+// IB pass, then the lattice step and the wall fill.  Stream `work2`: after the
+// geometry, repulsion and hinge forces (concurrent with the IB pass); after
+// the IB pass, the structure update (concurrent with the lattice step).  The
+// update touches no lattice data and the lattice step no structure data.
 ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<Mark>* marks) {
     DevState& D = ctx->dev;
     cudaStream_t s = ctx->work, s2 = ctx->work2;
@@ -608,13 +609,15 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<Mark>* 
     if (caps) {
         CKS(begin(s));
         CK(launch_geometry(D, 0, s));
+        CK(cudaEventRecord(ctx->ev_fork, s));
         CK(launch_ib(D, parity, zh_on, s));
         CKS(end(TK_IB, s));
-        CK(cudaEventRecord(ctx->ev_fork, s));
+        CK(cudaEventRecord(ctx->ev_ib, s));
         CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
         CKS(begin(s2));
-        CK(launch_edges(D, s2));
         CK(launch_repulsion(D, s2));
+        CK(launch_edges(D, s2));
+        CK(cudaStreamWaitEvent(s2, ctx->ev_ib, 0));
         CK(launch_update(D, s2));
         CKS(end(TK_STRUCT, s2));
     }
@@ -733,6 +736,7 @@ ibl_status new_ctx(void* stream, ibl_ctx** out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->work2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_ib, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -1008,6 +1012,7 @@ void ibl_destroy(ibl_ctx* ctx) {
     if (ctx->work2) cudaStreamSynchronize(ctx->work2);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_ib) cudaEventDestroy(ctx->ev_ib);
     if (ctx->work2) cudaStreamDestroy(ctx->work2);
     if (ctx->work) cudaStreamDestroy(ctx->work);
     delete ctx;

@@ -16,121 +16,11 @@ constexpr double PIVOT_TOL = 1e-10;    // singular moment matrix -> nearest flui
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t STOP = ST_DAMAGED | ST_NONFINITE;
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
-// Support node k (0..26) of the point (X, Y, Z): the 3x3x3 block around the
-// nearest node (round half up), in user coordinates; node is the padded index
-// (-1 outside the domain), fluid false for solid or outside nodes.
-__device__ __forceinline__ void support_node(const MemberDev& d, const uint8_t* __restrict__ tag, double X, double Y,
-                                             double Z, int k, int& node, float& rx, float& ry, float& rz,
-                                             bool& fluid) {
-    const int bx = (int)floor(X + 0.5), by = (int)floor(Y + 0.5), bz = (int)floor(Z + 0.5);
-    int cx = bx + (k % 3) - 1, cy = by + (k / 3) % 3 - 1, cz = bz + k / 9 - 1;
-    rx = (float)((double)cx - X);
-    ry = (float)((double)cy - Y);
-    rz = (float)((double)cz - Z);
-    bool ok = k < 27;
-    if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx; else ok = ok && cx >= 0 && cx < d.nx;
-    if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny; else ok = ok && cy >= 0 && cy < d.ny;
-    if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz; else ok = ok && cz >= 0 && cz < d.nz;
-    node = ok ? (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz)) : -1;
-    fluid = ok && !(tag[d.node_off + node] & TAG_SOLID);
-}
-
 // Eq. intKernel with r normalised by the support side.
 __device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, float rz) {
     const float r = sqrtf(rx * rx + ry * ry + rz * rz) * (1.f / SUPPORT_SIDE);
     const float s = r * (1.f / ALPHA);
     return (fluid && r <= 1.f) ? expf(-s * s) : 0.f;
-}
-
-// Column j of A^{-1} for the symmetric 4x4 moment matrix by L D L^T in FP64;
-// good = every pivot above PIVOT_TOL * A00.
-__device__ void ldlt_column(const double A[4][4], int j, double col[4], bool& good) {
-    const double d0 = A[0][0];
-    good = d0 > 0.0;
-    const double s0 = d0 > 0.0 ? d0 : 1.0;
-    const double L10 = A[1][0] / s0, L20 = A[2][0] / s0, L30 = A[3][0] / s0;
-    const double d1 = A[1][1] - L10 * L10 * d0;
-    const double s1 = d1 != 0.0 ? d1 : 1.0;
-    const double L21 = (A[2][1] - L20 * L10 * d0) / s1;
-    const double L31 = (A[3][1] - L30 * L10 * d0) / s1;
-    const double d2 = A[2][2] - L20 * L20 * d0 - L21 * L21 * d1;
-    const double s2 = d2 != 0.0 ? d2 : 1.0;
-    const double L32 = (A[3][2] - L30 * L20 * d0 - L31 * L21 * d1) / s2;
-    const double d3 = A[3][3] - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
-    const double tol = PIVOT_TOL * s0;
-    good = good && d1 > tol && d2 > tol && d3 > tol;
-    if (!good) { col[0] = col[1] = col[2] = col[3] = 0.0; return; }
-    // L y = e_j
-    double y0 = j == 0 ? 1.0 : 0.0;
-    double y1 = (j == 1 ? 1.0 : 0.0) - L10 * y0;
-    double y2 = (j == 2 ? 1.0 : 0.0) - L20 * y0 - L21 * y1;
-    double y3 = (j == 3 ? 1.0 : 0.0) - L30 * y0 - L31 * y1 - L32 * y2;
-    // D z = y ; L^T c = z
-    const double z0 = y0 / d0, z1 = y1 / d1, z2 = y2 / d2, z3 = y3 / d3;
-    col[3] = z3;
-    col[2] = z2 - L32 * col[3];
-    col[1] = z1 - L21 * col[2] - L31 * col[3];
-    col[0] = z0 - L10 * col[1] - L20 * col[2] - L30 * col[3];
-}
-
-// Warp-cooperative MLS shape functions (Eq. l2norm with the linear basis
-// p = [1, x - X, y - Y, z - Z]): lane k < 27 holds W_k and its offsets and
-// receives phi_k = W_k (A^{-1} p_k)_0 and, if want_grad, the gradient weights
-// W_k (A^{-1} p_k)_{1..3}.  Moments are summed in FP32 (marker-relative
-// offsets), the 4x4 system is solved in FP64.  A singular system hands the
-// whole marker to the support node of largest weight.
-__device__ void mls_weights(float W, float rx, float ry, float rz, int lane, bool want_grad, float& phi,
-                            float& gx, float& gy, float& gz) {
-    float mo[10] = {W, W * rx, W * ry, W * rz, W * rx * rx, W * rx * ry, W * rx * rz, W * ry * ry, W * ry * rz,
-                    W * rz * rz};
-#pragma unroll
-    for (int i = 0; i < 10; ++i) mo[i] = warp_sum(mo[i]);
-    double col[4] = {0.0, 0.0, 0.0, 0.0};
-    bool good = false;
-    if (lane < 4) {
-        const double A[4][4] = {{mo[0], mo[1], mo[2], mo[3]},
-                                {mo[1], mo[4], mo[5], mo[6]},
-                                {mo[2], mo[5], mo[7], mo[8]},
-                                {mo[3], mo[6], mo[8], mo[9]}};
-        ldlt_column(A, lane, col, good);
-    }
-    good = __shfl_sync(FULL, (int)good, 0) != 0;
-    gx = gy = gz = 0.f;
-    if (good) {
-        float r0[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) r0[c] = (float)__shfl_sync(FULL, col[c], 0);
-        phi = W * (r0[0] + r0[1] * rx + r0[2] * ry + r0[3] * rz);
-        if (want_grad) {
-            float r1[4], r2[4], r3[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                r1[c] = (float)__shfl_sync(FULL, col[c], 1);
-                r2[c] = (float)__shfl_sync(FULL, col[c], 2);
-                r3[c] = (float)__shfl_sync(FULL, col[c], 3);
-            }
-            gx = W * (r1[0] + r1[1] * rx + r1[2] * ry + r1[3] * rz);
-            gy = W * (r2[0] + r2[1] * rx + r2[2] * ry + r2[3] * rz);
-            gz = W * (r3[0] + r3[1] * rx + r3[2] * ry + r3[3] * rz);
-        }
-    } else {
-        float best = W;
-        int bl = lane;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const float ob = __shfl_xor_sync(FULL, best, o);
-            const int ol = __shfl_xor_sync(FULL, bl, o);
-            if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
-        }
-        phi = (best > 0.f && lane == bl) ? 1.f : 0.f;
-    }
-    if (lane >= 27) { phi = 0.f; gx = gy = gz = 0.f; }
 }
 
 template <typename T>
@@ -212,22 +102,39 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
                                                   const double* __restrict__ x, float4* __restrict__ vacc,
                                                   float* __restrict__ nrm, float* __restrict__ area, int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n_verts) return;
-    const int c = v_cap[v];
-    if (status[caps[c].member] & STOP) return;
-    const float4 a = vacc[v];
-    const float inv = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
-    nrm[3 * v] = a.x * inv;
-    nrm[3 * v + 1] = a.y * inv;
-    nrm[3 * v + 2] = a.z * inv;
-    area[v] = a.w;
-    vacc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool live = v < n_verts && !(status[caps[v_cap[min(v, n_verts - 1)]].member] & STOP);
+    const int c = live ? v_cap[v] : -1;
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    if (live) {
+        const float4 a = vacc[v];
+        const float inv = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+        nrm[3 * v] = a.x * inv;
+        nrm[3 * v + 1] = a.y * inv;
+        nrm[3 * v + 2] = a.z * inv;
+        area[v] = a.w;
+        vacc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double q = x[3 * v + k];
+            lo[k] = isfinite(q) ? (int)fmax(fmin(floor(q), 1e9), -1e9) : 0;
+            hi[k] = lo[k] + 1;
+        }
+    }
+    // lanes of one capsule reduce among themselves, then one lane per capsule
+    // and warp updates the box (consecutive vertices share a capsule)
+    const unsigned peers = __match_any_sync(FULL, c);
+    const int leader = __ffs(peers) - 1;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double q = x[3 * v + k];
-        const int f = isfinite(q) ? (int)fmax(fmin(floor(q), 1e9), -1e9) : 0;
-        atomicMin(&sums[c].box_lo[k], f);
-        atomicMax(&sums[c].box_hi[k], f + 1);
+        lo[k] = __reduce_min_sync(peers, lo[k]);
+        hi[k] = __reduce_max_sync(peers, hi[k]);
+    }
+    if (live && (int)(threadIdx.x & 31) == leader) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&sums[c].box_lo[k], lo[k]);
+            atomicMax(&sums[c].box_hi[k], hi[k]);
+        }
     }
 }
 
@@ -289,11 +196,20 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
 // singular system, the whole point goes to support node `fallback`.
 struct Mls {
     int bx, by, bz;
+    int base;               // padded index of the base node when the block is interior, else -1
     float ox, oy, oz;       // base node minus point
     float W[27];
     float inv[4][4];
     int fallback;           // -1: regular; 0..26: nearest fluid node; 27: none
 };
+
+// 1/d in FP64 by Newton's iteration r <- r (2 - d r) from the FP32
+// reciprocal (each step doubles the correct bits: 24 -> 48 -> full)
+__device__ __forceinline__ double rcp64(double d) {
+    double r = (double)__frcp_rn((float)d);
+    r = r * (2.0 - d * r);
+    return r * (2.0 - d * r);
+}
 
 __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy, int cz) {
     if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx; else if (cx < 0 || cx >= d.nx) return -1;
@@ -307,13 +223,17 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
                                           double Z, Mls& M) {
     M.bx = (int)floor(X + 0.5); M.by = (int)floor(Y + 0.5); M.bz = (int)floor(Z + 0.5);
     M.ox = (float)((double)M.bx - X); M.oy = (float)((double)M.by - Y); M.oz = (float)((double)M.bz - Z);
+    const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
+                          M.bz <= d.nz - 2;
+    M.base = interior ? (M.bx + d.px) + d.NX * ((M.by + d.py) + d.NY * (M.bz + d.pz)) : -1;
     float m0 = 0, m1 = 0, m2 = 0, m3 = 0, m11 = 0, m12 = 0, m13 = 0, m22 = 0, m23 = 0, m33 = 0;
     float best = 0.f;
     int bestk = 27;
 #pragma unroll
     for (int k = 0; k < 27; ++k) {
         const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-        const int node = support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
+        const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
+                                  : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
         const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
         const float rx = M.ox + dx, ry = M.oy + dy, rz = M.oz + dz;
         const float w = mls_weight(fluid, rx, ry, rz);
@@ -328,14 +248,17 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
                  a33 = m33;
     const double d0 = a00;
     const double s0 = d0 > 0.0 ? d0 : 1.0;
-    const double L10 = a10 / s0, L20 = a20 / s0, L30 = a30 / s0;
+    const double r0 = rcp64(s0);
+    const double L10 = a10 * r0, L20 = a20 * r0, L30 = a30 * r0;
     const double d1 = a11 - L10 * L10 * d0;
-    const double s1 = d1 != 0.0 ? d1 : 1.0;
-    const double L21 = (a21 - L20 * L10 * d0) / s1;
-    const double L31 = (a31 - L30 * L10 * d0) / s1;
+    const double s1 = d1 > 0.0 ? d1 : 1.0;
+    const double r1 = rcp64(s1);
+    const double L21 = (a21 - L20 * L10 * d0) * r1;
+    const double L31 = (a31 - L30 * L10 * d0) * r1;
     const double d2 = a22 - L20 * L20 * d0 - L21 * L21 * d1;
-    const double s2 = d2 != 0.0 ? d2 : 1.0;
-    const double L32 = (a32 - L30 * L20 * d0 - L31 * L21 * d1) / s2;
+    const double s2 = d2 > 0.0 ? d2 : 1.0;
+    const double r2 = rcp64(s2);
+    const double L32 = (a32 - L30 * L20 * d0 - L31 * L21 * d1) * r2;
     const double d3 = a33 - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
     const double tol = PIVOT_TOL * s0;
     const bool good = d0 > 0.0 && d1 > tol && d2 > tol && d3 > tol;
@@ -344,7 +267,7 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
         return;
     }
     M.fallback = -1;
-    const double r0 = 1.0 / d0, r1 = 1.0 / d1, r2 = 1.0 / d2, r3 = 1.0 / d3;
+    const double r3 = rcp64(d3);
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
         const double y0 = j == 0 ? 1.0 : 0.0;
@@ -365,7 +288,8 @@ __device__ __forceinline__ float mls_row(const Mls& M, int j, int k) {
 }
 
 __device__ __forceinline__ int mls_node(const MemberDev& d, const Mls& M, int k) {
-    return support_index(d, M.bx + (k % 3 - 1), M.by + ((k / 3) % 3 - 1), M.bz + (k / 9 - 1));
+    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    return M.base >= 0 ? M.base + dx + d.NX * (dy + d.NY * dz) : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
 }
 
 // ---------------------------------------------------------------------------
@@ -374,8 +298,8 @@ __device__ __forceinline__ int mls_node(const MemberDev& d, const Mls& M, int k)
 //  s = 0: Eq. uLag on u*, F_l = (U_b - U_l)/dt, Eq. bodyforce spreading with
 //         c_l = A_l into the dense f_ib field (float atomics) and the node's IB
 //         flag; u_v,0 = U_l (the tentative velocity of Eq. verletPos); the
-//         force accumulator starts at the volume penalty k_v (1 - V/V0) n A
-//         (Eq. volFor, restoring sign) of soft capsules (0 for rigid ones);
+//         volume penalty k_v (1 - V/V0) A (Eq. volFor, restoring sign) of soft
+//         capsules (0 for rigid ones);
 //  s = 1, 2: the probe at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u +
 //         grad u^T) from the MLS fit (Eqs. hydroForP, hydroForNu), stored for
 //         the update kernels, which add F_p + F_tau.
@@ -408,7 +332,7 @@ __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, u
     if (s == 0) {
         mls_build<1>(d, tag, X, Y, Z, M);
         float Ux = 0.f, Uy = 0.f, Uz = 0.f;
-#pragma unroll 1
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             float p[9];
             float4 q[9];
@@ -425,7 +349,7 @@ __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, u
         }
         const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
         const float A = area[l];
-#pragma unroll 1
+#pragma unroll
         for (int k = 0; k < 27; ++k) {
             const float p = M.fallback < 0 ? mls_row(M, 0, k) : (M.fallback == k ? 1.f : 0.f);
             if (p != 0.f) {
@@ -439,14 +363,16 @@ __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, u
             }
         }
         uv0[3 * l] = Ux; uv0[3 * l + 1] = Uy; uv0[3 * l + 2] = Uz;
+        // volume penalty magnitude k_v (1 - V/V0) A, kept in the spare slot of
+        // the + probe record; the update adds it along n
         float kvol = 0.f;
-        if (!C.rigid) kvol = (float)(C.kv * (1.0 - sums[cap].V / C.V0)) * A;
-        force[3 * l] = kvol * nx; force[3 * l + 1] = kvol * ny; force[3 * l + 2] = kvol * nz;
+        if (!C.rigid) kvol = (float)(C.kv * (1.0 - sums[cap].V * C.inv_V0)) * A;
+        probe[(size_t)2 * l * PROBE_STRIDE + 7] = kvol;
     } else {
         const double sg = s == 1 ? 1.2 : -1.2;
         mls_build<4>(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, M);
         float rP = 0.f, G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll 1
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             float4 q[9];
 #pragma unroll
@@ -482,7 +408,8 @@ __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, u
 }
 
 // F_p + F_tau of vertex v from its two probe records (Eqs. hydroForP,
-// hydroForNu): -(p+ - p-) n A + (tau+ - tau-) . n A.
+// hydroForNu): -(p+ - p-) n A + (tau+ - tau-) . n A, plus the volume penalty
+// (Eq. volFor) stored with them.
 __device__ __forceinline__ void hydro_force(const float* __restrict__ probe, const float* __restrict__ nrm,
                                             const float* __restrict__ area, int v, float& Hx, float& Hy,
                                             float& Hz) {
@@ -492,9 +419,10 @@ __device__ __forceinline__ void hydro_force(const float* __restrict__ probe, con
     const float dp = a[0] - b[0];
     const float t0 = a[1] - b[1], t1 = a[2] - b[2], t2 = a[3] - b[3], t3 = a[4] - b[4], t4 = a[5] - b[5],
                 t5 = a[6] - b[6];
-    Hx = (-dp * nx + t0 * nx + t3 * ny + t4 * nz) * A;
-    Hy = (-dp * ny + t3 * nx + t1 * ny + t5 * nz) * A;
-    Hz = (-dp * nz + t4 * nx + t5 * ny + t2 * nz) * A;
+    const float kv = a[7];   // volume penalty k_v (1 - V/V0) A of soft capsules
+    Hx = (-dp * nx + t0 * nx + t3 * ny + t4 * nz) * A + kv * nx;
+    Hy = (-dp * ny + t3 * nx + t1 * ny + t5 * nz) * A + kv * ny;
+    Hz = (-dp * nz + t4 * nx + t5 * ny + t2 * nz) * A + kv * nz;
 }
 
 // ---------------------------------------------------------------------------
@@ -636,7 +564,7 @@ __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __rest
 __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ caps, const int* __restrict__ v_cap,
                                                 const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
                                                 double* __restrict__ x, double* __restrict__ x_prev,
-                                                double* __restrict__ vel, const float* __restrict__ force,
+                                                double* __restrict__ vel, float* __restrict__ force,
                                                 const float* __restrict__ uv0, const float* __restrict__ probe,
                                                 const float* __restrict__ nrm, const float* __restrict__ area,
                                                 int n_verts) {
@@ -651,6 +579,7 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double acc = ((double)force[3 * v + a] + (double)H[a]) * half_inv_m;
+        force[3 * v + a] = 0.f;
         const double xt = x[3 * v + a];
         const double xp = xt + (double)uv0[3 * v + a] + acc;
         const double un = 1.5 * xp - 2.0 * xt + 0.5 * x_prev[3 * v + a];
@@ -666,7 +595,7 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
 __global__ void __launch_bounds__(256) k_rigid(CapsuleDev* __restrict__ caps, const uint32_t* __restrict__ status,
                                                uint32_t* __restrict__ status_new, double* __restrict__ x,
                                                double* __restrict__ x_prev, double* __restrict__ vel,
-                                               const float* __restrict__ force, const float* __restrict__ probe,
+                                               float* __restrict__ force, const float* __restrict__ probe,
                                                const float* __restrict__ nrm, const float* __restrict__ area) {
     __shared__ double red[32];
     __shared__ double sh_rig[16];
@@ -680,6 +609,7 @@ __global__ void __launch_bounds__(256) k_rigid(CapsuleDev* __restrict__ caps, co
         hydro_force(probe, nrm, area, v, H[0], H[1], H[2]);
         const double fx = (double)force[3 * v] + H[0], fy = (double)force[3 * v + 1] + H[1],
                      fz = (double)force[3 * v + 2] + H[2];
+        force[3 * v] = 0.f; force[3 * v + 1] = 0.f; force[3 * v + 2] = 0.f;
         const double rx = x[3 * v] - xc0, ry = x[3 * v + 1] - xc1, rz = x[3 * v + 2] - xc2;
         s[0] += fx; s[1] += fy; s[2] += fz;
         s[3] += ry * fz - rz * fy; s[4] += rz * fx - rx * fz; s[5] += rx * fy - ry * fx;

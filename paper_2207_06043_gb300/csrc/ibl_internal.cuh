@@ -72,7 +72,7 @@ struct CapsuleDev {
     int v_begin, v_count;
     int t_begin, t_count;
     int e_begin, e_count;
-    double kv, V0, S0, mass, mv, inertia;
+    double kv, V0, inv_V0, S0, mass, mv, inertia;
     double xc[3], u1[3], u2[3], w1[3], w2[3];
 };
 
@@ -137,7 +137,7 @@ struct DevState {
     double* x = nullptr;             // 3 per vertex
     double* x_prev = nullptr;
     double* vel = nullptr;
-    float* force = nullptr;          // 3 per vertex
+    float* force = nullptr;          // 3 per vertex: hinge + repulsion forces, cleared by the update
     float* uv0 = nullptr;            // 3 per vertex
     float* nrm = nullptr;            // 3 per vertex
     float* area = nullptr;           // per vertex
