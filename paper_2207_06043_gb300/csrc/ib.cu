@@ -205,11 +205,12 @@ struct Mls {
 
 // 1/d in FP64 by Newton's iteration r <- r (2 - d r) from the FP32
 // reciprocal (each step doubles the correct bits: 24 -> 48 -> full)
-__device__ __forceinline__ double rcp64(double d) {
+__device__ __forceinline__ double rcp_r(double d) {
     double r = (double)__frcp_rn((float)d);
     r = r * (2.0 - d * r);
     return r * (2.0 - d * r);
 }
+__device__ __forceinline__ float rcp_r(float d) { return __frcp_rn(d); }
 
 __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy, int cz) {
     if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx; else if (cx < 0 || cx >= d.nx) return -1;
@@ -218,7 +219,53 @@ __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy,
     return (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
 }
 
-template <int ROWS>
+// L D L^T of the symmetric moment matrix m (m00 m01 m02 m03 m11 m12 m13 m22 m23
+// m33) in precision R, then the first ROWS rows of its inverse.  Returns the
+// pivots relative to the first one in `rel` (min of d1, d2, d3 over d0) and
+// false when the matrix fails the singularity test.
+template <int ROWS, typename R>
+__device__ __forceinline__ bool ldlt_solve(const float (&m)[10], float (&inv)[4][4], R& rel) {
+    const R a00 = m[0], a10 = m[1], a20 = m[2], a30 = m[3], a11 = m[4], a21 = m[5], a31 = m[6], a22 = m[7],
+            a32 = m[8], a33 = m[9];
+    const R d0 = a00;
+    const R s0 = d0 > R(0) ? d0 : R(1);
+    const R r0 = rcp_r(s0);
+    const R L10 = a10 * r0, L20 = a20 * r0, L30 = a30 * r0;
+    const R d1 = a11 - L10 * L10 * d0;
+    const R s1 = d1 > R(0) ? d1 : R(1);
+    const R r1 = rcp_r(s1);
+    const R L21 = (a21 - L20 * L10 * d0) * r1;
+    const R L31 = (a31 - L30 * L10 * d0) * r1;
+    const R d2 = a22 - L20 * L20 * d0 - L21 * L21 * d1;
+    const R s2 = d2 > R(0) ? d2 : R(1);
+    const R r2 = rcp_r(s2);
+    const R L32 = (a32 - L30 * L20 * d0 - L31 * L21 * d1) * r2;
+    const R d3 = a33 - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
+    const R tol = R(PIVOT_TOL) * s0;
+    rel = fmin(fmin(d1, d2), d3) * r0;
+    if (!(d0 > R(0) && d1 > tol && d2 > tol && d3 > tol)) return false;
+    const R r3 = rcp_r(d3);
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        const R y0 = j == 0 ? R(1) : R(0);
+        const R y1 = (j == 1 ? R(1) : R(0)) - L10 * y0;
+        const R y2 = (j == 2 ? R(1) : R(0)) - L20 * y0 - L21 * y1;
+        const R y3 = (j == 3 ? R(1) : R(0)) - L30 * y0 - L31 * y1 - L32 * y2;
+        const R c3 = y3 * r3;
+        const R c2 = y2 * r2 - L32 * c3;
+        const R c1 = y1 * r1 - L21 * c2 - L31 * c3;
+        const R c0 = y0 * r0 - L10 * c1 - L20 * c2 - L30 * c3;
+        inv[j][0] = (float)c0; inv[j][1] = (float)c1; inv[j][2] = (float)c2; inv[j][3] = (float)c3;
+    }
+    return true;
+}
+
+// Pivots this far above the singularity threshold (relative to d0) keep the
+// FP32 solve's error below ~1e-4 of the inverse; closer ones are redone in
+// FP64, which then takes the singularity decision exactly as an FP64 solve.
+constexpr float FP32_PIVOT_FLOOR = 1e-3f;
+
+template <int ROWS, bool FAST32>
 __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __restrict__ tag, double X, double Y,
                                           double Z, Mls& M) {
     M.bx = (int)floor(X + 0.5); M.by = (int)floor(Y + 0.5); M.bz = (int)floor(Z + 0.5);
@@ -226,7 +273,7 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
     const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
                           M.bz <= d.nz - 2;
     M.base = interior ? (M.bx + d.px) + d.NX * ((M.by + d.py) + d.NY * (M.bz + d.pz)) : -1;
-    float m0 = 0, m1 = 0, m2 = 0, m3 = 0, m11 = 0, m12 = 0, m13 = 0, m22 = 0, m23 = 0, m33 = 0;
+    float m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     float best = 0.f;
     int bestk = 27;
 #pragma unroll
@@ -239,47 +286,23 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
         const float w = mls_weight(fluid, rx, ry, rz);
         M.W[k] = w;
         if (w > best) { best = w; bestk = k; }
-        m0 += w; m1 += w * rx; m2 += w * ry; m3 += w * rz;
-        m11 += w * rx * rx; m12 += w * rx * ry; m13 += w * rx * rz;
-        m22 += w * ry * ry; m23 += w * ry * rz; m33 += w * rz * rz;
+        m[0] += w; m[1] += w * rx; m[2] += w * ry; m[3] += w * rz;
+        m[4] += w * rx * rx; m[5] += w * rx * ry; m[6] += w * rx * rz;
+        m[7] += w * ry * ry; m[8] += w * ry * rz; m[9] += w * rz * rz;
     }
-    // L D L^T in FP64
-    const double a00 = m0, a10 = m1, a20 = m2, a30 = m3, a11 = m11, a21 = m12, a31 = m13, a22 = m22, a32 = m23,
-                 a33 = m33;
-    const double d0 = a00;
-    const double s0 = d0 > 0.0 ? d0 : 1.0;
-    const double r0 = rcp64(s0);
-    const double L10 = a10 * r0, L20 = a20 * r0, L30 = a30 * r0;
-    const double d1 = a11 - L10 * L10 * d0;
-    const double s1 = d1 > 0.0 ? d1 : 1.0;
-    const double r1 = rcp64(s1);
-    const double L21 = (a21 - L20 * L10 * d0) * r1;
-    const double L31 = (a31 - L30 * L10 * d0) * r1;
-    const double d2 = a22 - L20 * L20 * d0 - L21 * L21 * d1;
-    const double s2 = d2 > 0.0 ? d2 : 1.0;
-    const double r2 = rcp64(s2);
-    const double L32 = (a32 - L30 * L20 * d0 - L31 * L21 * d1) * r2;
-    const double d3 = a33 - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
-    const double tol = PIVOT_TOL * s0;
-    const bool good = d0 > 0.0 && d1 > tol && d2 > tol && d3 > tol;
-    if (!good) {
-        M.fallback = best > 0.f ? bestk : 27;
-        return;
+    bool good;
+    if (FAST32) {
+        float rel;
+        good = ldlt_solve<ROWS, float>(m, M.inv, rel) && rel >= FP32_PIVOT_FLOOR;
+        if (!good) {
+            double rel64;
+            good = ldlt_solve<ROWS, double>(m, M.inv, rel64);
+        }
+    } else {
+        double rel64;
+        good = ldlt_solve<ROWS, double>(m, M.inv, rel64);
     }
-    M.fallback = -1;
-    const double r3 = rcp64(d3);
-#pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const double y0 = j == 0 ? 1.0 : 0.0;
-        const double y1 = (j == 1 ? 1.0 : 0.0) - L10 * y0;
-        const double y2 = (j == 2 ? 1.0 : 0.0) - L20 * y0 - L21 * y1;
-        const double y3 = (j == 3 ? 1.0 : 0.0) - L30 * y0 - L31 * y1 - L32 * y2;
-        const double c3 = y3 * r3;
-        const double c2 = y2 * r2 - L32 * c3;
-        const double c1 = y1 * r1 - L21 * c2 - L31 * c3;
-        const double c0 = y0 * r0 - L10 * c1 - L20 * c2 - L30 * c3;
-        M.inv[j][0] = (float)c0; M.inv[j][1] = (float)c1; M.inv[j][2] = (float)c2; M.inv[j][3] = (float)c3;
-    }
+    M.fallback = good ? -1 : (best > 0.f ? bestk : 27);
 }
 
 __device__ __forceinline__ float mls_row(const Mls& M, int j, int k) {
@@ -307,6 +330,11 @@ __device__ __forceinline__ int mls_node(const MemberDev& d, const Mls& M, int k)
 // ---------------------------------------------------------------------------
 constexpr int PROBE_STRIDE = 8;   // floats per probe record: p, tau xx yy zz xy xz yz, pad
 
+// The probe stencils (stress only) solve their 4x4 system in FP32 unless a
+// pivot is small; the marker stencil, which interpolates and spreads, always
+// solves in FP64.  GB300's FP64 pipe is narrow and this kernel's busiest unit.
+constexpr bool PROBE_FAST32 = true;
+
 __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag,
                                             float* __restrict__ fib, const uint32_t* __restrict__ status,
                                             const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
@@ -330,7 +358,7 @@ __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, u
     const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
     Mls M;
     if (s == 0) {
-        mls_build<1>(d, tag, X, Y, Z, M);
+        mls_build<1, false>(d, tag, X, Y, Z, M);
         float Ux = 0.f, Uy = 0.f, Uz = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -370,7 +398,7 @@ __global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, u
         probe[(size_t)2 * l * PROBE_STRIDE + 7] = kvol;
     } else {
         const double sg = s == 1 ? 1.2 : -1.2;
-        mls_build<4>(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, M);
+        mls_build<4, PROBE_FAST32>(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, M);
         float rP = 0.f, G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
