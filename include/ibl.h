@@ -184,6 +184,29 @@ ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 ibl_status ibl_enable_timing(ibl_ctx* ctx, int32_t on);
 ibl_status ibl_kernel_times(ibl_ctx* ctx, double* out4);
 
+/* Allocation-free read of member `member`'s macroscopic fields into HOST
+ * buffers rho[N] and u[3N] (either may be NULL, not both); same values and
+ * layout as ibl_member_read_fields with on_device = 0.  The paper has no
+ * counterpart: this is a service entry for callers that may not allocate
+ * device memory (a caching allocator owns the device, or the call runs in a
+ * memory-capped phase).  ibl_read_fields with host buffers allocates device
+ * staging buffers on every call; this one stages through a fixed static
+ * device array of 4 * IBL_NOALLOC_MAX_NODES floats (16 MiB) built into the
+ * library and calls no cudaMalloc / cudaFree.
+ *   - Lattices of more than IBL_NOALLOC_MAX_NODES nodes are rejected with
+ *     IBL_ERR_ARG (use ibl_member_read_fields).
+ *   - The context must already hold its device state (stepped, initialised or
+ *     read once): setting it up allocates, so otherwise IBL_ERR_STATE.
+ *   - The first call on a device looks up that device's copy of the static
+ *     array (cudaGetSymbolAddress, with the context's device current); make it
+ *     before any stream capture.  The call synchronises its work stream and
+ *     cannot itself be captured.
+ *   - All contexts of the process share the one array per device: calls whose
+ *     GPU work overlaps (other host threads, contexts on other streams) race
+ *     on it and may return each other's data.  Serialise them. */
+#define IBL_NOALLOC_MAX_NODES (1 << 20)
+ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, float* u);
+
 /* Message of the last failed call on ctx (or of the last failed ibl_create /
  * ibl_ensemble_create when ctx is NULL). */
 const char* ibl_last_error(const ibl_ctx* ctx);

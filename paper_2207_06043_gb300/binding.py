@@ -83,6 +83,7 @@ def lib():
         "ibl_member_read_capsule": ([vp, i32, i32, P(CapsuleStats), vp], i32),
         "ibl_member_read_populations": ([vp, i32, vp, i32], i32),
         "ibl_member_steps": ([vp, i32, P(i32)], i32),
+        "ibl_read_fields_noalloc": ([vp, i32, vp, vp], i32),
         "ibl_set_launch": ([vp, i32, i32], i32),
         "ibl_enable_timing": ([vp, i32], i32),
         "ibl_kernel_times": ([vp, vp], i32),

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -728,6 +729,43 @@ ibl_status read_capsule_member(ibl_ctx* ctx, int m, int id, ibl_capsule_stats* s
     return IBL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Static staging array of ibl_read_fields_noalloc, for callers that may not
+// allocate device memory: rho in the first IBL_NOALLOC_MAX_NODES floats, u in
+// the next 3 * IBL_NOALLOC_MAX_NODES.  Nothing in it needs to start at zero:
+// the read kernel writes every element that is then copied out (solid nodes
+// as 0).  One array per device, shared by every context of the process, so
+// overlapping calls race on it.
+// ---------------------------------------------------------------------------
+}  // namespace
+
+static __device__ __align__(256) float g_noalloc_scratch[4 * (size_t)IBL_NOALLOC_MAX_NODES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Address of the current device's copy of the static array, looked up once
+// per device (with that device current) and cached.
+ibl_status noalloc_scratch(ibl_ctx* ctx, float** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(ctx, IBL_ERR_ARG, "device ordinal beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, IBL_ERR_CUDA, std::string("cudaGetSymbolAddress of the static read array failed: ") +
+                                               cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (float*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return IBL_OK;
+}
+
 ibl_status new_ctx(void* stream, ibl_ctx** out) {
     ibl_ctx* ctx = new (std::nothrow) ibl_ctx();
     if (!ctx) return fail(nullptr, IBL_ERR_OOM, "host allocation failed");
@@ -943,6 +981,32 @@ ibl_status ibl_ensemble_create(ibl_ctx* const* members, int32_t n, void* cuda_st
         return fail(nullptr, IBL_ERR_ARG, "too many members");
     }
     *out = ctx;
+    return IBL_OK;
+}
+
+ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, float* u) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (!rho && !u) return fail(ctx, IBL_ERR_ARG, "null outputs");
+    if (member < 0 || member >= (int)ctx->members.size()) return fail(ctx, IBL_ERR_ARG, "member out of range");
+    const ibl_lattice_desc& dsc = ctx->members[member].desc;
+    const size_t Nu = (size_t)dsc.nx * dsc.ny * dsc.nz;
+    if (Nu > (size_t)IBL_NOALLOC_MAX_NODES)
+        return fail(ctx, IBL_ERR_ARG, "lattice of " + std::to_string(Nu) + " nodes exceeds the static read array (" +
+                                          std::to_string(IBL_NOALLOC_MAX_NODES) +
+                                          " nodes, IBL_NOALLOC_MAX_NODES); use ibl_member_read_fields");
+    if (!ctx->finalized)
+        return fail(ctx, IBL_ERR_STATE, "no device state yet (its set-up allocates): step, initialise or read first");
+    float* scratch = nullptr;
+    CKS(noalloc_scratch(ctx, &scratch));
+    float* dr = rho ? scratch : nullptr;
+    float* du = u ? scratch + IBL_NOALLOC_MAX_NODES : nullptr;
+    const int cnt = ctx->h_counters[member];
+    CKS(enter(ctx));
+    CK(launch_read(ctx->dev, member, cnt & 1, cnt > 0 ? 1 : 0, dr, du, nullptr, ctx->work));
+    if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(float) * Nu, cudaMemcpyDeviceToHost, ctx->work));
+    if (u) CK(cudaMemcpyAsync(u, du, sizeof(float) * 3 * Nu, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    CKS(leave(ctx));
     return IBL_OK;
 }
 
