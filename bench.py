@@ -107,16 +107,20 @@ def fluid_updates(case):
     return int(np.count_nonzero(case["geometry"].tag == 0))
 
 
-def kernels_per_step(case):
-    caps = case["capsules"]
-    n = 2
-    if caps:
-        n += 4                         # geometry, IB pre-pass, post-step markers, update
-        if any(not c["params"]["rigid"] for c in caps):
-            n += 1                     # hinges
-        if len(caps) >= 2:
-            n += 2                     # cell list fill + repulsion
-    return n
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank returns it)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(fluid_nodes_per_rank, steps, ms, world):
+    """Fluid-node updates of all ranks (weak scaling: each rank its own
+    replica of the workload) per second of the slowest rank, in millions."""
+    return world * fluid_nodes_per_rank * steps / (ms * 1e-3) / 1e6
 
 
 def cpu_sample_case(case, x1=CPU_SAMPLE_X):
@@ -176,7 +180,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="throughput", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="throughput", choices=sorted(WORKLOADS) + ["sweep"])
+    ap.add_argument("--members", type=int, default=64, help="lattices of the batched sweep workload")
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -189,6 +194,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, rank)
+        return
+    if args.workload == "sweep":
+        sweep_bench(args, rank, world, local)
         return
 
     import torch
@@ -234,12 +242,9 @@ def main():
     g1.record(stream)
     torch.cuda.synchronize()
     ms_graph = g0.elapsed_time(g1)
-    ms_best = min(ms, ms_graph)
-    if dist:
-        t = torch.tensor([ms_best], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_best = float(t.item())
-    value = world * nf * args.steps / (ms_best * 1e-3) / 1e6
+    ms_best = max_over_ranks(min(ms, ms_graph), dist, "cuda")
+    value = whole_job_mlups(nf, args.steps, ms_best, world)
+    launches = s.kernels_per_step() * args.steps
 
     bpu = BYTES_PER_UPDATE[args.storage]
     peak, peak_kind = load_peaks()
@@ -263,7 +268,7 @@ def main():
            "kernel_ms_per_step": {k: v / args.steps for k, v in kt.items()},
            "ms_per_step_timed_events": ms / args.steps, "ms_per_step_graph": ms_graph / args.steps,
            "clocks": clk.summary(),
-           "gpu_launches": kernels_per_step(case) * args.steps}
+           "gpu_launches": launches}
 
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_run(case, args)
@@ -274,6 +279,88 @@ def main():
                                "kind": "oracle",
                                "sample": f"x-slab [0,{CPU_SAMPLE_X}) of the workload ({nfs} fluid nodes, "
                                          f"{len(sample['capsules'])} capsules), {args.cpu_steps} steps"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _sweep_member(k):
+    from paper_2207_06043_gb300 import workloads as W
+    c = W.sweep_member(k)
+    c["geometry"].sdf = None          # closures do not cross process boundaries
+    return c
+
+
+def sweep_bench(args, rank, world, local):
+    """Batched sweep: the members of the sweep workload stepped together as one
+    context (one launch per kernel per step for all lattices, CUDA graphs),
+    launch shape chosen by the library's autotuner.  MLUPS counts the fluid
+    nodes of the members that are still running (a capsule that breaks stops
+    its lattice, as the damage rule says)."""
+    import multiprocessing as mp
+    # inputs are generated before CUDA starts, in spawned workers
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        members = pool.map(_sweep_member, range(args.members))
+    import torch
+    torch.cuda.set_device(local)
+    torch.zeros(1, device="cuda")
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2207_06043_gb300 import binding
+    from paper_2207_06043_gb300 import workloads as W
+    nf = [fluid_updates(c) for c in members]
+    ens = binding.ensemble([W.make_solver(c) for c in members])
+    ens.step(args.warmup, allow_damage=True)
+    thr, bps, _ = ens.autotune(4)
+    n_m = len(members)
+
+    def steps_done():
+        return [ens.member_steps(m) for m in range(n_m)]
+
+    stream = torch.cuda.current_stream()
+    # lattice-kernel time per step from a timing-mode pass
+    ens.enable_timing(True)
+    c0 = steps_done()
+    ens.step(args.steps, allow_damage=True)
+    c1 = steps_done()
+    kt = ens.kernel_times()
+    ens.enable_timing(False)
+    upd_timing = sum(nf[m] * (c1[m] - c0[m]) for m in range(n_m))
+    # timed region: graph replay
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        ens.step(args.steps, allow_damage=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    c2 = steps_done()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    upd = sum(nf[m] * (c2[m] - c1[m]) for m in range(n_m))
+    value = world * upd / (ms * 1e-3) / 1e6
+    bpu = BYTES_PER_UPDATE["f32"]
+    peak, peak_kind = load_peaks()
+    achieved = bpu * upd_timing / (kt["lattice"] * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched sweep: {n_m} bifurcations of uneven size, one capsule each",
+                      "fluid_nodes": int(sum(nf)), "box_nodes": int(sum(c["geometry"].n_nodes for c in members)),
+                      "running_members": int(sum(1 for m in range(n_m) if c2[m] - c1[m] == args.steps)),
+                      "l2": "inputs larger than L2", "launch": {"threads": thr, "blocks_per_sm": bps,
+                                                                "chosen_by": "ibl_autotune"}},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "k_lbm (all members in one launch)", "peak_source": f"{peak_kind} hbm_gbs"},
+           "kernel_ms_per_step": {k: v / args.steps for k, v in kt.items()},
+           "clocks": clk.summary(), "gpu_launches": ens.kernels_per_step() * args.steps}
+    ens.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

@@ -173,16 +173,43 @@ ibl_status ibl_member_read_capsule(ibl_ctx* ctx, int32_t member, int32_t id,
                                    ibl_capsule_stats* stats, double* verts_out);
 ibl_status ibl_member_steps(const ibl_ctx* ctx, int32_t member, int32_t* steps_done);
 
-/* Launch shape of the lattice kernel: threads per block (multiple of 32,
- * <= 1024) and blocks per SM of the persistent grid (0 = one block per tile).
- * Used by the autotuner; takes effect at the next step. */
+/* Launch shape of the lattice kernel: threads per block (a multiple of 32, at
+ * most 256, the bound the kernel is compiled for; one warp per 32-node fluid
+ * run) and blocks per SM of a persistent grid (0 = one block per group of
+ * runs).  Used by the autotuner; takes effect at the next step. */
 ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
+
+/* Autotuner of the lattice kernel's launch shape: times `steps` steps of the
+ * context for each block size (64, 128, 256 threads) and persistent-grid
+ * setting (blocks_per_sm 0, 1, 2, 4, 8, 16), restoring the state after every
+ * trial, and keeps the fastest.  The trials are timed with CUDA events around
+ * the lattice kernels; the context's state and step count are as before the
+ * call.  Allocates a device snapshot of the state for the duration of the
+ * call.  Outputs may be NULL. */
+ibl_status ibl_autotune(ibl_ctx* ctx, int32_t steps, int32_t* threads_out,
+                        int32_t* blocks_per_sm_out, double* lattice_ms_out);
 
 /* Device time of the last ibl_step's kernels by kind, in milliseconds, when
  * timing was enabled with ibl_enable_timing (0 otherwise):
  * out[0] lattice, out[1] walls, out[2] IB pre-pass, out[3] structure. */
 ibl_status ibl_enable_timing(ibl_ctx* ctx, int32_t on);
+
+/* Kernel launches of one regular time step: the kernel nodes of the step's
+ * CUDA graph (captured by this call if it does not exist yet; do not call it
+ * inside a stream capture). */
+ibl_status ibl_kernels_per_step(ibl_ctx* ctx, int32_t* n);
 ibl_status ibl_kernel_times(ibl_ctx* ctx, double* out4);
+
+/* Checkpoint / restart.  ibl_save_state copies the dynamic state of every
+ * lattice of ctx (populations, status, step counters, capsule vertices x(t),
+ * x(t - dt), velocities and rigid-body state) into the HOST buffer buf of
+ * *bytes bytes; with buf = NULL it only sets *bytes to the size needed.
+ * ibl_load_state restores such a snapshot into a context set up with the same
+ * lattices, storage and capsules (IBL_ERR_ARG otherwise); stepping then
+ * continues exactly where the saved context was.  Both synchronise the
+ * context's stream. */
+ibl_status ibl_save_state(ibl_ctx* ctx, void* buf, size_t* bytes);
+ibl_status ibl_load_state(ibl_ctx* ctx, const void* buf, size_t bytes);
 
 /* Allocation-free read of member `member`'s macroscopic fields into HOST
  * buffers rho[N] and u[3N] (either may be NULL, not both); same values and

@@ -86,6 +86,10 @@ def lib():
         "ibl_read_fields_noalloc": ([vp, i32, vp, vp], i32),
         "ibl_set_launch": ([vp, i32, i32], i32),
         "ibl_enable_timing": ([vp, i32], i32),
+        "ibl_kernels_per_step": ([vp, P(i32)], i32),
+        "ibl_save_state": ([vp, vp, P(sz)], i32),
+        "ibl_autotune": ([vp, i32, P(i32), P(i32), P(dbl)], i32),
+        "ibl_load_state": ([vp, vp, sz], i32),
         "ibl_kernel_times": ([vp, vp], i32),
         "ibl_last_error": ([vp], C.c_char_p),
         "ibl_destroy": ([vp], None),
@@ -237,6 +241,32 @@ class Solver:
 
     def enable_timing(self, on=True):
         self._check(self._L.ibl_enable_timing(self._h, 1 if on else 0))
+
+    def autotune(self, steps=4):
+        """Pick the fastest lattice launch shape by timing trial steps (the
+        state is restored).  Returns (threads, blocks_per_sm, lattice ms)."""
+        t, b, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+        self._check(self._L.ibl_autotune(self._h, int(steps), C.byref(t), C.byref(b), C.byref(ms)))
+        return int(t.value), int(b.value), float(ms.value)
+
+    def save_state(self):
+        """Snapshot of the dynamic state (bytes)."""
+        n = C.c_size_t(0)
+        self._check(self._L.ibl_save_state(self._h, None, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._check(self._L.ibl_save_state(self._h, _ptr(buf), C.byref(n)))
+        return buf.tobytes()
+
+    def load_state(self, blob):
+        """Restore a snapshot taken by save_state on an identical set-up."""
+        buf = np.frombuffer(blob, dtype=np.uint8).copy()
+        self._check(self._L.ibl_load_state(self._h, _ptr(buf), buf.size))
+
+    def kernels_per_step(self):
+        """Kernel launches of one regular time step (nodes of its CUDA graph)."""
+        n = C.c_int32(0)
+        self._check(self._L.ibl_kernels_per_step(self._h, C.byref(n)))
+        return int(n.value)
 
     def kernel_times(self):
         out = np.zeros(4, dtype=np.float64)

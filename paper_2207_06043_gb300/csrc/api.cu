@@ -65,6 +65,7 @@ struct ibl_ctx {
     std::vector<std::vector<int>> member_caps;   // global capsule ids per member
     std::vector<void*> allocs;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_kernels[2] = {0, 0};   // kernel nodes of each parity's step graph
     bool use_graphs = true;
     int threads = 256;
     int blocks_per_sm = 0;
@@ -247,16 +248,15 @@ ibl_status leave(ibl_ctx* ctx) {
     return IBL_OK;
 }
 
+// Lattice-kernel blocks for the current block size: one warp per fluid segment.
 void layout_tiles(ibl_ctx* ctx) {
-    int tiles = 0;
-    for (auto& m : ctx->hmem) {
-        m.tile_begin = tiles;
-        m.tile_count = (m.N + ctx->threads - 1) / ctx->threads;
-        tiles += m.tile_count;
-    }
+    const int per_block = ctx->threads / 32;
+    const int blocks = (ctx->dev.n_segs + per_block - 1) / per_block;
     ctx->dev.threads = ctx->threads;
-    ctx->dev.total_tiles = tiles;
-    ctx->dev.grid_lbm = ctx->blocks_per_sm > 0 ? std::min(tiles, ctx->blocks_per_sm * ctx->n_sm) : 0;
+    ctx->dev.lbm_blocks = blocks;
+    ctx->dev.lbm_bblocks = (ctx->dev.n_bsegs + per_block - 1) / per_block;
+    ctx->dev.grid_lbm = ctx->blocks_per_sm > 0 ? std::min(blocks, ctx->blocks_per_sm * ctx->n_sm) : 0;
+    ctx->dev.n_sm = ctx->n_sm;
 }
 
 void drop_graphs(ibl_ctx* ctx) {
@@ -483,9 +483,60 @@ ibl_status finalize(ibl_ctx* ctx) {
     }
     if (max_nv > 12000) return fail(ctx, IBL_ERR_ARG, "a capsule has more than 12000 vertices");
 
+    // fluid-segment work lists of the lattice kernel: aligned 32-node runs of
+    // the padded layout holding at least one fluid node, split into border
+    // runs (a fluid node on the wrap plane of a periodic axis: coordinates
+    // needed) and interior runs; and the list of fluid nodes on Zou-He faces
+    std::vector<uint32_t> segs, bsegs, fc_node, fc_meta;
+    {
+        size_t base = 0;
+        for (int m = 0; m < nm; ++m) {
+            MemberDev& md = ctx->hmem[m];
+            md.seg_begin = (int)segs.size();
+            md.bseg_begin = (int)bsegs.size();
+            const int ns = (md.N + 31) / 32;
+            const bool per[3] = {(md.per & 1) != 0, (md.per & 2) != 0, (md.per & 4) != 0};
+            const int dimP[3] = {md.NX, md.NY, md.NZ};
+            for (int j = 0; j < ns; ++j) {
+                bool any = false, border = false;
+                for (int t = 0; t < 32; ++t) {
+                    const long long n = 32LL * j + t;
+                    if (n >= md.N || (tag_all[base + n] & TAG_SOLID)) continue;
+                    any = true;
+                    const int c[3] = {(int)(n % md.NX), (int)((n / md.NX) % md.NY), (int)(n / ((long long)md.NX * md.NY))};
+                    int face = -1;
+                    for (int a = 0; a < 3; ++a) {
+                        if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) border = true;          // wrap plane
+                        if (!per[a] && face < 0 && c[a] == 1) face = 2 * a;                        // box faces
+                        if (!per[a] && face < 0 && c[a] == dimP[a] - 2) face = 2 * a + 1;
+                    }
+                    if (face >= 0 && md.face_kind[face] != FACE_NONE) {
+                        fc_node.push_back((uint32_t)n);
+                        fc_meta.push_back((uint32_t)face | ((uint32_t)m << 8));
+                    }
+                }
+                if (any) (border ? bsegs : segs).push_back((uint32_t)j);
+            }
+            md.seg_count = (int)segs.size() - md.seg_begin;
+            md.bseg_count = (int)bsegs.size() - md.bseg_begin;
+            base += round_up((size_t)md.N, 256);
+        }
+        D.n_segs = (int)segs.size();
+        D.n_bsegs = (int)bsegs.size();
+        D.n_face_nodes = (int)fc_node.size();
+    }
     layout_tiles(ctx);
     // device buffers
-    CKS(dev_alloc(ctx, (uint8_t*&)D.f, (size_t)f_off * esize));
+    CKS(dev_alloc(ctx, D.segs, std::max<size_t>(segs.size(), 1)));
+    CKS(dev_alloc(ctx, D.bsegs, std::max<size_t>(bsegs.size(), 1)));
+    CKS(upload(ctx, D.segs, segs));
+    CKS(upload(ctx, D.bsegs, bsegs));
+    CKS(dev_alloc(ctx, D.fc_node, std::max<size_t>(fc_node.size(), 1)));
+    CKS(dev_alloc(ctx, D.fc_meta, std::max<size_t>(fc_meta.size(), 1)));
+    CKS(upload(ctx, D.fc_node, fc_node));
+    CKS(upload(ctx, D.fc_meta, fc_meta));
+    D.f_bytes = (size_t)f_off * esize;
+    CKS(dev_alloc(ctx, (uint8_t*&)D.f, D.f_bytes));
     CKS(dev_alloc(ctx, D.tag, tag_all.size()));
     CKS(dev_alloc(ctx, D.face_vel, std::max<size_t>(face_all.size(), 3)));
     CKS(dev_alloc(ctx, D.status, nm));
@@ -587,7 +638,7 @@ struct Mark {
 // geometry, repulsion and hinge forces (concurrent with the IB pass); after
 // the IB pass, the structure update (concurrent with the lattice step).  The
 // update touches no lattice data and the lattice step no structure data.
-ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<Mark>* marks) {
+ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks) {
     DevState& D = ctx->dev;
     cudaStream_t s = ctx->work, s2 = ctx->work2;
     cudaEvent_t e0 = nullptr;
@@ -611,7 +662,7 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<Mark>* 
         CKS(begin(s));
         CK(launch_geometry(D, 0, s));
         CK(cudaEventRecord(ctx->ev_fork, s));
-        CK(launch_ib(D, parity, zh_on, s));
+        CK(launch_ib(D, parity, s));
         CKS(end(TK_IB, s));
         CK(cudaEventRecord(ctx->ev_ib, s));
         CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
@@ -623,10 +674,11 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, int zh_on, std::vector<Mark>* 
         CKS(end(TK_STRUCT, s2));
     }
     CKS(begin(s));
-    CK(launch_lbm(D, parity, zh_on, s));
+    CK(launch_lbm(D, parity, s));
     CKS(end(TK_LBM, s));
     CKS(begin(s));
     CK(launch_bfl(D, parity, s));
+    CK(launch_faces(D, parity, s));
     CKS(end(TK_BFL, s));
     if (caps) {
         CK(cudaEventRecord(ctx->ev_join, s2));
@@ -639,10 +691,22 @@ ibl_status capture_graph(ibl_ctx* ctx, int parity) {
     if (ctx->graph[parity]) return IBL_OK;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->work, cudaStreamCaptureModeThreadLocal));
-    ibl_status st = enqueue_step(ctx, parity, 1, nullptr);
+    ibl_status st = enqueue_step(ctx, parity, nullptr);
     cudaError_t e = cudaStreamEndCapture(ctx->work, &g);
     if (st != IBL_OK) { if (g) cudaGraphDestroy(g); return st; }
     CK(e);
+    // kernel launches per step = kernel nodes of the captured step
+    size_t n_nodes = 0;
+    int n_kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if (cudaGraphGetNodes(g, nodes.data(), &n_nodes) == cudaSuccess)
+            for (size_t i = 0; i < n_nodes; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++n_kernels;
+            }
+    }
+    ctx->graph_kernels[parity] = n_kernels;
     e = cudaGraphInstantiate(&ctx->graph[parity], g, 0);
     cudaGraphDestroy(g);
     CK(e);
@@ -669,15 +733,15 @@ ibl_status read_fields_member(ibl_ctx* ctx, int m, float* rho, float* u, float* 
     const MemberDev& md = ctx->hmem[m];
     const size_t Nu = (size_t)md.nx * md.ny * md.nz;
     const int cnt = ctx->h_counters[m];
-    const int parity = cnt & 1, zh_on = cnt > 0 ? 1 : 0;
+    const int parity = cnt & 1;
     if (on_device) {
-        CK(launch_read(ctx->dev, m, parity, zh_on, rho, u, g, ctx->work));
+        CK(launch_read(ctx->dev, m, parity, rho, u, g, ctx->work));
     } else {
         float *dr = nullptr, *du = nullptr, *dg = nullptr;
         if (rho) CK(cudaMalloc((void**)&dr, sizeof(float) * Nu));
         if (u) CK(cudaMalloc((void**)&du, sizeof(float) * 3 * Nu));
         if (g) CK(cudaMalloc((void**)&dg, sizeof(float) * 19 * Nu));
-        CK(launch_read(ctx->dev, m, parity, zh_on, dr, du, dg, ctx->work));
+        CK(launch_read(ctx->dev, m, parity, dr, du, dg, ctx->work));
         if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(float) * Nu, cudaMemcpyDeviceToHost, ctx->work));
         if (u) CK(cudaMemcpyAsync(u, du, sizeof(float) * 3 * Nu, cudaMemcpyDeviceToHost, ctx->work));
         if (g) CK(cudaMemcpyAsync(g, dg, sizeof(float) * 19 * Nu, cudaMemcpyDeviceToHost, ctx->work));
@@ -764,6 +828,59 @@ ibl_status noalloc_scratch(ibl_ctx* ctx, float** out) {
     }
     *out = g_noalloc_ptr[dev];
     return IBL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// State snapshot: everything a later step reads that the steps themselves
+// change.  Between steps f_ib, the IB tag bits, the force and normal/area
+// accumulators are zero or recomputed, so they are not part of it.
+// ---------------------------------------------------------------------------
+struct StateHeader {
+    char magic[8];
+    uint32_t version, storage;
+    uint64_t f_bytes;
+    int32_t n_members, n_caps, n_verts, reserved;
+    int64_t t;
+};
+
+struct StateSection {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<StateSection> state_sections(ibl_ctx* ctx) {
+    const DevState& D = ctx->dev;
+    const size_t nm = (size_t)D.n_members, nv3 = 3 * (size_t)D.n_verts;
+    std::vector<StateSection> s = {{D.f, D.f_bytes},
+                                   {D.status, sizeof(uint32_t) * nm},
+                                   {D.status_new, sizeof(uint32_t) * nm},
+                                   {D.counters, sizeof(int) * nm}};
+    if (D.n_caps > 0) {
+        s.push_back({D.caps, sizeof(CapsuleDev) * (size_t)D.n_caps});
+        s.push_back({D.x, sizeof(double) * nv3});
+        s.push_back({D.x_prev, sizeof(double) * nv3});
+        s.push_back({D.vel, sizeof(double) * nv3});
+    }
+    return s;
+}
+
+StateHeader state_header(ibl_ctx* ctx) {
+    StateHeader h{};
+    std::memcpy(h.magic, "IBLSTAT", 8);
+    h.version = 1;
+    h.storage = (uint32_t)ctx->storage;
+    h.f_bytes = ctx->dev.f_bytes;
+    h.n_members = ctx->dev.n_members;
+    h.n_caps = ctx->dev.n_caps;
+    h.n_verts = ctx->dev.n_verts;
+    h.t = ctx->t;
+    return h;
+}
+
+size_t state_bytes(ibl_ctx* ctx) {
+    size_t n = sizeof(StateHeader);
+    for (const StateSection& s : state_sections(ctx)) n += s.bytes;
+    return n;
 }
 
 ibl_status new_ctx(void* stream, ibl_ctx** out) {
@@ -894,14 +1011,13 @@ ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done) {
     std::vector<Mark> marks;
     for (int s = 0; s < n_steps; ++s) {
         const int parity = (int)(ctx->t & 1);
-        const int zh_on = ctx->t > 0 ? 1 : 0;
         if (ctx->timing) {
-            CKS(enqueue_step(ctx, parity, zh_on, &marks));
-        } else if (zh_on && ctx->use_graphs) {
+            CKS(enqueue_step(ctx, parity, &marks));
+        } else if (ctx->use_graphs) {
             CKS(capture_graph(ctx, parity));
             CK(cudaGraphLaunch(ctx->graph[parity], ctx->work));
         } else {
-            CKS(enqueue_step(ctx, parity, zh_on, nullptr));
+            CKS(enqueue_step(ctx, parity, nullptr));
         }
         ctx->t += 1;
     }
@@ -984,6 +1100,54 @@ ibl_status ibl_ensemble_create(ibl_ctx* const* members, int32_t n, void* cuda_st
     return IBL_OK;
 }
 
+ibl_status ibl_save_state(ibl_ctx* ctx, void* buf, size_t* bytes) {
+    if (!ctx || !bytes) return fail(ctx, IBL_ERR_ARG, "null argument");
+    CKS(finalize(ctx));
+    const size_t need = state_bytes(ctx);
+    if (!buf) {
+        *bytes = need;
+        return IBL_OK;
+    }
+    if (*bytes < need) return fail(ctx, IBL_ERR_ARG, "state buffer too small: " + std::to_string(need) + " bytes needed");
+    CKS(enter(ctx));
+    const StateHeader h = state_header(ctx);
+    std::memcpy(buf, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (const StateSection& s : state_sections(ctx)) {
+        if (s.bytes) CK(cudaMemcpyAsync((char*)buf + off, s.dev, s.bytes, cudaMemcpyDeviceToHost, ctx->work));
+        off += s.bytes;
+    }
+    CK(cudaStreamSynchronize(ctx->work));
+    CKS(leave(ctx));
+    *bytes = need;
+    return IBL_OK;
+}
+
+ibl_status ibl_load_state(ibl_ctx* ctx, const void* buf, size_t bytes) {
+    if (!ctx || !buf) return fail(ctx, IBL_ERR_ARG, "null argument");
+    CKS(finalize(ctx));
+    const size_t need = state_bytes(ctx);
+    StateHeader h{};
+    if (bytes < sizeof(h)) return fail(ctx, IBL_ERR_ARG, "state buffer too small");
+    std::memcpy(&h, buf, sizeof(h));
+    const StateHeader mine = state_header(ctx);
+    if (std::memcmp(h.magic, mine.magic, 8) != 0 || h.version != mine.version)
+        return fail(ctx, IBL_ERR_ARG, "not a state snapshot of this library version");
+    if (h.storage != mine.storage || h.f_bytes != mine.f_bytes || h.n_members != mine.n_members ||
+        h.n_caps != mine.n_caps || h.n_verts != mine.n_verts || bytes < need)
+        return fail(ctx, IBL_ERR_ARG, "state snapshot of a different set-up (lattices, storage or capsules)");
+    CKS(enter(ctx));
+    size_t off = sizeof(h);
+    for (const StateSection& s : state_sections(ctx)) {
+        if (s.bytes) CK(cudaMemcpyAsync(s.dev, (const char*)buf + off, s.bytes, cudaMemcpyHostToDevice, ctx->work));
+        off += s.bytes;
+    }
+    ctx->t = h.t;
+    CKS(sync_host_state(ctx));
+    CKS(leave(ctx));
+    return IBL_OK;
+}
+
 ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, float* u) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
     if (!rho && !u) return fail(ctx, IBL_ERR_ARG, "null outputs");
@@ -1002,7 +1166,7 @@ ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, flo
     float* du = u ? scratch + IBL_NOALLOC_MAX_NODES : nullptr;
     const int cnt = ctx->h_counters[member];
     CKS(enter(ctx));
-    CK(launch_read(ctx->dev, member, cnt & 1, cnt > 0 ? 1 : 0, dr, du, nullptr, ctx->work));
+    CK(launch_read(ctx->dev, member, cnt & 1, dr, du, nullptr, ctx->work));
     if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(float) * Nu, cudaMemcpyDeviceToHost, ctx->work));
     if (u) CK(cudaMemcpyAsync(u, du, sizeof(float) * 3 * Nu, cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
@@ -1038,8 +1202,9 @@ ibl_status ibl_member_steps(const ibl_ctx* ctx, int32_t member, int32_t* steps_d
 
 ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
-    if (threads < 32 || threads > 1024 || threads % 32 || blocks_per_sm < 0 || blocks_per_sm > 64)
-        return fail(ctx, IBL_ERR_ARG, "threads must be a multiple of 32 in [32, 1024], blocks_per_sm in [0, 64]");
+    if (threads < 32 || threads > lbm_max_threads() || threads % 32 || blocks_per_sm < 0 || blocks_per_sm > 64)
+        return fail(ctx, IBL_ERR_ARG, "threads must be a multiple of 32 in [32, " + std::to_string(lbm_max_threads()) +
+                                          "], blocks_per_sm in [0, 64]");
     ctx->threads = threads;
     ctx->blocks_per_sm = blocks_per_sm;
     if (ctx->finalized) {
@@ -1049,6 +1214,74 @@ ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm) 
         CK(cudaStreamSynchronize(ctx->work));
         drop_graphs(ctx);
     }
+    return IBL_OK;
+}
+
+ibl_status ibl_autotune(ibl_ctx* ctx, int32_t steps, int32_t* threads_out, int32_t* blocks_per_sm_out,
+                        double* ms_out) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (steps < 1) return fail(ctx, IBL_ERR_ARG, "steps must be >= 1");
+    CKS(finalize(ctx));
+    // device-side snapshot of the dynamic state, restored after every trial
+    const std::vector<StateSection> secs = state_sections(ctx);
+    size_t total = 0;
+    for (const StateSection& sc : secs) total += sc.bytes;
+    char* snap = nullptr;
+    CK(cudaMalloc((void**)&snap, std::max<size_t>(total, 1)));
+    auto copy_state = [&](bool save) -> ibl_status {
+        size_t off = 0;
+        for (const StateSection& sc : secs) {
+            if (sc.bytes) {
+                const cudaError_t e = save ? cudaMemcpyAsync(snap + off, sc.dev, sc.bytes, cudaMemcpyDeviceToDevice, ctx->work)
+                                           : cudaMemcpyAsync(sc.dev, snap + off, sc.bytes, cudaMemcpyDeviceToDevice, ctx->work);
+                if (e != cudaSuccess) return fail(ctx, IBL_ERR_CUDA, std::string("state copy: ") + cudaGetErrorString(e));
+            }
+            off += sc.bytes;
+        }
+        return IBL_OK;
+    };
+    const long long t0 = ctx->t;
+    const bool timing0 = ctx->timing;
+    const int thr0 = ctx->threads, bps0 = ctx->blocks_per_sm;
+    ibl_status st = enter(ctx);
+    if (st == IBL_OK) st = copy_state(true);
+    int best_t = thr0, best_b = bps0;
+    double best = 1e300;
+    const int cand_t[3] = {64, 128, 256};
+    const int cand_b[6] = {0, 1, 2, 4, 8, 16};
+    ctx->timing = true;
+    for (int it = 0; it < 3 && st == IBL_OK; ++it) {
+        if (cand_t[it] > lbm_max_threads()) continue;
+        for (int ib = 0; ib < 6 && st == IBL_OK; ++ib) {
+            if (cand_b[ib] * cand_t[it] > 2048) continue;
+            st = ibl_set_launch(ctx, cand_t[it], cand_b[ib]);
+            if (st == IBL_OK) st = ibl_step(ctx, steps, nullptr);
+            if (st == IBL_ERR_DAMAGED || st == IBL_ERR_NONFINITE) st = IBL_OK;   // the state is restored below
+            const double ms = ctx->ktime[0] / steps;
+            if (st == IBL_OK && ms < best) { best = ms; best_t = cand_t[it]; best_b = cand_b[ib]; }
+            if (st == IBL_OK) st = copy_state(false);
+            ctx->t = t0;
+            if (st == IBL_OK) st = sync_host_state(ctx);
+        }
+    }
+    ctx->timing = timing0;
+    const ibl_status st_launch = ibl_set_launch(ctx, st == IBL_OK ? best_t : thr0, st == IBL_OK ? best_b : bps0);
+    cudaStreamSynchronize(ctx->work);
+    cudaFree(snap);
+    if (st != IBL_OK) return st;
+    CKS(st_launch);
+    CKS(leave(ctx));
+    if (threads_out) *threads_out = best_t;
+    if (blocks_per_sm_out) *blocks_per_sm_out = best_b;
+    if (ms_out) *ms_out = best;
+    return IBL_OK;
+}
+
+ibl_status ibl_kernels_per_step(ibl_ctx* ctx, int32_t* n) {
+    if (!ctx || !n) return fail(ctx, IBL_ERR_ARG, "null argument");
+    CKS(finalize(ctx));
+    CKS(capture_graph(ctx, 1));
+    *n = ctx->graph_kernels[1];
     return IBL_OK;
 }
 

@@ -25,13 +25,11 @@ __device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, floa
 
 template <typename T>
 __device__ __forceinline__ void node_state(const MemberDev& d, const T* __restrict__ f,
-                                           const float* __restrict__ face_vel, int node, int parity, int zh_on,
-                                           float& rho, float& ux, float& uy, float& uz) {
+                                           int node, int parity, float& rho, float& ux, float& uy, float& uz) {
     int X, Y, Z;
     node_coords(d, node, X, Y, Z);
     float g[Q];
     load_pre<T>(d, f + d.f_off, node, X, Y, Z, parity, g);
-    if (zh_on) apply_face(d, X, Y, Z, face_vel, g);
     moments_of(g, rho, ux, uy, uz);
 }
 
@@ -149,10 +147,10 @@ constexpr int SHELL_BLOCKS = 32;   // blocks per capsule
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
-                                               const uint8_t* __restrict__ tag, const float* __restrict__ face_vel,
+                                               const uint8_t* __restrict__ tag,
                                                const uint32_t* __restrict__ status, const CapsuleDev* __restrict__ caps,
                                                const CapsuleSums* __restrict__ sums, float4* __restrict__ macro,
-                                               int parity, int zh_on) {
+                                               int parity) {
     const int c = blockIdx.x / SHELL_BLOCKS;
     const CapsuleDev& C = caps[c];
     if (status[C.member] & STOP) return;
@@ -184,7 +182,7 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
         const int node = (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
         if (tag[d.node_off + node] & TAG_SOLID) continue;
         float rho, ux, uy, uz;
-        node_state<T>(d, f, face_vel, node, parity, zh_on, rho, ux, uy, uz);
+        node_state<T>(d, f, node, parity, rho, ux, uy, uz);
         macro[d.node_off + node] = make_float4(rho, ux, uy, uz);
     }
 }
@@ -725,9 +723,9 @@ cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) {
 }
 
 template <typename T>
-static cudaError_t ib_t(const DevState& d, int parity, int zh_on, cudaStream_t s) {
-    k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.face_vel, d.status, d.caps,
-                                                       d.sums, d.macro, parity, zh_on);
+static cudaError_t ib_t(const DevState& d, int parity, cudaStream_t s) {
+    k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.status, d.caps, d.sums,
+                                                       d.macro, parity);
     const long long threads = 3LL * d.n_verts;
     k_ib<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d.mem, d.tag, d.fib, d.status, d.v_cap, d.caps, d.sums, d.x,
                                                            d.vel, d.nrm, d.area, d.force, d.uv0, d.probe, d.n_verts,
@@ -735,12 +733,12 @@ static cudaError_t ib_t(const DevState& d, int parity, int zh_on, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_ib(const DevState& d, int parity, int zh_on, cudaStream_t s) {
+cudaError_t launch_ib(const DevState& d, int parity, cudaStream_t s) {
     if (d.n_verts == 0) return cudaSuccess;
     switch (d.storage) {
-        case 1: return ib_t<__half>(d, parity, zh_on, s);
-        case 2: return ib_t<__nv_bfloat16>(d, parity, zh_on, s);
-        default: return ib_t<float>(d, parity, zh_on, s);
+        case 1: return ib_t<__half>(d, parity, s);
+        case 2: return ib_t<__nv_bfloat16>(d, parity, s);
+        default: return ib_t<float>(d, parity, s);
     }
 }
 

@@ -57,7 +57,8 @@ struct MemberDev {
     int face_kind[6];
     float face_rho[6];
     long long face_off[6];   // float3 record offset into the face velocity array
-    int tile_begin, tile_count;
+    int seg_begin, seg_count;    // range of this member in the interior-segment list
+    int bseg_begin, bseg_count;  // and in the border-segment list
     int link_begin, link_count;
     int cap_begin, cap_count;
     int vert_begin, vert_count;
@@ -112,17 +113,30 @@ struct DevState {
     int n_members = 0;
     const MemberDev* h_mem = nullptr;
     MemberDev* mem = nullptr;         // device copy of the member table (one per context)
-    int threads = 256;               // lattice tile size (threads per block)
-    int total_tiles = 0;
-    int grid_lbm = 0;                // persistent grid (0: one block per tile)
+    int threads = 256;               // lattice kernel threads per block (one warp per segment)
+    // 32-node segments holding at least one fluid node, all members, split
+    // into interior ones and border ones (a fluid node on a box face or a
+    // periodic wrap plane); entries are segment indices (padded node / 32)
+    // within their member
+    int n_segs = 0, n_bsegs = 0;
+    uint32_t* segs = nullptr;
+    uint32_t* bsegs = nullptr;
+    int lbm_blocks = 0, lbm_bblocks = 0;   // ceil(count / (threads / 32))
+    int grid_lbm = 0;                // persistent grid of the interior kernel (0: default)
+    int n_sm = 0;                    // multiprocessors of the device
 
     void* f = nullptr;               // 19 planes per member, f - w
+    size_t f_bytes = 0;
     uint8_t* tag = nullptr;          // per padded node
     float* fib = nullptr;            // 3 per padded node, zero outside the IB shell
     float* face_vel = nullptr;       // float3 per face node of velocity faces
     uint32_t* status = nullptr;      // per member, constant during a step
     uint32_t* status_new = nullptr;  // flags raised during a step, merged at the next step begin
     int* counters = nullptr;         // steps completed, per member
+
+    int n_face_nodes = 0;            // fluid nodes on a Zou-He face, all members
+    uint32_t* fc_node = nullptr;     // padded node
+    uint32_t* fc_meta = nullptr;     // face | member << 8
 
     int n_links = 0;
     uint32_t* l_node = nullptr;      // padded node of the link
@@ -158,14 +172,16 @@ struct DevState {
 constexpr int CELL_CAP = 32;
 
 
-cudaError_t launch_lbm(const DevState& d, int parity, int zh_on, cudaStream_t s);
+cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s);
+cudaError_t launch_faces(const DevState& d, int parity_done, cudaStream_t s);
+int lbm_max_threads();   // block-size bound the lattice kernel was compiled for
 cudaError_t launch_bfl(const DevState& d, int parity_done, cudaStream_t s);
 cudaError_t launch_init_member(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s);
-cudaError_t launch_read(const DevState& d, int member, int parity, int zh_on, float* rho, float* u,
+cudaError_t launch_read(const DevState& d, int member, int parity, float* rho, float* u,
                         float* g, cudaStream_t s);
 
 cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s);
-cudaError_t launch_ib(const DevState& d, int parity, int zh_on, cudaStream_t s);
+cudaError_t launch_ib(const DevState& d, int parity, cudaStream_t s);
 cudaError_t launch_step_begin(const DevState& d, cudaStream_t s);
 cudaError_t launch_edges(const DevState& d, cudaStream_t s);
 cudaError_t launch_repulsion(const DevState& d, cudaStream_t s);

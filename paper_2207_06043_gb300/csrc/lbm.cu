@@ -1,15 +1,24 @@
-// Lattice kernels: fused collide + stream (AA pattern, in place, Zou-He faces
-// fused), the sparse Bouzidi-Firdaouss-Lallemand fill pass, initialisation and
-// read-out.
+// Lattice kernels: fused collide + stream (AA pattern, in place), the sparse
+// Bouzidi-Firdaouss-Lallemand wall fill and Zou-He face passes,
+// initialisation and read-out.
+#include <algorithm>
+#include <type_traits>
+
 #include "lbm_device.cuh"
 
-// launch bounds of the lattice kernel (threads per block, minimum resident
-// blocks per SM); the register budget is 64K / (threads * blocks)
+// launch bounds of the register-gather lattice kernel (threads per block,
+// minimum resident blocks per SM); the register budget is 64K / (threads *
+// blocks)
 #ifndef LBM_THREADS
 #define LBM_THREADS 256
 #endif
 #ifndef LBM_MIN_BLOCKS
-#define LBM_MIN_BLOCKS 8
+#define LBM_MIN_BLOCKS 6
+#endif
+// resident blocks per SM of the FP32 lattice kernel that stages its gathers
+// through shared memory with cp.async
+#ifndef LBMA_MIN_BLOCKS
+#define LBMA_MIN_BLOCKS 4
 #endif
 
 namespace ibl {
@@ -40,49 +49,46 @@ cudaError_t launch_step_begin(const DevState& d, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Zou-He face rule, out of line: only face nodes take this call, so its
-// registers stay out of the bulk path of the lattice kernel.
-struct G19 {
-    float v[Q];
-};
-
-__device__ __noinline__ G19 face_rule(const MemberDev* __restrict__ dp, int X, int Y, int Z,
-                                      const float* __restrict__ face_vel, G19 h) {
-    apply_face(*dp, X, Y, Z, face_vel, h.v);
-    return h;
-}
-
 // One time step of every fluid node of every member (Eq. evoleq): gather the
-// pre-collision populations (AA parity), apply the Zou-He face rule, add the
-// body force and the spread IB force (which is then cleared), collide, store.
+// pre-collision populations (AA parity; the face and wall rules of the
+// previous step already sit in the gathered slots), add the body force and
+// the spread IB force (which is then cleared), collide, store.
+// Work list: the 32-node segments (aligned, padded-node order) that hold at
+// least one fluid node, one warp per segment, so all-solid stretches of the
+// box cost no thread.  Interior segments (BORDER false) address every
+// neighbour by a constant offset and need no coordinates (the ghost layer of
+// non-periodic axes absorbs the steps off the box); border segments, which
+// hold a node on the wrap plane of a periodic axis, take the coordinate-based
+// path in a launch of their own.  Each population slot is read and written
+// by one node per step (AA pattern), so the two launches are independent.
 // SINGLE: the context holds one lattice, whose descriptor arrives by value in
-// the kernel's parameter bank (its fields are then constant operands).
-template <typename T, bool SINGLE>
-__global__ void __launch_bounds__(LBM_THREADS, LBM_MIN_BLOCKS)
+// the kernel's parameter bank.
+template <typename T, bool SINGLE, bool BORDER>
+__global__ void __launch_bounds__(LBM_THREADS, BORDER ? 4 : LBM_MIN_BLOCKS)
 k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T* __restrict__ f,
       uint8_t* __restrict__ tag, float* __restrict__ fib, const float* __restrict__ face_vel,
-      const uint32_t* __restrict__ status, int n_mem, int total_tiles, int parity, int zh_on) {
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-        const int m = SINGLE ? 0 : find_member_by_tile(mem, n_mem, tile);
+      const uint32_t* __restrict__ status, const uint32_t* __restrict__ segs, int n_mem, int n_segs, int n_blocks,
+      int parity) {
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+        const int si = b * warps + (threadIdx.x >> 5);
+        if (si >= n_segs) continue;
+        const int m = SINGLE ? 0 : find_member_by_seg<BORDER>(mem, n_mem, si);
         const MemberDev& d = SINGLE ? d0 : mem[m];
         if (status[m] & (ST_DAMAGED | ST_NONFINITE)) continue;
-        const int n = (tile - d.tile_begin) * blockDim.x + threadIdx.x;
+        const int n = (int)(segs[si] << 5) + lane;
         if (n >= d.N) continue;
         const long long gn = d.node_off + n;
         const uint8_t tg = tag[gn];
         if (tg & TAG_SOLID) continue;
-        int X, Y, Z;
-        node_coords(d, n, X, Y, Z);
         T* fm = f + d.f_off;
         float g[Q];
-        load_pre<T>(d, fm, n, X, Y, Z, parity, g);
-        if (zh_on && face_of(d, X, Y, Z) >= 0) {
-            G19 h;
-#pragma unroll
-            for (int k = 0; k < Q; ++k) h.v[k] = g[k];
-            h = face_rule(mem + m, X, Y, Z, face_vel, h);
-#pragma unroll
-            for (int k = 0; k < Q; ++k) g[k] = h.v[k];
+        int X = 0, Y = 0, Z = 0;
+        if (BORDER) {
+            node_coords(d, n, X, Y, Z);
+            load_pre<T>(d, fm, n, X, Y, Z, parity, g);
+        } else {
+            load_pre_lin<T>(d, fm, n, parity, g);
         }
         float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
         bool hasF = d.hasF != 0;
@@ -94,7 +100,94 @@ k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T
             hasF = true;
         }
         collide(g, d.omega, d.guo, Fx, Fy, Fz, hasF);
-        store_post<T>(d, fm, n, X, Y, Z, parity, g);
+        if (BORDER) store_post<T>(d, fm, n, X, Y, Z, parity, g);
+        else store_post_lin<T>(d, fm, n, parity, g);
+    }
+}
+
+// FP32 interior runs with the gathers decoupled from the registers: each
+// thread copies its node's 19 pre-collision populations into shared memory
+// with cp.async (4 bytes each, no register held while in flight), one group
+// of runs ahead of the group it computes (two buffers per block), then
+// collides from shared memory and stores to global memory.  A thread reads
+// back only the copies it issued itself, so completion needs no barrier,
+// only cp.async.wait_group.  Persistent grid over groups of blockDim/32 runs.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct RunNode {
+    int m;          // member
+    int n;          // padded node within the member (-1: no work)
+};
+
+template <bool SINGLE>
+__device__ __forceinline__ RunNode run_node(const MemberDev& d0, const MemberDev* __restrict__ mem,
+                                            const uint8_t* __restrict__ tag, const uint32_t* __restrict__ status,
+                                            const uint32_t* __restrict__ segs, int n_mem, int n_segs, int group) {
+    RunNode r{0, -1};
+    const int si = group * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    if (si >= n_segs) return r;
+    r.m = SINGLE ? 0 : find_member_by_seg<false>(mem, n_mem, si);
+    const MemberDev& d = SINGLE ? d0 : mem[r.m];
+    if (status[r.m] & (ST_DAMAGED | ST_NONFINITE)) return r;
+    const int n = (int)(segs[si] << 5) + (int)(threadIdx.x & 31);
+    if (n >= d.N || (tag[d.node_off + n] & TAG_SOLID)) return r;
+    r.n = n;
+    return r;
+}
+
+template <bool SINGLE>
+__global__ void __launch_bounds__(256, LBMA_MIN_BLOCKS)
+k_lbm_async(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, float* __restrict__ f,
+            uint8_t* __restrict__ tag, float* __restrict__ fib, const uint32_t* __restrict__ status,
+            const uint32_t* __restrict__ segs, int n_mem, int n_segs, int n_groups, int parity) {
+    extern __shared__ float stage[];   // [2][Q][blockDim.x]
+    const int B = blockDim.x, tid = threadIdx.x;
+    auto issue = [&](int group, int buf) {
+        if (group >= n_groups) return;
+        const RunNode r = run_node<SINGLE>(d0, mem, tag, status, segs, n_mem, n_segs, group);
+        if (r.n < 0) return;
+        const MemberDev& d = SINGLE ? d0 : mem[r.m];
+        const float* fm = f + d.f_off;
+        const size_t S = (size_t)d.S;
+        float* dst = stage + (size_t)buf * Q * B + tid;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const float* src = parity == 0 ? fm + k * S + r.n : fm + opp(k) * S + (r.n - lin_off(d, k));
+            cp_async4(dst + k * B, src);
+        }
+    };
+    int buf = 0;
+    issue(blockIdx.x, 0);
+    cp_async_commit();
+    for (int group = blockIdx.x; group < n_groups; group += gridDim.x, buf ^= 1) {
+        issue(group + gridDim.x, buf ^ 1);
+        cp_async_commit();
+        cp_async_wait1();
+        const RunNode r = run_node<SINGLE>(d0, mem, tag, status, segs, n_mem, n_segs, group);
+        if (r.n < 0) continue;
+        const MemberDev& d = SINGLE ? d0 : mem[r.m];
+        const float* src = stage + (size_t)buf * Q * B + tid;
+        float g[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[k] = src[k * B];
+        const long long gn = d.node_off + r.n;
+        const uint8_t tg = tag[gn];
+        float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
+        bool hasF = d.hasF != 0;
+        if (tg & TAG_IB) {
+            float* p = fib + 3 * gn;
+            Fx += p[0]; Fy += p[1]; Fz += p[2];
+            p[0] = 0.f; p[1] = 0.f; p[2] = 0.f;
+            tag[gn] = tg & (uint8_t)~TAG_IB;
+            hasF = true;
+        }
+        collide(g, d.omega, d.guo, Fx, Fy, Fz, hasF);
+        store_post_lin<float>(d, f + d.f_off, r.n, parity, g);
     }
 }
 
@@ -163,6 +256,59 @@ __global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, 
     else Store<T>::st(fm + ib * S + xb, v, d.st_scale);           // next step even: own slot
 }
 
+// Zou-He faces (Eq. extbound) after the stream and the wall fill of a step
+// (parity pp done): every fluid node of a velocity or pressure face gathers
+// its populations as the next step will (parity 1 - pp), takes the face rule,
+// and writes the populations entering from outside the box back into the
+// slots the next step reads.  Wall-link values filled by the BFL pass are
+// among the populations the rule reads, and it replaces only those entering
+// through the box face.
+template <typename T>
+__global__ void __launch_bounds__(256) k_faces(const MemberDev* __restrict__ mem, T* __restrict__ f,
+                                               const uint32_t* __restrict__ fc_node,
+                                               const uint32_t* __restrict__ fc_meta,
+                                               const float* __restrict__ face_vel, const uint32_t* __restrict__ status,
+                                               int n_face_nodes, int pp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_face_nodes) return;
+    const uint32_t meta = fc_meta[i];
+    const int m = (int)(meta >> 8), fc = (int)(meta & 7u);
+    if (status[m] & (ST_DAMAGED | ST_NONFINITE)) return;
+    const MemberDev& d = mem[m];
+    const int n = (int)fc_node[i];
+    int X, Y, Z;
+    node_coords(d, n, X, Y, Z);
+    T* fm = f + d.f_off;
+    const int parity = 1 - pp;
+    float g[Q];
+    load_pre<T>(d, fm, n, X, Y, Z, parity, g);
+    apply_face(d, X, Y, Z, face_vel, g);
+    const int nx = fc == 0 ? -1 : (fc == 1 ? 1 : 0);
+    const int ny = fc == 2 ? -1 : (fc == 3 ? 1 : 0);
+    const int nz = fc == 4 ? -1 : (fc == 5 ? 1 : 0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        if (ex(k) * nx + ey(k) * ny + ez(k) * nz < 0)
+            Store<T>::st(fm + pre_slot(d, n, X, Y, Z, parity, k), g[k], d.st_scale);
+    }
+}
+
+template <typename T>
+static cudaError_t faces_t(const DevState& d, int pp, cudaStream_t s) {
+    if (d.n_face_nodes == 0) return cudaSuccess;
+    k_faces<T><<<(d.n_face_nodes + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.fc_node, d.fc_meta, d.face_vel,
+                                                             d.status, d.n_face_nodes, pp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_faces(const DevState& d, int pp, cudaStream_t s) {
+    switch (d.storage) {
+        case 1: return faces_t<__half>(d, pp, s);
+        case 2: return faces_t<__nv_bfloat16>(d, pp, s);
+        default: return faces_t<float>(d, pp, s);
+    }
+}
+
 // Equilibrium initial state (parity 0 layout) from user-layout rho[N], u[3N].
 template <typename T>
 __global__ void k_init(const MemberDev* __restrict__ mem, T* __restrict__ f, const uint8_t* __restrict__ tag, int m, const float* __restrict__ rho,
@@ -195,7 +341,7 @@ __global__ void k_init(const MemberDev* __restrict__ mem, T* __restrict__ f, con
 // Macroscopic fields / populations of one member in user layout.
 template <typename T>
 __global__ void k_read(const MemberDev* __restrict__ mem, const T* __restrict__ f, const uint8_t* __restrict__ tag, const float* __restrict__ face_vel,
-                       int m, int parity, int zh_on, float* __restrict__ rho, float* __restrict__ u,
+                       int m, int parity, float* __restrict__ rho, float* __restrict__ u,
                        float* __restrict__ gout) {
     const MemberDev& d = mem[m];
     const long long Nu = (long long)d.nx * d.ny * d.nz;
@@ -211,7 +357,6 @@ __global__ void k_read(const MemberDev* __restrict__ mem, const T* __restrict__ 
         for (int k = 0; k < Q; ++k) g[k] = 0.f;
     } else {
         load_pre<T>(d, f + d.f_off, n, X, Y, Z, parity, g);
-        if (zh_on) apply_face(d, X, Y, Z, face_vel, g);
     }
     if (gout) {
 #pragma unroll
@@ -236,22 +381,48 @@ __global__ void k_read(const MemberDev* __restrict__ mem, const T* __restrict__ 
 }
 
 template <typename T>
-static cudaError_t lbm_t(const DevState& d, int parity, int zh_on, cudaStream_t s) {
-    const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.total_tiles;
-    if (d.n_members == 1)
-        k_lbm<T, true><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel, d.status,
-                                                  d.n_members, d.total_tiles, parity, zh_on);
-    else
-        k_lbm<T, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel, d.status,
-                                                   d.n_members, d.total_tiles, parity, zh_on);
+static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s) {
+    const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.lbm_blocks;
+    const bool one = d.n_members == 1;
+    if (std::is_same<T, float>::value && d.lbm_blocks > 0) {
+        const int ag = std::min(d.lbm_blocks, (d.grid_lbm > 0 ? d.grid_lbm : LBMA_MIN_BLOCKS * d.n_sm));
+        const size_t smem = 2 * Q * sizeof(float) * (size_t)d.threads;
+        if (one)
+            k_lbm_async<true><<<ag, d.threads, smem, s>>>(d.h_mem[0], d.mem, (float*)d.f, d.tag, d.fib, d.status,
+                                                          d.segs, d.n_members, d.n_segs, d.lbm_blocks, parity);
+        else
+            k_lbm_async<false><<<ag, d.threads, smem, s>>>(d.h_mem[0], d.mem, (float*)d.f, d.tag, d.fib, d.status,
+                                                           d.segs, d.n_members, d.n_segs, d.lbm_blocks, parity);
+    } else if (grid > 0) {
+        if (one)
+            k_lbm<T, true, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
+                                                             d.status, d.segs, d.n_members, d.n_segs, d.lbm_blocks,
+                                                             parity);
+        else
+            k_lbm<T, false, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
+                                                              d.status, d.segs, d.n_members, d.n_segs, d.lbm_blocks,
+                                                              parity);
+    }
+    if (d.lbm_bblocks > 0) {
+        if (one)
+            k_lbm<T, true, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
+                                                                     d.face_vel, d.status, d.bsegs, d.n_members,
+                                                                     d.n_bsegs, d.lbm_bblocks, parity);
+        else
+            k_lbm<T, false, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
+                                                                      d.face_vel, d.status, d.bsegs, d.n_members,
+                                                                      d.n_bsegs, d.lbm_bblocks, parity);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbm(const DevState& d, int parity, int zh_on, cudaStream_t s) {
+int lbm_max_threads() { return LBM_THREADS; }
+
+cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s) {
     switch (d.storage) {
-        case 1: return lbm_t<__half>(d, parity, zh_on, s);
-        case 2: return lbm_t<__nv_bfloat16>(d, parity, zh_on, s);
-        default: return lbm_t<float>(d, parity, zh_on, s);
+        case 1: return lbm_t<__half>(d, parity, s);
+        case 2: return lbm_t<__nv_bfloat16>(d, parity, s);
+        default: return lbm_t<float>(d, parity, s);
     }
 }
 
@@ -286,21 +457,21 @@ cudaError_t launch_init_member(const DevState& d, int m, const float* rho, const
 }
 
 template <typename T>
-static cudaError_t read_t(const DevState& d, int m, int parity, int zh_on, float* rho, float* u, float* g,
+static cudaError_t read_t(const DevState& d, int m, int parity, float* rho, float* u, float* g,
                           cudaStream_t s) {
     const MemberDev& md = d.h_mem[m];
     const long long Nu = (long long)md.nx * md.ny * md.nz;
-    k_read<T><<<(unsigned)((Nu + 255) / 256), 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.face_vel, m, parity, zh_on, rho,
+    k_read<T><<<(unsigned)((Nu + 255) / 256), 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.face_vel, m, parity, rho,
                                                            u, g);
     return cudaGetLastError();
 }
 
-cudaError_t launch_read(const DevState& d, int m, int parity, int zh_on, float* rho, float* u, float* g,
+cudaError_t launch_read(const DevState& d, int m, int parity, float* rho, float* u, float* g,
                         cudaStream_t s) {
     switch (d.storage) {
-        case 1: return read_t<__half>(d, m, parity, zh_on, rho, u, g, s);
-        case 2: return read_t<__nv_bfloat16>(d, m, parity, zh_on, rho, u, g, s);
-        default: return read_t<float>(d, m, parity, zh_on, rho, u, g, s);
+        case 1: return read_t<__half>(d, m, parity, rho, u, g, s);
+        case 2: return read_t<__nv_bfloat16>(d, m, parity, rho, u, g, s);
+        default: return read_t<float>(d, m, parity, rho, u, g, s);
     }
 }
 

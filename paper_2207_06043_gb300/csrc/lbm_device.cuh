@@ -56,6 +56,15 @@ __device__ __forceinline__ void load_pre(const MemberDev& d, const T* __restrict
     }
 }
 
+// Element offset of the slot from which a step of the given parity gathers
+// population k of node n (the address load_pre reads).
+__device__ __forceinline__ long long pre_slot(const MemberDev& d, int n, int X, int Y, int Z, int parity, int k) {
+    if (parity == 0) return (long long)k * d.S + n;
+    const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
+    const int src = nbc(X, -ex(k), d.NX, px) + d.NX * (nbc(Y, -ey(k), d.NY, py) + d.NY * nbc(Z, -ez(k), d.NZ, pz));
+    return (long long)opp(k) * d.S + src;
+}
+
 // Post-collision populations of node n: even steps swap them into slot opp(k)
 // of their own node, odd steps push them to slot k of n + e_k.
 template <typename T>
@@ -76,7 +85,43 @@ __device__ __forceinline__ void store_post(const MemberDev& d, T* __restrict__ f
     }
 }
 
-// Box face of an interior node (-1: none).  Nodes on two faces are solid by
+// The same two accesses for a node that is neither on a box face nor on the
+// wrap plane of a periodic axis: every neighbour is n + e_k in the padded
+// layout (the ghost layer absorbs the step on non-periodic axes), so no
+// coordinates are needed.
+__device__ __forceinline__ int lin_off(const MemberDev& d, int k) {
+    return ex(k) + d.NX * (ey(k) + d.NY * ez(k));
+}
+
+template <typename T>
+__device__ __forceinline__ void load_pre_lin(const MemberDev& d, const T* __restrict__ fm, int n, int parity,
+                                             float g[Q]) {
+    const size_t S = (size_t)d.S;
+    const float ls = d.ld_scale;
+    if (parity == 0) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[k] = Store<T>::ld(fm + k * S + n, ls);
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[k] = Store<T>::ld(fm + opp(k) * S + (n - lin_off(d, k)), ls);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_post_lin(const MemberDev& d, T* __restrict__ fm, int n, int parity,
+                                               const float g[Q]) {
+    const size_t S = (size_t)d.S;
+    const float ss = d.st_scale;
+    if (parity == 0) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) Store<T>::st(fm + opp(k) * S + n, g[k], ss);
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) Store<T>::st(fm + k * S + (n + lin_off(d, k)), g[k], ss);
+    }
+}
+
+// Box face of a node (-1: none).  Nodes on two faces are solid by
 // construction of the geometry.
 __device__ __forceinline__ int face_of(const MemberDev& d, int X, int Y, int Z) {
     if (!(d.per & 1)) { if (X == 1) return 0; if (X == d.NX - 2) return 1; }
@@ -170,7 +215,7 @@ __device__ __forceinline__ void collide(float g[Q], float omega, float guo, floa
         if (ez(k) > 0) jz += g[k]; else if (ez(k) < 0) jz -= g[k];
     }
     const float rho = 1.f + drho;
-    const float inv = 1.f / rho;
+    const float inv = __frcp_rn(rho);   // correctly rounded, as 1.f / rho
     const float ux = (jx + 0.5f * Fx) * inv;
     const float uy = (jy + 0.5f * Fy) * inv;
     const float uz = (jz + 0.5f * Fz) * inv;
@@ -203,11 +248,12 @@ __device__ __forceinline__ void moments_of(const float g[Q], float& rho, float& 
     ux = jx * inv; uy = jy * inv; uz = jz * inv;
 }
 
-__device__ __forceinline__ int find_member_by_tile(const MemberDev* __restrict__ mem, int n_mem, int tile) {
+template <bool BORDER>
+__device__ __forceinline__ int find_member_by_seg(const MemberDev* __restrict__ mem, int n_mem, int seg) {
     int lo = 0, hi = n_mem - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (mem[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+        if ((BORDER ? mem[mid].bseg_begin : mem[mid].seg_begin) <= seg) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

@@ -105,31 +105,34 @@ def throughput_case(seed=SEED, n_capsules=64, nx=512, ny=192, nz=128, D=96.0, d=
                 geometry=g, tau=TAU, u_max=u_max, capsules=caps, steps=10000)
 
 
+def sweep_member(k, seed=SEED):
+    """Member k of the batched sweep, drawn from its own SplitMix64 stream
+    (seed, k): a bifurcation with dims from 128..384 x 48..128 x 32..96 in
+    multiples of 8, half-angle U[20, 80], occlusion U[0.3, 0.9], Ca
+    log-U[1e-3, 1e-1], junction rounding U[0, 10]; one capsule (642 v if
+    d <= 20 lu else 2562 v) near the inlet; 5k steps."""
+    rng = Ms.SplitMix64((seed << 20) + k)
+    nx = 8 * rng.randint(16, 48)
+    ny = 8 * rng.randint(6, 16)
+    nz = 8 * rng.randint(4, 12)
+    th = rng.uniform(20.0, 80.0)
+    occ = rng.uniform(0.3, 0.9)
+    Ca = 10.0 ** rng.uniform(-3.0, -1.0)
+    rj = rng.uniform(0.0, 10.0)
+    D = float(round(0.75 * min(ny, nz)))
+    d = occ * D
+    u_max = 0.02
+    g = G.bifurcation(nx, ny, nz, D, th, rj, u_max=u_max)
+    nv = 642 if d <= 20.0 else 2562
+    c = (d / 2 + 4.0, g.info["yc"], g.info["zc"])
+    V, T = Ms.sphere_mesh(nv, d, c, rng)
+    return dict(name=f"member {k}: {nx}x{ny}x{nz} th={th:.1f} occ={occ:.2f} Ca={Ca:.4f} rj={rj:.1f}",
+                geometry=g, tau=TAU, u_max=u_max, capsules=[_capsule(V, T, Ca=Ca, u_ref=u_max)], steps=5000)
+
+
 def sweep_case(seed=SEED, n=64):
-    """Batched sweep: n independent bifurcations of uneven size (dims drawn
-    from 128..384 x 48..128 x 32..96 in multiples of 8), half-angle U[20, 80],
-    occlusion U[0.3, 0.9], Ca log-U[1e-3, 1e-1], junction rounding U[0, 10];
-    one capsule each (642 v if d <= 20 lu else 2562 v); 5k steps."""
-    rng = Ms.SplitMix64(seed)
-    out = []
-    for k in range(n):
-        nx = 8 * rng.randint(16, 48)
-        ny = 8 * rng.randint(6, 16)
-        nz = 8 * rng.randint(4, 12)
-        th = rng.uniform(20.0, 80.0)
-        occ = rng.uniform(0.3, 0.9)
-        Ca = 10.0 ** rng.uniform(-3.0, -1.0)
-        rj = rng.uniform(0.0, 10.0)
-        D = float(round(0.75 * min(ny, nz)))
-        d = occ * D
-        u_max = 0.02
-        g = G.bifurcation(nx, ny, nz, D, th, rj, u_max=u_max)
-        nv = 642 if d <= 20.0 else 2562
-        c = (d / 2 + 4.0, g.info["yc"], g.info["zc"])
-        V, T = Ms.sphere_mesh(nv, d, c, rng)
-        out.append(dict(name=f"member {k}: {nx}x{ny}x{nz} th={th:.1f} occ={occ:.2f} Ca={Ca:.4f} rj={rj:.1f}",
-                        geometry=g, tau=TAU, u_max=u_max, capsules=[_capsule(V, T, Ca=Ca, u_ref=u_max)], steps=5000))
-    return out
+    """The batched sweep: n independent members (see sweep_member)."""
+    return [sweep_member(k, seed) for k in range(n)]
 
 
 def make_solver(case, storage="f32", stream=None):

@@ -170,3 +170,31 @@ def test_ensemble_matches_single_lattices_exactly():
         _, u2 = ens.read_fields(member=m)
         assert np.array_equal(u1, u2), m
         assert ens.member_steps(m) == 70
+
+
+def test_batched_members_with_capsules_match_the_plain_fp32_path():
+    """Three uneven bifurcations with a soft capsule each, stepped as one
+    batched context (autotuned launch shape) against each stepped alone:
+    velocity relative L2 <= 1e-3 (spreading atomics make the two differ in
+    the last FP32 bits only), centroids within 1e-4 lu."""
+    from paper_2207_06043_gb300.binding import ensemble
+    cases = []
+    for k, (dims, th) in enumerate([((48, 24, 20), 30.0), ((64, 28, 24), 50.0), ((40, 20, 20), 70.0)]):
+        g = G.bifurcation(*dims, 12.0 if dims[1] < 28 else 16.0, th, 2.0, u_max=0.02)
+        V, T = Ms.sphere_mesh(162, 7.0, (8.0, g.info["yc"], g.info["zc"]), Ms.SplitMix64(20 + k))
+        cases.append(case(g, capsules=[W._capsule(V, T, Ca=0.05)]))
+    singles = [gpu_for(c) for c in cases]
+    ens = ensemble([gpu_for(c) for c in cases])
+    ens.step(5)
+    thr, bps, ms = ens.autotune(2)
+    assert thr in (64, 128, 256) and ms > 0
+    assert ens.member_steps(0) == 5          # the autotuner restores the state
+    for s in singles:
+        s.step(65)
+    ens.step(60)
+    for m, (s, c) in enumerate(zip(singles, cases)):
+        _, u1 = s.read_fields()
+        _, u2 = ens.read_fields(member=m)
+        assert rel_l2(u2, u1, c["geometry"].tag == 0) <= 1e-3, m
+        d = np.abs(ens.read_capsule(0, member=m)["centroid"] - s.read_capsule(0)["centroid"]).max()
+        assert d <= 1e-4, (m, d)

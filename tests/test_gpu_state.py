@@ -1,0 +1,66 @@
+"""Checkpoint / restart through ibl_save_state / ibl_load_state (GPU): a
+context restored from a snapshot continues exactly as the saved one."""
+import numpy as np
+import pytest
+
+from paper_2207_06043_gb300 import geometry as G
+from paper_2207_06043_gb300 import meshes as Ms
+from paper_2207_06043_gb300 import workloads as W
+
+from helpers import case, gpu_for, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.zeros(1, device="cuda")
+
+
+def test_restart_without_capsules_is_bit_identical():
+    """No capsules: no atomics, so the continued runs agree bit for bit
+    (13 saved steps: the restart begins on an odd AA step)."""
+    c = case(G.bifurcation(40, 20, 16, 10.0, 30.0, 2.0))
+    a = gpu_for(c)
+    a.step(13)
+    blob = a.save_state()
+    a.step(10)
+    b = gpu_for(c)
+    b.load_state(blob)
+    assert b.member_steps(0) == 13
+    b.step(10)
+    assert np.array_equal(a.read_populations(), b.read_populations())
+
+
+def test_restart_with_a_soft_capsule_continues_the_run():
+    g = G.bifurcation(48, 20, 20, 14.0, 45.0, 2.0, u_max=0.02)
+    V, T = Ms.sphere_mesh(162, 7.0, (10.0, g.info["yc"] + 1.0, g.info["zc"] - 0.5), Ms.SplitMix64(3))
+    c = case(g, capsules=[W._capsule(V, T, Ca=0.05)])
+    a = gpu_for(c)
+    a.step(20)
+    blob = a.save_state()
+    a.step(15)
+    b = gpu_for(c)
+    b.load_state(blob)
+    b.step(15)
+    _, ua = a.read_fields()
+    _, ub = b.read_fields()
+    # spreading atomics sum in no fixed order: FP32 last-bit differences only
+    assert rel_l2(ub, ua, g.tag == 0) <= 1e-6
+    xa = a.read_capsule(0, with_verts=True)["verts"]
+    xb = b.read_capsule(0, with_verts=True)["verts"]
+    assert np.abs(xa - xb).max() <= 1e-6
+
+
+def test_snapshot_of_another_set_up_is_rejected():
+    from paper_2207_06043_gb300.binding import ERR_ARG, IBLError
+    a = gpu_for(case(G.periodic_box(12, 10, 8)))
+    a.step(2)
+    blob = a.save_state()
+    b = gpu_for(case(G.periodic_box(12, 10, 9)))
+    with pytest.raises(IBLError) as e:
+        b.load_state(blob)
+    assert e.value.status == ERR_ARG
