@@ -75,7 +75,7 @@ def bouzidi_value(q, fi_b, fi_1, fi_2, fib_b, fib_1, ok1, ok2):
     from the post-collision values f*_i at x_b, x_b - e_i, x_b - 2e_i and
     f*_ib at x_b, x_b - e_i; ok1 / ok2 say whether x_b - e_i / x_b - 2e_i are
     fluid."""
-    small = q < 0.5
+    small = np.real(q) < 0.5          # the branch is taken on the real link distance
     quad_s = q * (2 * q + 1) * fi_b + (1 - 4 * q * q) * fi_1 - q * (1 - 2 * q) * fi_2
     lin_s = 2 * q * fi_b + (1 - 2 * q) * fi_1
     val_s = np.where(ok1 & ok2, quad_s, np.where(ok1, lin_s, fi_b))
@@ -187,11 +187,22 @@ class Lattice:
         two-point rule, then to halfway bounce-back (Reading B')."""
         if self.links_node.size == 0:
             return fnew
+        xb, i, ib, m1, ok1, m2, ok2 = self.link_neighbours()
+        q = self.links_q
+        fi_b = fstar[i, xb]
+        fib_b = fstar[ib, xb]
+        fi_1 = np.where(ok1, fstar[i, np.where(ok1, m1, 0)], 0.0)
+        fi_2 = np.where(ok2, fstar[i, np.where(ok2, m2, 0)], 0.0)
+        fib_1 = np.where(ok1, fstar[ib, np.where(ok1, m1, 0)], 0.0)
+        fnew[ib, xb] = bouzidi_value(q, fi_b, fi_1, fi_2, fib_b, fib_1, ok1, ok2)
+        return fnew
+
+    def link_neighbours(self):
+        """Per wall link (x_b, i): x_b, i, the opposite direction ib, the nodes
+        x_b - e_i and x_b - 2 e_i and whether they are fluid."""
         xb = self.links_node
         i = self.links_dir
         ib = OPP[i]
-        q = self.links_q
-        # x_b - e_i and x_b - 2 e_i, per link (directions differ per link)
         m1 = np.empty_like(xb)
         ok1 = np.empty(xb.shape, dtype=bool)
         m2 = np.empty_like(xb)
@@ -204,13 +215,7 @@ class Lattice:
             b, okb = self.shift(xb[sel], -2 * E[d])
             m1[sel], ok1[sel] = a, self.is_fluid(a, oka)
             m2[sel], ok2[sel] = b, self.is_fluid(b, okb)
-        fi_b = fstar[i, xb]
-        fib_b = fstar[ib, xb]
-        fi_1 = np.where(ok1, fstar[i, np.where(ok1, m1, 0)], 0.0)
-        fi_2 = np.where(ok2, fstar[i, np.where(ok2, m2, 0)], 0.0)
-        fib_1 = np.where(ok1, fstar[ib, np.where(ok1, m1, 0)], 0.0)
-        fnew[ib, xb] = bouzidi_value(q, fi_b, fi_1, fi_2, fib_b, fib_1, ok1, ok2)
-        return fnew
+        return xb, i, ib, m1, ok1, m2, ok2
 
     def zou_he(self, fnew):
         """Eq. extbound generalised to the six faces through the velocity
@@ -234,7 +239,7 @@ class Lattice:
             Km = np.nonzero(en < 0)[0]
             S = fnew[K0][:, nodes].sum(axis=0) + 2.0 * fnew[Kp][:, nodes].sum(axis=0)
             if spec.kind == FACE_VELOCITY:
-                uw = np.asarray(spec.velocity, dtype=np.float64)[fidx]
+                uw = np.asarray(spec.velocity)[fidx].astype(np.result_type(spec.velocity, np.float64))
                 un = uw @ nrm
                 rho = S / (1.0 + un)
             else:

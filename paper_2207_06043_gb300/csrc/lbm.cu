@@ -20,6 +20,10 @@
 #ifndef LBMA_MIN_BLOCKS
 #define LBMA_MIN_BLOCKS 4
 #endif
+// 1: FP32 interior runs take the cp.async-staged kernel; 0: register gathers
+#ifndef LBM_ASYNC
+#define LBM_ASYNC 1
+#endif
 
 namespace ibl {
 
@@ -384,7 +388,7 @@ template <typename T>
 static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s) {
     const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.lbm_blocks;
     const bool one = d.n_members == 1;
-    if (std::is_same<T, float>::value && d.lbm_blocks > 0) {
+    if (LBM_ASYNC && std::is_same<T, float>::value && d.lbm_blocks > 0) {
         const int ag = std::min(d.lbm_blocks, (d.grid_lbm > 0 ? d.grid_lbm : LBMA_MIN_BLOCKS * d.n_sm));
         const size_t smem = 2 * Q * sizeof(float) * (size_t)d.threads;
         if (one)
