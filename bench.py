@@ -185,6 +185,9 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-ckpt", type=int, default=100)
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     args = ap.parse_args()
@@ -272,6 +275,8 @@ def main():
 
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_run(case, args)
+    if rank == 0 and not args.no_adjoint:
+        out["adjoint"] = adjoint_measure(args, case)
     if rank == 0 and not args.no_cpu:
         sample = cpu_sample_case(case)
         dt, nfs = run_oracle(sample, args.cpu_steps)
@@ -283,6 +288,69 @@ def main():
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _adjoint_run(c, n, K, lo, hi):
+    """Time n plain forward steps and one ibl_adjoint call of n steps on the
+    lattice of case c (no capsules), each on its own context; the adjoint is
+    timed on its second call (the first allocates its buffers and captures
+    its graphs)."""
+    import torch
+    from paper_2207_06043_gb300 import workloads as W
+    fwd = W.make_solver(c)
+    adj = W.make_solver(c)
+    fwd.step(10)
+    adj.step(10)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    fwd.step(n)
+    e[1].record(stream)
+    adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)     # allocates the buffers, captures the graphs
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    J, gs, gr = adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    ms_f, ms_a = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    fwd.close()
+    adj.close()
+    nf = fluid_updates(c)
+    return {"fluid_nodes": nf, "steps": n, "ckpt_every": K, "ms_forward": ms_f, "ms_adjoint_call": ms_a,
+            "cost_vs_forward": ms_a / ms_f, "mlups_adjoint": nf * n / (ms_a * 1e-3) / 1e6,
+            "J": J, "dJ_du_max": gs / c["u_max"], "dJ_dr_j": gr}
+
+
+def adjoint_measure(args, case):
+    """The discrete adjoint (ibl_adjoint) against the same number of plain
+    forward steps, on (a) the adjoint workload's lattice (192x64x48
+    bifurcation, junction radius 4 lu, 2000 steps, a checkpoint every 100) and
+    (b) the throughput workload's lattice (12.6 M nodes, 100 steps, every 10),
+    both without capsules: the adjoint covers the lattice step.  J = sum of
+    u_x over the upper half of the region just past the junction (a), of the
+    inlet region (b)."""
+    from paper_2207_06043_gb300 import workloads as W
+    out = {"note": "each call runs the forward sweep with checkpoints, the recompute with the tape and the "
+                   "reverse sweep; its device buffers are allocated inside the call"}
+    ca = dict(W.adjoint_case(), capsules=[])
+    g = ca["geometry"]
+    xj = int(g.info["x_junction"])
+    r = _adjoint_run(ca, args.adjoint_steps, args.adjoint_ckpt, (xj, int(g.info["yc"]), 0),
+                     (min(g.nx, xj + 24), g.ny, g.nz))
+    out["adjoint_workload"] = dict(r, workload="bifurcation 192x64x48, D 36, 45 deg, junction radius 4 lu, no capsule")
+    ct = dict(case, capsules=[])
+    g = ct["geometry"]
+    xj = int(g.info["x_junction"])
+    r = _adjoint_run(ct, 100, 10, (4, int(g.info["yc"]), 0), (52, g.ny, g.nz))
+    bpu = 152 + 168 + 168      # forward sweep, recompute with tape, adjoint step (B per fluid node and step)
+    peak, kind = load_peaks()
+    ach = bpu * r["fluid_nodes"] * r["steps"] / (r["ms_adjoint_call"] * 1e-3) / 1e9
+    out["throughput_lattice"] = dict(r, workload="throughput lattice 512x192x128 without capsules",
+                                     roofline={"bound": "hbm", "algorithmic_bytes_per_node_step": bpu,
+                                               "achieved": ach, "peak": peak, "unit": "GB/s",
+                                               "frac": ach / peak, "peak_source": f"{kind} hbm_gbs"})
+    return out
 
 
 def _sweep_member(k):

@@ -211,6 +211,39 @@ ibl_status ibl_kernel_times(ibl_ctx* ctx, double* out4);
 ibl_status ibl_save_state(ibl_ctx* ctx, void* buf, size_t* bytes);
 ibl_status ibl_load_state(ibl_ctx* ctx, const void* buf, size_t bytes);
 
+/* Objective of the adjoint: J = sum over the fluid nodes x with
+ * lo <= x < hi (user coordinates, per axis) of d . u(x) after the last step,
+ * u = (sum f e + F_body/2) / rho. */
+typedef struct {
+    int32_t lo[3], hi[3];
+    double d[3];
+} ibl_objective;
+
+/* Discrete adjoint of n_steps lattice steps (Eq. evoleq collide + stream, Eq.
+ * bbouzidi wall links, Eq. extbound faces) from the current state of a
+ * context holding ONE FP32 lattice without capsules (IBL_ERR_STATE otherwise).
+ * The call advances the context by n_steps exactly as ibl_step does and
+ * returns J at the last step (J_out) and its derivatives
+ *   grad_inlet_scale = dJ/ds for velocity-face data scaled as u_w (1 + s)
+ *                      (dJ/du_max = grad_inlet_scale / u_max when the inlet
+ *                      profile is proportional to its peak u_max), and
+ *   grad_rj          = sum over links of dJ/dq * dq (the dq of the
+ *                      ibl_wall_link records, e.g. dq/d(junction radius)),
+ * with the fluid/solid tags held fixed.  The forward pass keeps a copy of the
+ * populations every ckpt_every steps; the reverse pass recomputes each segment
+ * from its copy, recording (rho, u) per node, d(value)/dq per wall link and
+ * rho per face node (the tape), and then runs the adjoint steps of the segment
+ * backwards.  The device memory for checkpoints and tape,
+ *   ceil(n_steps / ckpt_every) * populations + ckpt_every * 16 B per node
+ *   + 3 * 19 * 4 B per node,
+ * is allocated by the first call that needs it (cudaMalloc) and kept by the
+ * context, with the CUDA graphs of the segments, until ibl_destroy; a later
+ * call with more checkpoints or longer segments reallocates it.
+ * Outputs may be NULL; gradients are accumulated in FP64. */
+ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every,
+                       const ibl_objective* obj, double* J_out,
+                       double* grad_inlet_scale, double* grad_rj);
+
 /* Allocation-free read of member `member`'s macroscopic fields into HOST
  * buffers rho[N] and u[3N] (either may be NULL, not both); same values and
  * layout as ibl_member_read_fields with on_device = 0.  The paper has no

@@ -45,6 +45,10 @@ class CapsuleStats(C.Structure):
                 ("velocity", C.c_double * 3), ("damaged", C.c_int32), ("reserved", C.c_int32)]
 
 
+class Objective(C.Structure):
+    _fields_ = [("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3), ("d", C.c_double * 3)]
+
+
 class IBLError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -89,6 +93,7 @@ def lib():
         "ibl_kernels_per_step": ([vp, P(i32)], i32),
         "ibl_save_state": ([vp, vp, P(sz)], i32),
         "ibl_autotune": ([vp, i32, P(i32), P(i32), P(dbl)], i32),
+        "ibl_adjoint": ([vp, i32, i32, P(Objective), P(dbl), P(dbl), P(dbl)], i32),
         "ibl_load_state": ([vp, vp, sz], i32),
         "ibl_kernel_times": ([vp, vp], i32),
         "ibl_last_error": ([vp], C.c_char_p),
@@ -248,6 +253,17 @@ class Solver:
         t, b, ms = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
         self._check(self._L.ibl_autotune(self._h, int(steps), C.byref(t), C.byref(b), C.byref(ms)))
         return int(t.value), int(b.value), float(ms.value)
+
+    def adjoint(self, steps, lo, hi, d, ckpt_every=100):
+        """Discrete adjoint of `steps` steps (the context advances by them):
+        J = sum over the fluid nodes of the box [lo, hi) of d . u at the last
+        step, dJ/ds for inlet velocities scaled by (1 + s), and sum_links
+        dJ/dq dq.  Returns (J, dJ/ds, dJ/dr)."""
+        ob = Objective((C.c_int32 * 3)(*lo), (C.c_int32 * 3)(*hi), (C.c_double * 3)(*d))
+        J, gs, gr = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+        self._check(self._L.ibl_adjoint(self._h, int(steps), int(ckpt_every), C.byref(ob), C.byref(J),
+                                        C.byref(gs), C.byref(gr)))
+        return float(J.value), float(gs.value), float(gr.value)
 
     def save_state(self):
         """Snapshot of the dynamic state (bytes)."""

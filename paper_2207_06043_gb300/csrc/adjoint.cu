@@ -1,0 +1,301 @@
+// Discrete adjoint of the lattice step (Eq. evoleq collide + stream, Eq.
+// bbouzidi wall links, Eq. extbound faces) for lattices without capsules:
+// the reverse sweep that carries lambda = dJ/df from the final step back to
+// the first, accumulating the derivatives of J with respect to the inlet
+// velocity scale and to the junction radius (through the link distances q).
+//
+// One reverse step t, with lambda the adjoint of the populations after step t:
+//   1. faces^T : at every face node, the populations the face rule wrote are
+//                replaced by their contributions to the ones it read;
+//   2. links^T : every wall link scatters lambda of the population it wrote
+//                onto the five post-collision values it read (atomics into a
+//                separate array, read once by step 3);
+//   3. stream^T + collide^T : every fluid node pulls lambda of the population
+//                it streamed to n + e_i, adds the link terms, and applies the
+//                transposed collision Jacobian at its (rho, u) of step t.
+// The (rho, u) of every node, d(value)/dq of every link and rho of every face
+// node come from a tape written while the forward steps are recomputed from a
+// checkpoint.
+#include "lbm_device.cuh"
+
+namespace ibl {
+
+constexpr unsigned FULLMASK = 0xffffffffu;
+
+__device__ __forceinline__ void block_add_d(double v, double* out) {
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(FULLMASK, t, o);
+        if (lane == 0 && t != 0.0) atomicAdd(out, t);
+    }
+}
+
+// J = sum over the fluid nodes of the box of d . u with u = (sum g e + F/2)/rho,
+// and lambda_i = dJ/dg_i = d . (e_i - u) / rho there (zero elsewhere; the
+// buffer is cleared before the launch).
+__global__ void __launch_bounds__(256) k_adj_objective(const MemberDev* __restrict__ mem, const float* __restrict__ f,
+                                                       const uint8_t* __restrict__ tag, int parity, int3 lo, int3 hi,
+                                                       double dx, double dy, double dz, float* __restrict__ lam,
+                                                       size_t LS, double* __restrict__ J) {
+    const MemberDev& d = mem[0];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double contrib = 0.0;
+    if (n < d.N && !(tag[n] & TAG_SOLID)) {
+        int X, Y, Z;
+        node_coords(d, n, X, Y, Z);
+        const int x = X - d.px, y = Y - d.py, z = Z - d.pz;
+        if (x >= lo.x && x < hi.x && y >= lo.y && y < hi.y && z >= lo.z && z < hi.z) {
+            float g[Q];
+            load_pre<float>(d, f + d.f_off, n, X, Y, Z, parity, g);
+            float rho, ux, uy, uz;
+            moments_of(g, rho, ux, uy, uz);
+            const float ir = __frcp_rn(rho);
+            ux += 0.5f * d.F[0] * ir;
+            uy += 0.5f * d.F[1] * ir;
+            uz += 0.5f * d.F[2] * ir;
+            contrib = dx * ux + dy * uy + dz * uz;
+            const float du = (float)(dx * ux + dy * uy + dz * uz);
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                lam[k * LS + n] = ((float)dx * ex(k) + (float)dy * ey(k) + (float)dz * ez(k) - du) * ir;
+        }
+    }
+    block_add_d(contrib, J);
+}
+
+// faces^T, in place.  With c_j = 1 (e_j.n = 0), 2 (e_j.n > 0), 0 (e_j.n < 0)
+// and D = 1 + u_w.n, the face rule writes for every k with e_k.n < 0,
+// t = e_k + n, o = opp(k):
+//   velocity face: v_k = g_o + rho a_k - (1/2) sum_{e_j.n=0} g_j (e_j.t),
+//                  rho = (1 + sum c_j g_j) / D,
+//                  a_k = -u_n/3 (t = 0) or -u_n/6 + u_t/2 (t != 0)
+//   pressure face: v_k = g_o - (1 + sum c_j g_j) / (3 or 6) - (1/2) sum_{e_j.n=0} g_j (e_j.t)
+// so dv_k/dg_j = delta_jo + (a_k / D or -1/3, -1/6) c_j - (1/2)[e_j.n = 0](e_j.t).
+// Scaling the inlet velocities by (1 + s) gives dv_k/ds = a_k rho / D.
+__global__ void __launch_bounds__(256) k_adj_faces(const MemberDev* __restrict__ mem,
+                                                   const uint32_t* __restrict__ fc_node,
+                                                   const uint32_t* __restrict__ fc_meta,
+                                                   const float* __restrict__ face_vel,
+                                                   const float* __restrict__ tape_rho, float* __restrict__ lam,
+                                                   size_t LS, int n_face_nodes, double* __restrict__ grad_s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ds = 0.0;
+    if (i < n_face_nodes) {
+        const MemberDev& d = mem[0];
+        const int fc = (int)(fc_meta[i] & 7u);
+        const int n = (int)fc_node[i];
+        const int nx = fc == 0 ? -1 : (fc == 1 ? 1 : 0);
+        const int ny = fc == 2 ? -1 : (fc == 3 ? 1 : 0);
+        const int nz = fc == 4 ? -1 : (fc == 5 ? 1 : 0);
+        const bool vel = d.face_kind[fc] == FACE_VELOCITY;
+        float uwx = 0.f, uwy = 0.f, uwz = 0.f;
+        if (vel) {
+            int X, Y, Z;
+            node_coords(d, n, X, Y, Z);
+            const float* u = face_vel + 3 * (d.face_off[fc] + face_index(d, fc, X, Y, Z));
+            uwx = u[0]; uwy = u[1]; uwz = u[2];
+        }
+        const float un = uwx * nx + uwy * ny + uwz * nz;
+        const float iD = 1.f / (1.f + un);
+        float l[Q], out[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            l[k] = lam[k * LS + n];
+            out[k] = (ex(k) * nx + ey(k) * ny + ez(k) * nz) < 0 ? 0.f : l[k];
+        }
+        const float rho = vel ? tape_rho[i] : 0.f;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            if (ex(k) * nx + ey(k) * ny + ez(k) * nz >= 0) continue;
+            const int tx = ex(k) + nx, ty = ey(k) + ny, tz = ez(k) + nz;
+            const bool axial = tx == 0 && ty == 0 && tz == 0;
+            const float ut = uwx * tx + uwy * ty + uwz * tz;
+            const float a = axial ? -un * (1.f / 3.f) : (-un * (1.f / 6.f) + 0.5f * ut);
+            const float crho = vel ? a * iD : (axial ? -1.f / 3.f : -1.f / 6.f);
+            const float lk = l[k];
+            out[opp(k)] += lk;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const int en = ex(j) * nx + ey(j) * ny + ez(j) * nz;
+                const float c = en == 0 ? 1.f : (en > 0 ? 2.f : 0.f);
+                float coef = crho * c;
+                if (en == 0) coef -= 0.5f * (float)(ex(j) * tx + ey(j) * ty + ez(j) * tz);
+                out[j] += coef * lk;
+            }
+            if (vel) ds += (double)lk * (double)(a * rho * iD);
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) lam[k * LS + n] = out[k];
+    }
+    block_add_d(ds, grad_s);
+}
+
+// links^T: the value the wall rule wrote at (opp(i), x_b) is a combination of
+// f*_i(x_b), f*_i(x_b - e_i), f*_i(x_b - 2 e_i), f*_opp(i)(x_b), f*_opp(i)(x_b - e_i)
+// with the coefficients of the forward rule; dJ/dr_j gains
+// lambda * (d value / dq) * (dq / dr_j).
+__global__ void __launch_bounds__(256) k_adj_links(const MemberDev* __restrict__ mem,
+                                                   const uint32_t* __restrict__ l_node,
+                                                   const uint32_t* __restrict__ l_meta, const float* __restrict__ l_q,
+                                                   const float* __restrict__ l_dq, const float* __restrict__ tape_dvdq,
+                                                   const float* __restrict__ lam, float* __restrict__ extra, size_t LS,
+                                                   int n_links, double* __restrict__ grad_q) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    double dqs = 0.0;
+    if (l < n_links) {
+        const MemberDev& d = mem[0];
+        const uint32_t meta = l_meta[l];
+        const int i = (int)(meta & 31u), ib = opp(i);
+        const bool ok1 = meta & 32u, ok2 = meta & 64u;
+        const int xb = (int)l_node[l];
+        const float lv = lam[ib * LS + xb];
+        if (lv != 0.f) {
+            const float q = l_q[l];
+            int X, Y, Z;
+            node_coords(d, xb, X, Y, Z);
+            const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
+            const int exi = ex(i), eyi = ey(i), ezi = ez(i);
+            const int X1 = nbc(X, -exi, d.NX, px), Y1 = nbc(Y, -eyi, d.NY, py), Z1 = nbc(Z, -ezi, d.NZ, pz);
+            const int m1 = X1 + d.NX * (Y1 + d.NY * Z1);
+            const int m2 = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
+            float* ei = extra + i * LS;
+            float* eb = extra + ib * LS;
+            if (q < 0.5f) {
+                if (ok1 && ok2) {
+                    atomicAdd(ei + xb, q * (2.f * q + 1.f) * lv);
+                    atomicAdd(ei + m1, (1.f - 4.f * q * q) * lv);
+                    atomicAdd(ei + m2, -q * (1.f - 2.f * q) * lv);
+                } else if (ok1) {
+                    atomicAdd(ei + xb, 2.f * q * lv);
+                    atomicAdd(ei + m1, (1.f - 2.f * q) * lv);
+                } else {
+                    atomicAdd(ei + xb, lv);
+                }
+            } else {
+                if (ok1) {
+                    atomicAdd(ei + xb, lv / (q * (2.f * q + 1.f)));
+                    atomicAdd(eb + xb, (2.f * q - 1.f) / q * lv);
+                    atomicAdd(eb + m1, (1.f - 2.f * q) / (1.f + 2.f * q) * lv);
+                } else {
+                    atomicAdd(ei + xb, lv / (2.f * q));
+                    atomicAdd(eb + xb, (2.f * q - 1.f) / (2.f * q) * lv);
+                }
+            }
+            dqs = (double)lv * (double)tape_dvdq[l] * (double)l_dq[l];
+        }
+    }
+    block_add_d(dqs, grad_q);
+}
+
+// stream^T + links + collide^T at every fluid node.  With omega = 1/tau,
+// guo = 1 - omega/2, the collision f*_j = f_j - omega (f_j - f^eq_j(rho, u))
+// + G_j(u) has d rho/d f_i = 1 and d u/d f_i = (e_i - u)/rho, so
+//   lambda_i = (1 - omega) lambda*_i + omega A + B . (e_i - u) / rho,
+//   A = sum_j lambda*_j w_j (1 + 3 e_j.u + 9/2 (e_j.u)^2 - 3/2 u^2),
+//   B = sum_j lambda*_j [omega w_j rho (3 e_j + 9 (e_j.u) e_j - 3 u)
+//                        + guo w_j (9 (e_j.F) e_j - 3 F)].
+__global__ void __launch_bounds__(256) k_adj_step(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag,
+                                                  const uint8_t* __restrict__ near, const float4* __restrict__ tape,
+                                                  const float* __restrict__ lam_in, float* __restrict__ lam_out,
+                                                  float* __restrict__ extra, size_t LS) {
+    const MemberDev& d = mem[0];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= d.N || (tag[n] & TAG_SOLID)) return;
+    int X, Y, Z;
+    node_coords(d, n, X, Y, Z);
+    const Nbr b = neighbours(d, X, Y, Z);
+    const bool nr = near[n] != 0;
+    float ls[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const int m = b.xs[1 + ex(k)] + d.NX * (b.ys[1 + ey(k)] + d.NY * b.zs[1 + ez(k)]);
+        float v = (tag[m] & TAG_SOLID) ? 0.f : lam_in[k * LS + m];
+        if (nr) {
+            v += extra[k * LS + n];
+            extra[k * LS + n] = 0.f;
+        }
+        ls[k] = v;
+    }
+    const float4 t = tape[n];
+    const float rho = t.x, ux = t.y, uy = t.z, uz = t.w;
+    const float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
+    const float om = d.omega, guo = d.guo;
+    const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+    float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const float eu = ex(k) * ux + ey(k) * uy + ez(k) * uz;
+        const float eF = ex(k) * Fx + ey(k) * Fy + ez(k) * Fz;
+        const float w = wgt(k) * ls[k];
+        A += w * (1.f + 3.f * eu + 4.5f * eu * eu - usq);
+        const float s1 = om * rho * (3.f + 9.f * eu) + guo * 9.f * eF;   // coefficient of e_k
+        const float s2 = om * rho * 3.f;                                  // coefficient of -u
+        Bx += w * (s1 * ex(k) - s2 * ux - guo * 3.f * Fx);
+        By += w * (s1 * ey(k) - s2 * uy - guo * 3.f * Fy);
+        Bz += w * (s1 * ez(k) - s2 * uz - guo * 3.f * Fz);
+    }
+    const float ir = 1.f / rho;
+    const float Bu = Bx * ux + By * uy + Bz * uz;
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        lam_out[k * LS + n] = (1.f - om) * ls[k] + om * A + (Bx * ex(k) + By * ey(k) + Bz * ez(k) - Bu) * ir;
+}
+
+// Nodes that receive link terms in links^T: x_b, and x_b - e_i / x_b - 2 e_i
+// where the rule reads them.
+__global__ void k_adj_near(const MemberDev* __restrict__ mem, const uint32_t* __restrict__ l_node,
+                           const uint32_t* __restrict__ l_meta, int n_links, uint8_t* __restrict__ near) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_links) return;
+    const MemberDev& d = mem[0];
+    const uint32_t meta = l_meta[l];
+    const int i = (int)(meta & 31u);
+    const bool ok1 = meta & 32u, ok2 = meta & 64u;
+    const int xb = (int)l_node[l];
+    int X, Y, Z;
+    node_coords(d, xb, X, Y, Z);
+    const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
+    const int X1 = nbc(X, -ex(i), d.NX, px), Y1 = nbc(Y, -ey(i), d.NY, py), Z1 = nbc(Z, -ez(i), d.NZ, pz);
+    near[xb] = 1;
+    if (ok1) near[X1 + d.NX * (Y1 + d.NY * Z1)] = 1;
+    if (ok2)
+        near[nbc(X1, -ex(i), d.NX, px) + d.NX * (nbc(Y1, -ey(i), d.NY, py) + d.NY * nbc(Z1, -ez(i), d.NZ, pz))] = 1;
+}
+
+cudaError_t launch_adj_near(const DevState& d, uint8_t* near, cudaStream_t s) {
+    if (d.n_links == 0) return cudaSuccess;
+    k_adj_near<<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, d.l_node, d.l_meta, d.n_links, near);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_objective(const DevState& d, int parity, const int lo[3], const int hi[3], const double w[3],
+                                 float* lam, size_t LS, double* J, cudaStream_t s) {
+    const int N = d.h_mem[0].N;
+    k_adj_objective<<<(N + 255) / 256, 256, 0, s>>>(d.mem, (const float*)d.f, d.tag, parity,
+                                                    make_int3(lo[0], lo[1], lo[2]), make_int3(hi[0], hi[1], hi[2]),
+                                                    w[0], w[1], w[2], lam, LS, J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const float* tape_dvdq, const float4* tape_rhou,
+                            const uint8_t* near, float* lam_in, float* lam_out, float* extra, size_t LS,
+                            double* grad_s, double* grad_q, cudaStream_t s) {
+    if (d.n_face_nodes > 0)
+        k_adj_faces<<<(d.n_face_nodes + 255) / 256, 256, 0, s>>>(d.mem, d.fc_node, d.fc_meta, d.face_vel, tape_rho,
+                                                                 lam_in, LS, d.n_face_nodes, grad_s);
+    if (d.n_links > 0)
+        k_adj_links<<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, d.l_node, d.l_meta, d.l_q, d.l_dq, tape_dvdq,
+                                                            lam_in, extra, LS, d.n_links, grad_q);
+    const int N = d.h_mem[0].N;
+    k_adj_step<<<(N + 255) / 256, 256, 0, s>>>(d.mem, d.tag, near, tape_rhou, lam_in, lam_out, extra, LS);
+    return cudaGetLastError();
+}
+
+}  // namespace ibl

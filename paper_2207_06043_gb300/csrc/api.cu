@@ -16,6 +16,12 @@
 
 using namespace ibl;
 
+// Elements added to every population plane beyond the padded node count
+// (a multiple of 32 keeps every 32-node run 128-byte aligned).
+#ifndef IBL_PLANE_PAD
+#define IBL_PLANE_PAD 0
+#endif
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -76,6 +82,17 @@ struct ibl_ctx {
     std::vector<int> h_counters;
     std::vector<uint32_t> h_status;
     std::string err;
+    // adjoint work buffers and segment graphs, kept between ibl_adjoint calls
+    struct AdjSeg { int parity, len; float* lin; cudaGraphExec_t exec; };
+    struct AdjCache {
+        size_t ck_bytes = 0, tape_steps = 0;
+        char *ck = nullptr, *snap = nullptr;
+        float4* tape_rhou = nullptr;
+        float *tape_dvdq = nullptr, *tape_rho = nullptr, *lamA = nullptr, *lamB = nullptr, *extra = nullptr;
+        uint8_t* near = nullptr;
+        double* acc = nullptr;
+        std::vector<AdjSeg> graphs;
+    } adj;
 };
 
 namespace {
@@ -262,6 +279,18 @@ void layout_tiles(ibl_ctx* ctx) {
 void drop_graphs(ibl_ctx* ctx) {
     for (auto& g : ctx->graph)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto& g : ctx->adj.graphs) cudaGraphExecDestroy(g.exec);
+    ctx->adj.graphs.clear();
+}
+
+void free_adjoint(ibl_ctx* ctx) {
+    auto& A = ctx->adj;
+    for (auto& g : A.graphs) cudaGraphExecDestroy(g.exec);
+    A.graphs.clear();
+    void* ptrs[] = {A.ck, A.snap, A.tape_rhou, A.tape_dvdq, A.tape_rho, A.lamA, A.lamB, A.extra, A.near, A.acc};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    A = ibl_ctx::AdjCache{};
 }
 
 ibl_status validate_member(ibl_ctx* ctx, const MemberHost& M) {
@@ -306,7 +335,7 @@ ibl_status finalize(ibl_ctx* ctx) {
     std::vector<uint8_t> tag_all;
     std::vector<float> face_all;
     std::vector<uint32_t> l_node, l_meta;
-    std::vector<float> l_q;
+    std::vector<float> l_q, l_dq;
     // capsule arrays
     std::vector<CapsuleDev> caps;
     std::vector<int> v_cap, tri_all, hinge_all, e_cap;
@@ -327,7 +356,7 @@ ibl_status finalize(ibl_ctx* ctx) {
         const long long Np = (long long)md.NX * md.NY * md.NZ;
         if (Np * 19 >= (1LL << 31)) return fail(ctx, IBL_ERR_ARG, "lattice too large for one member");
         md.N = (int)Np;
-        md.S = (int)round_up((size_t)Np, 64);
+        md.S = (int)round_up((size_t)Np, 64) + IBL_PLANE_PAD;
         md.f_off = f_off;
         md.node_off = node_off;
         f_off += 19LL * md.S;
@@ -391,6 +420,7 @@ ibl_status finalize(ibl_ctx* ctx) {
             l_node.push_back((uint32_t)pn);
             l_meta.push_back(L.dir | (ok1 ? 32u : 0u) | (ok2 ? 64u : 0u) | ((uint32_t)mi << 8));
             l_q.push_back(L.q);
+            l_dq.push_back(L.dq);
         }
         md.link_count = (int)M.links.size();
         link_off += md.link_count;
@@ -546,11 +576,13 @@ ibl_status finalize(ibl_ctx* ctx) {
     CKS(dev_alloc(ctx, D.l_node, l_node.size()));
     CKS(dev_alloc(ctx, D.l_meta, l_meta.size()));
     CKS(dev_alloc(ctx, D.l_q, l_q.size()));
+    CKS(dev_alloc(ctx, D.l_dq, l_dq.size()));
     CKS(upload(ctx, D.tag, tag_all));
     CKS(upload(ctx, D.face_vel, face_all));
     CKS(upload(ctx, D.l_node, l_node));
     CKS(upload(ctx, D.l_meta, l_meta));
     CKS(upload(ctx, D.l_q, l_q));
+    CKS(upload(ctx, D.l_dq, l_dq));
     CK(cudaMemsetAsync(D.status, 0, sizeof(uint32_t) * nm, ctx->work));
     CK(cudaMemsetAsync(D.status_new, 0, sizeof(uint32_t) * nm, ctx->work));
     CK(cudaMemsetAsync(D.counters, 0, sizeof(int) * nm, ctx->work));
@@ -1148,6 +1180,158 @@ ibl_status ibl_load_state(ibl_ctx* ctx, const void* buf, size_t bytes) {
     return IBL_OK;
 }
 
+ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const ibl_objective* obj,
+                       double* J_out, double* grad_inlet_scale, double* grad_rj) {
+    if (!ctx || !obj) return fail(ctx, IBL_ERR_ARG, "null argument");
+    if (n_steps < 1 || ckpt_every < 1) return fail(ctx, IBL_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+    CKS(finalize(ctx));
+    DevState& D = ctx->dev;
+    if (D.n_members != 1 || D.n_caps != 0 || ctx->storage != IBL_STORAGE_F32)
+        return fail(ctx, IBL_ERR_STATE, "the adjoint covers one FP32 lattice without capsules");
+    const MemberDev& md = ctx->hmem[0];
+    const size_t N = (size_t)md.N, LS = N;
+    const int K = std::min(ckpt_every, n_steps);
+    const int n_ck = (n_steps + K - 1) / K;
+    const std::vector<StateSection> secs = state_sections(ctx);
+    size_t snap_bytes = 0;
+    for (const StateSection& sc : secs) snap_bytes += sc.bytes;
+    // work buffers: allocated by the first call (or a call that needs more
+    // checkpoints or a longer segment) and kept in the context
+    auto& AC = ctx->adj;
+    const size_t ck_need = (size_t)n_ck * D.f_bytes;
+    if (AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc) {
+        cudaStreamSynchronize(ctx->work);
+        free_adjoint(ctx);
+        auto alloc = [&](size_t bytes, void** p) -> ibl_status {
+            const cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+            if (e != cudaSuccess) {
+                *p = nullptr;
+                return fail(ctx, IBL_ERR_OOM, "adjoint buffers: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+            }
+            return IBL_OK;
+        };
+        ibl_status ast = IBL_OK;
+        if (ast == IBL_OK) ast = alloc(ck_need, (void**)&AC.ck);
+        if (ast == IBL_OK) ast = alloc(snap_bytes, (void**)&AC.snap);
+        if (ast == IBL_OK) ast = alloc((size_t)K * N * sizeof(float4), (void**)&AC.tape_rhou);
+        if (ast == IBL_OK) ast = alloc((size_t)K * D.n_links * sizeof(float), (void**)&AC.tape_dvdq);
+        if (ast == IBL_OK) ast = alloc((size_t)K * D.n_face_nodes * sizeof(float), (void**)&AC.tape_rho);
+        if (ast == IBL_OK) ast = alloc(Q * LS * sizeof(float), (void**)&AC.lamA);
+        if (ast == IBL_OK) ast = alloc(Q * LS * sizeof(float), (void**)&AC.lamB);
+        if (ast == IBL_OK) ast = alloc(Q * LS * sizeof(float), (void**)&AC.extra);
+        if (ast == IBL_OK) ast = alloc(N, (void**)&AC.near);
+        if (ast == IBL_OK) ast = alloc(3 * sizeof(double), (void**)&AC.acc);
+        if (ast != IBL_OK) { free_adjoint(ctx); return ast; }
+        AC.ck_bytes = ck_need;
+        AC.tape_steps = (size_t)K;
+    }
+    char *ck = AC.ck, *snap = AC.snap;
+    float4* tape_rhou = AC.tape_rhou;
+    float *tape_dvdq = AC.tape_dvdq, *tape_rho = AC.tape_rho, *lamA = AC.lamA, *lamB = AC.lamB, *extra = AC.extra;
+    uint8_t* near = AC.near;
+    double* acc = AC.acc;   // J, dJ/ds_u, dJ/dr_j
+    auto run = [&]() -> ibl_status {
+        cudaStream_t s = ctx->work;
+        CKS(enter(ctx));
+        CK(cudaMemsetAsync(extra, 0, Q * LS * sizeof(float), s));
+        CK(cudaMemsetAsync(lamA, 0, Q * LS * sizeof(float), s));
+        CK(cudaMemsetAsync(near, 0, N, s));
+        CK(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s));
+        CK(launch_adj_near(D, near, s));
+        const long long t0 = ctx->t;
+        // forward sweep with a checkpoint of the populations every K steps
+        for (int k = 0; k < n_steps; ++k) {
+            if (k % K == 0)
+                CK(cudaMemcpyAsync(ck + (size_t)(k / K) * D.f_bytes, D.f, D.f_bytes, cudaMemcpyDeviceToDevice, s));
+            const int parity = (int)(ctx->t & 1);
+            if (ctx->use_graphs) {
+                CKS(capture_graph(ctx, parity));
+                CK(cudaGraphLaunch(ctx->graph[parity], s));
+            } else {
+                CKS(enqueue_step(ctx, parity, nullptr));
+            }
+            ctx->t += 1;
+        }
+        const int lo[3] = {obj->lo[0], obj->lo[1], obj->lo[2]}, hi[3] = {obj->hi[0], obj->hi[1], obj->hi[2]};
+        CK(launch_adj_objective(D, (int)(ctx->t & 1), lo, hi, obj->d, lamA, LS, acc, s));
+        {   // the final state, put back after the reverse sweep
+            size_t off = 0;
+            for (const StateSection& sc : secs) {
+                if (sc.bytes) CK(cudaMemcpyAsync(snap + off, sc.dev, sc.bytes, cudaMemcpyDeviceToDevice, s));
+                off += sc.bytes;
+            }
+        }
+        // one segment: recompute its steps from the checkpoint writing the tape,
+        // then its adjoint steps backwards; captured once per (start parity,
+        // length, adjoint buffer) as a CUDA graph and replayed
+        std::vector<ibl_ctx::AdjSeg>& graphs = AC.graphs;
+        auto enqueue_segment = [&](int parity0, int len, float* lin0) -> ibl_status {
+            float* li = lin0;
+            float* lo = lin0 == lamA ? lamB : lamA;
+            for (int k = 0; k < len; ++k) {
+                const int parity = (parity0 + k) & 1;
+                CK(launch_lbm(D, parity, s, tape_rhou + (size_t)k * N));
+                CK(launch_bfl(D, parity, s, tape_dvdq + (size_t)k * D.n_links));
+                CK(launch_faces(D, parity, s, tape_rho + (size_t)k * D.n_face_nodes));
+            }
+            for (int k = len - 1; k >= 0; --k) {
+                CK(launch_adj_step(D, tape_rho + (size_t)k * D.n_face_nodes, tape_dvdq + (size_t)k * D.n_links,
+                                   tape_rhou + (size_t)k * N, near, li, lo, extra, LS, acc + 1, acc + 2, s));
+                std::swap(li, lo);
+            }
+            return IBL_OK;
+        };
+        auto run_segment = [&](int parity0, int len, float* lin0) -> ibl_status {
+            for (const ibl_ctx::AdjSeg& g : graphs)
+                if (g.parity == parity0 && g.len == len && g.lin == lin0) {
+                    CK(cudaGraphLaunch(g.exec, s));
+                    return IBL_OK;
+                }
+            cudaGraph_t gr = nullptr;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const ibl_status est = enqueue_segment(parity0, len, lin0);
+            const cudaError_t e = cudaStreamEndCapture(s, &gr);
+            if (est != IBL_OK) { if (gr) cudaGraphDestroy(gr); return est; }
+            CK(e);
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+            cudaGraphDestroy(gr);
+            CK(ei);
+            graphs.push_back({parity0, len, lin0, ex});
+            CK(cudaGraphLaunch(ex, s));
+            return IBL_OK;
+        };
+        float* lin = lamA;
+        ibl_status sst = IBL_OK;
+        for (int seg = n_ck - 1; seg >= 0 && sst == IBL_OK; --seg) {
+            const int s0 = seg * K, s1 = std::min(n_steps, s0 + K);
+            const cudaError_t e = cudaMemcpyAsync(D.f, ck + (size_t)seg * D.f_bytes, D.f_bytes,
+                                                  cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) { sst = fail(ctx, IBL_ERR_CUDA, cudaGetErrorString(e)); break; }
+            sst = run_segment((int)((t0 + s0) & 1), s1 - s0, lin);
+            if ((s1 - s0) & 1) lin = lin == lamA ? lamB : lamA;
+        }
+        CKS(sst);
+        {
+            size_t off = 0;
+            for (const StateSection& sc : secs) {
+                if (sc.bytes) CK(cudaMemcpyAsync(sc.dev, snap + off, sc.bytes, cudaMemcpyDeviceToDevice, s));
+                off += sc.bytes;
+            }
+        }
+        ctx->t = t0 + n_steps;
+        double h[3];
+        CK(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CKS(sync_host_state(ctx));
+        CKS(leave(ctx));
+        if (J_out) *J_out = h[0];
+        if (grad_inlet_scale) *grad_inlet_scale = h[1];
+        if (grad_rj) *grad_rj = h[2];
+        return IBL_OK;
+    };
+    return run();
+}
+
 ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, float* u) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
     if (!rho && !u) return fail(ctx, IBL_ERR_ARG, "null outputs");
@@ -1303,6 +1487,7 @@ void ibl_destroy(ibl_ctx* ctx) {
     if (!ctx) return;
     if (ctx->work) cudaStreamSynchronize(ctx->work);
     drop_graphs(ctx);
+    free_adjoint(ctx);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);

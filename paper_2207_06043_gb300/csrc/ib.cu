@@ -332,105 +332,241 @@ constexpr int PROBE_STRIDE = 8;   // floats per probe record: p, tau xx yy zz xy
 // pivot is small; the marker stencil, which interpolates and spreads, always
 // solves in FP64.  GB300's FP64 pipe is narrow and this kernel's busiest unit.
 constexpr bool PROBE_FAST32 = true;
+#ifndef IB_MARKER_THREADS
+#define IB_MARKER_THREADS 128
+#endif
+#ifndef IB_MARKER_MIN_BLOCKS
+#define IB_MARKER_MIN_BLOCKS 6
+#endif
+#ifndef IB_PROBE_THREADS
+#define IB_PROBE_THREADS 128
+#endif
+#ifndef IB_PROBE_MIN_BLOCKS
+#define IB_PROBE_MIN_BLOCKS 6
+#endif
+#ifndef IBL_MARKER_FAST32
+#define IBL_MARKER_FAST32 1
+#endif
+constexpr bool MARKER_FAST32 = IBL_MARKER_FAST32 != 0;
 
-__global__ void __launch_bounds__(128) k_ib(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag,
-                                            float* __restrict__ fib, const uint32_t* __restrict__ status,
-                                            const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
-                                            const CapsuleSums* __restrict__ sums, const double* __restrict__ x,
-                                            const double* __restrict__ vel, const float* __restrict__ nrm,
-                                            const float* __restrict__ area, float* __restrict__ force,
-                                            float* __restrict__ uv0, float* __restrict__ probe, int n_verts,
-                                            const float4* __restrict__ macro) {
-    // threads [0, M) take the marker stencils, [M, 3M) the probes, so that
-    // whole warps follow one code path
+// The stencils run on groups of GL = 4 consecutive lanes: support node k of
+// a point belongs to lane k % 4 (slot k / 4), so each lane gathers at most 7
+// nodes, the moments and the interpolated sums are combined by shuffles within
+// the group, and every lane of the group holds the same solved rows.  A
+// stencil's latency chain is a quarter of the one-lane form and its registers
+// hold 7 weights instead of 27.
+constexpr int GL = 4;   // lanes per stencil
+constexpr int GS = 7;   // support nodes per lane
+
+struct MlsG {
+    int bx, by, bz;
+    int base;               // padded index of the base node when the block is interior, else -1
+    float ox, oy, oz;       // base node minus point
+    float W[GS];            // weights of this lane's support nodes (k = lane + 4 slot)
+    float inv[4][4];
+    int fallback;           // -1: regular; 0..26: nearest fluid node; 27: none
+};
+
+// The FP64 solve of a near-singular or FP64-only stencil, out of line so that
+// its registers do not count against the common FP32 path.
+struct Moments { float m[10]; };
+struct Rows { float v[4][4]; int good; };
+
+template <int ROWS>
+__device__ __noinline__ Rows ldlt_solve64(Moments mm) {
+    Rows out;
+    double rel;
+    out.good = ldlt_solve<ROWS, double>(mm.m, out.v, rel) ? 1 : 0;
+    return out;
+}
+
+template <int ROWS, bool FAST32>
+__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double X, double Y,
+                                            double Z, int r, unsigned mask, MlsG& M) {
+    M.bx = (int)floor(X + 0.5); M.by = (int)floor(Y + 0.5); M.bz = (int)floor(Z + 0.5);
+    M.ox = (float)((double)M.bx - X); M.oy = (float)((double)M.by - Y); M.oz = (float)((double)M.bz - Z);
+    const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
+                          M.bz <= d.nz - 2;
+    M.base = interior ? (M.bx + d.px) + d.NX * ((M.by + d.py) + d.NY * (M.bz + d.pz)) : -1;
+    float m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    float best = 0.f;
+    int bestk = 27;
+#pragma unroll
+    for (int j = 0; j < GS; ++j) {
+        const int k = r + GL * j;
+        float w = 0.f;
+        if (k < 27) {
+            const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+            const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
+                                      : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
+            const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
+            const float rx = M.ox + dx, ry = M.oy + dy, rz = M.oz + dz;
+            w = mls_weight(fluid, rx, ry, rz);
+            if (w > best) { best = w; bestk = k; }
+            m[0] += w; m[1] += w * rx; m[2] += w * ry; m[3] += w * rz;
+            m[4] += w * rx * rx; m[5] += w * rx * ry; m[6] += w * rx * rz;
+            m[7] += w * ry * ry; m[8] += w * ry * rz; m[9] += w * rz * rz;
+        }
+        M.W[j] = w;
+    }
+#pragma unroll
+    for (int o = 1; o < GL; o <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) m[i] += __shfl_xor_sync(mask, m[i], o);
+        const float ob = __shfl_xor_sync(mask, best, o);
+        const int ok = __shfl_xor_sync(mask, bestk, o);
+        if (ob > best || (ob == best && ok < bestk)) { best = ob; bestk = ok; }   // first k of the largest weight
+    }
+    bool good = false;
+    if (FAST32) {
+        float rel;
+        good = ldlt_solve<ROWS, float>(m, M.inv, rel) && rel >= FP32_PIVOT_FLOOR;
+    }
+    if (!good) {
+        Moments mm;
+#pragma unroll
+        for (int i = 0; i < 10; ++i) mm.m[i] = m[i];
+        const Rows rr = ldlt_solve64<ROWS>(mm);
+        good = rr.good != 0;
+#pragma unroll
+        for (int a = 0; a < ROWS; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) M.inv[a][b] = rr.v[a][b];
+    }
+    M.fallback = good ? -1 : (best > 0.f ? bestk : 27);
+}
+
+__device__ __forceinline__ float mls_row_g(const MlsG& M, int row, int j, int k) {
+    const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
+    return M.W[j] * (M.inv[row][0] + M.inv[row][1] * rx + M.inv[row][2] * ry + M.inv[row][3] * rz);
+}
+
+__device__ __forceinline__ int mls_node_g(const MemberDev& d, const MlsG& M, int k) {
+    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    return M.base >= 0 ? M.base + dx + d.NX * (dy + d.NY * dz) : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
+}
+
+__device__ __forceinline__ float group_sum(float v, unsigned mask) {
+#pragma unroll
+    for (int o = 1; o < GL; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(IB_MARKER_THREADS, IB_MARKER_MIN_BLOCKS)
+k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float* __restrict__ fib,
+             const uint32_t* __restrict__ status, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
+             const CapsuleSums* __restrict__ sums, const double* __restrict__ x, const double* __restrict__ vel,
+             const float* __restrict__ area, float* __restrict__ uv0, float* __restrict__ probe, int n_verts,
+             const float4* __restrict__ macro) {
+    // four lanes per marker
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int l = t < n_verts ? t : (t - n_verts) >> 1;
-    const int s = t < n_verts ? 0 : 1 + ((t - n_verts) & 1);
-    if (l >= n_verts) return;
+    const int r = t & (GL - 1);
+    const int l = min(t / GL, n_verts - 1);
     const int cap = v_cap[l];
     const CapsuleDev& C = caps[cap];
     const int m = C.member;
-    if (status[m] & STOP) return;
+    const bool valid = t / GL < n_verts && !(status[m] & STOP);
+    const unsigned mask = __ballot_sync(FULL, valid);   // whole groups: validity is shared by a group
+    if (!valid) return;
     const MemberDev& d = mem[m];
-    const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
-    const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
-    Mls M;
-    if (s == 0) {
-        mls_build<1, false>(d, tag, X, Y, Z, M);
-        float Ux = 0.f, Uy = 0.f, Uz = 0.f;
+    MlsG M;
+    mls_build_g<1, MARKER_FAST32>(d, tag, x[3 * l], x[3 * l + 1], x[3 * l + 2], r, mask, M);
+    float p[GS];
+    float4 q[GS];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float p[9];
-            float4 q[9];
+    for (int j = 0; j < GS; ++j) {
+        const int k = r + GL * j;
+        p[j] = k >= 27 ? 0.f : (M.fallback < 0 ? mls_row_g(M, 0, j, k) : (M.fallback == k ? 1.f : 0.f));
+        q[j] = p[j] != 0.f ? macro[d.node_off + mls_node_g(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float Ux = 0.f, Uy = 0.f, Uz = 0.f;
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const int k = 9 * c + j;
-                p[j] = M.fallback < 0 ? mls_row(M, 0, k) : (M.fallback == k ? 1.f : 0.f);
-                q[j] = p[j] != 0.f ? macro[d.node_off + mls_node(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+    for (int j = 0; j < GS; ++j) {
+        Ux += p[j] * q[j].y; Uy += p[j] * q[j].z; Uz += p[j] * q[j].w;
+    }
+    Ux = group_sum(Ux, mask);
+    Uy = group_sum(Uy, mask);
+    Uz = group_sum(Uz, mask);
+    const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
+    const float A = area[l];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                Ux += p[j] * q[j].y; Uy += p[j] * q[j].z; Uz += p[j] * q[j].w;
-            }
+    for (int j = 0; j < GS; ++j) {
+        if (p[j] != 0.f) {
+            const float c = A * p[j];
+            const size_t gi = (size_t)d.node_off + mls_node_g(d, M, r + GL * j);
+            float* f3 = fib + 3 * gi;
+            atomicAdd(f3, c * Fx);
+            atomicAdd(f3 + 1, c * Fy);
+            atomicAdd(f3 + 2, c * Fz);
+            tag[gi] = TAG_IB;   // fluid node: its tag byte was 0 or TAG_IB
         }
-        const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
-        const float A = area[l];
-#pragma unroll
-        for (int k = 0; k < 27; ++k) {
-            const float p = M.fallback < 0 ? mls_row(M, 0, k) : (M.fallback == k ? 1.f : 0.f);
-            if (p != 0.f) {
-                const float c = A * p;
-                const size_t gi = (size_t)d.node_off + mls_node(d, M, k);
-                float* f3 = fib + 3 * gi;
-                atomicAdd(f3, c * Fx);
-                atomicAdd(f3 + 1, c * Fy);
-                atomicAdd(f3 + 2, c * Fz);
-                tag[gi] = TAG_IB;   // fluid node: its tag byte was 0 or TAG_IB
-            }
-        }
+    }
+    if (r == 0) {
         uv0[3 * l] = Ux; uv0[3 * l + 1] = Uy; uv0[3 * l + 2] = Uz;
         // volume penalty magnitude k_v (1 - V/V0) A, kept in the spare slot of
         // the + probe record; the update adds it along n
         float kvol = 0.f;
         if (!C.rigid) kvol = (float)(C.kv * (1.0 - sums[cap].V * C.inv_V0)) * A;
         probe[(size_t)2 * l * PROBE_STRIDE + 7] = kvol;
-    } else {
-        const double sg = s == 1 ? 1.2 : -1.2;
-        mls_build<4, PROBE_FAST32>(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, M);
-        float rP = 0.f, G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float4 q[9];
-#pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const int k = 9 * c + j;
-                q[j] = M.W[k] > 0.f ? macro[d.node_off + mls_node(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const int k = 9 * c + j;
-                if (M.fallback < 0) {
-                    const float p = mls_row(M, 0, k), g0 = mls_row(M, 1, k), g1 = mls_row(M, 2, k),
-                                g2 = mls_row(M, 3, k);
-                    rP += p * q[j].x;
-                    G[0][0] += g0 * q[j].y; G[0][1] += g1 * q[j].y; G[0][2] += g2 * q[j].y;
-                    G[1][0] += g0 * q[j].z; G[1][1] += g1 * q[j].z; G[1][2] += g2 * q[j].z;
-                    G[2][0] += g0 * q[j].w; G[2][1] += g1 * q[j].w; G[2][2] += g2 * q[j].w;
-                } else if (M.fallback == k) {
-                    rP += q[j].x;
-                }
-            }
-        }
-        const float mu = rP * d.nu;
-        float* rec = probe + ((size_t)2 * l + (s - 1)) * PROBE_STRIDE;
-        rec[0] = rP * (1.f / 3.f);
-        rec[1] = mu * 2.f * G[0][0];
-        rec[2] = mu * 2.f * G[1][1];
-        rec[3] = mu * 2.f * G[2][2];
-        rec[4] = mu * (G[0][1] + G[1][0]);
-        rec[5] = mu * (G[0][2] + G[2][0]);
-        rec[6] = mu * (G[1][2] + G[2][1]);
     }
+}
+
+__global__ void __launch_bounds__(IB_PROBE_THREADS, IB_PROBE_MIN_BLOCKS)
+k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, const uint32_t* __restrict__ status,
+            const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps, const double* __restrict__ x,
+            const float* __restrict__ nrm, float* __restrict__ probe, int n_verts,
+            const float4* __restrict__ macro) {
+    // four lanes per probe, two probes per marker: x + 1.2 n (s = 1), x - 1.2 n (s = 2)
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = t & (GL - 1);
+    const int sid = t / GL;
+    const int l = min(sid >> 1, n_verts - 1);
+    const int s = 1 + (sid & 1);
+    const int m = caps[v_cap[l]].member;
+    const bool valid = (sid >> 1) < n_verts && !(status[m] & STOP);
+    const unsigned mask = __ballot_sync(FULL, valid);
+    if (!valid) return;
+    const MemberDev& d = mem[m];
+    const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
+    const double sg = s == 1 ? 1.2 : -1.2;
+    MlsG M;
+    mls_build_g<4, PROBE_FAST32>(d, tag, x[3 * l] + sg * nx, x[3 * l + 1] + sg * ny, x[3 * l + 2] + sg * nz, r,
+                                 mask, M);
+    float4 q[GS];
+#pragma unroll
+    for (int j = 0; j < GS; ++j) {
+        const int k = r + GL * j;
+        q[j] = (k < 27 && M.W[j] > 0.f) ? macro[d.node_off + mls_node_g(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // rho, then grad u row-major
+#pragma unroll
+    for (int j = 0; j < GS; ++j) {
+        const int k = r + GL * j;
+        if (k >= 27) continue;
+        if (M.fallback < 0) {
+            const float p = mls_row_g(M, 0, j, k), g0 = mls_row_g(M, 1, j, k), g1 = mls_row_g(M, 2, j, k),
+                        g2 = mls_row_g(M, 3, j, k);
+            acc[0] += p * q[j].x;
+            acc[1] += g0 * q[j].y; acc[2] += g1 * q[j].y; acc[3] += g2 * q[j].y;
+            acc[4] += g0 * q[j].z; acc[5] += g1 * q[j].z; acc[6] += g2 * q[j].z;
+            acc[7] += g0 * q[j].w; acc[8] += g1 * q[j].w; acc[9] += g2 * q[j].w;
+        } else if (M.fallback == k) {
+            acc[0] += q[j].x;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 10; ++i) acc[i] = group_sum(acc[i], mask);
+    if (r != 0) return;
+    const float rP = acc[0];
+    const float mu = rP * d.nu;
+    float* rec = probe + ((size_t)2 * l + (s - 1)) * PROBE_STRIDE;
+    rec[0] = rP * (1.f / 3.f);
+    rec[1] = mu * 2.f * acc[1];
+    rec[2] = mu * 2.f * acc[5];
+    rec[3] = mu * 2.f * acc[9];
+    rec[4] = mu * (acc[2] + acc[4]);
+    rec[5] = mu * (acc[3] + acc[7]);
+    rec[6] = mu * (acc[6] + acc[8]);
 }
 
 // F_p + F_tau of vertex v from its two probe records (Eqs. hydroForP,
@@ -726,10 +862,13 @@ template <typename T>
 static cudaError_t ib_t(const DevState& d, int parity, cudaStream_t s) {
     k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.status, d.caps, d.sums,
                                                        d.macro, parity);
-    const long long threads = 3LL * d.n_verts;
-    k_ib<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d.mem, d.tag, d.fib, d.status, d.v_cap, d.caps, d.sums, d.x,
-                                                           d.vel, d.nrm, d.area, d.force, d.uv0, d.probe, d.n_verts,
-                                                           d.macro);
+    const long long mt = (long long)GL * d.n_verts;
+    k_ib_markers<<<(unsigned)((mt + IB_MARKER_THREADS - 1) / IB_MARKER_THREADS), IB_MARKER_THREADS, 0, s>>>(
+        d.mem, d.tag, d.fib, d.status, d.v_cap, d.caps, d.sums, d.x, d.vel, d.area, d.uv0, d.probe, d.n_verts,
+        d.macro);
+    const long long pt = 2LL * GL * d.n_verts;
+    k_ib_probes<<<(unsigned)((pt + IB_PROBE_THREADS - 1) / IB_PROBE_THREADS), IB_PROBE_THREADS, 0, s>>>(
+        d.mem, d.tag, d.status, d.v_cap, d.caps, d.x, d.nrm, d.probe, d.n_verts, d.macro);
     return cudaGetLastError();
 }
 

@@ -142,6 +142,7 @@ struct DevState {
     uint32_t* l_node = nullptr;      // padded node of the link
     uint32_t* l_meta = nullptr;      // dir | ok1 << 5 | ok2 << 6 | member << 8
     float* l_q = nullptr;
+    float* l_dq = nullptr;           // dq / d(junction radius) per link (adjoint input)
 
     int n_caps = 0, n_verts = 0, n_tris = 0, n_edges = 0;
     int any_soft = 0, any_rigid = 0, any_cells = 0, max_nv = 0;
@@ -172,13 +173,25 @@ struct DevState {
 constexpr int CELL_CAP = 32;
 
 
-cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s);
-cudaError_t launch_faces(const DevState& d, int parity_done, cudaStream_t s);
+// The optional tape pointers record, per step, what the discrete adjoint needs
+// from the forward state: (rho, u) of every fluid node before the collision
+// (float4 per padded node), d(value)/dq of every wall link, rho of every face
+// node before the face rule.  Null in ordinary steps.
+cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou = nullptr);
+cudaError_t launch_faces(const DevState& d, int parity_done, cudaStream_t s, float* tape_rho = nullptr);
 int lbm_max_threads();   // block-size bound the lattice kernel was compiled for
-cudaError_t launch_bfl(const DevState& d, int parity_done, cudaStream_t s);
+cudaError_t launch_bfl(const DevState& d, int parity_done, cudaStream_t s, float* tape_dvdq = nullptr);
 cudaError_t launch_init_member(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s);
 cudaError_t launch_read(const DevState& d, int member, int parity, float* rho, float* u,
                         float* g, cudaStream_t s);
+
+// discrete adjoint of the lattice step (adjoint.cu)
+cudaError_t launch_adj_near(const DevState& d, uint8_t* near, cudaStream_t s);
+cudaError_t launch_adj_objective(const DevState& d, int parity, const int lo[3], const int hi[3], const double w[3],
+                                 float* lam, size_t LS, double* J, cudaStream_t s);
+cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const float* tape_dvdq, const float4* tape_rhou,
+                            const uint8_t* near, float* lam_in, float* lam_out, float* extra, size_t LS,
+                            double* grad_s, double* grad_q, cudaStream_t s);
 
 cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s);
 cudaError_t launch_ib(const DevState& d, int parity, cudaStream_t s);

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(LBM_THREADS, BORDER ? 4 : LBM_MIN_BLOCKS)
 k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T* __restrict__ f,
       uint8_t* __restrict__ tag, float* __restrict__ fib, const float* __restrict__ face_vel,
       const uint32_t* __restrict__ status, const uint32_t* __restrict__ segs, int n_mem, int n_segs, int n_blocks,
-      int parity) {
+      int parity, float4* __restrict__ tape) {
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int b = blockIdx.x; b < n_blocks; b += gridDim.x) {
         const int si = b * warps + (threadIdx.x >> 5);
@@ -102,6 +102,12 @@ k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T
             p[0] = 0.f; p[1] = 0.f; p[2] = 0.f;
             tag[gn] = tg & (uint8_t)~TAG_IB;
             hasF = true;
+        }
+        if (tape) {
+            float rho, ux, uy, uz;
+            moments_of(g, rho, ux, uy, uz);
+            const float ir = __frcp_rn(rho);
+            tape[gn] = make_float4(rho, ux + 0.5f * Fx * ir, uy + 0.5f * Fy * ir, uz + 0.5f * Fz * ir);
         }
         collide(g, d.omega, d.guo, Fx, Fy, Fz, hasF);
         if (BORDER) store_post<T>(d, fm, n, X, Y, Z, parity, g);
@@ -203,7 +209,8 @@ k_lbm_async(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, T* __restrict__ f, const uint32_t* __restrict__ l_node,
                                              const uint32_t* __restrict__ l_meta, const float* __restrict__ l_q,
-                                             const uint32_t* __restrict__ status, int n_links, int pp) {
+                                             const uint32_t* __restrict__ status, int n_links, int pp,
+                                             float* __restrict__ tape_dvdq) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n_links) return;
     const uint32_t meta = l_meta[l];
@@ -256,6 +263,20 @@ __global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, 
         if (ok1) v = fi_b / (q * (2.f * q + 1.f)) + (2.f * q - 1.f) / q * fib_b + (1.f - 2.f * q) / (1.f + 2.f * q) * fib_1;
         else v = fi_b / (2.f * q) + (2.f * q - 1.f) / (2.f * q) * fib_b;
     }
+    if (tape_dvdq) {
+        // d v / d q of the rule just applied (the derivative of each branch in q)
+        float dv;
+        if (q < 0.5f) {
+            if (ok1 && ok2) dv = (4.f * q + 1.f) * fi_b - 8.f * q * fi_1 - (1.f - 4.f * q) * fi_2;
+            else if (ok1) dv = 2.f * (fi_b - fi_1);
+            else dv = 0.f;
+        } else {
+            const float a = q * (2.f * q + 1.f);
+            if (ok1) dv = -(4.f * q + 1.f) / (a * a) * fi_b + fib_b / (q * q) - 4.f / ((1.f + 2.f * q) * (1.f + 2.f * q)) * fib_1;
+            else dv = (fib_b - fi_b) / (2.f * q * q);
+        }
+        tape_dvdq[l] = dv;
+    }
     if (pp == 0) Store<T>::st(fm + i * S + xsN, v, d.st_scale);   // next step odd: read from n - e_ib
     else Store<T>::st(fm + ib * S + xb, v, d.st_scale);           // next step even: own slot
 }
@@ -272,7 +293,7 @@ __global__ void __launch_bounds__(256) k_faces(const MemberDev* __restrict__ mem
                                                const uint32_t* __restrict__ fc_node,
                                                const uint32_t* __restrict__ fc_meta,
                                                const float* __restrict__ face_vel, const uint32_t* __restrict__ status,
-                                               int n_face_nodes, int pp) {
+                                               int n_face_nodes, int pp, float* __restrict__ tape_rho) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_face_nodes) return;
     const uint32_t meta = fc_meta[i];
@@ -286,10 +307,26 @@ __global__ void __launch_bounds__(256) k_faces(const MemberDev* __restrict__ mem
     const int parity = 1 - pp;
     float g[Q];
     load_pre<T>(d, fm, n, X, Y, Z, parity, g);
-    apply_face(d, X, Y, Z, face_vel, g);
     const int nx = fc == 0 ? -1 : (fc == 1 ? 1 : 0);
     const int ny = fc == 2 ? -1 : (fc == 3 ? 1 : 0);
     const int nz = fc == 4 ? -1 : (fc == 5 ? 1 : 0);
+    if (tape_rho) {
+        // rho of the face rule: (1 + Sg) / (1 + u.n) on a velocity face, the
+        // imposed density on a pressure face
+        float Sg = 0.f;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int en = ex(k) * nx + ey(k) * ny + ez(k) * nz;
+            Sg += (en == 0 ? 1.f : (en > 0 ? 2.f : 0.f)) * g[k];
+        }
+        float rho = d.face_rho[fc];
+        if (d.face_kind[fc] == FACE_VELOCITY) {
+            const float* u = face_vel + 3 * (d.face_off[fc] + face_index(d, fc, X, Y, Z));
+            rho = (1.f + Sg) / (1.f + (u[0] * nx + u[1] * ny + u[2] * nz));
+        }
+        tape_rho[i] = rho;
+    }
+    apply_face(d, X, Y, Z, face_vel, g);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         if (ex(k) * nx + ey(k) * ny + ez(k) * nz < 0)
@@ -298,18 +335,18 @@ __global__ void __launch_bounds__(256) k_faces(const MemberDev* __restrict__ mem
 }
 
 template <typename T>
-static cudaError_t faces_t(const DevState& d, int pp, cudaStream_t s) {
+static cudaError_t faces_t(const DevState& d, int pp, cudaStream_t s, float* tape) {
     if (d.n_face_nodes == 0) return cudaSuccess;
     k_faces<T><<<(d.n_face_nodes + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.fc_node, d.fc_meta, d.face_vel,
-                                                             d.status, d.n_face_nodes, pp);
+                                                             d.status, d.n_face_nodes, pp, tape);
     return cudaGetLastError();
 }
 
-cudaError_t launch_faces(const DevState& d, int pp, cudaStream_t s) {
+cudaError_t launch_faces(const DevState& d, int pp, cudaStream_t s, float* tape_rho) {
     switch (d.storage) {
-        case 1: return faces_t<__half>(d, pp, s);
-        case 2: return faces_t<__nv_bfloat16>(d, pp, s);
-        default: return faces_t<float>(d, pp, s);
+        case 1: return faces_t<__half>(d, pp, s, tape_rho);
+        case 2: return faces_t<__nv_bfloat16>(d, pp, s, tape_rho);
+        default: return faces_t<float>(d, pp, s, tape_rho);
     }
 }
 
@@ -385,10 +422,10 @@ __global__ void k_read(const MemberDev* __restrict__ mem, const T* __restrict__ 
 }
 
 template <typename T>
-static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s) {
+static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s, float4* tape) {
     const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.lbm_blocks;
     const bool one = d.n_members == 1;
-    if (LBM_ASYNC && std::is_same<T, float>::value && d.lbm_blocks > 0) {
+    if (LBM_ASYNC && !tape && std::is_same<T, float>::value && d.lbm_blocks > 0) {
         const int ag = std::min(d.lbm_blocks, (d.grid_lbm > 0 ? d.grid_lbm : LBMA_MIN_BLOCKS * d.n_sm));
         const size_t smem = 2 * Q * sizeof(float) * (size_t)d.threads;
         if (one)
@@ -401,47 +438,48 @@ static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s) {
         if (one)
             k_lbm<T, true, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
                                                              d.status, d.segs, d.n_members, d.n_segs, d.lbm_blocks,
-                                                             parity);
+                                                             parity, tape);
         else
             k_lbm<T, false, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
                                                               d.status, d.segs, d.n_members, d.n_segs, d.lbm_blocks,
-                                                              parity);
+                                                              parity, tape);
     }
     if (d.lbm_bblocks > 0) {
         if (one)
             k_lbm<T, true, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
                                                                      d.face_vel, d.status, d.bsegs, d.n_members,
-                                                                     d.n_bsegs, d.lbm_bblocks, parity);
+                                                                     d.n_bsegs, d.lbm_bblocks, parity, tape);
         else
             k_lbm<T, false, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
                                                                       d.face_vel, d.status, d.bsegs, d.n_members,
-                                                                      d.n_bsegs, d.lbm_bblocks, parity);
+                                                                      d.n_bsegs, d.lbm_bblocks, parity, tape);
     }
     return cudaGetLastError();
 }
 
 int lbm_max_threads() { return LBM_THREADS; }
 
-cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s) {
+cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou) {
     switch (d.storage) {
-        case 1: return lbm_t<__half>(d, parity, s);
-        case 2: return lbm_t<__nv_bfloat16>(d, parity, s);
-        default: return lbm_t<float>(d, parity, s);
+        case 1: return lbm_t<__half>(d, parity, s, tape_rhou);
+        case 2: return lbm_t<__nv_bfloat16>(d, parity, s, tape_rhou);
+        default: return lbm_t<float>(d, parity, s, tape_rhou);
     }
 }
 
 template <typename T>
-static cudaError_t bfl_t(const DevState& d, int pp, cudaStream_t s) {
+static cudaError_t bfl_t(const DevState& d, int pp, cudaStream_t s, float* tape) {
     if (d.n_links == 0) return cudaSuccess;
-    k_bfl<T><<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.l_node, d.l_meta, d.l_q, d.status, d.n_links, pp);
+    k_bfl<T><<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.l_node, d.l_meta, d.l_q, d.status, d.n_links, pp,
+                                                     tape);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bfl(const DevState& d, int pp, cudaStream_t s) {
+cudaError_t launch_bfl(const DevState& d, int pp, cudaStream_t s, float* tape_dvdq) {
     switch (d.storage) {
-        case 1: return bfl_t<__half>(d, pp, s);
-        case 2: return bfl_t<__nv_bfloat16>(d, pp, s);
-        default: return bfl_t<float>(d, pp, s);
+        case 1: return bfl_t<__half>(d, pp, s, tape_dvdq);
+        case 2: return bfl_t<__nv_bfloat16>(d, pp, s, tape_dvdq);
+        default: return bfl_t<float>(d, pp, s, tape_dvdq);
     }
 }
 
