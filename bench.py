@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage side measurements")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-ckpt", type=int, default=100)
     ap.add_argument("--threads", type=int, default=256)
@@ -277,6 +278,8 @@ def main():
         out["e2e"] = e2e_run(case, args)
     if rank == 0 and not args.no_adjoint:
         out["adjoint"] = adjoint_measure(args, case)
+    if rank == 0 and not args.no_variants and args.storage == "f32":
+        out["storage_variants"] = storage_variants(case, nf)
     if rank == 0 and not args.no_cpu:
         sample = cpu_sample_case(case)
         dt, nfs = run_oracle(sample, args.cpu_steps)
@@ -288,6 +291,38 @@ def main():
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def storage_variants(case, nf, steps=100):
+    """The same workload with f - w stored as FP16 (scaled by 2^12) or BF16,
+    FP32 arithmetic: whole-step MLUPS (graph replay) and the lattice kernel's
+    fraction of the HBM roofline at 76 B per fluid-node update."""
+    import torch
+    from paper_2207_06043_gb300 import workloads as W
+    peak, kind = load_peaks()
+    out = {}
+    stream = torch.cuda.current_stream()
+    for st in ("f16", "bf16"):
+        s = W.make_solver(case, storage=st)
+        s.step(5)
+        s.enable_timing(True)
+        s.step(steps)
+        lat = s.kernel_times()["lattice"] / steps
+        s.enable_timing(False)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        s.close()
+        ach = BYTES_PER_UPDATE[st] * nf / (lat * 1e-3) / 1e9
+        out[st] = {"value": nf / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
+                   "lattice_ms": lat, "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                                   "frac": ach / peak, "peak_source": f"{kind} hbm_gbs"}}
+    return out
 
 
 def _adjoint_run(c, n, K, lo, hi):

@@ -212,16 +212,21 @@ __global__ void __launch_bounds__(256) k_adj_step(const MemberDev* __restrict__ 
     node_coords(d, n, X, Y, Z);
     const Nbr b = neighbours(d, X, Y, Z);
     const bool nr = near[n] != 0;
+    // every neighbour index is in range (ghost layer / wrap), so all 19 loads
+    // are issued at once and the solid ones are discarded afterwards
     float ls[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         const int m = b.xs[1 + ex(k)] + d.NX * (b.ys[1 + ey(k)] + d.NY * b.zs[1 + ez(k)]);
-        float v = (tag[m] & TAG_SOLID) ? 0.f : lam_in[k * LS + m];
-        if (nr) {
-            v += extra[k * LS + n];
+        const float v = lam_in[k * LS + m];
+        ls[k] = (tag[m] & TAG_SOLID) ? 0.f : v;
+    }
+    if (nr) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            ls[k] += extra[k * LS + n];
             extra[k * LS + n] = 0.f;
         }
-        ls[k] = v;
     }
     const float4 t = tape[n];
     const float rho = t.x, ux = t.y, uy = t.z, uz = t.w;

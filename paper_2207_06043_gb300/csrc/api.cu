@@ -589,15 +589,15 @@ ibl_status finalize(ibl_ctx* ctx) {
     D.n_caps = cap_off; D.n_verts = vert_off; D.n_tris = tri_off; D.n_edges = edge_off;
     D.any_soft = any_soft; D.any_rigid = any_rigid; D.any_cells = any_cells; D.max_nv = max_nv;
     if (cap_off > 0) {
-        CKS(dev_alloc(ctx, D.fib, 3 * (size_t)node_off));
-        CK(cudaMemsetAsync(D.fib, 0, sizeof(float) * 3 * (size_t)node_off, ctx->work));
+        CKS(dev_alloc(ctx, D.fib, 4 * (size_t)node_off));
+        CK(cudaMemsetAsync(D.fib, 0, sizeof(float) * 4 * (size_t)node_off, ctx->work));
         CKS(dev_alloc(ctx, D.caps, caps.size()));
         CKS(dev_alloc(ctx, D.sums, caps.size()));
         CKS(dev_alloc(ctx, D.v_cap, v_cap.size()));
         CKS(dev_alloc(ctx, D.x, x_all.size()));
         CKS(dev_alloc(ctx, D.x_prev, x_all.size()));
         CKS(dev_alloc(ctx, D.vel, vel_all.size()));
-        CKS(dev_alloc(ctx, D.force, x_all.size()));
+        CKS(dev_alloc(ctx, D.force, 4 * (x_all.size() / 3)));
         CKS(dev_alloc(ctx, D.uv0, x_all.size()));
         CKS(dev_alloc(ctx, D.nrm, x_all.size()));
         CKS(dev_alloc(ctx, D.area, (size_t)vert_off));
@@ -619,7 +619,7 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(upload(ctx, D.x, x_all));
         CKS(upload(ctx, D.x_prev, x_all));
         CKS(upload(ctx, D.vel, vel_all));
-        CK(cudaMemsetAsync(D.force, 0, sizeof(float) * x_all.size(), ctx->work));
+        CK(cudaMemsetAsync(D.force, 0, sizeof(float) * 4 * (x_all.size() / 3), ctx->work));
         CK(cudaMemsetAsync(D.uv0, 0, sizeof(float) * x_all.size(), ctx->work));
         CKS(upload(ctx, D.tri, tri_all));
         CKS(upload(ctx, D.hinge, hinge_all));
@@ -1097,14 +1097,18 @@ ibl_status ibl_read_capsule_state(ibl_ctx* ctx, int32_t id, double* x, double* x
     const CapsuleRestHost& R = ctx->rest[ctx->member_caps[0][id]];
     const size_t n3 = 3 * (size_t)R.nv, off = 3 * (size_t)R.v_begin;
     CKS(enter(ctx));
-    std::vector<float> F(n3);
+    std::vector<float> F(4 * (size_t)R.nv);
     if (x) CK(cudaMemcpyAsync(x, ctx->dev.x + off, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->work));
     if (x_prev) CK(cudaMemcpyAsync(x_prev, ctx->dev.x_prev + off, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->work));
     if (vel) CK(cudaMemcpyAsync(vel, ctx->dev.vel + off, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->work));
-    if (force) CK(cudaMemcpyAsync(F.data(), ctx->dev.force + off, sizeof(float) * n3, cudaMemcpyDeviceToHost, ctx->work));
+    if (force)
+        CK(cudaMemcpyAsync(F.data(), ctx->dev.force + 4 * (size_t)R.v_begin, sizeof(float) * F.size(),
+                           cudaMemcpyDeviceToHost, ctx->work));
     CK(cudaStreamSynchronize(ctx->work));
     CKS(leave(ctx));
-    if (force) for (size_t i = 0; i < n3; ++i) force[i] = F[i];
+    if (force)
+        for (size_t v = 0; v < (size_t)R.nv; ++v)
+            for (int a = 0; a < 3; ++a) force[3 * v + a] = F[4 * v + a];
     return IBL_OK;
 }
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ void node_state(const MemberDev& d, const T* __restri
 // ---------------------------------------------------------------------------
 // Per-capsule geometry at x(t), spread over GEO_BLOCKS blocks per capsule:
 // per triangle, the area-weighted normal and a third of the area go to its
-// vertices (float atomics into vacc); the enclosed volume (divergence theorem,
+// vertices (float4 atomics into vacc); the enclosed volume (divergence theorem,
 // tetrahedra fanned from the capsule's first vertex) is summed in FP64.  Then
 // per vertex: A_v = 1/3 sum of adjacent triangle areas, n_v = normalised
 // area-weighted sum of adjacent normals, the integer bounding box, and vacc
@@ -81,15 +81,10 @@ __global__ void __launch_bounds__(256) k_geom_tri(const CapsuleDev* __restrict__
         const float vx = (float)(cx - ax), vy = (float)(cy - ay), vz = (float)(cz - az);
         const float Nx = uy * vz - uz * vy, Ny = uz * vx - ux * vz, Nz = ux * vy - uy * vx;
         const float a3 = sqrtf(Nx * Nx + Ny * Ny + Nz * Nz) * (1.f / 6.f);
-        const int ids[3] = {ia, ib, ic};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float* p = (float*)(vacc + ids[j]);
-            atomicAdd(p, 0.5f * Nx);
-            atomicAdd(p + 1, 0.5f * Ny);
-            atomicAdd(p + 2, 0.5f * Nz);
-            atomicAdd(p + 3, a3);
-        }
+        const float4 contrib = make_float4(0.5f * Nx, 0.5f * Ny, 0.5f * Nz, a3);
+        atomicAdd(vacc + ia, contrib);   // vector reductions, one per vertex of the triangle
+        atomicAdd(vacc + ib, contrib);
+        atomicAdd(vacc + ic, contrib);
     }
     const double s = block_sum_d(vol, red);
     if (threadIdx.x == 0) atomicAdd(&sums[c].V, s);
@@ -494,10 +489,8 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
         if (p[j] != 0.f) {
             const float c = A * p[j];
             const size_t gi = (size_t)d.node_off + mls_node_g(d, M, r + GL * j);
-            float* f3 = fib + 3 * gi;
-            atomicAdd(f3, c * Fx);
-            atomicAdd(f3 + 1, c * Fy);
-            atomicAdd(f3 + 2, c * Fz);
+            // one vector reduction per support node (f_ib is padded to float4)
+            atomicAdd(reinterpret_cast<float4*>(fib) + gi, make_float4(c * Fx, c * Fy, c * Fz, 0.f));
             tag[gi] = TAG_IB;   // fluid node: its tag byte was 0 or TAG_IB
         }
     }
@@ -598,8 +591,9 @@ __device__ __forceinline__ f3 sub(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.
 __device__ __forceinline__ f3 crs(f3 a, f3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
 __device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ f3 scl(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+// one vector reduction per vertex (the force array is padded to float4)
 __device__ __forceinline__ void add_force(float* F, int v, f3 a) {
-    atomicAdd(F + 3 * v, a.x); atomicAdd(F + 3 * v + 1, a.y); atomicAdd(F + 3 * v + 2, a.z);
+    atomicAdd(reinterpret_cast<float4*>(F) + v, make_float4(a.x, a.y, a.z, 0.f));
 }
 
 __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, const int* __restrict__ e_cap,
@@ -709,9 +703,9 @@ __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __rest
             }
     if (acc > 0.f) {
         const float c = d.umax * (1.f / (8.f * 1.41421356237f)) * acc;
-        force[3 * i] -= c * nrm[3 * i];
-        force[3 * i + 1] -= c * nrm[3 * i + 1];
-        force[3 * i + 2] -= c * nrm[3 * i + 2];
+        force[4 * i] -= c * nrm[3 * i];
+        force[4 * i + 1] -= c * nrm[3 * i + 1];
+        force[4 * i + 2] -= c * nrm[3 * i + 2];
     }
 }
 
@@ -740,8 +734,8 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double acc = ((double)force[3 * v + a] + (double)H[a]) * half_inv_m;
-        force[3 * v + a] = 0.f;
+        const double acc = ((double)force[4 * v + a] + (double)H[a]) * half_inv_m;
+        force[4 * v + a] = 0.f;
         const double xt = x[3 * v + a];
         const double xp = xt + (double)uv0[3 * v + a] + acc;
         const double un = 1.5 * xp - 2.0 * xt + 0.5 * x_prev[3 * v + a];
@@ -769,9 +763,9 @@ __global__ void __launch_bounds__(256) k_rigid(CapsuleDev* __restrict__ caps, co
     for (int v = vb + threadIdx.x; v < vb + nv; v += blockDim.x) {
         float H[3];
         hydro_force(probe, nrm, area, v, H[0], H[1], H[2]);
-        const double fx = (double)force[3 * v] + H[0], fy = (double)force[3 * v + 1] + H[1],
-                     fz = (double)force[3 * v + 2] + H[2];
-        force[3 * v] = 0.f; force[3 * v + 1] = 0.f; force[3 * v + 2] = 0.f;
+        const double fx = (double)force[4 * v] + H[0], fy = (double)force[4 * v + 1] + H[1],
+                     fz = (double)force[4 * v + 2] + H[2];
+        force[4 * v] = 0.f; force[4 * v + 1] = 0.f; force[4 * v + 2] = 0.f;
         const double rx = x[3 * v] - xc0, ry = x[3 * v + 1] - xc1, rz = x[3 * v + 2] - xc2;
         s[0] += fx; s[1] += fy; s[2] += fz;
         s[3] += ry * fz - rz * fy; s[4] += rz * fx - rx * fz; s[5] += rx * fy - ry * fx;

@@ -128,7 +128,7 @@ struct DevState {
     void* f = nullptr;               // 19 planes per member, f - w
     size_t f_bytes = 0;
     uint8_t* tag = nullptr;          // per padded node
-    float* fib = nullptr;            // 3 per padded node, zero outside the IB shell
+    float* fib = nullptr;            // float4 (x, y, z, pad) per padded node, zero outside the IB shell
     float* face_vel = nullptr;       // float3 per face node of velocity faces
     uint32_t* status = nullptr;      // per member, constant during a step
     uint32_t* status_new = nullptr;  // flags raised during a step, merged at the next step begin
@@ -152,7 +152,7 @@ struct DevState {
     double* x = nullptr;             // 3 per vertex
     double* x_prev = nullptr;
     double* vel = nullptr;
-    float* force = nullptr;          // 3 per vertex: hinge + repulsion forces, cleared by the update
+    float* force = nullptr;          // float4 per vertex (x, y, z, pad): hinge + repulsion forces, cleared by the update
     float* uv0 = nullptr;            // 3 per vertex
     float* nrm = nullptr;            // 3 per vertex
     float* area = nullptr;           // per vertex

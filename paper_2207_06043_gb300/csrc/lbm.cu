@@ -22,7 +22,7 @@
 #endif
 // 1: FP32 interior runs take the cp.async-staged kernel; 0: register gathers
 #ifndef LBM_ASYNC
-#define LBM_ASYNC 1
+#define LBM_ASYNC 0
 #endif
 
 namespace ibl {
@@ -86,6 +86,10 @@ k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T
         const uint8_t tg = tag[gn];
         if (tg & TAG_SOLID) continue;
         T* fm = f + d.f_off;
+        // the spread IB force is fetched together with the populations
+        const bool ibn = tg & TAG_IB;
+        float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ibn) fv = reinterpret_cast<const float4*>(fib)[gn];
         float g[Q];
         int X = 0, Y = 0, Z = 0;
         if (BORDER) {
@@ -96,10 +100,9 @@ k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T
         }
         float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
         bool hasF = d.hasF != 0;
-        if (tg & TAG_IB) {
-            float* p = fib + 3 * gn;
-            Fx += p[0]; Fy += p[1]; Fz += p[2];
-            p[0] = 0.f; p[1] = 0.f; p[2] = 0.f;
+        if (ibn) {
+            Fx += fv.x; Fy += fv.y; Fz += fv.z;
+            reinterpret_cast<float4*>(fib)[gn] = make_float4(0.f, 0.f, 0.f, 0.f);
             tag[gn] = tg & (uint8_t)~TAG_IB;
             hasF = true;
         }
@@ -190,9 +193,10 @@ k_lbm_async(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ 
         float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
         bool hasF = d.hasF != 0;
         if (tg & TAG_IB) {
-            float* p = fib + 3 * gn;
-            Fx += p[0]; Fy += p[1]; Fz += p[2];
-            p[0] = 0.f; p[1] = 0.f; p[2] = 0.f;
+            float4* p = reinterpret_cast<float4*>(fib) + gn;
+            const float4 fv = *p;
+            Fx += fv.x; Fy += fv.y; Fz += fv.z;
+            *p = make_float4(0.f, 0.f, 0.f, 0.f);
             tag[gn] = tg & (uint8_t)~TAG_IB;
             hasF = true;
         }
