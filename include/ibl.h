@@ -230,12 +230,14 @@ typedef struct {
  *   grad_rj          = sum over links of dJ/dq * dq (the dq of the
  *                      ibl_wall_link records, e.g. dq/d(junction radius)),
  * with the fluid/solid tags held fixed.  The forward pass keeps a copy of the
- * populations every ckpt_every steps; the reverse pass recomputes each segment
- * from its copy, recording (rho, u) per node, d(value)/dq per wall link and
- * rho per face node (the tape), and then runs the adjoint steps of the segment
- * backwards.  The device memory for checkpoints and tape,
- *   ceil(n_steps / ckpt_every) * populations + ckpt_every * 16 B per node
- *   + 3 * 19 * 4 B per node,
+ * populations at the start of every ckpt_every-step segment but the last,
+ * whose tape ((rho, u) per node, d(value)/dq per wall link, rho per face node)
+ * it records directly; the reverse pass runs the last segment's adjoint steps,
+ * then recomputes each earlier segment from its copy, recording its tape, and
+ * runs its adjoint steps backwards.  With ckpt_every >= n_steps nothing is
+ * recomputed.  The device memory,
+ *   (ceil(n_steps / ckpt_every) - 1) * populations
+ *   + ckpt_every * 16 B per node + 2 * 19 * 4 B per node,
  * is allocated by the first call that needs it (cudaMalloc) and kept by the
  * context, with the CUDA graphs of the segments, until ibl_destroy; a later
  * call with more checkpoints or longer segments reallocates it.

@@ -8,11 +8,15 @@
 //   1. faces^T : at every face node, the populations the face rule wrote are
 //                replaced by their contributions to the ones it read;
 //   2. links^T : every wall link scatters lambda of the population it wrote
-//                onto the five post-collision values it read (atomics into a
-//                separate array, read once by step 3);
-//   3. stream^T + collide^T : every fluid node pulls lambda of the population
-//                it streamed to n + e_i, adds the link terms, and applies the
-//                transposed collision Jacobian at its (rho, u) of step t.
+//                onto the (up to) three post-collision values it read, each
+//                added (atomically) to the lambda entry that the pull of
+//                step 3 reads for that value: lambda*_j(p) is found at
+//                (j, p + e_j), a solid entry or the entry of the population
+//                p streamed to;
+//   3. stream^T + collide^T : every fluid node pulls lambda*_i from
+//                (i, n + e_i) and applies the transposed collision Jacobian
+//                at its (rho, u) of step t; the solid entries holding link
+//                terms are then cleared for the buffer's next use.
 // The (rho, u) of every node, d(value)/dq of every link and rho of every face
 // node come from a tape written while the forward steps are recomputed from a
 // checkpoint.
@@ -140,13 +144,15 @@ __global__ void __launch_bounds__(256) k_adj_faces(const MemberDev* __restrict__
 // links^T: the value the wall rule wrote at (opp(i), x_b) is a combination of
 // f*_i(x_b), f*_i(x_b - e_i), f*_i(x_b - 2 e_i), f*_opp(i)(x_b), f*_opp(i)(x_b - e_i)
 // with the coefficients of the forward rule; dJ/dr_j gains
-// lambda * (d value / dq) * (dq / dr_j).
+// lambda * (d value / dq) * (dq / dr_j).  No entry that a link reads is
+// written by another link (a link's reads and writes sit on opposite sides of
+// its wall), so the scatter runs in place on lambda.
 __global__ void __launch_bounds__(256) k_adj_links(const MemberDev* __restrict__ mem,
                                                    const uint32_t* __restrict__ l_node,
                                                    const uint32_t* __restrict__ l_meta, const float* __restrict__ l_q,
                                                    const float* __restrict__ l_dq, const float* __restrict__ tape_dvdq,
-                                                   const float* __restrict__ lam, float* __restrict__ extra, size_t LS,
-                                                   int n_links, double* __restrict__ grad_q) {
+                                                   float* __restrict__ lam, size_t LS, int n_links,
+                                                   double* __restrict__ grad_q) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     double dqs = 0.0;
     if (l < n_links) {
@@ -162,30 +168,32 @@ __global__ void __launch_bounds__(256) k_adj_links(const MemberDev* __restrict__
             node_coords(d, xb, X, Y, Z);
             const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
             const int exi = ex(i), eyi = ey(i), ezi = ez(i);
+            const int s0 = nbc(X, exi, d.NX, px) + d.NX * (nbc(Y, eyi, d.NY, py) + d.NY * nbc(Z, ezi, d.NZ, pz));
             const int X1 = nbc(X, -exi, d.NX, px), Y1 = nbc(Y, -eyi, d.NY, py), Z1 = nbc(Z, -ezi, d.NZ, pz);
             const int m1 = X1 + d.NX * (Y1 + d.NY * Z1);
-            const int m2 = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
-            float* ei = extra + i * LS;
-            float* eb = extra + ib * LS;
+            float* li = lam + i * LS;    // lambda*_i(p) sits at (i, p + e_i)
+            float* lb = lam + ib * LS;   // lambda*_ib(p) sits at (ib, p - e_i)
             if (q < 0.5f) {
                 if (ok1 && ok2) {
-                    atomicAdd(ei + xb, q * (2.f * q + 1.f) * lv);
-                    atomicAdd(ei + m1, (1.f - 4.f * q * q) * lv);
-                    atomicAdd(ei + m2, -q * (1.f - 2.f * q) * lv);
+                    atomicAdd(li + s0, q * (2.f * q + 1.f) * lv);
+                    atomicAdd(li + xb, (1.f - 4.f * q * q) * lv);
+                    atomicAdd(li + m1, -q * (1.f - 2.f * q) * lv);
                 } else if (ok1) {
-                    atomicAdd(ei + xb, 2.f * q * lv);
-                    atomicAdd(ei + m1, (1.f - 2.f * q) * lv);
+                    atomicAdd(li + s0, 2.f * q * lv);
+                    atomicAdd(li + xb, (1.f - 2.f * q) * lv);
                 } else {
-                    atomicAdd(ei + xb, lv);
+                    atomicAdd(li + s0, lv);
                 }
             } else {
                 if (ok1) {
-                    atomicAdd(ei + xb, lv / (q * (2.f * q + 1.f)));
-                    atomicAdd(eb + xb, (2.f * q - 1.f) / q * lv);
-                    atomicAdd(eb + m1, (1.f - 2.f * q) / (1.f + 2.f * q) * lv);
+                    const int m2 = nbc(X1, -exi, d.NX, px) +
+                                   d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
+                    atomicAdd(li + s0, lv / (q * (2.f * q + 1.f)));
+                    atomicAdd(lb + m1, (2.f * q - 1.f) / q * lv);
+                    atomicAdd(lb + m2, (1.f - 2.f * q) / (1.f + 2.f * q) * lv);
                 } else {
-                    atomicAdd(ei + xb, lv / (2.f * q));
-                    atomicAdd(eb + xb, (2.f * q - 1.f) / (2.f * q) * lv);
+                    atomicAdd(li + s0, lv / (2.f * q));
+                    atomicAdd(lb + m1, (2.f * q - 1.f) / (2.f * q) * lv);
                 }
             }
             dqs = (double)lv * (double)tape_dvdq[l] * (double)l_dq[l];
@@ -201,32 +209,31 @@ __global__ void __launch_bounds__(256) k_adj_links(const MemberDev* __restrict__
 //   A = sum_j lambda*_j w_j (1 + 3 e_j.u + 9/2 (e_j.u)^2 - 3/2 u^2),
 //   B = sum_j lambda*_j [omega w_j rho (3 e_j + 9 (e_j.u) e_j - 3 u)
 //                        + guo w_j (9 (e_j.F) e_j - 3 F)].
-__global__ void __launch_bounds__(256) k_adj_step(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag,
-                                                  const uint8_t* __restrict__ near, const float4* __restrict__ tape,
-                                                  const float* __restrict__ lam_in, float* __restrict__ lam_out,
-                                                  float* __restrict__ extra, size_t LS) {
-    const MemberDev& d = mem[0];
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+// Entries at solid nodes hold only link terms (zero otherwise), so every
+// neighbour is pulled without a tag test; k_adj_clear zeroes the link terms
+// once they are consumed.  Work list: the fluid runs of the lattice kernel,
+// one warp per 32-node run; interior runs address neighbours by constant
+// offsets, border runs (periodic wrap planes) by coordinates.
+template <bool BORDER>
+__global__ void __launch_bounds__(256) k_adj_step(const __grid_constant__ MemberDev d, const uint8_t* __restrict__ tag,
+                                                  const uint32_t* __restrict__ segs, int n_segs,
+                                                  const float4* __restrict__ tape, const float* __restrict__ lam_in,
+                                                  float* __restrict__ lam_out, size_t LS) {
+    const int si = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (si >= n_segs) return;
+    const int n = (int)(segs[si] << 5) + (int)(threadIdx.x & 31);
     if (n >= d.N || (tag[n] & TAG_SOLID)) return;
-    int X, Y, Z;
-    node_coords(d, n, X, Y, Z);
-    const Nbr b = neighbours(d, X, Y, Z);
-    const bool nr = near[n] != 0;
-    // every neighbour index is in range (ghost layer / wrap), so all 19 loads
-    // are issued at once and the solid ones are discarded afterwards
     float ls[Q];
+    if (BORDER) {
+        int X, Y, Z;
+        node_coords(d, n, X, Y, Z);
+        const Nbr b = neighbours(d, X, Y, Z);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const int m = b.xs[1 + ex(k)] + d.NX * (b.ys[1 + ey(k)] + d.NY * b.zs[1 + ez(k)]);
-        const float v = lam_in[k * LS + m];
-        ls[k] = (tag[m] & TAG_SOLID) ? 0.f : v;
-    }
-    if (nr) {
+        for (int k = 0; k < Q; ++k)
+            ls[k] = lam_in[k * LS + b.xs[1 + ex(k)] + d.NX * (b.ys[1 + ey(k)] + d.NY * b.zs[1 + ez(k)])];
+    } else {
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            ls[k] += extra[k * LS + n];
-            extra[k * LS + n] = 0.f;
-        }
+        for (int k = 0; k < Q; ++k) ls[k] = lam_in[k * LS + (n + lin_off(d, k))];
     }
     const float4 t = tape[n];
     const float rho = t.x, ux = t.y, uy = t.z, uz = t.w;
@@ -253,31 +260,33 @@ __global__ void __launch_bounds__(256) k_adj_step(const MemberDev* __restrict__ 
         lam_out[k * LS + n] = (1.f - om) * ls[k] + om * A + (Bx * ex(k) + By * ey(k) + Bz * ez(k) - Bu) * ir;
 }
 
-// Nodes that receive link terms in links^T: x_b, and x_b - e_i / x_b - 2 e_i
-// where the rule reads them.
-__global__ void k_adj_near(const MemberDev* __restrict__ mem, const uint32_t* __restrict__ l_node,
-                           const uint32_t* __restrict__ l_meta, int n_links, uint8_t* __restrict__ near) {
+// The solid entries a link wrote in links^T, cleared after k_adj_step has
+// pulled them (its fluid entries are overwritten when the buffer next
+// receives a step's output).
+__global__ void __launch_bounds__(256) k_adj_clear(const __grid_constant__ MemberDev d,
+                                                   const uint8_t* __restrict__ tag,
+                                                   const uint32_t* __restrict__ l_node,
+                                                   const uint32_t* __restrict__ l_meta, float* __restrict__ lam,
+                                                   size_t LS, int n_links) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n_links) return;
-    const MemberDev& d = mem[0];
     const uint32_t meta = l_meta[l];
-    const int i = (int)(meta & 31u);
-    const bool ok1 = meta & 32u, ok2 = meta & 64u;
+    const int i = (int)(meta & 31u), ib = opp(i);
     const int xb = (int)l_node[l];
     int X, Y, Z;
     node_coords(d, xb, X, Y, Z);
     const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
-    const int X1 = nbc(X, -ex(i), d.NX, px), Y1 = nbc(Y, -ey(i), d.NY, py), Z1 = nbc(Z, -ez(i), d.NZ, pz);
-    near[xb] = 1;
-    if (ok1) near[X1 + d.NX * (Y1 + d.NY * Z1)] = 1;
-    if (ok2)
-        near[nbc(X1, -ex(i), d.NX, px) + d.NX * (nbc(Y1, -ey(i), d.NY, py) + d.NY * nbc(Z1, -ez(i), d.NZ, pz))] = 1;
-}
-
-cudaError_t launch_adj_near(const DevState& d, uint8_t* near, cudaStream_t s) {
-    if (d.n_links == 0) return cudaSuccess;
-    k_adj_near<<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, d.l_node, d.l_meta, d.n_links, near);
-    return cudaGetLastError();
+    const int exi = ex(i), eyi = ey(i), ezi = ez(i);
+    const int s0 = nbc(X, exi, d.NX, px) + d.NX * (nbc(Y, eyi, d.NY, py) + d.NY * nbc(Z, ezi, d.NZ, pz));
+    const int X1 = nbc(X, -exi, d.NX, px), Y1 = nbc(Y, -eyi, d.NY, py), Z1 = nbc(Z, -ezi, d.NZ, pz);
+    const int m1 = X1 + d.NX * (Y1 + d.NY * Z1);                // in range: x_b is an interior node
+    lam[i * LS + s0] = 0.f;                                     // s0 is solid
+    if (tag[m1] & TAG_SOLID) {
+        lam[ib * LS + m1] = 0.f;
+    } else {                                                    // m1 fluid: m2 is in range too
+        const int m2 = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
+        if (tag[m2] & TAG_SOLID) lam[ib * LS + m2] = 0.f;
+    }
 }
 
 cudaError_t launch_adj_objective(const DevState& d, int parity, const int lo[3], const int hi[3], const double w[3],
@@ -290,16 +299,22 @@ cudaError_t launch_adj_objective(const DevState& d, int parity, const int lo[3],
 }
 
 cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const float* tape_dvdq, const float4* tape_rhou,
-                            const uint8_t* near, float* lam_in, float* lam_out, float* extra, size_t LS,
-                            double* grad_s, double* grad_q, cudaStream_t s) {
+                            float* lam_in, float* lam_out, size_t LS, double* grad_s, double* grad_q,
+                            cudaStream_t s) {
     if (d.n_face_nodes > 0)
         k_adj_faces<<<(d.n_face_nodes + 255) / 256, 256, 0, s>>>(d.mem, d.fc_node, d.fc_meta, d.face_vel, tape_rho,
                                                                  lam_in, LS, d.n_face_nodes, grad_s);
     if (d.n_links > 0)
         k_adj_links<<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, d.l_node, d.l_meta, d.l_q, d.l_dq, tape_dvdq,
-                                                            lam_in, extra, LS, d.n_links, grad_q);
-    const int N = d.h_mem[0].N;
-    k_adj_step<<<(N + 255) / 256, 256, 0, s>>>(d.mem, d.tag, near, tape_rhou, lam_in, lam_out, extra, LS);
+                                                            lam_in, LS, d.n_links, grad_q);
+    const MemberDev& md = d.h_mem[0];
+    if (d.n_segs > 0)
+        k_adj_step<false><<<(d.n_segs + 7) / 8, 256, 0, s>>>(md, d.tag, d.segs, d.n_segs, tape_rhou, lam_in, lam_out, LS);
+    if (d.n_bsegs > 0)
+        k_adj_step<true><<<(d.n_bsegs + 7) / 8, 256, 0, s>>>(md, d.tag, d.bsegs, d.n_bsegs, tape_rhou, lam_in, lam_out,
+                                                             LS);
+    if (d.n_links > 0)
+        k_adj_clear<<<(d.n_links + 255) / 256, 256, 0, s>>>(md, d.tag, d.l_node, d.l_meta, lam_in, LS, d.n_links);
     return cudaGetLastError();
 }
 

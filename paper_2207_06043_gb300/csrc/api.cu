@@ -83,13 +83,12 @@ struct ibl_ctx {
     std::vector<uint32_t> h_status;
     std::string err;
     // adjoint work buffers and segment graphs, kept between ibl_adjoint calls
-    struct AdjSeg { int parity, len; float* lin; cudaGraphExec_t exec; };
+    struct AdjSeg { int mode, parity, len; float* lin; cudaGraphExec_t exec; };
     struct AdjCache {
         size_t ck_bytes = 0, tape_steps = 0;
         char *ck = nullptr, *snap = nullptr;
         float4* tape_rhou = nullptr;
-        float *tape_dvdq = nullptr, *tape_rho = nullptr, *lamA = nullptr, *lamB = nullptr, *extra = nullptr;
-        uint8_t* near = nullptr;
+        float *tape_dvdq = nullptr, *tape_rho = nullptr, *lamA = nullptr, *lamB = nullptr;
         double* acc = nullptr;
         std::vector<AdjSeg> graphs;
     } adj;
@@ -287,7 +286,7 @@ void free_adjoint(ibl_ctx* ctx) {
     auto& A = ctx->adj;
     for (auto& g : A.graphs) cudaGraphExecDestroy(g.exec);
     A.graphs.clear();
-    void* ptrs[] = {A.ck, A.snap, A.tape_rhou, A.tape_dvdq, A.tape_rho, A.lamA, A.lamB, A.extra, A.near, A.acc};
+    void* ptrs[] = {A.ck, A.snap, A.tape_rhou, A.tape_dvdq, A.tape_rho, A.lamA, A.lamB, A.acc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     A = ibl_ctx::AdjCache{};
@@ -1202,7 +1201,7 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
     // work buffers: allocated by the first call (or a call that needs more
     // checkpoints or a longer segment) and kept in the context
     auto& AC = ctx->adj;
-    const size_t ck_need = (size_t)n_ck * D.f_bytes;
+    const size_t ck_need = (size_t)std::max(n_ck - 1, 1) * D.f_bytes;
     if (AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc) {
         cudaStreamSynchronize(ctx->work);
         free_adjoint(ctx);
@@ -1222,8 +1221,6 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
         if (ast == IBL_OK) ast = alloc((size_t)K * D.n_face_nodes * sizeof(float), (void**)&AC.tape_rho);
         if (ast == IBL_OK) ast = alloc(Q * LS * sizeof(float), (void**)&AC.lamA);
         if (ast == IBL_OK) ast = alloc(Q * LS * sizeof(float), (void**)&AC.lamB);
-        if (ast == IBL_OK) ast = alloc(Q * LS * sizeof(float), (void**)&AC.extra);
-        if (ast == IBL_OK) ast = alloc(N, (void**)&AC.near);
         if (ast == IBL_OK) ast = alloc(3 * sizeof(double), (void**)&AC.acc);
         if (ast != IBL_OK) { free_adjoint(ctx); return ast; }
         AC.ck_bytes = ck_need;
@@ -1231,20 +1228,68 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
     }
     char *ck = AC.ck, *snap = AC.snap;
     float4* tape_rhou = AC.tape_rhou;
-    float *tape_dvdq = AC.tape_dvdq, *tape_rho = AC.tape_rho, *lamA = AC.lamA, *lamB = AC.lamB, *extra = AC.extra;
-    uint8_t* near = AC.near;
+    float *tape_dvdq = AC.tape_dvdq, *tape_rho = AC.tape_rho, *lamA = AC.lamA, *lamB = AC.lamB;
     double* acc = AC.acc;   // J, dJ/ds_u, dJ/dr_j
     auto run = [&]() -> ibl_status {
         cudaStream_t s = ctx->work;
         CKS(enter(ctx));
-        CK(cudaMemsetAsync(extra, 0, Q * LS * sizeof(float), s));
+        // solid entries of both lambda buffers start at zero (they then hold
+        // only the link terms of one step at a time)
         CK(cudaMemsetAsync(lamA, 0, Q * LS * sizeof(float), s));
-        CK(cudaMemsetAsync(near, 0, N, s));
+        CK(cudaMemsetAsync(lamB, 0, Q * LS * sizeof(float), s));
         CK(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s));
-        CK(launch_adj_near(D, near, s));
         const long long t0 = ctx->t;
-        // forward sweep with a checkpoint of the populations every K steps
-        for (int k = 0; k < n_steps; ++k) {
+        // Segment work, captured once per (mode, start parity, length, adjoint
+        // buffer) as a CUDA graph and replayed.  Mode 0: recompute the steps
+        // from the checkpoint writing the tape, then the adjoint steps
+        // backwards; mode 1: the adjoint steps only (the tape is already
+        // there); mode 2: forward steps writing the tape (the last segment of
+        // the forward sweep, which then needs no recompute).
+        std::vector<ibl_ctx::AdjSeg>& graphs = AC.graphs;
+        auto enqueue_segment = [&](int mode, int parity0, int len, float* lin0) -> ibl_status {
+            if (mode != 1)
+                for (int k = 0; k < len; ++k) {
+                    const int parity = (parity0 + k) & 1;
+                    if (mode == 2) CK(launch_step_begin(D, s));
+                    CK(launch_lbm(D, parity, s, tape_rhou + (size_t)k * N));
+                    CK(launch_bfl(D, parity, s, tape_dvdq + (size_t)k * D.n_links));
+                    CK(launch_faces(D, parity, s, tape_rho + (size_t)k * D.n_face_nodes));
+                }
+            if (mode != 2) {
+                float* li = lin0;
+                float* lo = lin0 == lamA ? lamB : lamA;
+                for (int k = len - 1; k >= 0; --k) {
+                    CK(launch_adj_step(D, tape_rho + (size_t)k * D.n_face_nodes, tape_dvdq + (size_t)k * D.n_links,
+                                       tape_rhou + (size_t)k * N, li, lo, LS, acc + 1, acc + 2, s));
+                    std::swap(li, lo);
+                }
+            }
+            return IBL_OK;
+        };
+        auto run_segment = [&](int mode, int parity0, int len, float* lin0) -> ibl_status {
+            for (const ibl_ctx::AdjSeg& g : graphs)
+                if (g.mode == mode && g.parity == parity0 && g.len == len && g.lin == lin0) {
+                    CK(cudaGraphLaunch(g.exec, s));
+                    return IBL_OK;
+                }
+            cudaGraph_t gr = nullptr;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const ibl_status est = enqueue_segment(mode, parity0, len, lin0);
+            const cudaError_t e = cudaStreamEndCapture(s, &gr);
+            if (est != IBL_OK) { if (gr) cudaGraphDestroy(gr); return est; }
+            CK(e);
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+            cudaGraphDestroy(gr);
+            CK(ei);
+            graphs.push_back({mode, parity0, len, lin0, ex});
+            CK(cudaGraphLaunch(ex, s));
+            return IBL_OK;
+        };
+        // forward sweep with a checkpoint of the populations at the start of
+        // every segment but the last, which records its tape directly
+        const int last0 = (n_ck - 1) * K;
+        for (int k = 0; k < last0; ++k) {
             if (k % K == 0)
                 CK(cudaMemcpyAsync(ck + (size_t)(k / K) * D.f_bytes, D.f, D.f_bytes, cudaMemcpyDeviceToDevice, s));
             const int parity = (int)(ctx->t & 1);
@@ -1256,6 +1301,8 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
             }
             ctx->t += 1;
         }
+        CKS(run_segment(2, (int)(ctx->t & 1), n_steps - last0, lamA));
+        ctx->t += n_steps - last0;
         const int lo[3] = {obj->lo[0], obj->lo[1], obj->lo[2]}, hi[3] = {obj->hi[0], obj->hi[1], obj->hi[2]};
         CK(launch_adj_objective(D, (int)(ctx->t & 1), lo, hi, obj->d, lamA, LS, acc, s));
         {   // the final state, put back after the reverse sweep
@@ -1265,54 +1312,16 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
                 off += sc.bytes;
             }
         }
-        // one segment: recompute its steps from the checkpoint writing the tape,
-        // then its adjoint steps backwards; captured once per (start parity,
-        // length, adjoint buffer) as a CUDA graph and replayed
-        std::vector<ibl_ctx::AdjSeg>& graphs = AC.graphs;
-        auto enqueue_segment = [&](int parity0, int len, float* lin0) -> ibl_status {
-            float* li = lin0;
-            float* lo = lin0 == lamA ? lamB : lamA;
-            for (int k = 0; k < len; ++k) {
-                const int parity = (parity0 + k) & 1;
-                CK(launch_lbm(D, parity, s, tape_rhou + (size_t)k * N));
-                CK(launch_bfl(D, parity, s, tape_dvdq + (size_t)k * D.n_links));
-                CK(launch_faces(D, parity, s, tape_rho + (size_t)k * D.n_face_nodes));
-            }
-            for (int k = len - 1; k >= 0; --k) {
-                CK(launch_adj_step(D, tape_rho + (size_t)k * D.n_face_nodes, tape_dvdq + (size_t)k * D.n_links,
-                                   tape_rhou + (size_t)k * N, near, li, lo, extra, LS, acc + 1, acc + 2, s));
-                std::swap(li, lo);
-            }
-            return IBL_OK;
-        };
-        auto run_segment = [&](int parity0, int len, float* lin0) -> ibl_status {
-            for (const ibl_ctx::AdjSeg& g : graphs)
-                if (g.parity == parity0 && g.len == len && g.lin == lin0) {
-                    CK(cudaGraphLaunch(g.exec, s));
-                    return IBL_OK;
-                }
-            cudaGraph_t gr = nullptr;
-            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            const ibl_status est = enqueue_segment(parity0, len, lin0);
-            const cudaError_t e = cudaStreamEndCapture(s, &gr);
-            if (est != IBL_OK) { if (gr) cudaGraphDestroy(gr); return est; }
-            CK(e);
-            cudaGraphExec_t ex = nullptr;
-            const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
-            cudaGraphDestroy(gr);
-            CK(ei);
-            graphs.push_back({parity0, len, lin0, ex});
-            CK(cudaGraphLaunch(ex, s));
-            return IBL_OK;
-        };
         float* lin = lamA;
         ibl_status sst = IBL_OK;
         for (int seg = n_ck - 1; seg >= 0 && sst == IBL_OK; --seg) {
             const int s0 = seg * K, s1 = std::min(n_steps, s0 + K);
-            const cudaError_t e = cudaMemcpyAsync(D.f, ck + (size_t)seg * D.f_bytes, D.f_bytes,
-                                                  cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) { sst = fail(ctx, IBL_ERR_CUDA, cudaGetErrorString(e)); break; }
-            sst = run_segment((int)((t0 + s0) & 1), s1 - s0, lin);
+            if (seg < n_ck - 1) {
+                const cudaError_t e = cudaMemcpyAsync(D.f, ck + (size_t)seg * D.f_bytes, D.f_bytes,
+                                                      cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) { sst = fail(ctx, IBL_ERR_CUDA, cudaGetErrorString(e)); break; }
+            }
+            sst = run_segment(seg < n_ck - 1 ? 0 : 1, (int)((t0 + s0) & 1), s1 - s0, lin);
             if ((s1 - s0) & 1) lin = lin == lamA ? lamB : lamA;
         }
         CKS(sst);

@@ -186,12 +186,11 @@ cudaError_t launch_read(const DevState& d, int member, int parity, float* rho, f
                         float* g, cudaStream_t s);
 
 // discrete adjoint of the lattice step (adjoint.cu)
-cudaError_t launch_adj_near(const DevState& d, uint8_t* near, cudaStream_t s);
 cudaError_t launch_adj_objective(const DevState& d, int parity, const int lo[3], const int hi[3], const double w[3],
                                  float* lam, size_t LS, double* J, cudaStream_t s);
 cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const float* tape_dvdq, const float4* tape_rhou,
-                            const uint8_t* near, float* lam_in, float* lam_out, float* extra, size_t LS,
-                            double* grad_s, double* grad_q, cudaStream_t s);
+                            float* lam_in, float* lam_out, size_t LS, double* grad_s, double* grad_q,
+                            cudaStream_t s);
 
 cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s);
 cudaError_t launch_ib(const DevState& d, int parity, cudaStream_t s);
