@@ -28,8 +28,9 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & % of HBM roofline (fwd, adjoint, batched); error vs FP64 oracle"
 BYTES_PER_UPDATE = {"f32": 152, "f16": 76, "bf16": 76}
 # DRAM read + write of one FP32 lattice-kernel launch on the throughput
-# workload (ncu capture summarised in profiles/k_lbm_throughput_workload.md);
-# valid only for the kernel as captured and that workload.
+# workload, from an ncu capture of two launches of the timed region (kept
+# with the profile summaries); valid only for the kernel as captured and that
+# workload.
 LBM_TRAFFIC_BYTES = {("throughput", "f32"): 598.6e6}
 CPU_SAMPLE_X = 64          # x-slab of the workload the oracle runs on (cpu_baseline)
 REF_SAMPLE_X = 16          # thinner slab per step of the reference arm
@@ -260,7 +261,8 @@ def main():
     achieved = bpu * nf / (lbm_ms * 1e-3) / 1e9
     traffic = LBM_TRAFFIC_BYTES.get((args.workload, args.storage))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_source": "profiles/k_lbm_throughput_workload.md" if traffic else None, "kernel": "k_lbm (fused collide+stream, AA pattern)",
+            "traffic": traffic, "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches"
+                               if traffic else None), "kernel": "k_lbm (fused collide+stream, AA pattern)",
             "peak_source": f"{peak_kind} hbm_gbs", "ms_per_launch": lbm_ms,
             "algorithmic_bytes_per_launch": bpu * nf}
     s.close()
