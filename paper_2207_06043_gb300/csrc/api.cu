@@ -59,8 +59,8 @@ struct ibl_ctx {
     cudaStream_t user_stream = nullptr;
     cudaStream_t work = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaStream_t work2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_ib = nullptr;
+    cudaStream_t work2 = nullptr, work3 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_ib = nullptr, ev_shell = nullptr, ev_probes = nullptr;
     int storage = IBL_STORAGE_F32;
     std::vector<MemberHost> members;
     bool finalized = false;
@@ -664,14 +664,16 @@ struct Mark {
     cudaEvent_t a, b;
 };
 
-// One time step.  Stream `work`: step begin, geometry, shell moments and the
-// IB pass, then the lattice step and the wall fill.  Stream `work2`: after the
-// geometry, repulsion and hinge forces (concurrent with the IB pass); after
-// the IB pass, the structure update (concurrent with the lattice step).  The
-// update touches no lattice data and the lattice step no structure data.
+// One time step.  Stream `work`: step begin, geometry, shell moments, the
+// marker stencils, then the lattice step, the wall fill and the faces.
+// Stream `work3`: the probe stencils, beside the marker stencils and the
+// lattice step.  Stream `work2`: after the geometry, repulsion and hinge
+// forces (beside the IB pass); after the markers and the probes, the
+// structure update (beside the lattice step).  The update touches no lattice
+// data and the lattice step no structure data.
 ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks) {
     DevState& D = ctx->dev;
-    cudaStream_t s = ctx->work, s2 = ctx->work2;
+    cudaStream_t s = ctx->work, s2 = ctx->work2, s3 = ctx->work3;
     cudaEvent_t e0 = nullptr;
     auto begin = [&](cudaStream_t st) -> ibl_status {
         if (!marks) return IBL_OK;
@@ -693,14 +695,20 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks) {
         CKS(begin(s));
         CK(launch_geometry(D, 0, s));
         CK(cudaEventRecord(ctx->ev_fork, s));
-        CK(launch_ib(D, parity, s));
+        CK(launch_shell(D, parity, s));
+        CK(cudaEventRecord(ctx->ev_shell, s));
+        CK(launch_markers(D, s));
         CKS(end(TK_IB, s));
         CK(cudaEventRecord(ctx->ev_ib, s));
+        CK(cudaStreamWaitEvent(s3, ctx->ev_shell, 0));
+        CK(launch_probes(D, s3));
+        CK(cudaEventRecord(ctx->ev_probes, s3));
         CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
         CKS(begin(s2));
         CK(launch_repulsion(D, s2));
         CK(launch_edges(D, s2));
         CK(cudaStreamWaitEvent(s2, ctx->ev_ib, 0));
+        CK(cudaStreamWaitEvent(s2, ctx->ev_probes, 0));
         CK(launch_update(D, s2));
         CKS(end(TK_STRUCT, s2));
     }
@@ -920,6 +928,9 @@ ibl_status new_ctx(void* stream, ibl_ctx** out) {
     ctx->user_stream = (cudaStream_t)stream;
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->work2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->work3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_shell, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_probes, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_ib, cudaEventDisableTiming);
@@ -1508,6 +1519,10 @@ void ibl_destroy(ibl_ctx* ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->ev_ib) cudaEventDestroy(ctx->ev_ib);
+    if (ctx->work3) cudaStreamSynchronize(ctx->work3);
+    if (ctx->ev_shell) cudaEventDestroy(ctx->ev_shell);
+    if (ctx->ev_probes) cudaEventDestroy(ctx->ev_probes);
+    if (ctx->work3) cudaStreamDestroy(ctx->work3);
     if (ctx->work2) cudaStreamDestroy(ctx->work2);
     if (ctx->work) cudaStreamDestroy(ctx->work);
     delete ctx;

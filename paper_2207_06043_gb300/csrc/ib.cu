@@ -853,26 +853,36 @@ cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) {
 }
 
 template <typename T>
-static cudaError_t ib_t(const DevState& d, int parity, cudaStream_t s) {
+static cudaError_t shell_t(const DevState& d, int parity, cudaStream_t s) {
     k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.status, d.caps, d.sums,
                                                        d.macro, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shell(const DevState& d, int parity, cudaStream_t s) {
+    if (d.n_verts == 0) return cudaSuccess;
+    switch (d.storage) {
+        case 1: return shell_t<__half>(d, parity, s);
+        case 2: return shell_t<__nv_bfloat16>(d, parity, s);
+        default: return shell_t<float>(d, parity, s);
+    }
+}
+
+cudaError_t launch_markers(const DevState& d, cudaStream_t s) {
+    if (d.n_verts == 0) return cudaSuccess;
     const long long mt = (long long)GL * d.n_verts;
     k_ib_markers<<<(unsigned)((mt + IB_MARKER_THREADS - 1) / IB_MARKER_THREADS), IB_MARKER_THREADS, 0, s>>>(
         d.mem, d.tag, d.fib, d.status, d.v_cap, d.caps, d.sums, d.x, d.vel, d.area, d.uv0, d.probe, d.n_verts,
         d.macro);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probes(const DevState& d, cudaStream_t s) {
+    if (d.n_verts == 0) return cudaSuccess;
     const long long pt = 2LL * GL * d.n_verts;
     k_ib_probes<<<(unsigned)((pt + IB_PROBE_THREADS - 1) / IB_PROBE_THREADS), IB_PROBE_THREADS, 0, s>>>(
         d.mem, d.tag, d.status, d.v_cap, d.caps, d.x, d.nrm, d.probe, d.n_verts, d.macro);
     return cudaGetLastError();
-}
-
-cudaError_t launch_ib(const DevState& d, int parity, cudaStream_t s) {
-    if (d.n_verts == 0) return cudaSuccess;
-    switch (d.storage) {
-        case 1: return ib_t<__half>(d, parity, s);
-        case 2: return ib_t<__nv_bfloat16>(d, parity, s);
-        default: return ib_t<float>(d, parity, s);
-    }
 }
 
 cudaError_t launch_edges(const DevState& d, cudaStream_t s) {

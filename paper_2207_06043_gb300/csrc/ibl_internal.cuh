@@ -193,7 +193,13 @@ cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const floa
                             cudaStream_t s);
 
 cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s);
-cudaError_t launch_ib(const DevState& d, int parity, cudaStream_t s);
+// IB pass: shell moments, then the marker stencils (interpolation, force,
+// spreading) and the probe stencils (stresses), which are independent of
+// each other (the markers set only the IB bit of fluid tags, the probes read
+// only the solid bit; they write different slots of the probe records).
+cudaError_t launch_shell(const DevState& d, int parity, cudaStream_t s);
+cudaError_t launch_markers(const DevState& d, cudaStream_t s);
+cudaError_t launch_probes(const DevState& d, cudaStream_t s);
 cudaError_t launch_step_begin(const DevState& d, cudaStream_t s);
 cudaError_t launch_edges(const DevState& d, cudaStream_t s);
 cudaError_t launch_repulsion(const DevState& d, cudaStream_t s);
