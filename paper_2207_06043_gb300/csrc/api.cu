@@ -631,6 +631,7 @@ ibl_status finalize(ibl_ctx* ctx) {
             D.n_cells = cell_off;
             CKS(dev_alloc(ctx, D.cell_count, (size_t)cell_off));
             CKS(dev_alloc(ctx, D.cell_items, (size_t)cell_off * CELL_CAP));
+            CKS(dev_alloc(ctx, D.cell_vid, (size_t)cell_off * CELL_CAP));
         }
     }
     D.h_mem = ctx->hmem.data();

@@ -23,15 +23,6 @@ __device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, floa
     return (fluid && r <= 1.f) ? expf(-s * s) : 0.f;
 }
 
-template <typename T>
-__device__ __forceinline__ void node_state(const MemberDev& d, const T* __restrict__ f,
-                                           int node, int parity, float& rho, float& ux, float& uy, float& uz) {
-    int X, Y, Z;
-    node_coords(d, node, X, Y, Z);
-    float g[Q];
-    load_pre<T>(d, f + d.f_off, node, X, Y, Z, parity, g);
-    moments_of(g, rho, ux, uy, uz);
-}
 
 // ---------------------------------------------------------------------------
 // Per-capsule geometry at x(t), spread over GEO_BLOCKS blocks per capsule:
@@ -42,7 +33,7 @@ __device__ __forceinline__ void node_state(const MemberDev& d, const T* __restri
 // area-weighted sum of adjacent normals, the integer bounding box, and vacc
 // is cleared for the next step.  V and the box are reset at the step begin.
 // ---------------------------------------------------------------------------
-constexpr int GEO_BLOCKS = 4;
+constexpr int GEO_BLOCKS = 16;
 
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
 #pragma unroll
@@ -133,12 +124,15 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
 
 // Moments (rho, u* = sum g e / rho) of the current populations at every fluid
 // node of each capsule's vertex bounding box grown by SHELL_MARGIN, which
-// holds every support node of the marker and probe stencils (probes sit
-// 1.2 dx off the surface, supports reach 1.5 dx further).  The IB kernel then
-// reads one float4 per support node instead of 19 scattered populations.
-// Overlapping boxes write identical values.
-constexpr int SHELL_MARGIN = 4;
-constexpr int SHELL_BLOCKS = 32;   // blocks per capsule
+// holds every support node of the marker and probe stencils: a probe sits
+// 1.2 dx off its vertex, its base node is within 0.5 dx of it and the support
+// one node further, so every support coordinate lies within 2.7 dx of a
+// vertex, i.e. within [floor(min) - 2, floor(max) + 3] per axis, and the box
+// [floor(min), floor(max) + 1] grown by 3 holds it with a node to spare.  The
+// IB kernels then read one float4 per support node instead of 19 scattered
+// populations.  Overlapping boxes write identical values.
+constexpr int SHELL_MARGIN = 3;
+constexpr int SHELL_BLOCKS = 64;   // blocks per capsule
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
@@ -165,19 +159,22 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
         ext[a] = h - l + 1;
     }
     if (ext[0] <= 0 || ext[1] <= 0 || ext[2] <= 0) return;
-    const long long total = (long long)ext[0] * ext[1] * ext[2];
-    for (long long i = (blockIdx.x % SHELL_BLOCKS) * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)SHELL_BLOCKS * blockDim.x) {
-        int cx = lo[0] + (int)(i % ext[0]);
-        int cy = lo[1] + (int)((i / ext[0]) % ext[1]);
-        int cz = lo[2] + (int)(i / ((long long)ext[0] * ext[1]));
+    const int exy = ext[0] * ext[1];
+    const int total = exy * ext[2];     // a box of one lattice: below 2^31 nodes
+    const T* fm = f + d.f_off;
+    for (int i = (blockIdx.x % SHELL_BLOCKS) * blockDim.x + threadIdx.x; i < total; i += SHELL_BLOCKS * blockDim.x) {
+        const int iz = i / exy, r = i - iz * exy, iy = r / ext[0];
+        int cx = lo[0] + (r - iy * ext[0]), cy = lo[1] + iy, cz = lo[2] + iz;
         if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx;
         if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny;
         if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz;
-        const int node = (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
+        const int X = cx + d.px, Y = cy + d.py, Z = cz + d.pz;
+        const int node = X + d.NX * (Y + d.NY * Z);
         if (tag[d.node_off + node] & TAG_SOLID) continue;
+        float g[Q];
+        load_pre<T>(d, fm, node, X, Y, Z, parity, g);
         float rho, ux, uy, uz;
-        node_state<T>(d, f, node, parity, rho, ux, uy, uz);
+        moments_of(g, rho, ux, uy, uz);
         macro[d.node_off + node] = make_float4(rho, ux, uy, uz);
     }
 }
@@ -642,7 +639,7 @@ __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, co
 __global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
                              const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
                              const double* __restrict__ x, int* __restrict__ count, float4* __restrict__ items,
-                             int n_verts) {
+                             int* __restrict__ vids, int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_verts) return;
     const int cap = v_cap[v];
@@ -654,17 +651,21 @@ __global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __res
     const int cz = min(max((int)floor(x[3 * v + 2] * 0.5), 0), d.cnz - 1);
     const long long idx = d.cell_off + cx + (long long)d.cnx * (cy + (long long)d.cny * cz);
     const int slot = atomicAdd(count + idx, 1);
-    // item: FP32 position (prefilter) and the vertex id; its capsule is v_cap
-    if (slot < CELL_CAP)
+    // item: FP32 position (prefilter) and the capsule id; the vertex id beside it
+    if (slot < CELL_CAP) {
         items[idx * CELL_CAP + slot] = make_float4((float)x[3 * v], (float)x[3 * v + 1], (float)x[3 * v + 2],
-                                                   __int_as_float(v));
-    else atomicOr(status_new + m, ST_OVERFLOW);
+                                                   __int_as_float(cap));
+        vids[idx * CELL_CAP + slot] = v;
+    } else {
+        atomicOr(status_new + m, ST_OVERFLOW);
+    }
 }
 
 __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
                             const uint32_t* __restrict__ status, const double* __restrict__ x,
                             const float* __restrict__ nrm, const int* __restrict__ count,
-                            const float4* __restrict__ items, float* __restrict__ force, int n_verts) {
+                            const float4* __restrict__ items, const int* __restrict__ vids,
+                            float* __restrict__ force, int n_verts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_verts) return;
     const int ci = v_cap[i];
@@ -686,12 +687,12 @@ __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __rest
                 const int cnt = min(count[idx], CELL_CAP);
                 for (int s = 0; s < cnt; ++s) {
                     const float4 it = items[idx * CELL_CAP + s];
+                    if (__float_as_int(it.w) == ci) continue;   // same body
                     // FP32 prefilter (coordinates below 1e4 lu round by < 1e-3,
                     // far inside the 0.01 margin on d^2)
                     const float fx = Xf - it.x, fy = Yf - it.y, fz = Zf - it.z;
                     if (fx * fx + fy * fy + fz * fz > 4.01f) continue;
-                    const int j = __float_as_int(it.w);
-                    if (v_cap[j] == ci) continue;
+                    const int j = vids[idx * CELL_CAP + s];
                     // the cutoff decides a discontinuous force: take it in FP64
                     const double rx = X - x[3 * j], ry = Y - x[3 * j + 1], rz = Z - x[3 * j + 2];
                     const double d2 = rx * rx + ry * ry + rz * rz;
@@ -898,8 +899,9 @@ cudaError_t launch_repulsion(const DevState& d, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int blocks = (d.n_verts + 255) / 256;
     k_cells_fill<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.status_new, d.x, d.cell_count, d.cell_items,
+                                        d.cell_vid,
                                         d.n_verts);
-    k_repulsion<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.x, d.nrm, d.cell_count, d.cell_items, d.force,
+    k_repulsion<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.x, d.nrm, d.cell_count, d.cell_items, d.cell_vid, d.force,
                                        d.n_verts);
     return cudaGetLastError();
 }

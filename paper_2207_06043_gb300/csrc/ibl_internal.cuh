@@ -167,7 +167,8 @@ struct DevState {
     float* kb = nullptr;
     int* e_cap = nullptr;
     int* cell_count = nullptr;
-    float4* cell_items = nullptr;    // (x, y, z, vertex id bits) per slot
+    float4* cell_items = nullptr;    // (x, y, z, capsule id bits) per slot
+    int* cell_vid = nullptr;         // vertex id per slot
     long long n_cells = 0;
 };
 constexpr int CELL_CAP = 32;
