@@ -191,7 +191,11 @@ ibl_status ibl_autotune(ibl_ctx* ctx, int32_t steps, int32_t* threads_out,
 
 /* Device time of the last ibl_step's kernels by kind, in milliseconds, when
  * timing was enabled with ibl_enable_timing (0 otherwise):
- * out[0] lattice, out[1] walls, out[2] IB pre-pass, out[3] structure. */
+ * out[0] lattice, out[1] walls and faces, out[2] IB pass (geometry, shell,
+ * marker and probe stencils), out[3] structure (repulsion, hinges, update).
+ * With timing on, the steps run without CUDA graphs and every phase runs
+ * alone, one after another on the context's stream (without timing the
+ * structure and probe kernels overlap the IB pass and the lattice step). */
 ibl_status ibl_enable_timing(ibl_ctx* ctx, int32_t on);
 
 /* Kernel launches of one regular time step: the kernel nodes of the step's

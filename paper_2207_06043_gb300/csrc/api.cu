@@ -667,6 +667,7 @@ struct Mark {
 
 // One time step.  Stream `work`: step begin, geometry, shell moments, the
 // marker stencils, then the lattice step, the wall fill and the faces.
+// (Timing mode runs every phase on `work`, one after another.)
 // Stream `work3`: the probe stencils, beside the marker stencils and the
 // lattice step.  Stream `work2`: after the geometry, repulsion and hinge
 // forces (beside the IB pass); after the markers and the probes, the
@@ -692,26 +693,36 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks) {
     };
     CK(launch_step_begin(D, s));
     const bool caps = D.n_caps > 0;
-    if (caps) {
+    if (caps && marks) {
+        // timing mode: the phases run one after another on one stream, so
+        // that each phase's events time it alone
         CKS(begin(s));
+        CK(launch_geometry(D, 0, s));
+        CK(launch_shell(D, parity, s));
+        CK(launch_markers(D, s));
+        CK(launch_probes(D, s));
+        CKS(end(TK_IB, s));
+        CKS(begin(s));
+        CK(launch_repulsion(D, s));
+        CK(launch_edges(D, s));
+        CK(launch_update(D, s));
+        CKS(end(TK_STRUCT, s));
+    } else if (caps) {
         CK(launch_geometry(D, 0, s));
         CK(cudaEventRecord(ctx->ev_fork, s));
         CK(launch_shell(D, parity, s));
         CK(cudaEventRecord(ctx->ev_shell, s));
         CK(launch_markers(D, s));
-        CKS(end(TK_IB, s));
         CK(cudaEventRecord(ctx->ev_ib, s));
         CK(cudaStreamWaitEvent(s3, ctx->ev_shell, 0));
         CK(launch_probes(D, s3));
         CK(cudaEventRecord(ctx->ev_probes, s3));
         CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0));
-        CKS(begin(s2));
         CK(launch_repulsion(D, s2));
         CK(launch_edges(D, s2));
         CK(cudaStreamWaitEvent(s2, ctx->ev_ib, 0));
         CK(cudaStreamWaitEvent(s2, ctx->ev_probes, 0));
         CK(launch_update(D, s2));
-        CKS(end(TK_STRUCT, s2));
     }
     CKS(begin(s));
     CK(launch_lbm(D, parity, s));
@@ -720,7 +731,7 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks) {
     CK(launch_bfl(D, parity, s));
     CK(launch_faces(D, parity, s));
     CKS(end(TK_BFL, s));
-    if (caps) {
+    if (caps && !marks) {
         CK(cudaEventRecord(ctx->ev_join, s2));
         CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     }
