@@ -179,6 +179,13 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
     }
 }
 
+// Offsets (dx, dy, dz) of support node k = (dx+1) + 3 (dy+1) + 9 (dz+1) of
+// the 3x3x3 MLS block, packed two bits per node, so that a run-time k costs a
+// shift and a mask instead of divisions.
+__device__ __forceinline__ int sdx(int k) { return (int)((0x24924924924924ull >> (2 * k)) & 3ull) - 1; }
+__device__ __forceinline__ int sdy(int k) { return (int)((0x2a540a9502a540ull >> (2 * k)) & 3ull) - 1; }
+__device__ __forceinline__ int sdz(int k) { return (int)((0x2aaaa555540000ull >> (2 * k)) & 3ull) - 1; }
+
 // MLS operator of one point: weights W_k of the 27 support nodes (Eq.
 // intKernel) and the first ROWS rows of A^{-1} (Eq. l2norm, basis
 // [1, x-X, y-Y, z-Z]; A is symmetric, so row j is A^{-1} e_j); moments summed
@@ -268,7 +275,7 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
     int bestk = 27;
 #pragma unroll
     for (int k = 0; k < 27; ++k) {
-        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+        const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
         const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
                                   : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
         const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
@@ -296,12 +303,12 @@ __device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __r
 }
 
 __device__ __forceinline__ float mls_row(const Mls& M, int j, int k) {
-    const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
+    const float rx = M.ox + sdx(k), ry = M.oy + sdy(k), rz = M.oz + sdz(k);
     return M.W[k] * (M.inv[j][0] + M.inv[j][1] * rx + M.inv[j][2] * ry + M.inv[j][3] * rz);
 }
 
 __device__ __forceinline__ int mls_node(const MemberDev& d, const Mls& M, int k) {
-    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
     return M.base >= 0 ? M.base + dx + d.NX * (dy + d.NY * dz) : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
 }
 
@@ -388,7 +395,7 @@ __device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* _
         const int k = r + GL * j;
         float w = 0.f;
         if (k < 27) {
-            const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+            const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
             const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
                                       : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
             const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
@@ -429,12 +436,12 @@ __device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* _
 }
 
 __device__ __forceinline__ float mls_row_g(const MlsG& M, int row, int j, int k) {
-    const float rx = M.ox + (k % 3 - 1), ry = M.oy + ((k / 3) % 3 - 1), rz = M.oz + (k / 9 - 1);
+    const float rx = M.ox + sdx(k), ry = M.oy + sdy(k), rz = M.oz + sdz(k);
     return M.W[j] * (M.inv[row][0] + M.inv[row][1] * rx + M.inv[row][2] * ry + M.inv[row][3] * rz);
 }
 
 __device__ __forceinline__ int mls_node_g(const MemberDev& d, const MlsG& M, int k) {
-    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
     return M.base >= 0 ? M.base + dx + d.NX * (dy + d.NY * dz) : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
 }
 
