@@ -149,10 +149,17 @@ inline double vdot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 inline double vnorm(V3 a) { return std::sqrt(vdot(a, a)); }
 
 // hinges: for every edge {p<q}: (wing of p->q, p, q, wing of q->p), sorted by (p, q)
+// Hinges of a closed, consistently oriented triangle mesh: for every edge
+// u < v, the wing vertex of the triangle holding the half-edge u->v, u, v, and
+// the wing of the triangle holding v->u (edges in (u, v) order).  Half-edges
+// are sorted by (u, v) instead of kept in a tree: meshes of thousands of
+// vertices are set up in a millisecond.
 bool build_hinges(const std::vector<int>& tris, int nv, std::vector<int>& hinge, std::vector<int>& tri_a,
                   std::vector<int>& tri_b, std::string& why) {
-    std::map<std::pair<int, int>, std::pair<int, int>> half;   // (u,v) -> (tri, wing)
+    struct Half { long long key; int t, wing; };
     const int nt = (int)tris.size() / 3;
+    std::vector<Half> half;
+    half.reserve(3 * (size_t)nt);
     for (int t = 0; t < nt; ++t) {
         const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
         if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv || a == b || b == c || a == c) {
@@ -160,31 +167,31 @@ bool build_hinges(const std::vector<int>& tris, int nv, std::vector<int>& hinge,
             return false;
         }
         const int uvw[3][3] = {{a, b, c}, {b, c, a}, {c, a, b}};
-        for (auto& r : uvw) {
-            auto key = std::make_pair(r[0], r[1]);
-            if (half.count(key)) { why = "edge used twice in the same direction (mesh not consistently oriented)"; return false; }
-            half[key] = std::make_pair(t, r[2]);
-        }
+        for (auto& r : uvw) half.push_back({(long long)r[0] * nv + r[1], t, r[2]});
     }
-    hinge.clear(); tri_a.clear(); tri_b.clear();
-    for (auto& kv : half) {
-        const int u = kv.first.first, v = kv.first.second;
-        if (u > v) continue;
-        auto it = half.find(std::make_pair(v, u));
-        if (it == half.end()) { why = "mesh is not closed"; return false; }
-        hinge.push_back(kv.second.second);
-        hinge.push_back(u);
-        hinge.push_back(v);
-        hinge.push_back(it->second.second);
-        tri_a.push_back(kv.second.first);
-        tri_b.push_back(it->second.first);
-    }
-    for (auto& kv : half) {
-        if (kv.first.first > kv.first.second && !half.count(std::make_pair(kv.first.second, kv.first.first))) {
-            why = "mesh is not closed";
+    std::sort(half.begin(), half.end(), [](const Half& x, const Half& y) { return x.key < y.key; });
+    for (size_t i = 1; i < half.size(); ++i)
+        if (half[i].key == half[i - 1].key) {
+            why = "edge used twice in the same direction (mesh not consistently oriented)";
             return false;
         }
+    hinge.clear(); tri_a.clear(); tri_b.clear();
+    size_t paired = 0;
+    for (const Half& h : half) {
+        const int u = (int)(h.key / nv), v = (int)(h.key % nv);
+        if (u > v) continue;
+        const long long rk = (long long)v * nv + u;
+        auto it = std::lower_bound(half.begin(), half.end(), rk, [](const Half& x, long long k) { return x.key < k; });
+        if (it == half.end() || it->key != rk) { why = "mesh is not closed"; return false; }
+        hinge.push_back(h.wing);
+        hinge.push_back(u);
+        hinge.push_back(v);
+        hinge.push_back(it->wing);
+        tri_a.push_back(h.t);
+        tri_b.push_back(it->t);
+        ++paired;
     }
+    if (2 * paired != half.size()) { why = "mesh is not closed"; return false; }
     return true;
 }
 
@@ -297,21 +304,25 @@ ibl_status validate_member(ibl_ctx* ctx, const MemberHost& M) {
     const long long N = (long long)d.nx * d.ny * d.nz;
     if ((long long)M.tag.size() != N) return fail(ctx, IBL_ERR_STATE, "geometry not set");
     const int dims[3] = {d.nx, d.ny, d.nz};
-    for (long long n = 0; n < N; ++n) {
-        if (M.tag[n] != 0) continue;
-        const int c[3] = {(int)(n % d.nx), (int)((n / d.nx) % d.ny), (int)(n / ((long long)d.nx * d.ny))};
-        int nf = 0, face = -1;
-        for (int a = 0; a < 3; ++a) {
-            if (d.periodic[a]) continue;
-            if (c[a] == 0) { ++nf; face = 2 * a; }
-            if (c[a] == dims[a] - 1) { ++nf; face = 2 * a + 1; }
-        }
-        if (nf > 1)
-            return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on an edge of the box (two faces)");
-        if (nf == 1 && M.face_kind[face] == IBL_FACE_NONE)
-            return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on face " + std::to_string(face) +
-                                               " which has no velocity or pressure condition");
-    }
+    long long n = 0;   // x fastest, coordinates kept by the loops (no divisions)
+    for (int z = 0; z < d.nz; ++z)
+        for (int y = 0; y < d.ny; ++y)
+            for (int x = 0; x < d.nx; ++x, ++n) {
+                if (M.tag[n] != 0) continue;
+                const int c[3] = {x, y, z};
+                int nf = 0, face = -1;
+                for (int a = 0; a < 3; ++a) {
+                    if (d.periodic[a]) continue;
+                    if (c[a] == 0) { ++nf; face = 2 * a; }
+                    if (c[a] == dims[a] - 1) { ++nf; face = 2 * a + 1; }
+                }
+                if (nf > 1)
+                    return fail(ctx, IBL_ERR_ARG,
+                                "fluid node " + std::to_string(n) + " lies on an edge of the box (two faces)");
+                if (nf == 1 && M.face_kind[face] == IBL_FACE_NONE)
+                    return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on face " +
+                                                      std::to_string(face) + " which has no velocity or pressure condition");
+            }
     return IBL_OK;
 }
 
@@ -526,23 +537,26 @@ ibl_status finalize(ibl_ctx* ctx) {
             const int ns = (md.N + 31) / 32;
             const bool per[3] = {(md.per & 1) != 0, (md.per & 2) != 0, (md.per & 4) != 0};
             const int dimP[3] = {md.NX, md.NY, md.NZ};
+            int c[3] = {0, 0, 0};   // coordinates of node n, kept by counters (no divisions)
             for (int j = 0; j < ns; ++j) {
                 bool any = false, border = false;
                 for (int t = 0; t < 32; ++t) {
                     const long long n = 32LL * j + t;
-                    if (n >= md.N || (tag_all[base + n] & TAG_SOLID)) continue;
-                    any = true;
-                    const int c[3] = {(int)(n % md.NX), (int)((n / md.NX) % md.NY), (int)(n / ((long long)md.NX * md.NY))};
-                    int face = -1;
-                    for (int a = 0; a < 3; ++a) {
-                        if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) border = true;          // wrap plane
-                        if (!per[a] && face < 0 && c[a] == 1) face = 2 * a;                        // box faces
-                        if (!per[a] && face < 0 && c[a] == dimP[a] - 2) face = 2 * a + 1;
+                    if (n >= md.N) break;
+                    if (!(tag_all[base + n] & TAG_SOLID)) {
+                        any = true;
+                        int face = -1;
+                        for (int a = 0; a < 3; ++a) {
+                            if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) border = true;          // wrap plane
+                            if (!per[a] && face < 0 && c[a] == 1) face = 2 * a;                        // box faces
+                            if (!per[a] && face < 0 && c[a] == dimP[a] - 2) face = 2 * a + 1;
+                        }
+                        if (face >= 0 && md.face_kind[face] != FACE_NONE) {
+                            fc_node.push_back((uint32_t)n);
+                            fc_meta.push_back((uint32_t)face | ((uint32_t)m << 8));
+                        }
                     }
-                    if (face >= 0 && md.face_kind[face] != FACE_NONE) {
-                        fc_node.push_back((uint32_t)n);
-                        fc_meta.push_back((uint32_t)face | ((uint32_t)m << 8));
-                    }
+                    if (++c[0] == md.NX) { c[0] = 0; if (++c[1] == md.NY) { c[1] = 0; ++c[2]; } }
                 }
                 if (any) (border ? bsegs : segs).push_back((uint32_t)j);
             }
@@ -949,7 +963,7 @@ ibl_status new_ctx(void* stream, ibl_ctx** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        delete ctx;
+        ibl_destroy(ctx);   // releases whatever was created
         return fail(nullptr, IBL_ERR_CUDA, std::string("stream/event creation failed: ") + cudaGetErrorString(e));
     }
     *out = ctx;
