@@ -335,13 +335,13 @@ constexpr bool PROBE_FAST32 = true;
 #define IB_MARKER_THREADS 128
 #endif
 #ifndef IB_MARKER_MIN_BLOCKS
-#define IB_MARKER_MIN_BLOCKS 6
+#define IB_MARKER_MIN_BLOCKS 8
 #endif
 #ifndef IB_PROBE_THREADS
 #define IB_PROBE_THREADS 128
 #endif
 #ifndef IB_PROBE_MIN_BLOCKS
-#define IB_PROBE_MIN_BLOCKS 6
+#define IB_PROBE_MIN_BLOCKS 8
 #endif
 #ifndef IBL_MARKER_FAST32
 #define IBL_MARKER_FAST32 1
@@ -354,8 +354,11 @@ constexpr bool MARKER_FAST32 = IBL_MARKER_FAST32 != 0;
 // the group, and every lane of the group holds the same solved rows.  A
 // stencil's latency chain is a quarter of the one-lane form and its registers
 // hold 7 weights instead of 27.
-constexpr int GL = 4;   // lanes per stencil
-constexpr int GS = 7;   // support nodes per lane
+#ifndef IB_GROUP_LANES
+#define IB_GROUP_LANES 4
+#endif
+constexpr int GL = IB_GROUP_LANES;      // lanes per stencil (a power of two, at most 32)
+constexpr int GS = (27 + GL - 1) / GL;  // support nodes per lane
 
 struct MlsG {
     int bx, by, bz;
@@ -738,19 +741,23 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
     if (C.rigid || (status[C.member] & STOP)) return;
     float H[3];
     hydro_force(probe, nrm, area, v, H[0], H[1], H[2]);
-    const double half_inv_m = 0.5 / C.mv;
+    const float half_inv_m = 0.5f / (float)C.mv;
     bool bad = false;
+    // With a = F / (2 m_v): predictor x* = x + u_0 + a, velocity
+    // u = 3/2 x* - 2 x + 1/2 x_prev = 3/2 (u_0 + a) + 1/2 (x_prev - x), corrector
+    // x_new = x + u + a.  Positions stay FP64; the increments, of the size of
+    // a velocity, are formed in FP32 (GB300's FP64 pipe is narrow).
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double acc = ((double)force[4 * v + a] + (double)H[a]) * half_inv_m;
+        const float acc = (force[4 * v + a] + H[a]) * half_inv_m;
         force[4 * v + a] = 0.f;
         const double xt = x[3 * v + a];
-        const double xp = xt + (double)uv0[3 * v + a] + acc;
-        const double un = 1.5 * xp - 2.0 * xt + 0.5 * x_prev[3 * v + a];
-        const double xn = xt + un + acc;
+        const float back = (float)(x_prev[3 * v + a] - xt);
+        const float un = 1.5f * (uv0[3 * v + a] + acc) + 0.5f * back;
+        const double xn = xt + (double)(un + acc);
         x_prev[3 * v + a] = xt;
         x[3 * v + a] = xn;
-        vel[3 * v + a] = un;
+        vel[3 * v + a] = (double)un;
         bad |= !isfinite(xn);
     }
     if (bad) atomicOr(status_new + C.member, ST_NONFINITE);
@@ -844,9 +851,12 @@ __global__ void __launch_bounds__(256) k_damage(const CapsuleDev* __restrict__ c
     const CapsuleDev& C = caps[e_cap[e]];
     if (C.rigid || (status[C.member] & STOP)) return;
     const int a = hinge[4 * e + 1], b = hinge[4 * e + 2];
-    const double dx = x[3 * a] - x[3 * b], dy = x[3 * a + 1] - x[3 * b + 1], dz = x[3 * a + 2] - x[3 * b + 2];
-    const double l0e = (double)l0[e];
-    if (dx * dx + dy * dy + dz * dz >= 4.0 * l0e * l0e) atomicOr(status_new + C.member, ST_DAMAGED);
+    // differences in FP64, the squared length in FP32 (a relative 1e-7 at the
+    // threshold of twice the rest length)
+    const float dx = (float)(x[3 * a] - x[3 * b]), dy = (float)(x[3 * a + 1] - x[3 * b + 1]),
+                dz = (float)(x[3 * a + 2] - x[3 * b + 2]);
+    const float l0e = l0[e];
+    if (dx * dx + dy * dy + dz * dz >= 4.f * l0e * l0e) atomicOr(status_new + C.member, ST_DAMAGED);
 }
 
 // ---------------------------------------------------------------------------
