@@ -1238,7 +1238,7 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
     // work buffers: allocated by the first call (or a call that needs more
     // checkpoints or a longer segment) and kept in the context
     auto& AC = ctx->adj;
-    const size_t ck_need = (size_t)std::max(n_ck - 1, 1) * D.f_bytes;
+    const size_t ck_need = (size_t)(n_ck - 1) * D.f_bytes;   // no copy when one segment covers the steps
     if (AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc) {
         cudaStreamSynchronize(ctx->work);
         free_adjoint(ctx);
