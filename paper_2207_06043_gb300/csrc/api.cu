@@ -271,13 +271,14 @@ ibl_status leave(ibl_ctx* ctx) {
     return IBL_OK;
 }
 
-// Lattice-kernel blocks for the current block size: one warp per fluid segment.
+// Lattice-kernel blocks for the current block size: one warp per group of 32
+// fluid nodes.
 void layout_tiles(ibl_ctx* ctx) {
     const int per_block = ctx->threads / 32;
-    const int blocks = (ctx->dev.n_segs + per_block - 1) / per_block;
+    const int blocks = (ctx->dev.n_groups + per_block - 1) / per_block;
     ctx->dev.threads = ctx->threads;
     ctx->dev.lbm_blocks = blocks;
-    ctx->dev.lbm_bblocks = (ctx->dev.n_bsegs + per_block - 1) / per_block;
+    ctx->dev.lbm_bblocks = (ctx->dev.n_bgroups + per_block - 1) / per_block;
     ctx->dev.grid_lbm = ctx->blocks_per_sm > 0 ? std::min(blocks, ctx->blocks_per_sm * ctx->n_sm) : 0;
     ctx->dev.n_sm = ctx->n_sm;
 }
@@ -527,7 +528,8 @@ ibl_status finalize(ibl_ctx* ctx) {
     // the padded layout holding at least one fluid node, split into border
     // runs (a fluid node on the wrap plane of a periodic axis: coordinates
     // needed) and interior runs; and the list of fluid nodes on Zou-He faces
-    std::vector<uint32_t> segs, bsegs, fc_node, fc_meta;
+    std::vector<uint32_t> segs, bsegs, fc_node, fc_meta, nodes, bnodes;
+    std::vector<int> group_mem, bgroup_mem;
     {
         size_t base = 0;
         for (int m = 0; m < nm; ++m) {
@@ -546,11 +548,14 @@ ibl_status finalize(ibl_ctx* ctx) {
                     if (!(tag_all[base + n] & TAG_SOLID)) {
                         any = true;
                         int face = -1;
+                        bool wrap = false;
                         for (int a = 0; a < 3; ++a) {
-                            if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) border = true;          // wrap plane
+                            if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) wrap = true;            // wrap plane
                             if (!per[a] && face < 0 && c[a] == 1) face = 2 * a;                        // box faces
                             if (!per[a] && face < 0 && c[a] == dimP[a] - 2) face = 2 * a + 1;
                         }
+                        border = border || wrap;
+                        (wrap ? bnodes : nodes).push_back((uint32_t)n);
                         if (face >= 0 && md.face_kind[face] != FACE_NONE) {
                             fc_node.push_back((uint32_t)n);
                             fc_meta.push_back((uint32_t)face | ((uint32_t)m << 8));
@@ -560,12 +565,20 @@ ibl_status finalize(ibl_ctx* ctx) {
                 }
                 if (any) (border ? bsegs : segs).push_back((uint32_t)j);
             }
+            // close the member's node lists on a whole group of 32
+            for (auto* lst : {&nodes, &bnodes}) {
+                while (lst->size() % 32) lst->push_back(NO_NODE);
+                std::vector<int>& gm = lst == &nodes ? group_mem : bgroup_mem;
+                gm.resize(lst->size() / 32, m);
+            }
             md.seg_count = (int)segs.size() - md.seg_begin;
             md.bseg_count = (int)bsegs.size() - md.bseg_begin;
             base += round_up((size_t)md.N, 256);
         }
         D.n_segs = (int)segs.size();
         D.n_bsegs = (int)bsegs.size();
+        D.n_groups = (int)(nodes.size() / 32);
+        D.n_bgroups = (int)(bnodes.size() / 32);
         D.n_face_nodes = (int)fc_node.size();
     }
     layout_tiles(ctx);
@@ -574,6 +587,16 @@ ibl_status finalize(ibl_ctx* ctx) {
     CKS(dev_alloc(ctx, D.bsegs, std::max<size_t>(bsegs.size(), 1)));
     CKS(upload(ctx, D.segs, segs));
     CKS(upload(ctx, D.bsegs, bsegs));
+    CKS(dev_alloc(ctx, D.nodes, std::max<size_t>(nodes.size(), 1)));
+    CKS(dev_alloc(ctx, D.bnodes, std::max<size_t>(bnodes.size(), 1)));
+    CKS(upload(ctx, D.nodes, nodes));
+    CKS(upload(ctx, D.bnodes, bnodes));
+    if (nm > 1) {
+        CKS(dev_alloc(ctx, D.group_mem, std::max<size_t>(group_mem.size(), 1)));
+        CKS(dev_alloc(ctx, D.bgroup_mem, std::max<size_t>(bgroup_mem.size(), 1)));
+        CKS(upload(ctx, D.group_mem, group_mem));
+        CKS(upload(ctx, D.bgroup_mem, bgroup_mem));
+    }
     CKS(dev_alloc(ctx, D.fc_node, std::max<size_t>(fc_node.size(), 1)));
     CKS(dev_alloc(ctx, D.fc_meta, std::max<size_t>(fc_meta.size(), 1)));
     CKS(upload(ctx, D.fc_node, fc_node));
@@ -646,6 +669,7 @@ ibl_status finalize(ibl_ctx* ctx) {
             CKS(dev_alloc(ctx, D.cell_count, (size_t)cell_off));
             CKS(dev_alloc(ctx, D.cell_items, (size_t)cell_off * CELL_CAP));
             CKS(dev_alloc(ctx, D.cell_vid, (size_t)cell_off * CELL_CAP));
+            CKS(dev_alloc(ctx, D.near, caps.size() * NEAR_STRIDE));
         }
     }
     D.h_mem = ctx->hmem.data();

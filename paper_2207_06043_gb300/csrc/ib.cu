@@ -464,6 +464,8 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = t & (GL - 1);
     const int l = min(t / GL, n_verts - 1);
+    // the marker's position is fetched beside its capsule's flags
+    const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
     const int cap = v_cap[l];
     const CapsuleDev& C = caps[cap];
     const int m = C.member;
@@ -472,7 +474,7 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     if (!valid) return;
     const MemberDev& d = mem[m];
     MlsG M;
-    mls_build_g<1, MARKER_FAST32>(d, tag, x[3 * l], x[3 * l + 1], x[3 * l + 2], r, mask, M);
+    mls_build_g<1, MARKER_FAST32>(d, tag, X, Y, Z, r, mask, M);
     float p[GS];
     float4 q[GS];
 #pragma unroll
@@ -522,16 +524,17 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
     const int sid = t / GL;
     const int l = min(sid >> 1, n_verts - 1);
     const int s = 1 + (sid & 1);
+    // the probe's position is fetched beside its capsule's flags
+    const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
+    const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
     const int m = caps[v_cap[l]].member;
     const bool valid = (sid >> 1) < n_verts && !(status[m] & STOP);
     const unsigned mask = __ballot_sync(FULL, valid);
     if (!valid) return;
     const MemberDev& d = mem[m];
-    const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
     const double sg = s == 1 ? 1.2 : -1.2;
     MlsG M;
-    mls_build_g<4, PROBE_FAST32>(d, tag, x[3 * l] + sg * nx, x[3 * l + 1] + sg * ny, x[3 * l + 2] + sg * nz, r,
-                                 mask, M);
+    mls_build_g<4, PROBE_FAST32>(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, r, mask, M);
     float4 q[GS];
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
@@ -645,26 +648,90 @@ __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, co
 // ---------------------------------------------------------------------------
 // Inter-body repulsion (Eq. collision) for markers of different capsules
 // closer than 2 dx, found on a uniform grid of 2 dx cells.
+//
+// Broad phase first: a marker i of capsule c can be within 2 dx of a marker of
+// capsule o only if it lies inside o's vertex box grown by 2 dx.  k_broad
+// lists, per capsule, the boxes of the capsules of its lattice that, grown by
+// 3, meet its own box; a marker outside every listed box neither enters the
+// cell grid nor searches it.  The relation is symmetric, so every pair closer
+// than the cutoff has both markers in the grid and both searching.  The boxes
+// are those of the geometry pass at the same positions.  With the integer box
+// [lo, hi] of o (lo <= x < hi for its vertices), a marker at X closer than 2
+// to one of them has lo - 2 < X < hi + 2, hence lo - 2 <= floor(X) <= hi + 1;
+// the test takes floor of X rounded to FP32 against [lo - 2, hi + 2], which
+// holds whatever the rounding, in integer compares (GB300's FP64 pipe is
+// narrow).
 // ---------------------------------------------------------------------------
+constexpr int NEAR_GROW = 3;   // capsule-level margin (cutoff 2 plus one node)
+
+__global__ void __launch_bounds__(128) k_broad(const MemberDev* __restrict__ mem, const CapsuleDev* __restrict__ caps,
+                                               const CapsuleSums* __restrict__ sums,
+                                               const uint32_t* __restrict__ status, int4* __restrict__ near) {
+    __shared__ int cnt;
+    const int c = blockIdx.x;
+    const int m = caps[c].member;
+    const MemberDev& d = mem[m];
+    int4* out = near + (size_t)c * NEAR_STRIDE;
+    if (!d.has_cells || (status[m] & STOP)) {   // uniform over the block
+        if (threadIdx.x == 0) out[0] = make_int4(0, 0, 0, 0);
+        return;
+    }
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const CapsuleSums& A = sums[c];
+    for (int o = d.cap_begin + threadIdx.x; o < d.cap_begin + d.cap_count; o += blockDim.x) {
+        if (o == c) continue;
+        const CapsuleSums& B = sums[o];
+        bool meet = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            meet = meet && A.box_lo[a] <= B.box_hi[a] + NEAR_GROW && B.box_lo[a] - NEAR_GROW <= A.box_hi[a];
+        if (meet) {
+            const int k = atomicAdd(&cnt, 1);
+            if (k < NEAR_CAP) {
+                out[1 + 2 * k] = make_int4(B.box_lo[0] - 2, B.box_lo[1] - 2, B.box_lo[2] - 2, 0);
+                out[2 + 2 * k] = make_int4(B.box_hi[0] + 2, B.box_hi[1] + 2, B.box_hi[2] + 2, 0);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) out[0] = make_int4(cnt > NEAR_CAP ? -1 : cnt, 0, 0, 0);
+}
+
+// Whether a marker of capsule c at (X, Y, Z) lies inside a box listed as
+// near c (always when the list overflowed).
+__device__ __forceinline__ bool near_other(const int4* __restrict__ near, int c, double X, double Y, double Z) {
+    const int4* e = near + (size_t)c * NEAR_STRIDE;
+    const int n = e[0].x;
+    if (n < 0) return true;
+    const int xi = (int)floorf((float)X), yi = (int)floorf((float)Y), zi = (int)floorf((float)Z);
+    for (int k = 0; k < n; ++k) {
+        const int4 lo = e[1 + 2 * k], hi = e[2 + 2 * k];
+        if (xi >= lo.x && xi <= hi.x && yi >= lo.y && yi <= hi.y && zi >= lo.z && zi <= hi.z) return true;
+    }
+    return false;
+}
+
 __global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
                              const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
-                             const double* __restrict__ x, int* __restrict__ count, float4* __restrict__ items,
-                             int* __restrict__ vids, int n_verts) {
+                             const double* __restrict__ x, const int4* __restrict__ near, int* __restrict__ count,
+                             float4* __restrict__ items, int* __restrict__ vids, int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_verts) return;
+    const double X = x[3 * v], Y = x[3 * v + 1], Z = x[3 * v + 2];   // issued beside the capsule lookups
     const int cap = v_cap[v];
     const int m = caps[cap].member;
     const MemberDev& d = mem[m];
     if (!d.has_cells || (status[m] & STOP)) return;
-    const int cx = min(max((int)floor(x[3 * v] * 0.5), 0), d.cnx - 1);
-    const int cy = min(max((int)floor(x[3 * v + 1] * 0.5), 0), d.cny - 1);
-    const int cz = min(max((int)floor(x[3 * v + 2] * 0.5), 0), d.cnz - 1);
+    if (!near_other(near, cap, X, Y, Z)) return;
+    const int cx = min(max((int)floor(X * 0.5), 0), d.cnx - 1);
+    const int cy = min(max((int)floor(Y * 0.5), 0), d.cny - 1);
+    const int cz = min(max((int)floor(Z * 0.5), 0), d.cnz - 1);
     const long long idx = d.cell_off + cx + (long long)d.cnx * (cy + (long long)d.cny * cz);
     const int slot = atomicAdd(count + idx, 1);
     // item: FP32 position (prefilter) and the capsule id; the vertex id beside it
     if (slot < CELL_CAP) {
-        items[idx * CELL_CAP + slot] = make_float4((float)x[3 * v], (float)x[3 * v + 1], (float)x[3 * v + 2],
-                                                   __int_as_float(cap));
+        items[idx * CELL_CAP + slot] = make_float4((float)X, (float)Y, (float)Z, __int_as_float(cap));
         vids[idx * CELL_CAP + slot] = v;
     } else {
         atomicOr(status_new + m, ST_OVERFLOW);
@@ -673,16 +740,18 @@ __global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __res
 
 __global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
                             const uint32_t* __restrict__ status, const double* __restrict__ x,
-                            const float* __restrict__ nrm, const int* __restrict__ count,
+                            const float* __restrict__ nrm, const int4* __restrict__ near,
+                            const int* __restrict__ count,
                             const float4* __restrict__ items, const int* __restrict__ vids,
                             float* __restrict__ force, int n_verts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_verts) return;
+    const double X = x[3 * i], Y = x[3 * i + 1], Z = x[3 * i + 2];   // issued beside the capsule lookups
     const int ci = v_cap[i];
     const int m = caps[ci].member;
     const MemberDev& d = mem[m];
     if (!d.has_cells || (status[m] & STOP)) return;
-    const double X = x[3 * i], Y = x[3 * i + 1], Z = x[3 * i + 2];
+    if (!near_other(near, ci, X, Y, Z)) return;
     const float Xf = (float)X, Yf = (float)Y, Zf = (float)Z;
     const int cx = min(max((int)floor(X * 0.5), 0), d.cnx - 1);
     const int cy = min(max((int)floor(Y * 0.5), 0), d.cny - 1);
@@ -737,11 +806,25 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
                                                 int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_verts) return;
-    const CapsuleDev& C = caps[v_cap[v]];
-    if (C.rigid || (status[C.member] & STOP)) return;
+    const int cap = v_cap[v];
+    // every per-vertex load is issued before the capsule's flags arrive, so
+    // that their latencies overlap instead of following one another
+    const float4 fo = reinterpret_cast<const float4*>(force)[v];
+    double xt[3], xp[3];
+    float u0[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xt[a] = x[3 * v + a];
+        xp[a] = x_prev[3 * v + a];
+        u0[a] = uv0[3 * v + a];
+    }
     float H[3];
     hydro_force(probe, nrm, area, v, H[0], H[1], H[2]);
+    const CapsuleDev& C = caps[cap];
+    if (C.rigid || (status[C.member] & STOP)) return;
+    reinterpret_cast<float4*>(force)[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     const float half_inv_m = 0.5f / (float)C.mv;
+    const float F[3] = {fo.x, fo.y, fo.z};
     bool bad = false;
     // With a = F / (2 m_v): predictor x* = x + u_0 + a, velocity
     // u = 3/2 x* - 2 x + 1/2 x_prev = 3/2 (u_0 + a) + 1/2 (x_prev - x), corrector
@@ -749,13 +832,11 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
     // a velocity, are formed in FP32 (GB300's FP64 pipe is narrow).
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float acc = (force[4 * v + a] + H[a]) * half_inv_m;
-        force[4 * v + a] = 0.f;
-        const double xt = x[3 * v + a];
-        const float back = (float)(x_prev[3 * v + a] - xt);
-        const float un = 1.5f * (uv0[3 * v + a] + acc) + 0.5f * back;
-        const double xn = xt + (double)(un + acc);
-        x_prev[3 * v + a] = xt;
+        const float acc = (F[a] + H[a]) * half_inv_m;
+        const float back = (float)(xp[a] - xt[a]);
+        const float un = 1.5f * (u0[a] + acc) + 0.5f * back;
+        const double xn = xt[a] + (double)(un + acc);
+        x_prev[3 * v + a] = xt[a];
         x[3 * v + a] = xn;
         vel[3 * v + a] = (double)un;
         bad |= !isfinite(xn);
@@ -848,14 +929,17 @@ __global__ void __launch_bounds__(256) k_damage(const CapsuleDev* __restrict__ c
                                                 const float* __restrict__ l0, int n_edges) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_edges) return;
-    const CapsuleDev& C = caps[e_cap[e]];
-    if (C.rigid || (status[C.member] & STOP)) return;
-    const int a = hinge[4 * e + 1], b = hinge[4 * e + 2];
+    // the edge's vertices and positions are fetched before the capsule's
+    // flags, so that the two chains of loads overlap
+    const int4 h = reinterpret_cast<const int4*>(hinge)[e];
+    const int a = h.y, b = h.z;
+    const float l0e = l0[e];
     // differences in FP64, the squared length in FP32 (a relative 1e-7 at the
     // threshold of twice the rest length)
     const float dx = (float)(x[3 * a] - x[3 * b]), dy = (float)(x[3 * a + 1] - x[3 * b + 1]),
                 dz = (float)(x[3 * a + 2] - x[3 * b + 2]);
-    const float l0e = l0[e];
+    const CapsuleDev& C = caps[e_cap[e]];
+    if (C.rigid || (status[C.member] & STOP)) return;
     if (dx * dx + dy * dy + dz * dz >= 4.f * l0e * l0e) atomicOr(status_new + C.member, ST_DAMAGED);
 }
 
@@ -915,11 +999,11 @@ cudaError_t launch_repulsion(const DevState& d, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(d.cell_count, 0, sizeof(int) * d.n_cells, s);
     if (e != cudaSuccess) return e;
     const int blocks = (d.n_verts + 255) / 256;
-    k_cells_fill<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.status_new, d.x, d.cell_count, d.cell_items,
-                                        d.cell_vid,
-                                        d.n_verts);
-    k_repulsion<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.x, d.nrm, d.cell_count, d.cell_items, d.cell_vid, d.force,
-                                       d.n_verts);
+    k_broad<<<d.n_caps, 128, 0, s>>>(d.mem, d.caps, d.sums, d.status, d.near);
+    k_cells_fill<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.status_new, d.x, d.near, d.cell_count,
+                                        d.cell_items, d.cell_vid, d.n_verts);
+    k_repulsion<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.x, d.nrm, d.near, d.cell_count,
+                                       d.cell_items, d.cell_vid, d.force, d.n_verts);
     return cudaGetLastError();
 }
 

@@ -108,20 +108,31 @@ template <> struct Store<__nv_bfloat16> {
 // host-side launch entry points (one per translation unit)
 // ---------------------------------------------------------------------------
 // Device buffers of a context (all members concatenated).
+constexpr uint32_t NO_NODE = 0xffffffffu;   // padding entry of the lattice work lists
+
 struct DevState {
     int storage = 0;                 // 0 f32, 1 f16, 2 bf16
     int n_members = 0;
     const MemberDev* h_mem = nullptr;
     MemberDev* mem = nullptr;         // device copy of the member table (one per context)
-    int threads = 256;               // lattice kernel threads per block (one warp per segment)
+    int threads = 256;               // lattice kernel threads per block (one warp per group of 32 nodes)
     // 32-node segments holding at least one fluid node, all members, split
-    // into interior ones and border ones (a fluid node on a box face or a
-    // periodic wrap plane); entries are segment indices (padded node / 32)
-    // within their member
+    // into interior ones and border ones (a fluid node on a periodic wrap
+    // plane); entries are segment indices (padded node / 32) within their
+    // member.  The adjoint sweep runs over these.
     int n_segs = 0, n_bsegs = 0;
     uint32_t* segs = nullptr;
     uint32_t* bsegs = nullptr;
-    int lbm_blocks = 0, lbm_bblocks = 0;   // ceil(count / (threads / 32))
+    // Work lists of the lattice kernel: the fluid nodes of each member
+    // (padded index within the member) in ascending order, interior ones and
+    // wrap-plane ones apart, each member's list padded with NO_NODE to a
+    // multiple of 32; one warp per group of 32 entries.
+    int n_groups = 0, n_bgroups = 0;
+    uint32_t* nodes = nullptr;
+    uint32_t* bnodes = nullptr;
+    int* group_mem = nullptr;        // member of each group (batched contexts; null with one member)
+    int* bgroup_mem = nullptr;
+    int lbm_blocks = 0, lbm_bblocks = 0;   // ceil(groups / (threads / 32))
     int grid_lbm = 0;                // persistent grid of the interior kernel (0: default)
     int n_sm = 0;                    // multiprocessors of the device
 
@@ -169,9 +180,12 @@ struct DevState {
     int* cell_count = nullptr;
     float4* cell_items = nullptr;    // (x, y, z, capsule id bits) per slot
     int* cell_vid = nullptr;         // vertex id per slot
+    int4* near = nullptr;            // NEAR_STRIDE per capsule: count (-1: too many), then grown boxes
     long long n_cells = 0;
 };
 constexpr int CELL_CAP = 32;
+constexpr int NEAR_CAP = 31;          // capsules listed as near one capsule; more: all its markers search
+constexpr int NEAR_STRIDE = 1 + 2 * NEAR_CAP;   // int4 entries: the count, then two per listed box
 
 
 // The optional tape pointers record, per step, what the discrete adjoint needs

@@ -15,15 +15,6 @@
 #ifndef LBM_MIN_BLOCKS
 #define LBM_MIN_BLOCKS 6
 #endif
-// resident blocks per SM of the FP32 lattice kernel that stages its gathers
-// through shared memory with cp.async
-#ifndef LBMA_MIN_BLOCKS
-#define LBMA_MIN_BLOCKS 4
-#endif
-// 1: FP32 interior runs take the cp.async-staged kernel; 0: register gathers
-#ifndef LBM_ASYNC
-#define LBM_ASYNC 0
-#endif
 
 namespace ibl {
 
@@ -71,20 +62,21 @@ template <typename T, bool SINGLE, bool BORDER>
 __global__ void __launch_bounds__(LBM_THREADS, BORDER ? 4 : LBM_MIN_BLOCKS)
 k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T* __restrict__ f,
       uint8_t* __restrict__ tag, float* __restrict__ fib, const float* __restrict__ face_vel,
-      const uint32_t* __restrict__ status, const uint32_t* __restrict__ segs, int n_mem, int n_segs, int n_blocks,
-      int parity, float4* __restrict__ tape) {
+      const uint32_t* __restrict__ status, const uint32_t* __restrict__ nodes, const int* __restrict__ group_mem,
+      int n_groups, int n_blocks, int parity, float4* __restrict__ tape) {
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int b = blockIdx.x; b < n_blocks; b += gridDim.x) {
-        const int si = b * warps + (threadIdx.x >> 5);
-        if (si >= n_segs) continue;
-        const int m = SINGLE ? 0 : find_member_by_seg<BORDER>(mem, n_mem, si);
+        const int gi = b * warps + (threadIdx.x >> 5);
+        if (gi >= n_groups) continue;
+        // the node index and the member arrive together; the list holds
+        // fluid nodes only, so the populations' loads wait on nothing else
+        const uint32_t nn = nodes[(size_t)gi * 32 + lane];
+        const int m = SINGLE ? 0 : group_mem[gi];
         const MemberDev& d = SINGLE ? d0 : mem[m];
-        if (status[m] & (ST_DAMAGED | ST_NONFINITE)) continue;
-        const int n = (int)(segs[si] << 5) + lane;
-        if (n >= d.N) continue;
+        if (nn == NO_NODE || (status[m] & (ST_DAMAGED | ST_NONFINITE))) continue;
+        const int n = (int)nn;
         const long long gn = d.node_off + n;
         const uint8_t tg = tag[gn];
-        if (tg & TAG_SOLID) continue;
         T* fm = f + d.f_off;
         // the spread IB force is fetched together with the populations
         const bool ibn = tg & TAG_IB;
@@ -115,93 +107,6 @@ k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T
         collide(g, d.omega, d.guo, Fx, Fy, Fz, hasF);
         if (BORDER) store_post<T>(d, fm, n, X, Y, Z, parity, g);
         else store_post_lin<T>(d, fm, n, parity, g);
-    }
-}
-
-// FP32 interior runs with the gathers decoupled from the registers: each
-// thread copies its node's 19 pre-collision populations into shared memory
-// with cp.async (4 bytes each, no register held while in flight), one group
-// of runs ahead of the group it computes (two buffers per block), then
-// collides from shared memory and stores to global memory.  A thread reads
-// back only the copies it issued itself, so completion needs no barrier,
-// only cp.async.wait_group.  Persistent grid over groups of blockDim/32 runs.
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-struct RunNode {
-    int m;          // member
-    int n;          // padded node within the member (-1: no work)
-};
-
-template <bool SINGLE>
-__device__ __forceinline__ RunNode run_node(const MemberDev& d0, const MemberDev* __restrict__ mem,
-                                            const uint8_t* __restrict__ tag, const uint32_t* __restrict__ status,
-                                            const uint32_t* __restrict__ segs, int n_mem, int n_segs, int group) {
-    RunNode r{0, -1};
-    const int si = group * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
-    if (si >= n_segs) return r;
-    r.m = SINGLE ? 0 : find_member_by_seg<false>(mem, n_mem, si);
-    const MemberDev& d = SINGLE ? d0 : mem[r.m];
-    if (status[r.m] & (ST_DAMAGED | ST_NONFINITE)) return r;
-    const int n = (int)(segs[si] << 5) + (int)(threadIdx.x & 31);
-    if (n >= d.N || (tag[d.node_off + n] & TAG_SOLID)) return r;
-    r.n = n;
-    return r;
-}
-
-template <bool SINGLE>
-__global__ void __launch_bounds__(256, LBMA_MIN_BLOCKS)
-k_lbm_async(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, float* __restrict__ f,
-            uint8_t* __restrict__ tag, float* __restrict__ fib, const uint32_t* __restrict__ status,
-            const uint32_t* __restrict__ segs, int n_mem, int n_segs, int n_groups, int parity) {
-    extern __shared__ float stage[];   // [2][Q][blockDim.x]
-    const int B = blockDim.x, tid = threadIdx.x;
-    auto issue = [&](int group, int buf) {
-        if (group >= n_groups) return;
-        const RunNode r = run_node<SINGLE>(d0, mem, tag, status, segs, n_mem, n_segs, group);
-        if (r.n < 0) return;
-        const MemberDev& d = SINGLE ? d0 : mem[r.m];
-        const float* fm = f + d.f_off;
-        const size_t S = (size_t)d.S;
-        float* dst = stage + (size_t)buf * Q * B + tid;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const float* src = parity == 0 ? fm + k * S + r.n : fm + opp(k) * S + (r.n - lin_off(d, k));
-            cp_async4(dst + k * B, src);
-        }
-    };
-    int buf = 0;
-    issue(blockIdx.x, 0);
-    cp_async_commit();
-    for (int group = blockIdx.x; group < n_groups; group += gridDim.x, buf ^= 1) {
-        issue(group + gridDim.x, buf ^ 1);
-        cp_async_commit();
-        cp_async_wait1();
-        const RunNode r = run_node<SINGLE>(d0, mem, tag, status, segs, n_mem, n_segs, group);
-        if (r.n < 0) continue;
-        const MemberDev& d = SINGLE ? d0 : mem[r.m];
-        const float* src = stage + (size_t)buf * Q * B + tid;
-        float g[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) g[k] = src[k * B];
-        const long long gn = d.node_off + r.n;
-        const uint8_t tg = tag[gn];
-        float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
-        bool hasF = d.hasF != 0;
-        if (tg & TAG_IB) {
-            float4* p = reinterpret_cast<float4*>(fib) + gn;
-            const float4 fv = *p;
-            Fx += fv.x; Fy += fv.y; Fz += fv.z;
-            *p = make_float4(0.f, 0.f, 0.f, 0.f);
-            tag[gn] = tg & (uint8_t)~TAG_IB;
-            hasF = true;
-        }
-        collide(g, d.omega, d.guo, Fx, Fy, Fz, hasF);
-        store_post_lin<float>(d, f + d.f_off, r.n, parity, g);
     }
 }
 
@@ -429,34 +334,25 @@ template <typename T>
 static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s, float4* tape) {
     const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.lbm_blocks;
     const bool one = d.n_members == 1;
-    if (LBM_ASYNC && !tape && std::is_same<T, float>::value && d.lbm_blocks > 0) {
-        const int ag = std::min(d.lbm_blocks, (d.grid_lbm > 0 ? d.grid_lbm : LBMA_MIN_BLOCKS * d.n_sm));
-        const size_t smem = 2 * Q * sizeof(float) * (size_t)d.threads;
-        if (one)
-            k_lbm_async<true><<<ag, d.threads, smem, s>>>(d.h_mem[0], d.mem, (float*)d.f, d.tag, d.fib, d.status,
-                                                          d.segs, d.n_members, d.n_segs, d.lbm_blocks, parity);
-        else
-            k_lbm_async<false><<<ag, d.threads, smem, s>>>(d.h_mem[0], d.mem, (float*)d.f, d.tag, d.fib, d.status,
-                                                           d.segs, d.n_members, d.n_segs, d.lbm_blocks, parity);
-    } else if (grid > 0) {
+    if (grid > 0) {
         if (one)
             k_lbm<T, true, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
-                                                             d.status, d.segs, d.n_members, d.n_segs, d.lbm_blocks,
-                                                             parity, tape);
+                                                             d.status, d.nodes, d.group_mem, d.n_groups,
+                                                             d.lbm_blocks, parity, tape);
         else
             k_lbm<T, false, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
-                                                              d.status, d.segs, d.n_members, d.n_segs, d.lbm_blocks,
-                                                              parity, tape);
+                                                              d.status, d.nodes, d.group_mem, d.n_groups,
+                                                              d.lbm_blocks, parity, tape);
     }
     if (d.lbm_bblocks > 0) {
         if (one)
             k_lbm<T, true, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
-                                                                     d.face_vel, d.status, d.bsegs, d.n_members,
-                                                                     d.n_bsegs, d.lbm_bblocks, parity, tape);
+                                                                     d.face_vel, d.status, d.bnodes, d.bgroup_mem,
+                                                                     d.n_bgroups, d.lbm_bblocks, parity, tape);
         else
             k_lbm<T, false, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
-                                                                      d.face_vel, d.status, d.bsegs, d.n_members,
-                                                                      d.n_bsegs, d.lbm_bblocks, parity, tape);
+                                                                      d.face_vel, d.status, d.bnodes, d.bgroup_mem,
+                                                                      d.n_bgroups, d.lbm_bblocks, parity, tape);
     }
     return cudaGetLastError();
 }

@@ -248,14 +248,4 @@ __device__ __forceinline__ void moments_of(const float g[Q], float& rho, float& 
     ux = jx * inv; uy = jy * inv; uz = jz * inv;
 }
 
-template <bool BORDER>
-__device__ __forceinline__ int find_member_by_seg(const MemberDev* __restrict__ mem, int n_mem, int seg) {
-    int lo = 0, hi = n_mem - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((BORDER ? mem[mid].bseg_begin : mem[mid].seg_begin) <= seg) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 }  // namespace ibl

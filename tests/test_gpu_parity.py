@@ -135,6 +135,35 @@ def test_two_capsules_with_repulsion():
     assert err <= VEL_TOL, err
 
 
+def test_four_capsules_two_close_pairs():
+    """Four capsules in a row along the carrier flow: pairs (0, 1) and (2, 3)
+    come within 1.1 lu (repulsion), capsules 1 and 2 stay 3 lu apart (boxes
+    close enough to be listed as near, markers outside the cutoff) and the
+    rest are far.  Checks the broad phase that keeps markers away from the
+    cell search against the oracle's all-pairs repulsion."""
+    from oracle import lattice as L
+    g = G.periodic_box(40, 24, 20)
+    spec = [((7.5, 10.0, 10.0), (0.013, 0.001, 0)), ((16.3, 10.4, 9.8), (0.007, -0.001, 0)),
+            ((27.0, 12.0, 10.0), (0.012, 0.0, 0.0)), ((35.6, 11.5, 10.2), (0.008, 0.0, 0.0))]
+    caps = []
+    for k, (ctr, v) in enumerate(spec):
+        V, T = Ms.sphere_mesh(162, 8.0, ctr, Ms.SplitMix64(7 + k))
+        caps.append(W._capsule(V, T, Ca=0.05, vel0=v))
+    c = case(g, tau=0.9, capsules=caps)
+    lat = L.Lattice(g.nx, g.ny, g.nz, 0.9, g.tag, g.links, g.faces, g.periodic)
+    u0 = np.zeros((lat.N, 3))
+    u0[:, 0] = np.float32(0.01)
+    f0 = lat.init_equilibrium(None, u0)
+    err, perr, s, o, lat = _compare_fields(c, 60, f0=f0)
+    gap = lambda a, b: np.sqrt(((a[:, None, :] - b[None, :, :]) ** 2).sum(-1)).min()
+    X = [b.x for b in o.bodies]
+    assert gap(X[0], X[1]) < 2.0 and gap(X[2], X[3]) < 2.0 and gap(X[1], X[2]) > 2.0
+    for k in range(4):
+        dc = np.abs(s.read_capsule(k)["centroid"] - o.stats(k)["centroid"]).max()
+        assert dc <= CEN_TOL, (k, dc)
+    assert err <= VEL_TOL, err
+
+
 @pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", 2e-3)])
 def test_reduced_storage_against_fp32(storage, tol):
     """16-bit storage of f - w with FP32 arithmetic against the FP32 path:
