@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
     const bool live = v < n_verts && !(status[caps[v_cap[min(v, n_verts - 1)]].member] & STOP);
     const int c = live ? v_cap[v] : -1;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    int r2lo = 0x7f800000, r2hi = 0;   // FP32 bits (non-negative: integer order is value order)
     if (live) {
         const float4 a = vacc[v];
         const float inv = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
@@ -97,12 +98,17 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
         nrm[3 * v + 2] = a.z * inv;
         area[v] = a.w;
         vacc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float r2 = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const double q = x[3 * v + k];
             lo[k] = isfinite(q) ? (int)fmax(fmin(floor(q), 1e9), -1e9) : 0;
             hi[k] = lo[k] + 1;
+            const float dq = (float)(q - sums[c].rc[k]);
+            r2 += dq * dq;
         }
+        if (r2 >= 0.f && r2 < 1e30f) { r2lo = __float_as_int(r2); r2hi = r2lo; }
+        else { r2lo = 0; r2hi = 0x7f800000; }   // not finite: no radial bound
     }
     // lanes of one capsule reduce among themselves, then one lane per capsule
     // and warp updates the box (consecutive vertices share a capsule)
@@ -113,25 +119,34 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
         lo[k] = __reduce_min_sync(peers, lo[k]);
         hi[k] = __reduce_max_sync(peers, hi[k]);
     }
+    r2lo = __reduce_min_sync(peers, r2lo);
+    r2hi = __reduce_max_sync(peers, r2hi);
     if (live && (int)(threadIdx.x & 31) == leader) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             atomicMin(&sums[c].box_lo[k], lo[k]);
             atomicMax(&sums[c].box_hi[k], hi[k]);
         }
+        atomicMin(&sums[c].r2_lo, r2lo);
+        atomicMax(&sums[c].r2_hi, r2hi);
     }
 }
 
-// Moments (rho, u* = sum g e / rho) of the current populations at every fluid
-// node of each capsule's vertex bounding box grown by SHELL_MARGIN, which
-// holds every support node of the marker and probe stencils: a probe sits
-// 1.2 dx off its vertex, its base node is within 0.5 dx of it and the support
-// one node further, so every support coordinate lies within 2.7 dx of a
-// vertex, i.e. within [floor(min) - 2, floor(max) + 3] per axis, and the box
-// [floor(min), floor(max) + 1] grown by 3 holds it with a node to spare.  The
-// IB kernels then read one float4 per support node instead of 19 scattered
-// populations.  Overlapping boxes write identical values.
-constexpr int SHELL_MARGIN = 3;
+// Moments (rho, u* = sum g e / rho) of the current populations at the fluid
+// nodes that a marker or probe stencil can reach.  A marker's support lies
+// within 1.5 dx of it per axis (the 3x3x3 block around its nearest node); a
+// probe sits 1.2 dx off its vertex along the unit normal, so its support lies
+// within 1.2 + 1.5 = 2.7 dx of the vertex per axis and within 1.2 + 1.5 sqrt 3
+// < 3.8 dx of it in distance.  Per axis every support coordinate lies in
+// [floor(min) - 2, floor(max) + 3], which is the vertex box
+// [floor(min), floor(max) + 1] grown by SHELL_MARGIN = 2.  Within the box, a
+// node farther than sqrt(r2_hi) + 3.8 from the step's reference point rc, or
+// nearer than sqrt(r2_lo) - 3.8, is within 3.8 of no vertex and is skipped
+// (a 0.05 slack covers the FP32 distances).  The IB kernels then read one
+// float4 per support node instead of 19 scattered populations.  Overlapping
+// boxes write identical values.
+constexpr int SHELL_MARGIN = 2;
+constexpr float SHELL_REACH = 3.85f;
 constexpr int SHELL_BLOCKS = 64;   // blocks per capsule
 
 template <typename T>
@@ -146,10 +161,12 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
     const MemberDev& d = mem[C.member];
     const int dims[3] = {d.nx, d.ny, d.nz};
     int lo[3], ext[3];
+    bool wide = false;   // a grown box wider than a periodic lattice: no radial test
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         int l = sums[c].box_lo[a] - SHELL_MARGIN, h = sums[c].box_hi[a] + SHELL_MARGIN;
         if ((d.per >> a) & 1) {
+            wide = wide || h > l + dims[a] - 1;
             h = min(h, l + dims[a] - 1);
         } else {
             l = max(l, 0);
@@ -159,12 +176,20 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
         ext[a] = h - l + 1;
     }
     if (ext[0] <= 0 || ext[1] <= 0 || ext[2] <= 0) return;
+    // annulus of the vertices about rc, grown by the stencils' reach
+    const float rhi = sqrtf(__int_as_float(sums[c].r2_hi)) + SHELL_REACH;
+    const float rlo = sqrtf(__int_as_float(sums[c].r2_lo)) - SHELL_REACH;
+    const float r2_out = wide ? INFINITY : rhi * rhi, r2_in = (!wide && rlo > 0.f) ? rlo * rlo : -1.f;
+    const float rcx = (float)sums[c].rc[0], rcy = (float)sums[c].rc[1], rcz = (float)sums[c].rc[2];
     const int exy = ext[0] * ext[1];
     const int total = exy * ext[2];     // a box of one lattice: below 2^31 nodes
     const T* fm = f + d.f_off;
     for (int i = (blockIdx.x % SHELL_BLOCKS) * blockDim.x + threadIdx.x; i < total; i += SHELL_BLOCKS * blockDim.x) {
         const int iz = i / exy, r = i - iz * exy, iy = r / ext[0];
         int cx = lo[0] + (r - iy * ext[0]), cy = lo[1] + iy, cz = lo[2] + iz;
+        const float qx = (float)cx - rcx, qy = (float)cy - rcy, qz = (float)cz - rcz;
+        const float q2 = qx * qx + qy * qy + qz * qz;
+        if (q2 > r2_out || q2 < r2_in) continue;
         if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx;
         if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny;
         if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz;
@@ -185,20 +210,6 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
 __device__ __forceinline__ int sdx(int k) { return (int)((0x24924924924924ull >> (2 * k)) & 3ull) - 1; }
 __device__ __forceinline__ int sdy(int k) { return (int)((0x2a540a9502a540ull >> (2 * k)) & 3ull) - 1; }
 __device__ __forceinline__ int sdz(int k) { return (int)((0x2aaaa555540000ull >> (2 * k)) & 3ull) - 1; }
-
-// MLS operator of one point: weights W_k of the 27 support nodes (Eq.
-// intKernel) and the first ROWS rows of A^{-1} (Eq. l2norm, basis
-// [1, x-X, y-Y, z-Z]; A is symmetric, so row j is A^{-1} e_j); moments summed
-// in FP32, the 4x4 system factorised and solved in FP64.  fallback >= 0:
-// singular system, the whole point goes to support node `fallback`.
-struct Mls {
-    int bx, by, bz;
-    int base;               // padded index of the base node when the block is interior, else -1
-    float ox, oy, oz;       // base node minus point
-    float W[27];
-    float inv[4][4];
-    int fallback;           // -1: regular; 0..26: nearest fluid node; 27: none
-};
 
 // 1/d in FP64 by Newton's iteration r <- r (2 - d r) from the FP32
 // reciprocal (each step doubles the correct bits: 24 -> 48 -> full)
@@ -262,58 +273,8 @@ __device__ __forceinline__ bool ldlt_solve(const float (&m)[10], float (&inv)[4]
 // FP64, which then takes the singularity decision exactly as an FP64 solve.
 constexpr float FP32_PIVOT_FLOOR = 1e-3f;
 
-template <int ROWS, bool FAST32>
-__device__ __forceinline__ void mls_build(const MemberDev& d, const uint8_t* __restrict__ tag, double X, double Y,
-                                          double Z, Mls& M) {
-    M.bx = (int)floor(X + 0.5); M.by = (int)floor(Y + 0.5); M.bz = (int)floor(Z + 0.5);
-    M.ox = (float)((double)M.bx - X); M.oy = (float)((double)M.by - Y); M.oz = (float)((double)M.bz - Z);
-    const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
-                          M.bz <= d.nz - 2;
-    M.base = interior ? (M.bx + d.px) + d.NX * ((M.by + d.py) + d.NY * (M.bz + d.pz)) : -1;
-    float m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    float best = 0.f;
-    int bestk = 27;
-#pragma unroll
-    for (int k = 0; k < 27; ++k) {
-        const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
-        const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
-                                  : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
-        const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
-        const float rx = M.ox + dx, ry = M.oy + dy, rz = M.oz + dz;
-        const float w = mls_weight(fluid, rx, ry, rz);
-        M.W[k] = w;
-        if (w > best) { best = w; bestk = k; }
-        m[0] += w; m[1] += w * rx; m[2] += w * ry; m[3] += w * rz;
-        m[4] += w * rx * rx; m[5] += w * rx * ry; m[6] += w * rx * rz;
-        m[7] += w * ry * ry; m[8] += w * ry * rz; m[9] += w * rz * rz;
-    }
-    bool good;
-    if (FAST32) {
-        float rel;
-        good = ldlt_solve<ROWS, float>(m, M.inv, rel) && rel >= FP32_PIVOT_FLOOR;
-        if (!good) {
-            double rel64;
-            good = ldlt_solve<ROWS, double>(m, M.inv, rel64);
-        }
-    } else {
-        double rel64;
-        good = ldlt_solve<ROWS, double>(m, M.inv, rel64);
-    }
-    M.fallback = good ? -1 : (best > 0.f ? bestk : 27);
-}
-
-__device__ __forceinline__ float mls_row(const Mls& M, int j, int k) {
-    const float rx = M.ox + sdx(k), ry = M.oy + sdy(k), rz = M.oz + sdz(k);
-    return M.W[k] * (M.inv[j][0] + M.inv[j][1] * rx + M.inv[j][2] * ry + M.inv[j][3] * rz);
-}
-
-__device__ __forceinline__ int mls_node(const MemberDev& d, const Mls& M, int k) {
-    const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
-    return M.base >= 0 ? M.base + dx + d.NX * (dy + d.NY * dz) : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
-}
-
 // ---------------------------------------------------------------------------
-// IB pre-pass and marker stencils, three threads per marker, all on the fluid
+// IB marker and probe stencils, four lanes per stencil, all on the fluid
 // solution at t (moments of the current populations from the shell pass):
 //  s = 0: Eq. uLag on u*, F_l = (U_b - U_l)/dt, Eq. bodyforce spreading with
 //         c_l = A_l into the dense f_ib field (float atomics) and the node's IB
@@ -323,13 +284,15 @@ __device__ __forceinline__ int mls_node(const MemberDev& d, const Mls& M, int k)
 //  s = 1, 2: the probe at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u +
 //         grad u^T) from the MLS fit (Eqs. hydroForP, hydroForNu), stored for
 //         the update kernels, which add F_p + F_tau.
-// Gathers are issued nine at a time so that their latencies overlap.
+// Each lane gathers its support nodes' moments at once (at most GS loads in
+// flight), so that their latencies overlap.
 // ---------------------------------------------------------------------------
 constexpr int PROBE_STRIDE = 8;   // floats per probe record: p, tau xx yy zz xy xz yz, pad
 
-// The probe stencils (stress only) solve their 4x4 system in FP32 unless a
-// pivot is small; the marker stencil, which interpolates and spreads, always
-// solves in FP64.  GB300's FP64 pipe is narrow and this kernel's busiest unit.
+// Both stencils solve their 4x4 system in FP32 unless a pivot falls below
+// FP32_PIVOT_FLOOR of the first, and then redo it in FP64 (GB300's FP64 pipe
+// is narrow).  IBL_MARKER_FAST32=0 makes the marker stencil, which
+// interpolates and spreads, always solve in FP64.
 constexpr bool PROBE_FAST32 = true;
 #ifndef IB_MARKER_THREADS
 #define IB_MARKER_THREADS 128
@@ -359,7 +322,13 @@ constexpr bool MARKER_FAST32 = IBL_MARKER_FAST32 != 0;
 #endif
 constexpr int GL = IB_GROUP_LANES;      // lanes per stencil (a power of two, at most 32)
 constexpr int GS = (27 + GL - 1) / GL;  // support nodes per lane
+static_assert(GL >= 4 && GL <= 32 && (GL & (GL - 1)) == 0, "a stencil group needs a lane per axis");
 
+// MLS operator of one point, held by the GL lanes of its group: weights W_k of
+// this lane's support nodes (Eq. intKernel) and the first ROWS rows of A^{-1}
+// (Eq. l2norm, basis [1, x-X, y-Y, z-Z]; A is symmetric, so row j is
+// A^{-1} e_j), the same in every lane of the group.  fallback >= 0: singular
+// system, the whole point goes to support node `fallback`.
 struct MlsG {
     int bx, by, bz;
     int base;               // padded index of the base node when the block is interior, else -1
@@ -382,11 +351,18 @@ __device__ __noinline__ Rows ldlt_solve64(Moments mm) {
     return out;
 }
 
+// P is the point's coordinate along axis min(r, 2): lanes 0, 1, 2 of a group
+// each take the FP64 steps (nearest node, offset) for one axis and the group
+// exchanges the results, so that GB300's narrow FP64 pipe does a third of the
+// work it would if every lane took all three axes.
 template <int ROWS, bool FAST32>
-__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double X, double Y,
-                                            double Z, int r, unsigned mask, MlsG& M) {
-    M.bx = (int)floor(X + 0.5); M.by = (int)floor(Y + 0.5); M.bz = (int)floor(Z + 0.5);
-    M.ox = (float)((double)M.bx - X); M.oy = (float)((double)M.by - Y); M.oz = (float)((double)M.bz - Z);
+__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double P, int r,
+                                            unsigned mask, MlsG& M) {
+    const double b = floor(P + 0.5);
+    const int bi = (int)b;
+    const float o = (float)(b - P);
+    M.bx = __shfl_sync(mask, bi, 0, GL); M.by = __shfl_sync(mask, bi, 1, GL); M.bz = __shfl_sync(mask, bi, 2, GL);
+    M.ox = __shfl_sync(mask, o, 0, GL); M.oy = __shfl_sync(mask, o, 1, GL); M.oz = __shfl_sync(mask, o, 2, GL);
     const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
                           M.bz <= d.nz - 2;
     M.base = interior ? (M.bx + d.px) + d.NX * ((M.by + d.py) + d.NY * (M.bz + d.pz)) : -1;
@@ -464,8 +440,11 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = t & (GL - 1);
     const int l = min(t / GL, n_verts - 1);
-    // the marker's position is fetched beside its capsule's flags
-    const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
+    const int ax = min(r, 2);   // the axis this lane converts from FP64
+    // the marker's coordinate and velocity along ax, fetched beside its
+    // capsule's flags
+    const double P = x[3 * l + ax];
+    const float Vb = (float)vel[3 * l + ax];
     const int cap = v_cap[l];
     const CapsuleDev& C = caps[cap];
     const int m = C.member;
@@ -474,7 +453,7 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     if (!valid) return;
     const MemberDev& d = mem[m];
     MlsG M;
-    mls_build_g<1, MARKER_FAST32>(d, tag, X, Y, Z, r, mask, M);
+    mls_build_g<1, MARKER_FAST32>(d, tag, P, r, mask, M);
     float p[GS];
     float4 q[GS];
 #pragma unroll
@@ -491,7 +470,8 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     Ux = group_sum(Ux, mask);
     Uy = group_sum(Uy, mask);
     Uz = group_sum(Uz, mask);
-    const float Fx = (float)vel[3 * l] - Ux, Fy = (float)vel[3 * l + 1] - Uy, Fz = (float)vel[3 * l + 2] - Uz;
+    const float Fx = __shfl_sync(mask, Vb, 0, GL) - Ux, Fy = __shfl_sync(mask, Vb, 1, GL) - Uy,
+                Fz = __shfl_sync(mask, Vb, 2, GL) - Uz;
     const float A = area[l];
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
@@ -524,9 +504,10 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
     const int sid = t / GL;
     const int l = min(sid >> 1, n_verts - 1);
     const int s = 1 + (sid & 1);
-    // the probe's position is fetched beside its capsule's flags
-    const float nx = nrm[3 * l], ny = nrm[3 * l + 1], nz = nrm[3 * l + 2];
-    const double X = x[3 * l], Y = x[3 * l + 1], Z = x[3 * l + 2];
+    const int ax = min(r, 2);   // the axis this lane converts from FP64
+    // the probe's coordinate along ax, fetched beside its capsule's flags
+    const float na = nrm[3 * l + ax];
+    const double xa = x[3 * l + ax];
     const int m = caps[v_cap[l]].member;
     const bool valid = (sid >> 1) < n_verts && !(status[m] & STOP);
     const unsigned mask = __ballot_sync(FULL, valid);
@@ -534,7 +515,7 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
     const MemberDev& d = mem[m];
     const double sg = s == 1 ? 1.2 : -1.2;
     MlsG M;
-    mls_build_g<4, PROBE_FAST32>(d, tag, X + sg * nx, Y + sg * ny, Z + sg * nz, r, mask, M);
+    mls_build_g<4, PROBE_FAST32>(d, tag, xa + sg * na, r, mask, M);
     float4 q[GS];
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
@@ -738,50 +719,60 @@ __global__ void k_cells_fill(const MemberDev* __restrict__ mem, const int* __res
     }
 }
 
-__global__ void k_repulsion(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
-                            const uint32_t* __restrict__ status, const double* __restrict__ x,
-                            const float* __restrict__ nrm, const int4* __restrict__ near,
-                            const int* __restrict__ count,
-                            const float4* __restrict__ items, const int* __restrict__ vids,
-                            float* __restrict__ force, int n_verts) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_verts) return;
+// RL lanes per marker: lane r searches cells k = r, r + RL, ... of the 27
+// around the marker's cell, and the group sums the contributions.
+constexpr int RL = 8;
+
+__global__ void __launch_bounds__(256) k_repulsion(const MemberDev* __restrict__ mem, const int* __restrict__ v_cap,
+                                                   const CapsuleDev* __restrict__ caps,
+                                                   const uint32_t* __restrict__ status, const double* __restrict__ x,
+                                                   const float* __restrict__ nrm, const int4* __restrict__ near,
+                                                   const int* __restrict__ count, const float4* __restrict__ items,
+                                                   const int* __restrict__ vids, float* __restrict__ force,
+                                                   int n_verts) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / RL, r = t & (RL - 1);
+    if (i >= n_verts) return;   // whole groups
     const double X = x[3 * i], Y = x[3 * i + 1], Z = x[3 * i + 2];   // issued beside the capsule lookups
     const int ci = v_cap[i];
     const int m = caps[ci].member;
     const MemberDev& d = mem[m];
     if (!d.has_cells || (status[m] & STOP)) return;
     if (!near_other(near, ci, X, Y, Z)) return;
+    const unsigned gmask = ((1u << RL) - 1u) << ((threadIdx.x & 31) & ~(RL - 1));
+    // the cell of the marker: lanes 0, 1, 2 take one axis each (FP64), the
+    // group exchanges them
+    const int ax = min(r, 2);
+    const int cdim = ax == 0 ? d.cnx : (ax == 1 ? d.cny : d.cnz);
+    const int ca = min(max((int)floor((ax == 0 ? X : (ax == 1 ? Y : Z)) * 0.5), 0), cdim - 1);
+    const int cx = __shfl_sync(gmask, ca, 0, RL), cy = __shfl_sync(gmask, ca, 1, RL), cz = __shfl_sync(gmask, ca, 2, RL);
     const float Xf = (float)X, Yf = (float)Y, Zf = (float)Z;
-    const int cx = min(max((int)floor(X * 0.5), 0), d.cnx - 1);
-    const int cy = min(max((int)floor(Y * 0.5), 0), d.cny - 1);
-    const int cz = min(max((int)floor(Z * 0.5), 0), d.cnz - 1);
     float acc = 0.f;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int qx = cx + dx, qy = cy + dy, qz = cz + dz;
-                if (qx < 0 || qy < 0 || qz < 0 || qx >= d.cnx || qy >= d.cny || qz >= d.cnz) continue;
-                const long long idx = d.cell_off + qx + (long long)d.cnx * (qy + (long long)d.cny * qz);
-                const int cnt = min(count[idx], CELL_CAP);
-                for (int s = 0; s < cnt; ++s) {
-                    const float4 it = items[idx * CELL_CAP + s];
-                    if (__float_as_int(it.w) == ci) continue;   // same body
-                    // FP32 prefilter (coordinates below 1e4 lu round by < 1e-3,
-                    // far inside the 0.01 margin on d^2)
-                    const float fx = Xf - it.x, fy = Yf - it.y, fz = Zf - it.z;
-                    if (fx * fx + fy * fy + fz * fz > 4.01f) continue;
-                    const int j = vids[idx * CELL_CAP + s];
-                    // the cutoff decides a discontinuous force: take it in FP64
-                    const double rx = X - x[3 * j], ry = Y - x[3 * j + 1], rz = Z - x[3 * j + 2];
-                    const double d2 = rx * rx + ry * ry + rz * rz;
-                    if (d2 < 4.0) {
-                        const float dist = sqrtf((float)d2);
-                        acc += 1.f / (dist * dist * sqrtf(dist));
-                    }
-                }
+    for (int k = r; k < 27; k += RL) {
+        const int qx = cx + sdx(k), qy = cy + sdy(k), qz = cz + sdz(k);
+        if (qx < 0 || qy < 0 || qz < 0 || qx >= d.cnx || qy >= d.cny || qz >= d.cnz) continue;
+        const long long idx = d.cell_off + qx + (long long)d.cnx * (qy + (long long)d.cny * qz);
+        const int cnt = min(count[idx], CELL_CAP);
+        for (int s = 0; s < cnt; ++s) {
+            const float4 it = items[idx * CELL_CAP + s];
+            if (__float_as_int(it.w) == ci) continue;   // same body
+            // FP32 prefilter (coordinates below 1e4 lu round by < 1e-3, far
+            // inside the 0.01 margin on d^2)
+            const float fx = Xf - it.x, fy = Yf - it.y, fz = Zf - it.z;
+            if (fx * fx + fy * fy + fz * fz > 4.01f) continue;
+            const int j = vids[idx * CELL_CAP + s];
+            // the cutoff decides a discontinuous force: take it in FP64
+            const double rx = X - x[3 * j], ry = Y - x[3 * j + 1], rz = Z - x[3 * j + 2];
+            const double d2 = rx * rx + ry * ry + rz * rz;
+            if (d2 < 4.0) {
+                const float dist = sqrtf((float)d2);
+                acc += 1.f / (dist * dist * sqrtf(dist));
             }
-    if (acc > 0.f) {
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < RL; o <<= 1) acc += __shfl_xor_sync(gmask, acc, o, RL);
+    if (r == 0 && acc > 0.f) {
         const float c = d.umax * (1.f / (8.f * 1.41421356237f)) * acc;
         force[4 * i] -= c * nrm[3 * i];
         force[4 * i + 1] -= c * nrm[3 * i + 1];
@@ -1002,8 +993,10 @@ cudaError_t launch_repulsion(const DevState& d, cudaStream_t s) {
     k_broad<<<d.n_caps, 128, 0, s>>>(d.mem, d.caps, d.sums, d.status, d.near);
     k_cells_fill<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.status_new, d.x, d.near, d.cell_count,
                                         d.cell_items, d.cell_vid, d.n_verts);
-    k_repulsion<<<blocks, 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.x, d.nrm, d.near, d.cell_count,
-                                       d.cell_items, d.cell_vid, d.force, d.n_verts);
+    const long long rt = (long long)RL * d.n_verts;
+    k_repulsion<<<(unsigned)((rt + 255) / 256), 256, 0, s>>>(d.mem, d.v_cap, d.caps, d.status, d.x, d.nrm, d.near,
+                                                             d.cell_count, d.cell_items, d.cell_vid, d.force,
+                                                             d.n_verts);
     return cudaGetLastError();
 }
 

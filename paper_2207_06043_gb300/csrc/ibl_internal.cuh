@@ -85,6 +85,8 @@ struct CapsuleSums {
     double ref[3];
     double max_stretch;
     int box_lo[3], box_hi[3];   // integer bounding box of the vertices (user coordinates)
+    double rc[3];               // reference point of the step: centre of the previous step's box
+    int r2_lo, r2_hi;           // FP32 bits of the least / largest squared vertex distance from rc
 };
 
 // ---------------------------------------------------------------------------

@@ -33,9 +33,15 @@ __global__ void k_step_begin(uint32_t* __restrict__ status, uint32_t* __restrict
     for (int c = threadIdx.x; c < n_caps; c += blockDim.x) {
         sums[c].V = 0.0;
         for (int a = 0; a < 3; ++a) {
+            // the previous box's centre (any point serves: it only anchors
+            // the radial bounds of this step's vertices)
+            const int lo = sums[c].box_lo[a], hi = sums[c].box_hi[a];
+            sums[c].rc[a] = lo <= hi ? 0.5 * ((double)lo + (double)hi) : 0.0;
             sums[c].box_lo[a] = 0x7fffffff;
             sums[c].box_hi[a] = -0x7fffffff - 1;
         }
+        sums[c].r2_lo = 0x7f800000;   // +inf
+        sums[c].r2_hi = 0;
     }
 }
 
@@ -48,14 +54,15 @@ cudaError_t launch_step_begin(const DevState& d, cudaStream_t s) {
 // pre-collision populations (AA parity; the face and wall rules of the
 // previous step already sit in the gathered slots), add the body force and
 // the spread IB force (which is then cleared), collide, store.
-// Work list: the 32-node segments (aligned, padded-node order) that hold at
-// least one fluid node, one warp per segment, so all-solid stretches of the
-// box cost no thread.  Interior segments (BORDER false) address every
-// neighbour by a constant offset and need no coordinates (the ghost layer of
-// non-periodic axes absorbs the steps off the box); border segments, which
-// hold a node on the wrap plane of a periodic axis, take the coordinate-based
-// path in a launch of their own.  Each population slot is read and written
-// by one node per step (AA pattern), so the two launches are independent.
+// Work list: the fluid nodes of each lattice in ascending order, one warp per
+// group of 32 (each lattice's list padded to whole groups), so no lane idles
+// on a solid node and consecutive lanes mostly read consecutive addresses.
+// Interior nodes (BORDER false) address every neighbour by a constant offset
+// and need no coordinates (the ghost layer of non-periodic axes absorbs the
+// steps off the box); nodes on the wrap plane of a periodic axis take the
+// coordinate-based path in a launch of their own.  Each population slot is
+// read and written by one node per step (AA pattern), so the two launches are
+// independent.
 // SINGLE: the context holds one lattice, whose descriptor arrives by value in
 // the kernel's parameter bank.
 template <typename T, bool SINGLE, bool BORDER>
