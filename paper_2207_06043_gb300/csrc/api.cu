@@ -632,6 +632,7 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(dev_alloc(ctx, D.v_cap, v_cap.size()));
         CKS(dev_alloc(ctx, D.x, x_all.size()));
         CKS(dev_alloc(ctx, D.x_prev, x_all.size()));
+        CKS(dev_alloc(ctx, D.xm, 2 * (x_all.size() / 3)));
         CKS(dev_alloc(ctx, D.vel, vel_all.size()));
         CKS(dev_alloc(ctx, D.force, 4 * (x_all.size() / 3)));
         CKS(dev_alloc(ctx, D.uv0, x_all.size()));
@@ -654,6 +655,7 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(upload(ctx, D.v_cap, v_cap));
         CKS(upload(ctx, D.x, x_all));
         CKS(upload(ctx, D.x_prev, x_all));
+        CK(launch_mirror(D, ctx->work));
         CKS(upload(ctx, D.vel, vel_all));
         CK(cudaMemsetAsync(D.force, 0, sizeof(float) * 4 * (x_all.size() / 3), ctx->work));
         CK(cudaMemsetAsync(D.uv0, 0, sizeof(float) * x_all.size(), ctx->work));
@@ -1238,6 +1240,7 @@ ibl_status ibl_load_state(ibl_ctx* ctx, const void* buf, size_t bytes) {
         if (s.bytes) CK(cudaMemcpyAsync(s.dev, (const char*)buf + off, s.bytes, cudaMemcpyHostToDevice, ctx->work));
         off += s.bytes;
     }
+    CK(launch_mirror(ctx->dev, ctx->work));   // derived from x
     ctx->t = h.t;
     CKS(sync_host_state(ctx));
     CKS(leave(ctx));
@@ -1495,6 +1498,10 @@ ibl_status ibl_autotune(ibl_ctx* ctx, int32_t steps, int32_t* threads_out, int32
                 if (e != cudaSuccess) return fail(ctx, IBL_ERR_CUDA, std::string("state copy: ") + cudaGetErrorString(e));
             }
             off += sc.bytes;
+        }
+        if (!save) {
+            const cudaError_t e = launch_mirror(ctx->dev, ctx->work);   // derived from x
+            if (e != cudaSuccess) return fail(ctx, IBL_ERR_CUDA, std::string("mirror: ") + cudaGetErrorString(e));
         }
         return IBL_OK;
     };

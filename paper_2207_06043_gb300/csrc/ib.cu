@@ -1,6 +1,6 @@
 // Immersed-boundary and structure kernels: per-capsule geometry, the MLS
-// interpolate/force/spread pass with the probe stresses and volume penalty (one
-// thread per Lagrangian marker), per-hinge stretching + bending, inter-body
+// interpolate/force/spread pass with the probe stresses and volume penalty
+// (four lanes per stencil), per-hinge stretching + bending, inter-body
 // repulsion on a cell list, and the Verlet / Newton-Euler update with the
 // damage rule.
 #include <climits>
@@ -16,6 +16,35 @@ constexpr double PIVOT_TOL = 1e-10;    // singular moment matrix -> nearest flui
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t STOP = ST_DAMAGED | ST_NONFINITE;
 
+struct f3 { float x, y, z; };
+__device__ __forceinline__ f3 sub(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 crs(f3 a, f3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+__device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 scl(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+
+// Two-float mirror of the FP64 vertex positions, 32 bytes per vertex:
+// (hi, 0) then (lo, 0) with hi = fl32(x) and lo = fl32(x - hi) (x - hi is
+// exact).  The difference of two positions taken as (hi_a - hi_b) +
+// (lo_a - lo_b) in FP32 is the FP64 difference rounded to FP32 within an ulp,
+// with no FP64 arithmetic (GB300's FP64 pipe is narrow).  Written with x by
+// the update kernels, and by k_mirror after x is set from the host.
+__device__ __forceinline__ void mirror_put(float4* __restrict__ xm, int v, double X, double Y, double Z) {
+    const float hx = (float)X, hy = (float)Y, hz = (float)Z;
+    xm[2 * v] = make_float4(hx, hy, hz, 0.f);
+    xm[2 * v + 1] = make_float4((float)(X - (double)hx), (float)(Y - (double)hy), (float)(Z - (double)hz), 0.f);
+}
+
+// x_a - x_b
+__device__ __forceinline__ f3 mirror_diff(const float4* __restrict__ xm, int a, int b) {
+    const float4 ha = xm[2 * a], la = xm[2 * a + 1], hb = xm[2 * b], lb = xm[2 * b + 1];
+    return {(ha.x - hb.x) + (la.x - lb.x), (ha.y - hb.y) + (la.y - lb.y), (ha.z - hb.z) + (la.z - lb.z)};
+}
+
+__global__ void __launch_bounds__(256) k_mirror(const double* __restrict__ x, float4* __restrict__ xm, int n_verts) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n_verts) mirror_put(xm, v, x[3 * v], x[3 * v + 1], x[3 * v + 2]);
+}
+
 // Eq. intKernel with r normalised by the support side.
 __device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, float rz) {
     const float r = sqrtf(rx * rx + ry * ry + rz * rz) * (1.f / SUPPORT_SIDE);
@@ -28,7 +57,8 @@ __device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, floa
 // Per-capsule geometry at x(t), spread over GEO_BLOCKS blocks per capsule:
 // per triangle, the area-weighted normal and a third of the area go to its
 // vertices (float4 atomics into vacc); the enclosed volume (divergence theorem,
-// tetrahedra fanned from the capsule's first vertex) is summed in FP64.  Then
+// tetrahedra fanned from the capsule's first vertex, each term in FP32 from
+// FP64 differences) is summed in FP64.  Then
 // per vertex: A_v = 1/3 sum of adjacent triangle areas, n_v = normalised
 // area-weighted sum of adjacent normals, the integer bounding box, and vacc
 // is cleared for the next step.  V and the box are reset at the step begin.
@@ -52,25 +82,25 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(256) k_geom_tri(const CapsuleDev* __restrict__ caps, CapsuleSums* __restrict__ sums,
-                                                  const uint32_t* __restrict__ status, const double* __restrict__ x,
+                                                  const uint32_t* __restrict__ status, const float4* __restrict__ xm,
                                                   const int* __restrict__ tri, float4* __restrict__ vacc) {
     __shared__ double red[32];
     const int c = blockIdx.x / GEO_BLOCKS, part = blockIdx.x % GEO_BLOCKS;
     const CapsuleDev& C = caps[c];
     if (status[C.member] & STOP) return;
     const int vb = C.v_begin;
-    const double rx0 = x[3 * vb], ry0 = x[3 * vb + 1], rz0 = x[3 * vb + 2];
     double vol = 0.0;
     for (int t = C.t_begin + part * blockDim.x + threadIdx.x; t < C.t_begin + C.t_count;
          t += GEO_BLOCKS * blockDim.x) {
         const int ia = tri[3 * t], ib = tri[3 * t + 1], ic = tri[3 * t + 2];
-        const double ax = x[3 * ia] - rx0, ay = x[3 * ia + 1] - ry0, az = x[3 * ia + 2] - rz0;
-        const double bx = x[3 * ib] - rx0, by = x[3 * ib + 1] - ry0, bz = x[3 * ib + 2] - rz0;
-        const double cx = x[3 * ic] - rx0, cy = x[3 * ic + 1] - ry0, cz = x[3 * ic + 2] - rz0;
-        vol += (ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx)) * (1.0 / 6.0);
-        const float ux = (float)(bx - ax), uy = (float)(by - ay), uz = (float)(bz - az);
-        const float vx = (float)(cx - ax), vy = (float)(cy - ay), vz = (float)(cz - az);
-        const float Nx = uy * vz - uz * vy, Ny = uz * vx - ux * vz, Nz = ux * vy - uy * vx;
+        // edges from vertex a
+        const f3 u = mirror_diff(xm, ib, ia), w = mirror_diff(xm, ic, ia);
+        const float Nx = u.y * w.z - u.z * w.y, Ny = u.z * w.x - u.x * w.z, Nz = u.x * w.y - u.y * w.x;
+        // tetrahedron (r0, a, b, c): a . (b x c) / 6 = a . ((b - a) x (c - a)) / 6
+        // with a relative to r0 = the first vertex; the term in FP32, the sum
+        // in FP64
+        const f3 a = mirror_diff(xm, ia, vb);
+        vol += (double)(a.x * Nx + a.y * Ny + a.z * Nz);
         const float a3 = sqrtf(Nx * Nx + Ny * Ny + Nz * Nz) * (1.f / 6.f);
         const float4 contrib = make_float4(0.5f * Nx, 0.5f * Ny, 0.5f * Nz, a3);
         atomicAdd(vacc + ia, contrib);   // vector reductions, one per vertex of the triangle
@@ -78,12 +108,12 @@ __global__ void __launch_bounds__(256) k_geom_tri(const CapsuleDev* __restrict__
         atomicAdd(vacc + ic, contrib);
     }
     const double s = block_sum_d(vol, red);
-    if (threadIdx.x == 0) atomicAdd(&sums[c].V, s);
+    if (threadIdx.x == 0) atomicAdd(&sums[c].V, s * (1.0 / 6.0));
 }
 
 __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__ caps, const int* __restrict__ v_cap,
                                                   CapsuleSums* __restrict__ sums, const uint32_t* __restrict__ status,
-                                                  const double* __restrict__ x, float4* __restrict__ vacc,
+                                                  const float4* __restrict__ xm, float4* __restrict__ vacc,
                                                   float* __restrict__ nrm, float* __restrict__ area, int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = v < n_verts && !(status[caps[v_cap[min(v, n_verts - 1)]].member] & STOP);
@@ -98,13 +128,18 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
         nrm[3 * v + 2] = a.z * inv;
         area[v] = a.w;
         vacc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 h4 = xm[2 * v], l4 = xm[2 * v + 1];
+        const float hv[3] = {h4.x, h4.y, h4.z}, lv[3] = {l4.x, l4.y, l4.z};
         float r2 = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double q = x[3 * v + k];
-            lo[k] = isfinite(q) ? (int)fmax(fmin(floor(q), 1e9), -1e9) : 0;
+            // floor(x) from x = hi + lo (|lo| <= half an ulp of hi): floor(hi),
+            // less one when hi is an integer and lo < 0
+            const float fh = floorf(hv[k]);
+            const float fx = (fh == hv[k] && lv[k] < 0.f) ? fh - 1.f : fh;
+            lo[k] = isfinite(hv[k]) ? (int)fmaxf(fminf(fx, 1e9f), -1e9f) : 0;
             hi[k] = lo[k] + 1;
-            const float dq = (float)(q - sums[c].rc[k]);
+            const float dq = (hv[k] - sums[c].rcf[k]) + lv[k];
             r2 += dq * dq;
         }
         if (r2 >= 0.f && r2 < 1e30f) { r2lo = __float_as_int(r2); r2hi = r2lo; }
@@ -577,11 +612,6 @@ __device__ __forceinline__ void hydro_force(const float* __restrict__ probe, con
 // gradient carries the beta_b = k_b sin(theta - theta0)/sin(theta) factor of
 // Eq. bendFor; theta is the signed angle between the outward normals.
 // ---------------------------------------------------------------------------
-struct f3 { float x, y, z; };
-__device__ __forceinline__ f3 sub(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ f3 crs(f3 a, f3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
-__device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ f3 scl(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
 // one vector reduction per vertex (the force array is padded to float4)
 __device__ __forceinline__ void add_force(float* F, int v, f3 a) {
     atomicAdd(reinterpret_cast<float4*>(F) + v, make_float4(a.x, a.y, a.z, 0.f));
@@ -589,18 +619,17 @@ __device__ __forceinline__ void add_force(float* F, int v, f3 a) {
 
 __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, const int* __restrict__ e_cap,
                                                const CapsuleDev* __restrict__ caps, const uint32_t* __restrict__ status,
-                                               const double* __restrict__ x, const float* __restrict__ l0,
+                                               const float4* __restrict__ xm, const float* __restrict__ l0,
                                                const float* __restrict__ ks, const float* __restrict__ th0,
                                                const float* __restrict__ kb, float* __restrict__ force, int n_edges) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_edges) return;
     const CapsuleDev& C = caps[e_cap[e]];
     if (C.rigid || (status[C.member] & STOP)) return;
-    const int v1 = hinge[4 * e], v2 = hinge[4 * e + 1], v3 = hinge[4 * e + 2], v4 = hinge[4 * e + 3];
-    const double ox = x[3 * v2], oy = x[3 * v2 + 1], oz = x[3 * v2 + 2];
-    const f3 a = {(float)(x[3 * v1] - ox), (float)(x[3 * v1 + 1] - oy), (float)(x[3 * v1 + 2] - oz)};
-    const f3 c = {(float)(x[3 * v3] - ox), (float)(x[3 * v3 + 1] - oy), (float)(x[3 * v3 + 2] - oz)};
-    const f3 dd = {(float)(x[3 * v4] - ox), (float)(x[3 * v4 + 1] - oy), (float)(x[3 * v4 + 2] - oz)};
+    const int4 hg = reinterpret_cast<const int4*>(hinge)[e];
+    const int v1 = hg.x, v2 = hg.y, v3 = hg.z, v4 = hg.w;
+    // positions relative to v2
+    const f3 a = mirror_diff(xm, v1, v2), c = mirror_diff(xm, v3, v2), dd = mirror_diff(xm, v4, v2);
     // stretching on the edge (v2, v3): F_2 = -k (l - l0) r_23 / l, r_23 = v2 - v3
     const f3 r23 = scl(c, -1.f);
     const float l = sqrtf(dot3(r23, r23));
@@ -794,7 +823,7 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
                                                 double* __restrict__ vel, float* __restrict__ force,
                                                 const float* __restrict__ uv0, const float* __restrict__ probe,
                                                 const float* __restrict__ nrm, const float* __restrict__ area,
-                                                int n_verts) {
+                                                float4* __restrict__ xm, int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n_verts) return;
     const int cap = v_cap[v];
@@ -817,6 +846,7 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
     const float half_inv_m = 0.5f / (float)C.mv;
     const float F[3] = {fo.x, fo.y, fo.z};
     bool bad = false;
+    double xn[3];
     // With a = F / (2 m_v): predictor x* = x + u_0 + a, velocity
     // u = 3/2 x* - 2 x + 1/2 x_prev = 3/2 (u_0 + a) + 1/2 (x_prev - x), corrector
     // x_new = x + u + a.  Positions stay FP64; the increments, of the size of
@@ -826,12 +856,13 @@ __global__ void __launch_bounds__(256) k_verlet(const CapsuleDev* __restrict__ c
         const float acc = (F[a] + H[a]) * half_inv_m;
         const float back = (float)(xp[a] - xt[a]);
         const float un = 1.5f * (u0[a] + acc) + 0.5f * back;
-        const double xn = xt[a] + (double)(un + acc);
+        xn[a] = xt[a] + (double)(un + acc);
         x_prev[3 * v + a] = xt[a];
-        x[3 * v + a] = xn;
+        x[3 * v + a] = xn[a];
         vel[3 * v + a] = (double)un;
-        bad |= !isfinite(xn);
+        bad |= !isfinite(xn[a]);
     }
+    mirror_put(xm, v, xn[0], xn[1], xn[2]);
     if (bad) atomicOr(status_new + C.member, ST_NONFINITE);
 }
 
@@ -839,7 +870,8 @@ __global__ void __launch_bounds__(256) k_rigid(CapsuleDev* __restrict__ caps, co
                                                uint32_t* __restrict__ status_new, double* __restrict__ x,
                                                double* __restrict__ x_prev, double* __restrict__ vel,
                                                float* __restrict__ force, const float* __restrict__ probe,
-                                               const float* __restrict__ nrm, const float* __restrict__ area) {
+                                               const float* __restrict__ nrm, const float* __restrict__ area,
+                                               float4* __restrict__ xm) {
     __shared__ double red[32];
     __shared__ double sh_rig[16];
     CapsuleDev& C = caps[blockIdx.x];
@@ -900,6 +932,7 @@ __global__ void __launch_bounds__(256) k_rigid(CapsuleDev* __restrict__ caps, co
         const double qz = R[6] * rx + R[7] * ry + R[8] * rz;
         x_prev[3 * v] = x[3 * v]; x_prev[3 * v + 1] = x[3 * v + 1]; x_prev[3 * v + 2] = x[3 * v + 2];
         x[3 * v] = ncx + qx; x[3 * v + 1] = ncy + qy; x[3 * v + 2] = ncz + qz;
+        mirror_put(xm, v, ncx + qx, ncy + qy, ncz + qz);
         const double wx = sh_rig[12], wy = sh_rig[13], wz = sh_rig[14];
         vel[3 * v] = sh_rig[9] + (wy * qz - wz * qy);
         vel[3 * v + 1] = sh_rig[10] + (wz * qx - wx * qz);
@@ -912,11 +945,10 @@ __global__ void __launch_bounds__(256) k_rigid(CapsuleDev* __restrict__ caps, co
     if (anybad && threadIdx.x == 0) atomicOr(status_new + C.member, ST_NONFINITE);
 }
 
-// l >= 2 l0 decided on squared lengths in FP64 (no square root or division
-// on the slow FP64 path).
+// l >= 2 l0 decided on squared lengths (no square root or division).
 __global__ void __launch_bounds__(256) k_damage(const CapsuleDev* __restrict__ caps, const int* __restrict__ e_cap,
                                                 const uint32_t* __restrict__ status, uint32_t* __restrict__ status_new,
-                                                const double* __restrict__ x, const int* __restrict__ hinge,
+                                                const float4* __restrict__ xm, const int* __restrict__ hinge,
                                                 const float* __restrict__ l0, int n_edges) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_edges) return;
@@ -925,10 +957,10 @@ __global__ void __launch_bounds__(256) k_damage(const CapsuleDev* __restrict__ c
     const int4 h = reinterpret_cast<const int4*>(hinge)[e];
     const int a = h.y, b = h.z;
     const float l0e = l0[e];
-    // differences in FP64, the squared length in FP32 (a relative 1e-7 at the
-    // threshold of twice the rest length)
-    const float dx = (float)(x[3 * a] - x[3 * b]), dy = (float)(x[3 * a + 1] - x[3 * b + 1]),
-                dz = (float)(x[3 * a + 2] - x[3 * b + 2]);
+    // the FP64 difference rounded to FP32 (two-float mirror), the squared
+    // length in FP32 (a relative 1e-7 at the threshold of twice the rest length)
+    const f3 r = mirror_diff(xm, a, b);
+    const float dx = r.x, dy = r.y, dz = r.z;
     const CapsuleDev& C = caps[e_cap[e]];
     if (C.rigid || (status[C.member] & STOP)) return;
     if (dx * dx + dy * dy + dz * dz >= 4.f * l0e * l0e) atomicOr(status_new + C.member, ST_DAMAGED);
@@ -939,8 +971,8 @@ __global__ void __launch_bounds__(256) k_damage(const CapsuleDev* __restrict__ c
 // ---------------------------------------------------------------------------
 cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) {
     if (d.n_caps == 0) return cudaSuccess;
-    k_geom_tri<<<d.n_caps * GEO_BLOCKS, 256, 0, s>>>(d.caps, d.sums, d.status, d.x, d.tri, d.vacc);
-    k_geom_vtx<<<(d.n_verts + 255) / 256, 256, 0, s>>>(d.caps, d.v_cap, d.sums, d.status, d.x, d.vacc, d.nrm, d.area,
+    k_geom_tri<<<d.n_caps * GEO_BLOCKS, 256, 0, s>>>(d.caps, d.sums, d.status, d.xm, d.tri, d.vacc);
+    k_geom_vtx<<<(d.n_verts + 255) / 256, 256, 0, s>>>(d.caps, d.v_cap, d.sums, d.status, d.xm, d.vacc, d.nrm, d.area,
                                                        d.n_verts);
     return cudaGetLastError();
 }
@@ -980,7 +1012,7 @@ cudaError_t launch_probes(const DevState& d, cudaStream_t s) {
 
 cudaError_t launch_edges(const DevState& d, cudaStream_t s) {
     if (!d.any_soft || d.n_edges == 0) return cudaSuccess;
-    k_edges<<<(d.n_edges + 255) / 256, 256, 0, s>>>(d.hinge, d.e_cap, d.caps, d.status, d.x, d.l0, d.ks, d.th0, d.kb,
+    k_edges<<<(d.n_edges + 255) / 256, 256, 0, s>>>(d.hinge, d.e_cap, d.caps, d.status, d.xm, d.l0, d.ks, d.th0, d.kb,
                                                      d.force, d.n_edges);
     return cudaGetLastError();
 }
@@ -1004,13 +1036,19 @@ cudaError_t launch_update(const DevState& d, cudaStream_t s) {
     if (d.n_caps == 0) return cudaSuccess;
     if (d.any_soft)
         k_verlet<<<(d.n_verts + 255) / 256, 256, 0, s>>>(d.caps, d.v_cap, d.status, d.status_new, d.x, d.x_prev, d.vel,
-                                                         d.force, d.uv0, d.probe, d.nrm, d.area, d.n_verts);
+                                                         d.force, d.uv0, d.probe, d.nrm, d.area, d.xm, d.n_verts);
     if (d.any_rigid)
         k_rigid<<<d.n_caps, 256, 0, s>>>(d.caps, d.status, d.status_new, d.x, d.x_prev, d.vel, d.force, d.probe, d.nrm,
-                                         d.area);
+                                         d.area, d.xm);
     if (d.any_soft && d.n_edges > 0)
-        k_damage<<<(d.n_edges + 255) / 256, 256, 0, s>>>(d.caps, d.e_cap, d.status, d.status_new, d.x, d.hinge, d.l0,
+        k_damage<<<(d.n_edges + 255) / 256, 256, 0, s>>>(d.caps, d.e_cap, d.status, d.status_new, d.xm, d.hinge, d.l0,
                                                          d.n_edges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mirror(const DevState& d, cudaStream_t s) {
+    if (d.n_verts == 0) return cudaSuccess;
+    k_mirror<<<(d.n_verts + 255) / 256, 256, 0, s>>>(d.x, d.xm, d.n_verts);
     return cudaGetLastError();
 }
 

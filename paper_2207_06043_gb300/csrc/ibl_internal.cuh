@@ -86,6 +86,7 @@ struct CapsuleSums {
     double max_stretch;
     int box_lo[3], box_hi[3];   // integer bounding box of the vertices (user coordinates)
     double rc[3];               // reference point of the step: centre of the previous step's box
+    float rcf[3];               // the same in FP32 (a half-integer: exact)
     int r2_lo, r2_hi;           // FP32 bits of the least / largest squared vertex distance from rc
 };
 
@@ -182,6 +183,7 @@ struct DevState {
     int* cell_count = nullptr;
     float4* cell_items = nullptr;    // (x, y, z, capsule id bits) per slot
     int* cell_vid = nullptr;         // vertex id per slot
+    float4* xm = nullptr;            // two-float mirror of x: (hi, 0), (lo, 0) per vertex, x = hi + lo
     int4* near = nullptr;            // NEAR_STRIDE per capsule: count (-1: too many), then grown boxes
     long long n_cells = 0;
 };
@@ -221,5 +223,7 @@ cudaError_t launch_step_begin(const DevState& d, cudaStream_t s);
 cudaError_t launch_edges(const DevState& d, cudaStream_t s);
 cudaError_t launch_repulsion(const DevState& d, cudaStream_t s);
 cudaError_t launch_update(const DevState& d, cudaStream_t s);
+// refresh the two-float mirror of the vertex positions after x is set from the host
+cudaError_t launch_mirror(const DevState& d, cudaStream_t s);
 
 }  // namespace ibl

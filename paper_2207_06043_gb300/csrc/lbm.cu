@@ -37,6 +37,7 @@ __global__ void k_step_begin(uint32_t* __restrict__ status, uint32_t* __restrict
             // the radial bounds of this step's vertices)
             const int lo = sums[c].box_lo[a], hi = sums[c].box_hi[a];
             sums[c].rc[a] = lo <= hi ? 0.5 * ((double)lo + (double)hi) : 0.0;
+            sums[c].rcf[a] = (float)sums[c].rc[a];
             sums[c].box_lo[a] = 0x7fffffff;
             sums[c].box_hi[a] = -0x7fffffff - 1;
         }
