@@ -177,15 +177,63 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
 // [floor(min), floor(max) + 1] grown by SHELL_MARGIN = 2.  Within the box, a
 // node farther than sqrt(r2_hi) + 3.8 from the step's reference point rc, or
 // nearer than sqrt(r2_lo) - 3.8, is within 3.8 of no vertex and is skipped
-// (a 0.05 slack covers the FP32 distances).  The IB kernels then read one
+// (a 0.05 slack covers the FP32 distances and square roots).  The IB kernels then read one
 // float4 per support node instead of 19 scattered populations.  Overlapping
 // boxes write identical values.
 constexpr int SHELL_MARGIN = 2;
 constexpr float SHELL_REACH = 3.85f;
-constexpr int SHELL_BLOCKS = 64;   // blocks per capsule
+constexpr int SHELL_BLOCKS = 32;   // blocks per capsule
+
+// One warp per row (y, z) of a capsule's box, lanes along x over the part of
+// the row inside the outer sphere, less the part inside the inner one.
+template <typename T, bool LIN>
+__device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restrict__ fm, float4* __restrict__ macro,
+                                           const int lo[3], const int ext[3], bool radial, float r2_out, float r2_in,
+                                           float rcx, float rcy, float rcz, int parity) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = SHELL_BLOCKS * (int)(blockDim.x >> 5);
+    const int rows = ext[1] * ext[2];
+    for (int row = (blockIdx.x % SHELL_BLOCKS) * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); row < rows;
+         row += nwarps) {
+        const int iz = row / ext[1], iy = row - iz * ext[1];
+        int cy = lo[1] + iy, cz = lo[2] + iz;
+        const float qy = (float)cy - rcy, qz = (float)cz - rcz;
+        const float d2 = qy * qy + qz * qz;
+        int x0 = lo[0], x1 = lo[0] + ext[0] - 1;
+        float hin = -1.f;
+        if (radial) {
+            if (d2 > r2_out) continue;   // the whole row (uniform over the warp)
+            const float hw = sqrtf(r2_out - d2);
+            x0 = max(x0, (int)ceilf(rcx - hw));
+            x1 = min(x1, (int)floorf(rcx + hw));
+            if (r2_in > d2) hin = sqrtf(r2_in - d2);
+        }
+        if (!LIN) {
+            if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny;
+            if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz;
+        }
+        const int Y = cy + d.py, Z = cz + d.pz;
+        for (int cx = x0 + lane; cx <= x1; cx += 32) {
+            if (fabsf((float)cx - rcx) < hin) continue;
+            int wx = cx;
+            if (!LIN && (d.per & 1)) wx = ((wx % d.nx) + d.nx) % d.nx;
+            const int X = wx + d.px;
+            const int node = X + d.NX * (Y + d.NY * Z);
+            // solid nodes are not skipped: their slots are in the array, and
+            // the stencils never read their moments, so the populations'
+            // loads need not wait on the tag
+            float g[Q];
+            if (LIN) load_pre_lin<T>(d, fm, node, parity, g);
+            else load_pre<T>(d, fm, node, X, Y, Z, parity, g);
+            float rho, ux, uy, uz;
+            moments_of(g, rho, ux, uy, uz);
+            macro[d.node_off + node] = make_float4(rho, ux, uy, uz);
+        }
+    }
+}
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
+__global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
                                                const uint8_t* __restrict__ tag,
                                                const uint32_t* __restrict__ status, const CapsuleDev* __restrict__ caps,
                                                const CapsuleSums* __restrict__ sums, float4* __restrict__ macro,
@@ -214,29 +262,16 @@ __global__ void __launch_bounds__(256) k_shell(const MemberDev* __restrict__ mem
     // annulus of the vertices about rc, grown by the stencils' reach
     const float rhi = sqrtf(__int_as_float(sums[c].r2_hi)) + SHELL_REACH;
     const float rlo = sqrtf(__int_as_float(sums[c].r2_lo)) - SHELL_REACH;
-    const float r2_out = wide ? INFINITY : rhi * rhi, r2_in = (!wide && rlo > 0.f) ? rlo * rlo : -1.f;
-    const float rcx = (float)sums[c].rc[0], rcy = (float)sums[c].rc[1], rcz = (float)sums[c].rc[2];
-    const int exy = ext[0] * ext[1];
-    const int total = exy * ext[2];     // a box of one lattice: below 2^31 nodes
+    const bool radial = !wide && rhi < 1e6f;   // no radial test for a non-finite or over-wide capsule
+    const float r2_out = rhi * rhi, r2_in = (radial && rlo > 0.f) ? rlo * rlo : -1.f;
+    const float rcx = sums[c].rcf[0], rcy = sums[c].rcf[1], rcz = sums[c].rcf[2];
     const T* fm = f + d.f_off;
-    for (int i = (blockIdx.x % SHELL_BLOCKS) * blockDim.x + threadIdx.x; i < total; i += SHELL_BLOCKS * blockDim.x) {
-        const int iz = i / exy, r = i - iz * exy, iy = r / ext[0];
-        int cx = lo[0] + (r - iy * ext[0]), cy = lo[1] + iy, cz = lo[2] + iz;
-        const float qx = (float)cx - rcx, qy = (float)cy - rcy, qz = (float)cz - rcz;
-        const float q2 = qx * qx + qy * qy + qz * qz;
-        if (q2 > r2_out || q2 < r2_in) continue;
-        if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx;
-        if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny;
-        if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz;
-        const int X = cx + d.px, Y = cy + d.py, Z = cz + d.pz;
-        const int node = X + d.NX * (Y + d.NY * Z);
-        if (tag[d.node_off + node] & TAG_SOLID) continue;
-        float g[Q];
-        load_pre<T>(d, fm, node, X, Y, Z, parity, g);
-        float rho, ux, uy, uz;
-        moments_of(g, rho, ux, uy, uz);
-        macro[d.node_off + node] = make_float4(rho, ux, uy, uz);
-    }
+    // a lattice with no periodic axis reaches every upstream node at a
+    // constant offset (the ghost layer absorbs the steps off the box)
+    if (d.per == 0)
+        shell_rows<T, true>(d, fm, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
+    else
+        shell_rows<T, false>(d, fm, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
 }
 
 // Offsets (dx, dy, dz) of support node k = (dx+1) + 3 (dy+1) + 9 (dz+1) of
