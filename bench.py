@@ -194,7 +194,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage side measurements")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-ckpt", type=int, default=2000)
-    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     args = ap.parse_args()
 

@@ -174,13 +174,13 @@ ibl_status ibl_member_read_capsule(ibl_ctx* ctx, int32_t member, int32_t id,
 ibl_status ibl_member_steps(const ibl_ctx* ctx, int32_t member, int32_t* steps_done);
 
 /* Launch shape of the lattice kernel: threads per block (a multiple of 32, at
- * most 256, the bound the kernel is compiled for; one warp per 32-node fluid
- * run) and blocks per SM of a persistent grid (0 = one block per group of
- * runs).  Used by the autotuner; takes effect at the next step. */
+ * most 128, the bound the kernel is compiled for; one warp per group of 32
+ * fluid nodes) and blocks per SM of a persistent grid (0 = one block per
+ * threads/32 groups).  Used by the autotuner; takes effect at the next step. */
 ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
 
 /* Autotuner of the lattice kernel's launch shape: times `steps` steps of the
- * context for each block size (64, 128, 256 threads) and persistent-grid
+ * context for each block size (32, 64, 128 threads) and persistent-grid
  * setting (blocks_per_sm 0, 1, 2, 4, 8, 16), restoring the state after every
  * trial, and keeps the fastest.  The trials are timed with CUDA events around
  * the lattice kernels; the context's state and step count are as before the

@@ -73,7 +73,7 @@ struct ibl_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_kernels[2] = {0, 0};   // kernel nodes of each parity's step graph
     bool use_graphs = true;
-    int threads = 256;
+    int threads = 128;   // lattice kernel block size (the compiled bound)
     int blocks_per_sm = 0;
     int n_sm = 0;
     bool timing = false;
@@ -1512,7 +1512,7 @@ ibl_status ibl_autotune(ibl_ctx* ctx, int32_t steps, int32_t* threads_out, int32
     if (st == IBL_OK) st = copy_state(true);
     int best_t = thr0, best_b = bps0;
     double best = 1e300;
-    const int cand_t[3] = {64, 128, 256};
+    const int cand_t[3] = {32, 64, 128};
     const int cand_b[6] = {0, 1, 2, 4, 8, 16};
     ctx->timing = true;
     for (int it = 0; it < 3 && st == IBL_OK; ++it) {

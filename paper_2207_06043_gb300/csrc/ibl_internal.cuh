@@ -118,7 +118,7 @@ struct DevState {
     int n_members = 0;
     const MemberDev* h_mem = nullptr;
     MemberDev* mem = nullptr;         // device copy of the member table (one per context)
-    int threads = 256;               // lattice kernel threads per block (one warp per group of 32 nodes)
+    int threads = 128;               // lattice kernel threads per block (one warp per group of 32 nodes)
     // 32-node segments holding at least one fluid node, all members, split
     // into interior ones and border ones (a fluid node on a periodic wrap
     // plane); entries are segment indices (padded node / 32) within their

@@ -10,10 +10,10 @@
 // minimum resident blocks per SM); the register budget is 64K / (threads *
 // blocks)
 #ifndef LBM_THREADS
-#define LBM_THREADS 256
+#define LBM_THREADS 128
 #endif
 #ifndef LBM_MIN_BLOCKS
-#define LBM_MIN_BLOCKS 6
+#define LBM_MIN_BLOCKS 12
 #endif
 
 namespace ibl {

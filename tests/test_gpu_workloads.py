@@ -93,7 +93,7 @@ def test_throughput_workload_full_size_sampled_step():
     c = W.throughput_case()
     g = c["geometry"]
     s = W.make_solver(c)
-    s.set_launch(256, 0)
+    s.set_launch(128, 0)
     s.step(3)
     g0 = s.read_populations().astype(np.float64)
     s.step(1)
