@@ -211,8 +211,8 @@ __global__ void __launch_bounds__(256) k_adj_links(const MemberDev* __restrict__
 //                        + guo w_j (9 (e_j.F) e_j - 3 F)].
 // Entries at solid nodes hold only link terms (zero otherwise), so every
 // neighbour is pulled without a tag test; k_adj_clear zeroes the link terms
-// once they are consumed.  Work list: the fluid runs of the lattice kernel,
-// one warp per 32-node run; interior runs address neighbours by constant
+// once they are consumed.  Work list: the aligned 32-node runs that hold a
+// fluid node, one warp per run; interior runs address neighbours by constant
 // offsets, border runs (periodic wrap planes) by coordinates.
 template <bool BORDER>
 __global__ void __launch_bounds__(256) k_adj_step(const __grid_constant__ MemberDev d, const uint8_t* __restrict__ tag,

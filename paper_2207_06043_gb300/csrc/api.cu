@@ -415,6 +415,12 @@ ibl_status finalize(ibl_ctx* ctx) {
             return ok;
         };
         auto fluid_at = [&](int c[3]) { return M.tag[c[0] + (long long)d.nx * (c[1] + (long long)d.ny * c[2])] == 0; };
+        // the member's links in (direction, node) order: consecutive threads
+        // of the wall pass then touch consecutive nodes of one population
+        // plane along a wall
+        struct LinkRec { uint32_t node, meta; float q, dq; };
+        std::vector<LinkRec> recs;
+        recs.reserve(M.links.size());
         for (size_t li = 0; li < M.links.size(); ++li) {
             const ibl_wall_link& L = M.links[li];
             const long long Nu = (long long)d.nx * d.ny * d.nz;
@@ -428,10 +434,16 @@ ibl_status finalize(ibl_ctx* ctx) {
             const bool ok1 = shift(c, -1, L.dir, m1) && fluid_at(m1);
             const bool ok2 = shift(c, -2, L.dir, m2) && fluid_at(m2);
             const long long pn = (c[0] + md.px) + (long long)md.NX * ((c[1] + md.py) + (long long)md.NY * (c[2] + md.pz));
-            l_node.push_back((uint32_t)pn);
-            l_meta.push_back(L.dir | (ok1 ? 32u : 0u) | (ok2 ? 64u : 0u) | ((uint32_t)mi << 8));
-            l_q.push_back(L.q);
-            l_dq.push_back(L.dq);
+            recs.push_back({(uint32_t)pn, L.dir | (ok1 ? 32u : 0u) | (ok2 ? 64u : 0u) | ((uint32_t)mi << 8), L.q, L.dq});
+        }
+        std::sort(recs.begin(), recs.end(), [](const LinkRec& a, const LinkRec& b) {
+            return (a.meta & 31u) != (b.meta & 31u) ? (a.meta & 31u) < (b.meta & 31u) : a.node < b.node;
+        });
+        for (const LinkRec& r : recs) {
+            l_node.push_back(r.node);
+            l_meta.push_back(r.meta);
+            l_q.push_back(r.q);
+            l_dq.push_back(r.dq);
         }
         md.link_count = (int)M.links.size();
         link_off += md.link_count;
@@ -655,7 +667,6 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(upload(ctx, D.v_cap, v_cap));
         CKS(upload(ctx, D.x, x_all));
         CKS(upload(ctx, D.x_prev, x_all));
-        CK(launch_mirror(D, ctx->work));
         CKS(upload(ctx, D.vel, vel_all));
         CK(cudaMemsetAsync(D.force, 0, sizeof(float) * 4 * (x_all.size() / 3), ctx->work));
         CK(cudaMemsetAsync(D.uv0, 0, sizeof(float) * x_all.size(), ctx->work));
@@ -666,6 +677,7 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(upload(ctx, D.th0, th0_all));
         CKS(upload(ctx, D.kb, kb_all));
         CKS(upload(ctx, D.e_cap, e_cap));
+        CK(launch_mirror(D, ctx->work));   // derived from x
         if (any_cells) {
             D.n_cells = cell_off;
             CKS(dev_alloc(ctx, D.cell_count, (size_t)cell_off));

@@ -139,13 +139,23 @@ __global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, 
     const int ib = opp(i);
     const int xb = (int)l_node[l];
     const float q = l_q[l];
-    int X, Y, Z;
-    node_coords(d, xb, X, Y, Z);
-    const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
-    const int exi = ex(i), eyi = ey(i), ezi = ez(i);
-    const int xsN = nbc(X, exi, d.NX, px) + d.NX * (nbc(Y, eyi, d.NY, py) + d.NY * nbc(Z, ezi, d.NZ, pz));
-    const int m1N = nbc(X, -exi, d.NX, px) + d.NX * (nbc(Y, -eyi, d.NY, py) + d.NY * nbc(Z, -ezi, d.NZ, pz));
-    const int X1 = nbc(X, -exi, d.NX, px), Y1 = nbc(Y, -eyi, d.NY, py), Z1 = nbc(Z, -ezi, d.NZ, pz);
+    // x_b + e_i (solid, inside the box), x_b - e_i and x_b - 2 e_i (read only
+    // when fluid): constant offsets in a lattice without periodic axes, else
+    // wrapped coordinates
+    int xsN, m1N, m2N;
+    if (d.per == 0) {
+        const int o = lin_off(d, i);
+        xsN = xb + o; m1N = xb - o; m2N = xb - 2 * o;
+    } else {
+        int X, Y, Z;
+        node_coords(d, xb, X, Y, Z);
+        const bool px = d.per & 1, py = d.per & 2, pz = d.per & 4;
+        const int exi = ex(i), eyi = ey(i), ezi = ez(i);
+        xsN = nbc(X, exi, d.NX, px) + d.NX * (nbc(Y, eyi, d.NY, py) + d.NY * nbc(Z, ezi, d.NZ, pz));
+        const int X1 = nbc(X, -exi, d.NX, px), Y1 = nbc(Y, -eyi, d.NY, py), Z1 = nbc(Z, -ezi, d.NZ, pz);
+        m1N = X1 + d.NX * (Y1 + d.NY * Z1);
+        m2N = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
+    }
     const size_t S = (size_t)d.S;
     const float ls = d.ld_scale;
     T* fm = f + d.f_off;
@@ -156,17 +166,13 @@ __global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, 
         if (ok1) {
             fi_1 = Store<T>::ld(fm + ib * S + m1N, ls);
             fib_1 = Store<T>::ld(fm + i * S + m1N, ls);
-            if (ok2) {
-                const int m2N = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
-                fi_2 = Store<T>::ld(fm + ib * S + m2N, ls);
-            }
+            if (ok2) fi_2 = Store<T>::ld(fm + ib * S + m2N, ls);
         }
     } else {
         fi_b = Store<T>::ld(fm + i * S + xsN, ls);
         fib_b = Store<T>::ld(fm + ib * S + m1N, ls);
         if (ok1) {
             fi_1 = Store<T>::ld(fm + i * S + xb, ls);
-            const int m2N = nbc(X1, -exi, d.NX, px) + d.NX * (nbc(Y1, -eyi, d.NY, py) + d.NY * nbc(Z1, -ezi, d.NZ, pz));
             fib_1 = Store<T>::ld(fm + ib * S + m2N, ls);
             if (ok2) fi_2 = Store<T>::ld(fm + i * S + m1N, ls);
         }
