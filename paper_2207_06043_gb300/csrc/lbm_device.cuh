@@ -221,16 +221,33 @@ __device__ __forceinline__ void collide(float g[Q], float omega, float guo, floa
     const float uz = (jz + 0.5f * Fz) * inv;
     const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float uF = ux * Fx + uy * Fy + uz * Fz;
+    // rest population, then each pair (k, opp(k)) at once: e.u and e.F change
+    // sign between the two, so f_eq shares drho + rho (9/2 (e.u)^2 - 3/2 u^2)
+    // and the Guo term shares 9 (e.u)(e.F) - 3 u.F
+    {
+        const float geq = wgt(0) * (drho - rho * usq);
+        float o = g[0] + omega * (geq - g[0]);
+        if (hasF) o += guo * wgt(0) * (-3.f * uF);
+        g[0] = o;
+    }
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
+    for (int k = 1; k < Q; ++k) {
+        if (opp(k) < k) continue;
+        const int kb = opp(k);
         const float eu = ex(k) * ux + ey(k) * uy + ez(k) * uz;
-        const float geq = wgt(k) * (drho + rho * (3.f * eu + 4.5f * eu * eu - usq));
-        float o = g[k] - omega * (g[k] - geq);
+        const float c = drho + rho * (4.5f * eu * eu - usq);
+        const float t = 3.f * rho * eu;
+        const float w = wgt(k);
+        float ok = g[k] + omega * (w * (c + t) - g[k]);
+        float ob = g[kb] + omega * (w * (c - t) - g[kb]);
         if (hasF) {
             const float eF = ex(k) * Fx + ey(k) * Fy + ez(k) * Fz;
-            o += guo * wgt(k) * (3.f * (eF - uF) + 9.f * eu * eF);
+            const float s = 9.f * eu * eF - 3.f * uF, gw = guo * w;
+            ok += gw * (s + 3.f * eF);
+            ob += gw * (s - 3.f * eF);
         }
-        g[k] = o;
+        g[k] = ok;
+        g[kb] = ob;
     }
 }
 
