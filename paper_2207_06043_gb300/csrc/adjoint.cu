@@ -240,24 +240,45 @@ __global__ void __launch_bounds__(256) k_adj_step(const __grid_constant__ Member
     const float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
     const float om = d.omega, guo = d.guo;
     const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float orho = om * rho;
+    // A and B summed by opposite pairs (k, kb): e.u and e.F change sign
+    // between the two, so with dw = w_k l_k - w_kb l_kb and sw = w_k l_k +
+    // w_kb l_kb the pair adds 3 (e.u) dw + 9/2 (e.u)^2 sw to A (beyond
+    // (1 - 3/2 u^2) times the sum of all w l) and e_k [3 om rho dw +
+    // 9 (om rho e.u + guo e.F) sw] to B (beyond -(3 om rho u + 3 guo F)
+    // times the same sum).
+    float W = wgt(0) * ls[0];
     float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
+    for (int k = 1; k < Q; ++k) {
+        if (opp(k) < k) continue;
+        const int kb = opp(k);
         const float eu = ex(k) * ux + ey(k) * uy + ez(k) * uz;
         const float eF = ex(k) * Fx + ey(k) * Fy + ez(k) * Fz;
-        const float w = wgt(k) * ls[k];
-        A += w * (1.f + 3.f * eu + 4.5f * eu * eu - usq);
-        const float s1 = om * rho * (3.f + 9.f * eu) + guo * 9.f * eF;   // coefficient of e_k
-        const float s2 = om * rho * 3.f;                                  // coefficient of -u
-        Bx += w * (s1 * ex(k) - s2 * ux - guo * 3.f * Fx);
-        By += w * (s1 * ey(k) - s2 * uy - guo * 3.f * Fy);
-        Bz += w * (s1 * ez(k) - s2 * uz - guo * 3.f * Fz);
+        const float dw = wgt(k) * (ls[k] - ls[kb]), sw = wgt(k) * (ls[k] + ls[kb]);
+        W += sw;
+        A += eu * (3.f * dw + 4.5f * eu * sw);
+        const float c = 3.f * orho * dw + 9.f * (orho * eu + guo * eF) * sw;
+        if (ex(k)) Bx += ex(k) * c;
+        if (ey(k)) By += ey(k) * c;
+        if (ez(k)) Bz += ez(k) * c;
     }
+    A += W * (1.f - usq);
+    Bx -= W * (3.f * orho * ux + 3.f * guo * Fx);
+    By -= W * (3.f * orho * uy + 3.f * guo * Fy);
+    Bz -= W * (3.f * orho * uz + 3.f * guo * Fz);
     const float ir = 1.f / rho;
     const float Bu = Bx * ux + By * uy + Bz * uz;
+    const float base = om * A - Bu * ir, keep = 1.f - om;
+    lam_out[n] = keep * ls[0] + base;
 #pragma unroll
-    for (int k = 0; k < Q; ++k)
-        lam_out[k * LS + n] = (1.f - om) * ls[k] + om * A + (Bx * ex(k) + By * ey(k) + Bz * ez(k) - Bu) * ir;
+    for (int k = 1; k < Q; ++k) {
+        if (opp(k) < k) continue;
+        const int kb = opp(k);
+        const float be = (Bx * ex(k) + By * ey(k) + Bz * ez(k)) * ir;
+        lam_out[k * LS + n] = keep * ls[k] + base + be;
+        lam_out[kb * LS + n] = keep * ls[kb] + base - be;
+    }
 }
 
 // The solid entries a link wrote in links^T, cleared after k_adj_step has
