@@ -15,6 +15,11 @@
 #ifndef LBM_MIN_BLOCKS
 #define LBM_MIN_BLOCKS 12
 #endif
+// the batched form reads its lattice's descriptor from global memory and
+// needs more registers
+#ifndef LBM_MIN_BLOCKS_BATCHED
+#define LBM_MIN_BLOCKS_BATCHED 8
+#endif
 
 namespace ibl {
 
@@ -67,7 +72,7 @@ cudaError_t launch_step_begin(const DevState& d, cudaStream_t s) {
 // SINGLE: the context holds one lattice, whose descriptor arrives by value in
 // the kernel's parameter bank.
 template <typename T, bool SINGLE, bool BORDER>
-__global__ void __launch_bounds__(LBM_THREADS, BORDER ? 4 : LBM_MIN_BLOCKS)
+__global__ void __launch_bounds__(LBM_THREADS, BORDER ? 4 : (SINGLE ? LBM_MIN_BLOCKS : LBM_MIN_BLOCKS_BATCHED))
 k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T* __restrict__ f,
       uint8_t* __restrict__ tag, float* __restrict__ fib, const float* __restrict__ face_vel,
       const uint32_t* __restrict__ status, const uint32_t* __restrict__ nodes, const int* __restrict__ group_mem,
