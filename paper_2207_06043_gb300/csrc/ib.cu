@@ -695,10 +695,13 @@ __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, co
 // closer than 2 dx, found on a uniform grid of 2 dx cells.
 //
 // Broad phase first: a marker i of capsule c can be within 2 dx of a marker of
-// capsule o only if it lies inside o's vertex box grown by 2 dx.  k_broad
-// lists, per capsule, the boxes of the capsules of its lattice that, grown by
-// 3, meet its own box; a marker outside every listed box neither enters the
-// cell grid nor searches it.  The relation is symmetric, so every pair closer
+// capsule o only if it lies inside o's vertex box grown by 2 dx, and within
+// R_o + 2 dx of o's reference point rc_o, R_o being the largest distance of
+// o's vertices from rc_o (both from the geometry pass of this step).  k_broad
+// lists, per capsule, the capsules of its lattice whose box grown by 3 meets
+// its own box and whose sphere grown by 2 meets its own sphere; a marker
+// outside the grown box or the grown sphere of every listed capsule neither
+// enters the cell grid nor searches it.  The relation is symmetric, so every pair closer
 // than the cutoff has both markers in the grid and both searching.  The boxes
 // are those of the geometry pass at the same positions.  With the integer box
 // [lo, hi] of o (lo <= x < hi for its vertices), a marker at X closer than 2
@@ -708,6 +711,13 @@ __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, co
 // narrow).
 // ---------------------------------------------------------------------------
 constexpr int NEAR_GROW = 3;   // capsule-level margin (cutoff 2 plus one node)
+constexpr float NEAR_REACH = 2.01f;   // cutoff plus a slack for the FP32 distances
+
+// R_o + NEAR_REACH, or infinity when a vertex was not finite
+__device__ __forceinline__ float near_reach(const CapsuleSums& B) {
+    const float r = sqrtf(__int_as_float(B.r2_hi)) + NEAR_REACH;
+    return r < 1e6f ? r : INFINITY;
+}
 
 __global__ void __launch_bounds__(128) k_broad(const MemberDev* __restrict__ mem, const CapsuleDev* __restrict__ caps,
                                                const CapsuleSums* __restrict__ sums,
@@ -724,6 +734,7 @@ __global__ void __launch_bounds__(128) k_broad(const MemberDev* __restrict__ mem
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     const CapsuleSums& A = sums[c];
+    const float ra = near_reach(A);
     for (int o = d.cap_begin + threadIdx.x; o < d.cap_begin + d.cap_count; o += blockDim.x) {
         if (o == c) continue;
         const CapsuleSums& B = sums[o];
@@ -731,11 +742,17 @@ __global__ void __launch_bounds__(128) k_broad(const MemberDev* __restrict__ mem
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             meet = meet && A.box_lo[a] <= B.box_hi[a] + NEAR_GROW && B.box_lo[a] - NEAR_GROW <= A.box_hi[a];
+        const float rb = near_reach(B);
+        const float qx = A.rcf[0] - B.rcf[0], qy = A.rcf[1] - B.rcf[1], qz = A.rcf[2] - B.rcf[2];
+        const float reach = ra + rb;   // R_A + R_B + 2 with slack (infinite if either is)
+        meet = meet && qx * qx + qy * qy + qz * qz <= reach * reach;
         if (meet) {
             const int k = atomicAdd(&cnt, 1);
             if (k < NEAR_CAP) {
-                out[1 + 2 * k] = make_int4(B.box_lo[0] - 2, B.box_lo[1] - 2, B.box_lo[2] - 2, 0);
-                out[2 + 2 * k] = make_int4(B.box_hi[0] + 2, B.box_hi[1] + 2, B.box_hi[2] + 2, 0);
+                out[1 + 3 * k] = make_int4(B.box_lo[0] - 2, B.box_lo[1] - 2, B.box_lo[2] - 2, 0);
+                out[2 + 3 * k] = make_int4(B.box_hi[0] + 2, B.box_hi[1] + 2, B.box_hi[2] + 2, 0);
+                out[3 + 3 * k] = make_int4(__float_as_int(B.rcf[0]), __float_as_int(B.rcf[1]), __float_as_int(B.rcf[2]),
+                                           __float_as_int(rb));
             }
         }
     }
@@ -743,16 +760,22 @@ __global__ void __launch_bounds__(128) k_broad(const MemberDev* __restrict__ mem
     if (threadIdx.x == 0) out[0] = make_int4(cnt > NEAR_CAP ? -1 : cnt, 0, 0, 0);
 }
 
-// Whether a marker of capsule c at (X, Y, Z) lies inside a box listed as
-// near c (always when the list overflowed).
+// Whether a marker of capsule c at (X, Y, Z) lies inside the grown box and
+// the grown sphere of a capsule listed as near c (always when the list
+// overflowed).  The FP32 position is within 1e-3 of X below 1.6e4 lu, inside
+// the sphere's 0.01 slack.
 __device__ __forceinline__ bool near_other(const int4* __restrict__ near, int c, double X, double Y, double Z) {
     const int4* e = near + (size_t)c * NEAR_STRIDE;
     const int n = e[0].x;
     if (n < 0) return true;
-    const int xi = (int)floorf((float)X), yi = (int)floorf((float)Y), zi = (int)floorf((float)Z);
+    const float xf = (float)X, yf = (float)Y, zf = (float)Z;
+    const int xi = (int)floorf(xf), yi = (int)floorf(yf), zi = (int)floorf(zf);
     for (int k = 0; k < n; ++k) {
-        const int4 lo = e[1 + 2 * k], hi = e[2 + 2 * k];
-        if (xi >= lo.x && xi <= hi.x && yi >= lo.y && yi <= hi.y && zi >= lo.z && zi <= hi.z) return true;
+        const int4 lo = e[1 + 3 * k], hi = e[2 + 3 * k], sp = e[3 + 3 * k];
+        if (!(xi >= lo.x && xi <= hi.x && yi >= lo.y && yi <= hi.y && zi >= lo.z && zi <= hi.z)) continue;
+        const float qx = xf - __int_as_float(sp.x), qy = yf - __int_as_float(sp.y), qz = zf - __int_as_float(sp.z);
+        const float r = __int_as_float(sp.w);
+        if (qx * qx + qy * qy + qz * qz <= r * r) return true;
     }
     return false;
 }

@@ -184,12 +184,12 @@ struct DevState {
     float4* cell_items = nullptr;    // (x, y, z, capsule id bits) per slot
     int* cell_vid = nullptr;         // vertex id per slot
     float4* xm = nullptr;            // two-float mirror of x: (hi, 0), (lo, 0) per vertex, x = hi + lo
-    int4* near = nullptr;            // NEAR_STRIDE per capsule: count (-1: too many), then grown boxes
+    int4* near = nullptr;            // NEAR_STRIDE per capsule: count (-1: too many), then grown boxes and spheres
     long long n_cells = 0;
 };
 constexpr int CELL_CAP = 32;
 constexpr int NEAR_CAP = 31;          // capsules listed as near one capsule; more: all its markers search
-constexpr int NEAR_STRIDE = 1 + 2 * NEAR_CAP;   // int4 entries: the count, then two per listed box
+constexpr int NEAR_STRIDE = 1 + 3 * NEAR_CAP;   // int4 entries: the count, then three per listed capsule
 
 
 // The optional tape pointers record, per step, what the discrete adjoint needs
