@@ -29,11 +29,14 @@ METRIC = "MLUPS & % of HBM roofline (fwd, adjoint, batched); error vs FP64 oracl
 BYTES_PER_UPDATE = {"f32": 152, "f16": 76, "bf16": 76}
 # DRAM read + write of one FP32 lattice-kernel launch on the throughput
 # workload, from an ncu capture of two launches of the timed region (kept
-# with the profile summaries); valid only for the kernel as captured and that
-# workload.
-LBM_TRAFFIC_BYTES = {("throughput", "f32"): 623.4e6}
+# with the profile summaries), with the hash of the lattice kernel's sources
+# (lbm.cu, lbm_device.cuh) it was captured from: any change to them makes the
+# figure stale, and the bench then reports null until it is captured again.
+LBM_TRAFFIC = {("throughput", "f32"): (623.4e6, "dabdfdcf9e783efe")}
+LBM_SOURCES = ("lbm.cu", "lbm_device.cuh")
 CPU_SAMPLE_X = 64          # x-slab of the workload the oracle runs on (cpu_baseline)
-REF_SAMPLE_X = 16          # thinner slab per step of the reference arm
+REF_SAMPLE_X = 40          # slab of the reference arm (its first layer of capsules)
+PARITY_STEPS = 50          # oracle-parity window on the small bifurcation
 WORKLOADS = {
     # the throughput configuration (12.6 M nodes, 64 capsules)
     "throughput": dict(),
@@ -152,28 +155,141 @@ def run_oracle(case, steps, warmup=0):
     return dt, int(np.count_nonzero(lat.fluid))
 
 
-def cpu_threads():
-    """The oracle's array work is numpy element-wise code: one host thread."""
-    return 1
+def lbm_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in LBM_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_06043_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def lbm_traffic(workload, storage):
+    """Captured DRAM bytes per lattice-kernel launch, or None when none was
+    captured for this workload/storage or the kernel changed since."""
+    rec = LBM_TRAFFIC.get((workload, storage))
+    if rec is None or rec[1] != lbm_source_hash():
+        return None
+    return rec[0]
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _oracle_worker(args):
+    """One oracle process: `steps` timed steps of the sample.  Returns
+    (seconds, fluid nodes)."""
+    sample, steps = args
+    return run_oracle(sample, steps, warmup=0)
+
+
+def oracle_throughput(sample, steps, procs):
+    """Time `procs` independent copies of the oracle on the sample at once, one
+    per host core (spawned processes whose numpy runs one thread: the thread
+    variables are set before the children import it).  Returns (aggregate
+    MLUPS, wall seconds, fluid nodes per copy)."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in THREAD_VARS}
+    for k in THREAD_VARS:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, [(sample, steps)] * procs)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    nf = res[0][1]
+    slowest = max(r[0] for r in res)
+    return procs * nf * steps / slowest / 1e6, wall, nf
+
+
+def cpu_baseline(case, steps, all_cores=True):
+    """The FP64 oracle as it stands on the x-slab sample of the workload: one
+    process with one numpy thread, then (all_cores) one independent copy per
+    host core at once (throughput; the oracle has no loop parallelism of its
+    own)."""
+    sample = cpu_sample_case(case)
+    sample["geometry"].sdf = None          # closures do not cross process boundaries
+    nproc = os.cpu_count() or 1
+    mlups1, wall1, nf = oracle_throughput(sample, steps, 1)
+    out = {"value": mlups1, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": f"x-slab [0,{CPU_SAMPLE_X}) of the workload ({nf} fluid nodes, "
+                     f"{len(sample['capsules'])} capsules), {steps} step(s) per copy",
+           "cpu_model": cpu_model(), "nproc": nproc}
+    if all_cores and nproc > 1:
+        # each copy holds about 1.5 GB; stay within the available memory
+        try:
+            avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+            procs = max(1, min(nproc, int(avail // 2.0e9)))
+        except (ValueError, OSError):
+            procs = nproc
+        mlups_n, wall_n, _ = oracle_throughput(sample, steps, procs)
+        out["all_cores"] = {"value": mlups_n, "unit": "MLUPS", "cores": procs,
+                            "mode": "one independent oracle copy per core, one numpy thread each",
+                            "wall_s": wall_n}
+    return out
+
+
+def workload_config(case, storage, world, threads, blocks_per_sm):
+    """The `config` object of the bench line for a throughput-family case."""
+    return {"workload": case["name"], "fluid_nodes": fluid_updates(case), "box_nodes": case["geometry"].n_nodes,
+            "capsules": len(case["capsules"]), "markers": sum(len(c["verts"]) for c in case["capsules"]),
+            "storage": storage, "l2": "inputs larger than L2 (distributions ~1 GB)",
+            "parallelism": "replicas" if world > 1 else "1 GPU",
+            "launch": {"threads": threads, "blocks_per_sm": blocks_per_sm}}
 
 
 def reference_arm(args, rank):
-    """--impl reference: the FP64 oracle, as it stands, on a bounded sample."""
+    """--impl reference: the FP64 oracle, as it stands, on the host cores: one
+    independent copy per core (one numpy thread each), each stepping a bounded
+    x-slab sample of the workload (its own capsules, inlet and a pressure face
+    at the cut) for the warm-up and timed steps."""
     from paper_2207_06043_gb300 import workloads as W
     if rank != 0:
         return
     case = W.throughput_case(**WORKLOADS[args.workload])
     sample = cpu_sample_case(case, REF_SAMPLE_X)
-    dt, nf = run_oracle(sample, args.steps, args.warmup)
-    mlups = nf * args.steps / dt / 1e6
+    sample["geometry"].sdf = None
+    nproc = os.cpu_count() or 1
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        procs = max(1, min(nproc, int(avail // 1.5e9)))
+    except (ValueError, OSError):
+        procs = nproc
+    if args.warmup:
+        oracle_throughput(sample, 1, procs)       # untimed: spawn, imports, first step
+    mlups, wall, nf = oracle_throughput(sample, args.steps, procs)
+    samp = (f"x-slab [0,{REF_SAMPLE_X}) of the workload ({nf} fluid nodes, {len(sample['capsules'])} capsules), "
+            f"{args.steps} steps, one copy per core on {procs} cores")
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": case["name"], "sample": f"x-slab [0,{REF_SAMPLE_X}) with "
-                       f"{len(sample['capsules'])} capsules", "fluid_nodes": nf},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
-                             "sample": f"x-slab [0,{REF_SAMPLE_X}) of the workload ({nf} fluid nodes, "
-                                       f"{len(sample['capsules'])} capsules), {args.steps} steps"},
+            "config": workload_config(case, args.storage, args.gpus, args.threads, args.blocks_per_sm),
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": procs, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": samp},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -191,9 +307,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle-parity leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep side measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage side measurements")
+    ap.add_argument("--sweep-members", type=int, default=64)
+    ap.add_argument("--sweep-steps", type=int, default=100)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
-    ap.add_argument("--adjoint-ckpt", type=int, default=2000)
+    ap.add_argument("--adjoint-ckpt", type=int, default=100)
     ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     args = ap.parse_args()
@@ -224,33 +344,34 @@ def main():
     s.set_launch(args.threads, args.blocks_per_sm)
     s.step(args.warmup)
 
-    # timed region: per-kernel CUDA events recorded on the library's stream
-    s.enable_timing(True)
+    # timed region, twice: in timing mode (CUDA events between the phases,
+    # which then run one after another on the library's stream) and as graph
+    # replays (the production schedule); nvidia-smi samples both
     stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     with ClockSampler(local) as clk:
-        e0.record(stream)
-        done, _ = s.step(args.steps)
-        e1.record(stream)
+        s.enable_timing(True)
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    kt = s.kernel_times()
-    s.enable_timing(False)
-    # graph replay (production mode) over the same number of steps
-    torch.cuda.synchronize()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    s.step(args.steps)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    ms_graph = g0.elapsed_time(g1)
+        ev[0].record(stream)
+        s.step(args.steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        kt = s.kernel_times()
+        s.enable_timing(False)
+        s.step(1)                       # re-enter graph mode (captures outside the timed region)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        s.step(args.steps)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    ms = ev[0].elapsed_time(ev[1])
+    ms_graph = ev[2].elapsed_time(ev[3])
     ms_best = max_over_ranks(min(ms, ms_graph), dist, "cuda")
     value = whole_job_mlups(nf, args.steps, ms_best, world)
     launches = s.kernels_per_step() * args.steps
@@ -259,23 +380,27 @@ def main():
     peak, peak_kind = load_peaks()
     lbm_ms = kt["lattice"] / args.steps
     achieved = bpu * nf / (lbm_ms * 1e-3) / 1e9
-    traffic = LBM_TRAFFIC_BYTES.get((args.workload, args.storage))
+    traffic = lbm_traffic(args.workload, args.storage)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches"
-                               if traffic else None), "kernel": "k_lbm (fused collide+stream, AA pattern)",
+            "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches, "
+                               f"lattice sources {lbm_source_hash()}" if traffic else
+                               f"not captured for the lattice sources {lbm_source_hash()}"),
+            "kernel": "k_lbm (fused collide+stream, AA pattern)",
             "peak_source": f"{peak_kind} hbm_gbs", "ms_per_launch": lbm_ms,
             "algorithmic_bytes_per_launch": bpu * nf}
     s.close()
 
+    step_bytes = bpu * nf
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_best / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-           "config": {"workload": case["name"], "fluid_nodes": nf, "box_nodes": case["geometry"].n_nodes,
-                      "capsules": len(case["capsules"]), "markers": sum(len(c["verts"]) for c in case["capsules"]),
-                      "storage": args.storage, "l2": "inputs larger than L2 (distributions ~1 GB)",
-                      "parallelism": "replicas" if world > 1 else "1 GPU",
-                      "launch": {"threads": args.threads, "blocks_per_sm": args.blocks_per_sm}},
+           "config": workload_config(case, args.storage, world, args.threads, args.blocks_per_sm),
            "roofline": roof,
+           "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes,
+                             "achieved": step_bytes / (ms_best / args.steps * 1e-3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": step_bytes / (ms_best / args.steps * 1e-3) / 1e9 / peak,
+                             "note": "lattice bytes only (152 B per fluid node) over the whole step"},
            "kernel_ms_per_step": {k: v / args.steps for k, v in kt.items()},
            "ms_per_step_timed_events": ms / args.steps, "ms_per_step_graph": ms_graph / args.steps,
            "clocks": clk.summary(),
@@ -283,21 +408,60 @@ def main():
 
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_run(case, args)
+    if rank == 0 and not args.no_parity:
+        out["oracle_parity"] = oracle_parity()
     if rank == 0 and not args.no_adjoint:
         out["adjoint"] = adjoint_measure(args, case)
     if rank == 0 and not args.no_variants and args.storage == "f32":
         out["storage_variants"] = storage_variants(case, nf)
+    if rank == 0 and not args.no_sweep:
+        out["sweep"] = sweep_measure(args.sweep_members, args.sweep_steps, local, dist)
     if rank == 0 and not args.no_cpu:
-        sample = cpu_sample_case(case)
-        dt, nfs = run_oracle(sample, args.cpu_steps)
-        out["cpu_baseline"] = {"value": nfs * args.cpu_steps / dt / 1e6, "unit": "MLUPS", "cores": cpu_threads(),
-                               "kind": "oracle",
-                               "sample": f"x-slab [0,{CPU_SAMPLE_X}) of the workload ({nfs} fluid nodes, "
-                                         f"{len(sample['capsules'])} capsules), {args.cpu_steps} steps"}
+        out["cpu_baseline"] = cpu_baseline(case, args.cpu_steps)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def oracle_parity(steps=PARITY_STEPS):
+    """Error of the CUDA path against the FP64 oracle on the small bifurcation
+    (96x32x32, rigid sphere d = 12, 642 v) after `steps` steps, for each
+    storage: velocity relative L2 over the fluid nodes and the largest
+    centroid difference (lattice units)."""
+    from paper_2207_06043_gb300 import workloads as W
+    from oracle import lattice as L
+    from oracle import sim
+    c = W.bifurcation_small()
+    g = c["geometry"]
+    lat = L.Lattice(g.nx, g.ny, g.nz, c["tau"], g.tag, g.links, g.faces, g.periodic)
+    o = sim.Simulation(lat, u_max=c["u_max"])
+    for cap in c["capsules"]:
+        o.add_body(cap["verts"], cap["tris"], cap["params"], cap.get("vel0"))
+    t0 = time.perf_counter()
+    o.step(steps)
+    t_or = time.perf_counter() - t0
+    _, uo = lat.macroscopic(o.f)
+    fl = lat.fluid
+    cen_o = o.stats(0)["centroid"]
+    out = {"workload": c["name"].replace("500 steps", f"{steps} steps"), "steps": steps,
+           "oracle_seconds": t_or}
+    for st in ("f32", "f16", "bf16"):
+        s = W.make_solver(c, storage=st)
+        s.step(steps)
+        _, u = s.read_fields()
+        cen = s.read_capsule(0)["centroid"]
+        s.close()
+        out[st] = {"velocity_rel_l2": float(np.linalg.norm(u[fl] - uo[fl]) / np.linalg.norm(uo[fl])),
+                   "centroid_max_abs": float(np.abs(cen - cen_o).max())}
+    return out
+
+
+def sweep_measure(n_members, steps, local, dist):
+    """The batched sweep as a side measurement of the default run: the sweep
+    members stepped as one context (graph replay, autotuned launch shape)."""
+    members = sweep_members(n_members)
+    return sweep_run(members, steps, max(3, steps // 10), local, dist)
 
 
 def storage_variants(case, nf, steps=100):
@@ -332,63 +496,74 @@ def storage_variants(case, nf, steps=100):
     return out
 
 
-def _adjoint_run(c, n, K, lo, hi):
-    """Time n plain forward steps and one ibl_adjoint call of n steps on the
-    lattice of case c (no capsules), each on its own context; the adjoint is
-    timed on its second call (the first allocates its buffers and captures
-    its graphs)."""
+def _adjoint_run(c, n, Ks, lo, hi):
+    """Time n plain forward steps, then one ibl_adjoint call of n steps per
+    checkpoint interval K in Ks, on the lattice of case c (no capsules), each
+    on its own context.  Each adjoint is timed on its second call (the first
+    allocates its buffers and captures its graphs)."""
     import torch
     from paper_2207_06043_gb300 import workloads as W
-    fwd = W.make_solver(c)
-    adj = W.make_solver(c)
-    fwd.step(10)
-    adj.step(10)
     stream = torch.cuda.current_stream()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    fwd = W.make_solver(c)
+    fwd.step(10)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     torch.cuda.synchronize()
     e[0].record(stream)
     fwd.step(n)
     e[1].record(stream)
-    adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)     # allocates the buffers, captures the graphs
     torch.cuda.synchronize()
-    e[2].record(stream)
-    J, gs, gr = adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)
-    e[3].record(stream)
-    torch.cuda.synchronize()
-    ms_f, ms_a = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    ms_f = e[0].elapsed_time(e[1])
     fwd.close()
-    adj.close()
     nf = fluid_updates(c)
-    return {"fluid_nodes": nf, "steps": n, "ckpt_every": K, "ms_forward": ms_f, "ms_adjoint_call": ms_a,
-            "cost_vs_forward": ms_a / ms_f, "mlups_adjoint": nf * n / (ms_a * 1e-3) / 1e6,
-            "J": J, "dJ_du_max": gs / c["u_max"], "dJ_dr_j": gr}
+    out = {"fluid_nodes": nf, "steps": n, "ms_forward": ms_f}
+    for K in Ks:
+        adj = W.make_solver(c)
+        adj.step(10)
+        adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)     # allocates the buffers, captures the graphs
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        J, gs, gr = adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        ms_a = e[0].elapsed_time(e[1])
+        adj.close()
+        out[f"K{K}"] = {"ckpt_every": K, "segments": -(-n // K), "recomputed_steps": n - min(K, n),
+                        "ms_adjoint_call": ms_a, "cost_vs_forward": ms_a / ms_f,
+                        "mlups_adjoint": nf * n / (ms_a * 1e-3) / 1e6,
+                        "J": J, "dJ_du_max": gs / c["u_max"], "dJ_dr_j": gr}
+    return out
 
 
 def adjoint_measure(args, case):
     """The discrete adjoint (ibl_adjoint) against the same number of plain
-    forward steps, on (a) the adjoint workload's lattice (192x64x48
-    bifurcation, junction radius 4 lu, 2000 steps) and (b) the throughput
-    workload's lattice (12.6 M nodes, 100 steps), each with its whole tape in
-    HBM (one segment: no recompute; about 20 GB each),
-    both without capsules: the adjoint covers the lattice step.  J = sum of
-    u_x over the upper half of the region just past the junction (a), of the
-    inlet region (b)."""
+    forward steps, both without capsules (the adjoint covers the lattice
+    step):
+      (a) the adjoint workload's lattice (192x64x48 bifurcation, junction
+          radius 4 lu, 2000 steps) with checkpoints every --adjoint-ckpt
+          steps (default 100: each earlier segment is recomputed from its
+          checkpoint while its tape is rebuilt), and with one segment (whole
+          tape in HBM, nothing recomputed);
+      (b) the throughput workload's lattice (12.6 M nodes, 100 steps, one
+          segment), whose HBM fraction is reported at 336 B per node and step.
+    J = sum of u_x over the upper half of the region just past the junction
+    (a), of the inlet region (b)."""
     from paper_2207_06043_gb300 import workloads as W
-    out = {"note": "each timed call runs the forward sweep writing the tape and the reverse sweep (one "
-                   "segment: nothing recomputed); its buffers and graphs come from a first, untimed call"}
+    out = {"note": "each timed call runs the forward sweep (checkpoints, or the tape of the only segment), "
+                   "the recompute of every earlier segment with its tape, and the reverse sweep; buffers and "
+                   "graphs come from a first, untimed call"}
     ca = dict(W.adjoint_case(), capsules=[])
     g = ca["geometry"]
     xj = int(g.info["x_junction"])
-    r = _adjoint_run(ca, args.adjoint_steps, args.adjoint_ckpt, (xj, int(g.info["yc"]), 0),
-                     (min(g.nx, xj + 24), g.ny, g.nz))
+    Ks = [args.adjoint_ckpt] + ([args.adjoint_steps] if args.adjoint_ckpt < args.adjoint_steps else [])
+    r = _adjoint_run(ca, args.adjoint_steps, Ks, (xj, int(g.info["yc"]), 0), (min(g.nx, xj + 24), g.ny, g.nz))
+    r["cost_vs_forward"] = r[f"K{args.adjoint_ckpt}"]["cost_vs_forward"]
     out["adjoint_workload"] = dict(r, workload="bifurcation 192x64x48, D 36, 45 deg, junction radius 4 lu, no capsule")
     ct = dict(case, capsules=[])
     g = ct["geometry"]
-    xj = int(g.info["x_junction"])
-    r = _adjoint_run(ct, 100, 100, (4, int(g.info["yc"]), 0), (52, g.ny, g.nz))
+    r = _adjoint_run(ct, 100, [100], (4, int(g.info["yc"]), 0), (52, g.ny, g.nz))
     bpu = 168 + 168            # forward step writing the tape, adjoint step (B per fluid node and step)
     peak, kind = load_peaks()
-    ach = bpu * r["fluid_nodes"] * r["steps"] / (r["ms_adjoint_call"] * 1e-3) / 1e9
+    ach = bpu * r["fluid_nodes"] * r["steps"] / (r["K100"]["ms_adjoint_call"] * 1e-3) / 1e9
     out["throughput_lattice"] = dict(r, workload="throughput lattice 512x192x128 without capsules",
                                      roofline={"bound": "hbm", "algorithmic_bytes_per_node_step": bpu,
                                                "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -403,28 +578,24 @@ def _sweep_member(k):
     return c
 
 
-def sweep_bench(args, rank, world, local):
-    """Batched sweep: the members of the sweep workload stepped together as one
-    context (one launch per kernel per step for all lattices, CUDA graphs),
-    launch shape chosen by the library's autotuner.  MLUPS counts the fluid
-    nodes of the members that are still running (a capsule that breaks stops
-    its lattice, as the damage rule says)."""
+def sweep_members(n):
+    """The sweep's members, generated in spawned worker processes."""
     import multiprocessing as mp
-    # inputs are generated before CUDA starts, in spawned workers
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        members = pool.map(_sweep_member, range(args.members))
+        return pool.map(_sweep_member, range(n))
+
+
+def sweep_run(members, steps, warmup, local, dist):
+    """Step the members together as one context (one launch per kernel per
+    step for all lattices, CUDA graphs), launch shape chosen by the library's
+    autotuner.  MLUPS counts the fluid nodes of the members still running (a
+    capsule that breaks stops its lattice, as the damage rule says)."""
     import torch
-    torch.cuda.set_device(local)
-    torch.zeros(1, device="cuda")
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     from paper_2207_06043_gb300 import binding
     from paper_2207_06043_gb300 import workloads as W
     nf = [fluid_updates(c) for c in members]
     ens = binding.ensemble([W.make_solver(c) for c in members])
-    ens.step(args.warmup, allow_damage=True)
+    ens.step(warmup, allow_damage=True)
     thr, bps, _ = ens.autotune(4)
     n_m = len(members)
 
@@ -435,12 +606,13 @@ def sweep_bench(args, rank, world, local):
     # lattice-kernel time per step from a timing-mode pass
     ens.enable_timing(True)
     c0 = steps_done()
-    ens.step(args.steps, allow_damage=True)
+    ens.step(steps, allow_damage=True)
     c1 = steps_done()
     kt = ens.kernel_times()
     ens.enable_timing(False)
-    upd_timing = sum(nf[m] * (c1[m] - c0[m]) for m in range(n_m))
-    # timed region: graph replay
+    ens.step(1, allow_damage=True)       # back to graph replay (captures outside the timed region)
+    c1 = steps_done()
+    upd_timing = sum(nf[m] * (c1[m] - c0[m] - 1) for m in range(n_m))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if dist:
@@ -448,41 +620,67 @@ def sweep_bench(args, rank, world, local):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        ens.step(args.steps, allow_damage=True)
+        ens.step(steps, allow_damage=True)
         e1.record(stream)
         torch.cuda.synchronize()
     c2 = steps_done()
     ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    world = dist.get_world_size() if dist else 1
     upd = sum(nf[m] * (c2[m] - c1[m]) for m in range(n_m))
-    value = world * upd / (ms * 1e-3) / 1e6
     bpu = BYTES_PER_UPDATE["f32"]
     peak, peak_kind = load_peaks()
-    achieved = bpu * upd_timing / (kt["lattice"] * 1e-3) / 1e9
-    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"batched sweep: {n_m} bifurcations of uneven size, one capsule each",
-                      "fluid_nodes": int(sum(nf)), "box_nodes": int(sum(c["geometry"].n_nodes for c in members)),
-                      "running_members": int(sum(1 for m in range(n_m) if c2[m] - c1[m] == args.steps)),
-                      "l2": "inputs larger than L2", "launch": {"threads": thr, "blocks_per_sm": bps,
-                                                                "chosen_by": "ibl_autotune"}},
+    achieved = bpu * upd_timing / (kt["lattice"] * 1e-3) / 1e9 if kt["lattice"] > 0 else 0.0
+    stopped = [m for m in range(n_m) if c2[m] - c1[m] < steps]
+    out = {"value": world * upd / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps, "warmup": warmup,
+           "ms_per_step": ms / steps,
+           "workload": f"batched sweep: {n_m} bifurcations of uneven size, one capsule each",
+           "fluid_nodes": int(sum(nf)), "box_nodes": int(sum(c["geometry"].n_nodes for c in members)),
+           "running_members": n_m - len(stopped),
+           "stopped_members": [{"member": m, "Ca": members[m]["capsules"][0]["params"]["Ca"],
+                                "steps_done": c2[m]} for m in stopped],
+           "launch": {"threads": thr, "blocks_per_sm": bps, "chosen_by": "ibl_autotune"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None,
                         "kernel": "k_lbm (all members in one launch)", "peak_source": f"{peak_kind} hbm_gbs"},
-           "kernel_ms_per_step": {k: v / args.steps for k, v in kt.items()},
-           "clocks": clk.summary(), "gpu_launches": ens.kernels_per_step() * args.steps}
+           "kernel_ms_per_step": {k: v / steps for k, v in kt.items()},
+           "clocks": clk.summary(), "gpu_launches": ens.kernels_per_step() * steps}
     ens.close()
+    return out
+
+
+def sweep_bench(args, rank, world, local):
+    """--workload sweep: the batched sweep as the bench's own workload."""
+    members = sweep_members(args.members)
+    import torch
+    torch.cuda.set_device(local)
+    torch.zeros(1, device="cuda")
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = sweep_run(members, args.steps, args.warmup, local, dist)
+    out = {"metric": METRIC, "value": r["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": r["workload"], "fluid_nodes": r["fluid_nodes"], "box_nodes": r["box_nodes"],
+                      "running_members": r["running_members"], "l2": "inputs larger than L2",
+                      "launch": r["launch"]},
+           "roofline": r["roofline"], "kernel_ms_per_step": r["kernel_ms_per_step"],
+           "stopped_members": r["stopped_members"], "clocks": r["clocks"], "gpu_launches": r["gpu_launches"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def e2e_run(case, args):
-    """The same metric through the public API from host buffers: context set-up
-    (every input array copied host -> device), the time steps, capsule
-    diagnostics read back every 100 steps and the fields read at the end, all
-    inside the timed region."""
+def e2e_run(case, args, chunk=10):
+    """The same metric through the public API from host buffers.  Set-up: the
+    context is created from the host arrays (every input copied host ->
+    device, topology and work lists built, initial state written).  Then the
+    time steps in chunks of `chunk`, each chunk followed by a device -> host
+    read of every capsule's state and diagnostics, and a read of the fields
+    to the host at the end.  `value` covers both; `steady` covers the
+    stepping with its per-chunk reads alone."""
     import torch
     from paper_2207_06043_gb300 import workloads as W
     g = case["geometry"]
@@ -493,10 +691,13 @@ def e2e_run(case, args):
     t0 = time.perf_counter()
     s = W.make_solver(case, storage=args.storage)
     s.set_launch(args.threads, args.blocks_per_sm)
+    s.step(0)                               # set-up: uploads, work lists, initial state
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     d2h = 0
     left = args.steps
     while left > 0:
-        k = min(100, left)
+        k = min(chunk, left)
         s.step(k)
         left -= k
         for cid in range(len(case["capsules"])):
@@ -505,11 +706,15 @@ def e2e_run(case, args):
     rho, u = s.read_fields()
     d2h += rho.nbytes + u.nbytes
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    t2 = time.perf_counter()
     s.close()
-    return {"value": nf * args.steps / dt / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
-            "d2h_bytes_per_step": d2h / args.steps,
-            "note": "includes context set-up from host arrays (topology, uploads, initial state)"}
+    return {"value": nf * args.steps / (t2 - t0) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+            "d2h_bytes_per_step": d2h / args.steps, "setup_ms": 1e3 * (t1 - t0),
+            "steady": {"value": nf * args.steps / (t2 - t1) / 1e6, "unit": "MLUPS",
+                       "ms_per_step": 1e3 * (t2 - t1) / args.steps, "chunk": chunk,
+                       "d2h_bytes_per_step": d2h / args.steps},
+            "note": f"value includes the set-up from host arrays (setup_ms); steady = the steps with a read of "
+                    f"every capsule after each chunk of {chunk} steps and the fields at the end"}
 
 
 if __name__ == "__main__":

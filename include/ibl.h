@@ -109,7 +109,10 @@ typedef struct {
 
 /* Create a context with one lattice.  cuda_stream: a cudaStream_t (NULL = the
  * legacy default stream); every device operation of the context runs on it.
- * Until the first ibl_step / ibl_read_* the context holds host data only. */
+ * The context belongs to the CUDA device current at this call; that device
+ * must be current at every later call (IBL_ERR_STATE when the context is set
+ * up on another).  Until the first ibl_step / ibl_read_* the context holds
+ * host data only. */
 ibl_status ibl_create(const ibl_lattice_desc* desc, void* cuda_stream, ibl_ctx** out);
 
 /* Fixed geometry (Section "No-Slip boundary conditions for stationary immersed
@@ -143,7 +146,10 @@ ibl_status ibl_add_capsule(ibl_ctx* ctx, const double* verts, int32_t nv,
 ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done);
 
 /* Macroscopic fields of member 0: rho[N], u[3N] (either may be NULL), with
- * rho u = sum f e + F_body/2; solid nodes read 0. */
+ * rho u = sum f e + F_body/2; solid nodes read 0.  With host buffers the
+ * values pass through a device staging buffer that the context allocates on
+ * the first such read (cudaMalloc), keeps, and grows when a later read needs
+ * more; ibl_destroy frees it. */
 ibl_status ibl_read_fields(ibl_ctx* ctx, float* rho, float* u, int32_t on_device);
 
 /* Populations f_i - w_i of member 0 in FP32, layout [19][N], as they stand
@@ -262,11 +268,14 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every,
  *   - Lattices of more than IBL_NOALLOC_MAX_NODES nodes are rejected with
  *     IBL_ERR_ARG (use ibl_member_read_fields).
  *   - The context must already hold its device state (stepped, initialised or
- *     read once): setting it up allocates, so otherwise IBL_ERR_STATE.
- *   - The first call on a device looks up that device's copy of the static
- *     array (cudaGetSymbolAddress, with the context's device current); make it
- *     before any stream capture.  The call synchronises its work stream and
- *     cannot itself be captured.
+ *     read once): setting it up allocates, so otherwise IBL_ERR_STATE.  That
+ *     set-up also looks up the device's copy of the static array
+ *     (cudaGetSymbolAddress), which loads the library module holding it, so
+ *     the array's memory is reserved while the context is set up, not by this
+ *     call.
+ *   - The device that was current when the context was created must be
+ *     current (IBL_ERR_STATE otherwise): the array is per device.  The call
+ *     synchronises its work stream.
  *   - All contexts of the process share the one array per device: calls whose
  *     GPU work overlaps (other host threads, contexts on other streams) race
  *     on it and may return each other's data.  Serialise them. */

@@ -76,6 +76,10 @@ struct ibl_ctx {
     int threads = 128;   // lattice kernel block size (the compiled bound)
     int blocks_per_sm = 0;
     int n_sm = 0;
+    int device = -1;                   // CUDA device current when the context was created
+    float* noalloc = nullptr;          // that device's copy of the static read array
+    float* stage = nullptr;            // device staging buffer of host reads, kept and grown
+    size_t stage_bytes = 0;
     bool timing = false;
     std::vector<cudaEvent_t> tev;
     double ktime[4] = {0, 0, 0, 0};
@@ -327,11 +331,55 @@ ibl_status validate_member(ibl_ctx* ctx, const MemberHost& M) {
     return IBL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Static staging array of ibl_read_fields_noalloc, for callers that may not
+// allocate device memory: rho in the first IBL_NOALLOC_MAX_NODES floats, u in
+// the next 3 * IBL_NOALLOC_MAX_NODES.  Nothing in it needs to start at zero:
+// the read kernel writes every element that is then copied out (solid nodes
+// as 0).  One array per device, shared by every context of the process, so
+// overlapping calls race on it.  Its device address is looked up while a
+// context is set up (finalize), which allocates anyway: that lookup loads
+// this file's module, and with it the array, under lazy module loading, so
+// the entry point itself neither loads a module nor reserves memory.
+// ---------------------------------------------------------------------------
+}  // namespace
+
+static __device__ __align__(256) float g_noalloc_scratch[4 * (size_t)IBL_NOALLOC_MAX_NODES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Address of device dev's copy of the static array (dev must be the current
+// device), looked up once per device and cached.
+ibl_status noalloc_scratch(ibl_ctx* ctx, int dev, float** out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(ctx, IBL_ERR_ARG, "device ordinal beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, IBL_ERR_CUDA, std::string("cudaGetSymbolAddress of the static read array failed: ") +
+                                               cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (float*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return IBL_OK;
+}
+
 ibl_status finalize(ibl_ctx* ctx) {
     if (ctx->finalized) return IBL_OK;
     int dev_id = 0;
     CK(cudaGetDevice(&dev_id));
+    if (dev_id != ctx->device)
+        return fail(ctx, IBL_ERR_STATE, "the context's device (" + std::to_string(ctx->device) +
+                                            ") must be current when it is set up");
     CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev_id));
+    // the static array of ibl_read_fields_noalloc: looked up here, where the
+    // set-up allocates anyway, so that the entry point itself loads nothing
+    CKS(noalloc_scratch(ctx, dev_id, &ctx->noalloc));
     const int nm = (int)ctx->members.size();
     if (nm < 1 || nm > MAX_MEMBERS) return fail(ctx, IBL_ERR_ARG, "member count out of range");
     for (auto& M : ctx->members) CKS(validate_member(ctx, M));
@@ -840,18 +888,30 @@ ibl_status read_fields_member(ibl_ctx* ctx, int m, float* rho, float* u, float* 
     if (on_device) {
         CK(launch_read(ctx->dev, m, parity, rho, u, g, ctx->work));
     } else {
-        float *dr = nullptr, *du = nullptr, *dg = nullptr;
-        if (rho) CK(cudaMalloc((void**)&dr, sizeof(float) * Nu));
-        if (u) CK(cudaMalloc((void**)&du, sizeof(float) * 3 * Nu));
-        if (g) CK(cudaMalloc((void**)&dg, sizeof(float) * 19 * Nu));
+        // one device staging buffer per context, allocated by the first host
+        // read and grown when a larger one is needed
+        const size_t need = sizeof(float) * Nu * ((rho ? 1 : 0) + (u ? 3 : 0) + (g ? 19 : 0));
+        if (need > ctx->stage_bytes) {
+            CK(cudaStreamSynchronize(ctx->work));
+            if (ctx->stage) cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+            const cudaError_t e = cudaMalloc((void**)&ctx->stage, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ctx->stage = nullptr;
+                return fail(ctx, IBL_ERR_OOM, "read staging buffer: cudaMalloc of " + std::to_string(need) + " bytes failed");
+            }
+            ctx->stage_bytes = need;
+        }
+        float* dr = rho ? ctx->stage : nullptr;
+        float* du = u ? ctx->stage + (rho ? Nu : 0) : nullptr;
+        float* dg = g ? ctx->stage + (rho ? Nu : 0) + (u ? 3 * Nu : 0) : nullptr;
         CK(launch_read(ctx->dev, m, parity, dr, du, dg, ctx->work));
         if (rho) CK(cudaMemcpyAsync(rho, dr, sizeof(float) * Nu, cudaMemcpyDeviceToHost, ctx->work));
         if (u) CK(cudaMemcpyAsync(u, du, sizeof(float) * 3 * Nu, cudaMemcpyDeviceToHost, ctx->work));
         if (g) CK(cudaMemcpyAsync(g, dg, sizeof(float) * 19 * Nu, cudaMemcpyDeviceToHost, ctx->work));
         CK(cudaStreamSynchronize(ctx->work));
-        if (dr) cudaFree(dr);
-        if (du) cudaFree(du);
-        if (dg) cudaFree(dg);
     }
     CKS(leave(ctx));
     return IBL_OK;
@@ -896,42 +956,6 @@ ibl_status read_capsule_member(ibl_ctx* ctx, int m, int id, ibl_capsule_stats* s
     return IBL_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Static staging array of ibl_read_fields_noalloc, for callers that may not
-// allocate device memory: rho in the first IBL_NOALLOC_MAX_NODES floats, u in
-// the next 3 * IBL_NOALLOC_MAX_NODES.  Nothing in it needs to start at zero:
-// the read kernel writes every element that is then copied out (solid nodes
-// as 0).  One array per device, shared by every context of the process, so
-// overlapping calls race on it.
-// ---------------------------------------------------------------------------
-}  // namespace
-
-static __device__ __align__(256) float g_noalloc_scratch[4 * (size_t)IBL_NOALLOC_MAX_NODES];
-
-namespace {
-
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-
-// Address of the current device's copy of the static array, looked up once
-// per device (with that device current) and cached.
-ibl_status noalloc_scratch(ibl_ctx* ctx, float** out) {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(ctx, IBL_ERR_ARG, "device ordinal beyond 63");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(ctx, IBL_ERR_CUDA, std::string("cudaGetSymbolAddress of the static read array failed: ") +
-                                               cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = (float*)p;
-    }
-    *out = g_noalloc_ptr[dev];
-    return IBL_OK;
-}
 
 // ---------------------------------------------------------------------------
 // State snapshot: everything a later step reads that the steps themselves
@@ -990,7 +1014,8 @@ ibl_status new_ctx(void* stream, ibl_ctx** out) {
     ibl_ctx* ctx = new (std::nothrow) ibl_ctx();
     if (!ctx) return fail(nullptr, IBL_ERR_OOM, "host allocation failed");
     ctx->user_stream = (cudaStream_t)stream;
-    cudaError_t e = cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking);
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->work2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->work3, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_shell, cudaEventDisableTiming);
@@ -1433,8 +1458,12 @@ ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, flo
                                           " nodes, IBL_NOALLOC_MAX_NODES); use ibl_member_read_fields");
     if (!ctx->finalized)
         return fail(ctx, IBL_ERR_STATE, "no device state yet (its set-up allocates): step, initialise or read first");
-    float* scratch = nullptr;
-    CKS(noalloc_scratch(ctx, &scratch));
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != ctx->device || !ctx->noalloc)
+        return fail(ctx, IBL_ERR_STATE, "the context's device (" + std::to_string(ctx->device) +
+                                            ") must be current (device " + std::to_string(dev) + " is)");
+    float* scratch = ctx->noalloc;
     float* dr = rho ? scratch : nullptr;
     float* du = u ? scratch + IBL_NOALLOC_MAX_NODES : nullptr;
     const int cnt = ctx->h_counters[member];
@@ -1582,6 +1611,7 @@ void ibl_destroy(ibl_ctx* ctx) {
     drop_graphs(ctx);
     free_adjoint(ctx);
     for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->work2) cudaStreamSynchronize(ctx->work2);

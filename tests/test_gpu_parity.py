@@ -164,11 +164,10 @@ def test_four_capsules_two_close_pairs():
     assert err <= VEL_TOL, err
 
 
-@pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", 2e-3)])
-def test_reduced_storage_against_fp32(storage, tol):
-    """16-bit storage of f - w with FP32 arithmetic against the FP32 path:
-    velocity relative L2 <= 1e-3 for FP16 (10-bit mantissa, scaled by 2^12);
-    BF16 (8-bit mantissa) lands at ~1.0e-3 on this case and is held to 2e-3."""
+STORAGE_TARGET = 1e-3     # 16-bit storage against the plain FP32 path
+
+
+def _reduced_storage_error(storage):
     g = G.bifurcation(64, 28, 24, 16.0, 45.0, 2.0, u_max=0.02)
     V, T = Ms.sphere_mesh(642, 10.0, (12.0, g.info["yc"], g.info["zc"] + 0.5), Ms.SplitMix64(9))
     c = case(g, capsules=[W._capsule(V, T, Ca=0.02)])
@@ -178,8 +177,27 @@ def test_reduced_storage_against_fp32(storage, tol):
     b.step(300)
     _, ua = a.read_fields()
     _, ub = b.read_fields()
-    fl = g.tag == 0
-    assert rel_l2(ub, ua, fl) <= tol
+    err = rel_l2(ub, ua, g.tag == 0)
+    print(f"{storage} storage vs FP32: velocity rel L2 {err:.3e}")
+    return err
+
+
+def test_fp16_storage_against_fp32():
+    """f - w stored in FP16 (10-bit mantissa, scaled by 2^12), FP32 arithmetic,
+    against the FP32 path: velocity relative L2 within the 1e-3 target."""
+    assert _reduced_storage_error("f16") <= STORAGE_TARGET
+
+
+def test_bf16_storage_regression_bound():
+    """BF16 storage (8-bit mantissa) lands at about 1.0e-3 on this case: a
+    regression bound of twice the target, kept beside the target test below."""
+    assert _reduced_storage_error("bf16") <= 2 * STORAGE_TARGET
+
+
+@pytest.mark.xfail(reason="BF16 storage misses the 1e-3 target marginally: measured about 1.0e-3 "
+                          "(8-bit mantissa, rounding of f - w at 2^-9 relative per store)", strict=False)
+def test_bf16_storage_target():
+    assert _reduced_storage_error("bf16") <= STORAGE_TARGET
 
 
 def test_ensemble_matches_single_lattices_exactly():
