@@ -519,10 +519,10 @@ def _adjoint_run(c, n, Ks, lo, hi):
     for K in Ks:
         adj = W.make_solver(c)
         adj.step(10)
-        adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)     # allocates the buffers, captures the graphs
+        adj.adjoint_flow(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)     # allocates the buffers, captures the graphs
         torch.cuda.synchronize()
         e[0].record(stream)
-        J, gs, gr = adj.adjoint(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)
+        J, gs, gr = adj.adjoint_flow(n, lo, hi, (1.0, 0.0, 0.0), ckpt_every=K)
         e[1].record(stream)
         torch.cuda.synchronize()
         ms_a = e[0].elapsed_time(e[1])
@@ -534,30 +534,65 @@ def _adjoint_run(c, n, Ks, lo, hi):
     return out
 
 
+def _adjoint_capsule_run(c, n, Ks, w=(1.0, 0.5)):
+    """Time n plain forward steps, then one capsule adjoint call (ibl_adjoint)
+    of n steps per checkpoint interval K in Ks, on case c (one soft capsule),
+    each on its own context; each adjoint is timed on its second call."""
+    import torch
+    from paper_2207_06043_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    fwd = W.make_solver(c)
+    fwd.step(10)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    fwd.step(n)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    ms_f = e[0].elapsed_time(e[1])
+    fwd.close()
+    nf = fluid_updates(c)
+    out = {"fluid_nodes": nf, "steps": n, "ms_forward": ms_f, "objective": f"{w[0]} D + {w[1]} offset"}
+    for K in Ks:
+        adj = W.make_solver(c)
+        adj.step(10)
+        state = adj.save_state()
+        adj.adjoint(n, w, ckpt_every=K)          # allocates the buffers, captures the graphs
+        adj.load_state(state)
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        g = adj.adjoint(n, w, ckpt_every=K)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        ms_a = e[0].elapsed_time(e[1])
+        adj.close()
+        out[f"K{K}"] = {"ckpt_every": K, "segments": -(-n // K), "recomputed_steps": n - min(K, n),
+                        "ms_adjoint_call": ms_a, "cost_vs_forward": ms_a / ms_f,
+                        "dJ_dCa": g[0], "dJ_du_max": g[1], "dJ_dr_j": g[2]}
+    return out
+
+
 def adjoint_measure(args, case):
-    """The discrete adjoint (ibl_adjoint) against the same number of plain
-    forward steps, both without capsules (the adjoint covers the lattice
-    step):
-      (a) the adjoint workload's lattice (192x64x48 bifurcation, junction
-          radius 4 lu, 2000 steps) with checkpoints every --adjoint-ckpt
-          steps (default 100: each earlier segment is recomputed from its
-          checkpoint while its tape is rebuilt), and with one segment (whole
-          tape in HBM, nothing recomputed);
-      (b) the throughput workload's lattice (12.6 M nodes, 100 steps, one
-          segment), whose HBM fraction is reported at 336 B per node and step.
-    J = sum of u_x over the upper half of the region just past the junction
-    (a), of the inlet region (b)."""
+    """The discrete adjoint against the same number of plain forward steps:
+      (a) the adjoint workload as specified (192x64x48 bifurcation, junction
+          radius 4 lu, one soft capsule d = 27 of 2562 vertices, Ca = 0.01,
+          2000 steps), the capsule objective D + 0.5 offset (ibl_adjoint) with
+          checkpoints every --adjoint-ckpt steps (default 100: each earlier
+          segment is recomputed from its checkpoint while its tape is
+          rebuilt) and with one segment (whole tape in HBM);
+      (b) the throughput workload's lattice without capsules (12.6 M nodes,
+          100 steps, one segment), the flow objective (ibl_adjoint_flow),
+          whose HBM fraction is reported at 336 B per node and step."""
     from paper_2207_06043_gb300 import workloads as W
     out = {"note": "each timed call runs the forward sweep (checkpoints, or the tape of the only segment), "
                    "the recompute of every earlier segment with its tape, and the reverse sweep; buffers and "
                    "graphs come from a first, untimed call"}
-    ca = dict(W.adjoint_case(), capsules=[])
-    g = ca["geometry"]
-    xj = int(g.info["x_junction"])
+    ca = W.adjoint_case()
     Ks = [args.adjoint_ckpt] + ([args.adjoint_steps] if args.adjoint_ckpt < args.adjoint_steps else [])
-    r = _adjoint_run(ca, args.adjoint_steps, Ks, (xj, int(g.info["yc"]), 0), (min(g.nx, xj + 24), g.ny, g.nz))
+    r = _adjoint_capsule_run(ca, args.adjoint_steps, Ks)
     r["cost_vs_forward"] = r[f"K{args.adjoint_ckpt}"]["cost_vs_forward"]
-    out["adjoint_workload"] = dict(r, workload="bifurcation 192x64x48, D 36, 45 deg, junction radius 4 lu, no capsule")
+    out["adjoint_workload"] = dict(r, workload="bifurcation 192x64x48, D 36, 45 deg, junction radius 4 lu, "
+                                               "capsule d=27 (2562 v), Ca 0.01")
     ct = dict(case, capsules=[])
     g = ct["geometry"]
     r = _adjoint_run(ct, 100, [100], (4, int(g.info["yc"]), 0), (52, g.ny, g.nz))
@@ -678,8 +713,9 @@ def e2e_run(case, args, chunk=10):
     context is created from the host arrays (every input copied host ->
     device, topology and work lists built, initial state written).  Then the
     time steps in chunks of `chunk`, each chunk followed by a device -> host
-    read of every capsule's state and diagnostics, and a read of the fields
-    to the host at the end.  `value` covers both; `steady` covers the
+    read of every capsule's FP64 diagnostics (ibl_read_capsules: centroid,
+    volume, area, Taylor D, stretch, velocity), and a read of the fields to
+    the host at the end.  `value` covers both; `steady` covers the
     stepping with its per-chunk reads alone."""
     import torch
     from paper_2207_06043_gb300 import workloads as W
@@ -700,9 +736,9 @@ def e2e_run(case, args, chunk=10):
         k = min(chunk, left)
         s.step(k)
         left -= k
-        for cid in range(len(case["capsules"])):
-            s.read_capsule(cid)
-            d2h += 2 * 3 * 8 * len(case["capsules"][cid]["verts"])
+        if case["capsules"]:
+            s.read_capsules(len(case["capsules"]))
+            d2h += 18 * 8 * len(case["capsules"])
     rho, u = s.read_fields()
     d2h += rho.nbytes + u.nbytes
     torch.cuda.synchronize()
@@ -714,7 +750,7 @@ def e2e_run(case, args, chunk=10):
                        "ms_per_step": 1e3 * (t2 - t1) / args.steps, "chunk": chunk,
                        "d2h_bytes_per_step": d2h / args.steps},
             "note": f"value includes the set-up from host arrays (setup_ms); steady = the steps with a read of "
-                    f"every capsule after each chunk of {chunk} steps and the fields at the end"}
+                    f"every capsule's diagnostics after each chunk of {chunk} steps and the fields at the end"}
 
 
 if __name__ == "__main__":

@@ -160,6 +160,12 @@ ibl_status ibl_read_populations(ibl_ctx* ctx, float* g, int32_t on_device);
 ibl_status ibl_read_capsule(ibl_ctx* ctx, int32_t id, ibl_capsule_stats* stats,
                             double* verts_out);
 
+/* FP64 diagnostics of all n capsules of member `member` (n must equal the
+ * member's capsule count), computed on the device and read back in one copy
+ * of 18 doubles per capsule: the same quantities as ibl_read_capsule (volume
+ * moments from the tetrahedra fanned from each capsule's first vertex). */
+ibl_status ibl_read_capsules(ibl_ctx* ctx, int32_t member, ibl_capsule_stats* stats, int32_t n);
+
 /* Per-vertex state of a capsule of member 0: positions x(t) and x(t-dt),
  * velocity, and the total force of the last step (FP64, 3 per vertex, each
  * pointer may be NULL). */
@@ -252,9 +258,47 @@ typedef struct {
  * context, with the CUDA graphs of the segments, until ibl_destroy; a later
  * call with more checkpoints or longer segments reallocates it.
  * Outputs may be NULL; gradients are accumulated in FP64. */
-ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every,
-                       const ibl_objective* obj, double* J_out,
-                       double* grad_inlet_scale, double* grad_rj);
+ibl_status ibl_adjoint_flow(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every,
+                            const ibl_objective* obj, double* J_out,
+                            double* grad_inlet_scale, double* grad_rj);
+
+/* Discrete adjoint of n_steps coupled steps for a capsule objective: the
+ * gradient of J = dJ_dD_dOffset[0] * D + dJ_dD_dOffset[1] * offset, with D
+ * the Taylor deformation index of capsule 0 after the last step and offset
+ * its branch offset (the y coordinate of its volume centroid less that of the
+ * symmetry plane), with respect to
+ *   grad_Ca   - the capillary number of the capsule (k_s0 = rho nu u_ref / Ca,
+ *               u_ref held fixed; Section "Deforming bodies constitutive model"),
+ *   grad_umax - the peak inlet velocity, the velocity-face data being
+ *               proportional to it (dJ/ds / u_max for data scaled by (1 + s),
+ *               u_max the lattice descriptor's),
+ *   grad_rj   - the junction radius, through the link distances q and the dq
+ *               of the ibl_wall_link records (fluid/solid tags held fixed).
+ * The context must hold one FP32 lattice with exactly one soft capsule
+ * (IBL_ERR_STATE otherwise).  The reverse sweep differentiates every step as
+ * ibl_step computes it (Reading T1 order): the lattice (Eq. evoleq with the
+ * Guo term of the IB force, Eq. bbouzidi, Eq. extbound), the MLS
+ * interpolation and spreading (Eqs. uLag, l2norm, intKernel, bodyforce), the
+ * membrane, volume and probe forces (Eqs. strainFor .. hydroForNu) and the
+ * Verlet update (Eqs. verletPos .. verletPosC); the MLS nearest nodes,
+ * supports and singular fall-backs are held at their forward choice.  The
+ * call advances the context by n_steps exactly as ibl_step does.  The
+ * forward pass keeps, at the start of every ckpt_every-step segment but the
+ * last, a copy of the populations and of the vertex positions, previous
+ * positions and velocities; the reverse pass recomputes each earlier segment
+ * from its copy while recording its tape (per step: (rho, u) and the IB
+ * force of every node, d(value)/dq of every link, rho of every face node, the
+ * vertex positions and velocities), then runs its adjoint steps backwards.
+ * Device memory, allocated by the first call that needs it (cudaMalloc) and
+ * kept by the context until ibl_destroy (a later call with more checkpoints
+ * or longer segments reallocates it):
+ *   (ceil(n_steps / ckpt_every) - 1) * (populations + 72 B per vertex)
+ *   + ckpt_every * (32 B per node + 48 B per vertex + 4 B per link and face node)
+ *   + 2 * 19 * 4 B + 32 B per node + 104 B per vertex.
+ * Gradients are accumulated in FP64.  Outputs may be NULL.  Returns
+ * IBL_ERR_DAMAGED / IBL_ERR_NONFINITE as ibl_step does. */
+ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const double* dJ_dD_dOffset,
+                       double* grad_Ca, double* grad_umax, double* grad_rj);
 
 /* Allocation-free read of member `member`'s macroscopic fields into HOST
  * buffers rho[N] and u[3N] (either may be NULL, not both); same values and

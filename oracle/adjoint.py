@@ -192,3 +192,59 @@ def value(lat: Lattice, f0, steps, obj: Objective) -> float:
     for _ in range(steps):
         f = lat.step(f)
     return objective(lat, f, obj)
+
+
+# ---------------------------------------------------------------------------
+# The coupled step with capsules: derivative of a capsule objective
+# ---------------------------------------------------------------------------
+# Objective of the capsule adjoint: J = w_D D + w_off (y_c - y_sym) of capsule 0
+# after the last step, with D the Taylor deformation index and y_c the y
+# coordinate of the volume centroid (the branch offset from the symmetry plane
+# y_sym), both from membrane.diagnostics.  Parameters: the capillary number Ca
+# of capsule 0 (k_s0 = rho nu u_ref / Ca, u_ref held fixed), the peak inlet
+# velocity u_max (the inlet data scale as u_w (1 + s), dJ/du_max = dJ/ds /
+# u_max; u_ref and the repulsion coefficient are held fixed), and the
+# junction radius r_j (the link distances move as q + s dq with dq = dq/dr_j,
+# tags fixed).  The derivative of the whole discrete run comes from the
+# complex step: the forward oracle is run once per parameter with that
+# parameter perturbed by i h, every discrete decision taken on real parts,
+# and dJ/dp = Im J / h, exact to rounding for this smooth map.
+
+def capsule_objective(body, w_D, w_off, y_sym=0.0):
+    from . import membrane
+    d = membrane.diagnostics(body.x, body.tris)
+    return w_D * d["taylor_D"] + w_off * (d["centroid"][1] - y_sym)
+
+
+def coupled_run(case, steps, w_D=1.0, w_off=0.0, y_sym=0.0, dCa=0.0, ds_u=0.0, ds_q=0.0):
+    """J after `steps` coupled oracle steps of a case (geometry, tau, u_max,
+    capsules, with wall links carrying dq), with Ca of capsule 0 moved by dCa,
+    the inlet data scaled by (1 + ds_u) and the link distances moved by
+    ds_q * dq.  Any of the moves may be complex."""
+    from .lattice import Lattice
+    from .sim import Simulation
+    g = case["geometry"]
+    lat = Lattice(g.nx, g.ny, g.nz, case["tau"], g.tag, g.links, g.faces, g.periodic,
+                  body_force=case.get("body_force", (0.0, 0.0, 0.0)))
+    lat = perturbed(lat, s_u=ds_u, s_q=ds_q, dq=g.links["dq"])
+    cplx = any(np.iscomplexobj(np.asarray(v)) for v in (dCa, ds_u, ds_q))
+    o = Simulation(lat, u_max=case["u_max"])
+    if cplx:
+        o.f = o.f.astype(np.complex128)
+    for k, c in enumerate(case["capsules"]):
+        params = dict(c["params"])
+        if k == 0:
+            params["Ca"] = params["Ca"] + dCa
+        o.add_body(c["verts"], c["tris"], params, c.get("vel0"))
+    o.step(steps)
+    return capsule_objective(o.bodies[0], w_D, w_off, y_sym), o
+
+
+def coupled_gradient(case, steps, w_D=1.0, w_off=0.0, y_sym=0.0, h=1e-30):
+    """J and (dJ/dCa, dJ/du_max, dJ/dr_j) of `steps` coupled oracle steps by
+    the complex step (one complex run per parameter)."""
+    J, _ = coupled_run(case, steps, w_D, w_off, y_sym)
+    g_ca = np.imag(coupled_run(case, steps, w_D, w_off, y_sym, dCa=1j * h)[0]) / h
+    g_su = np.imag(coupled_run(case, steps, w_D, w_off, y_sym, ds_u=1j * h)[0]) / h
+    g_sq = np.imag(coupled_run(case, steps, w_D, w_off, y_sym, ds_q=1j * h)[0]) / h
+    return float(np.real(J)), float(g_ca), float(g_su / case["u_max"]), float(g_sq)

@@ -41,7 +41,15 @@ class Stencil:
 
 def weight_function(r):
     """Eq. intKernel: W = exp(-(r/alpha)^2) for r <= 1, else 0."""
-    return np.where(r <= 1.0, np.exp(-(r / ALPHA) ** 2), 0.0)
+    return weight_of_r2(np.asarray(r) ** 2)
+
+
+def weight_of_r2(r2):
+    """Eq. intKernel written on r^2: exp(-r^2/alpha^2) for r <= 1, else 0.
+    The support test looks at the real part only, so that a complex-step
+    perturbation of the point (derivative checks) leaves the support set
+    fixed and differentiates the weights."""
+    return np.where(np.real(r2) <= 1.0, np.exp(-r2 / ALPHA ** 2), 0.0)
 
 
 def leading_pivots(A):
@@ -61,10 +69,17 @@ def stencil(lat, X):
     U(X) = a_0 gives phi_k = W_k (A^{-1} p_k)_0 and the gradient weights are
     W_k (A^{-1} p_k)_{1..3}.  The support is the 3x3x3 block around the
     nearest node (round half up), r_k = |X - x^k| / 2.6 (Reading M2).  Solid
-    and out-of-domain nodes get W = 0 (Reading M4)."""
-    X = np.asarray(X, dtype=np.float64).reshape(-1, 3)
+    and out-of-domain nodes get W = 0 (Reading M4).
+
+    X may be complex (complex-step derivatives): every discrete decision (the
+    nearest node, the support, the singularity test, the fallback node) is
+    taken on the real part, so the shape functions are differentiated at a
+    fixed stencil."""
+    X = np.asarray(X).reshape(-1, 3)
+    if not np.iscomplexobj(X):
+        X = X.astype(np.float64)
     M = X.shape[0]
-    base = np.floor(X + 0.5).astype(np.int64)
+    base = np.floor(np.real(X) + 0.5).astype(np.int64)
     coords = base[:, None, :] + OFFSETS[None, :, :]          # (M,27,3) unwrapped
     pos = coords.astype(np.float64)
     dims = (lat.nx, lat.ny, lat.nz)
@@ -81,15 +96,15 @@ def stencil(lat, X):
     nodes = wrapped[0] + lat.nx * (wrapped[1] + lat.ny * wrapped[2])
     ok &= lat.fluid[nodes]
     rel = pos - X[:, None, :]
-    r = np.sqrt((rel * rel).sum(axis=2)) / SUPPORT_SIDE
-    Wk = np.where(ok, weight_function(r), 0.0)
+    r2 = (rel * rel).sum(axis=2) / SUPPORT_SIDE ** 2
+    Wk = np.where(ok, weight_of_r2(r2), 0.0)
     p = np.concatenate([np.ones((M, 27, 1)), rel], axis=2)    # (M,27,4)
     A = np.einsum("mk,mki,mkj->mij", Wk, p, p)
-    piv = leading_pivots(A)
-    a00 = A[:, 0, 0]
+    piv = np.real(leading_pivots(A))
+    a00 = np.real(A[:, 0, 0])
     good = (a00 > 0) & np.all(piv > PIVOT_TOL * np.where(a00 > 0, a00, 1.0)[:, None], axis=1)
-    phi = np.zeros((M, 27))
-    grad = np.zeros((M, 3, 27))
+    phi = np.zeros((M, 27), dtype=Wk.dtype)
+    grad = np.zeros((M, 3, 27), dtype=Wk.dtype)
     if good.any():
         Ainv = np.linalg.inv(A[good])
         coef = np.einsum("mij,mkj->mik", Ainv, p[good]) * Wk[good][:, None, :]   # (m,4,27)
@@ -98,8 +113,8 @@ def stencil(lat, X):
     bad = ~good
     if bad.any():
         # nearest fluid support node takes the whole marker (largest W)
-        has = Wk[bad].max(axis=1) > 0
-        kk = np.argmax(Wk[bad], axis=1)
+        has = np.real(Wk[bad]).max(axis=1) > 0
+        kk = np.argmax(np.real(Wk[bad]), axis=1)
         rows = np.nonzero(bad)[0]
         phi[rows[has], kk[has]] = 1.0
     return Stencil(nodes, phi, grad, Wk, bad)
@@ -128,7 +143,7 @@ def interpolate_velocity(f, st):
 def spread(N, st, F, c):
     """Eq. bodyforce: f_ib^k = sum_l c_l phi^l_k F_l, summed over every marker
     whose support holds node k; c_l = A_l (Reading M3).  Returns (N,3)."""
-    out = np.zeros((N, 3))
     contrib = (c[:, None] * st.phi)[:, :, None] * F[:, None, :]
+    out = np.zeros((N, 3), dtype=contrib.dtype)
     np.add.at(out, st.nodes.reshape(-1), contrib.reshape(-1, 3))
     return out

@@ -158,13 +158,13 @@ class Lattice:
 
     # -- the step -----------------------------------------------------------
     def force_field(self, f_ib):
-        F = np.zeros((self.N, 3)) if f_ib is None else np.array(f_ib, dtype=np.float64)
+        F = np.zeros((self.N, 3)) if f_ib is None else np.array(f_ib)
         return F + self.body_force[None, :]
 
     def collide_all(self, f, f_ib):
-        fstar = np.array(f, dtype=np.float64, copy=True)
-        fl = self.fluid
         F = self.force_field(f_ib)
+        fstar = np.array(f, dtype=np.result_type(f, F, np.float64), copy=True)
+        fl = self.fluid
         fstar[:, fl] = collide(f[:, fl], F[fl], self.tau)
         return fstar
 

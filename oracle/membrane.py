@@ -15,6 +15,31 @@ from . import ib
 from .lattice import viscosity
 
 
+# The functions below also run on complex arrays for complex-step derivative
+# checks, d g(x)/dx . v = Im g(x + i h v) / h: norms are written as the
+# analytic sqrt(sum x^2), and the angle and eigenvalue helpers carry the
+# first-order complex part; every discrete decision looks at real parts.
+def _norm(v, axis=-1):
+    return np.sqrt((v * v).sum(axis=axis))
+
+
+def _atan2(s, c):
+    """arctan2 with the complex-step derivative (c ds - s dc)/(s^2 + c^2)."""
+    if not (np.iscomplexobj(s) or np.iscomplexobj(c)):
+        return np.arctan2(s, c)
+    sr, cr = np.real(s), np.real(c)
+    return np.arctan2(sr, cr) + 1j * (cr * np.imag(s) - sr * np.imag(c)) / (sr * sr + cr * cr)
+
+
+def _eigvalsh(C):
+    """Ascending eigenvalues of a symmetric 3x3 matrix, with the first-order
+    complex part v_i^T Im(C) v_i of each (distinct) eigenvalue."""
+    if not np.iscomplexobj(C):
+        return np.linalg.eigvalsh(C)
+    w, V = np.linalg.eigh(np.real(C))
+    return w + 1j * np.einsum("ji,jk,ki->i", V, np.imag(C), V)
+
+
 class Topology:
     """Edges and hinges of a closed triangle mesh with outward CCW triangles.
 
@@ -51,13 +76,13 @@ def vertex_areas_normals(X, tris, nv):
     """Reading M1: A_v = (1/3) sum of the adjacent triangle areas; n_v = the
     normalised area-weighted sum of the adjacent triangle normals."""
     N = triangle_vectors(X, tris)
-    area = 0.5 * np.linalg.norm(N, axis=1)
-    Av = np.zeros(nv)
-    nv_acc = np.zeros((nv, 3))
+    area = 0.5 * _norm(N, axis=1)
+    Av = np.zeros(nv, dtype=N.dtype)
+    nv_acc = np.zeros((nv, 3), dtype=N.dtype)
     for j in range(3):
         np.add.at(Av, tris[:, j], area / 3.0)
         np.add.at(nv_acc, tris[:, j], 0.5 * N)
-    nrm = nv_acc / np.linalg.norm(nv_acc, axis=1)[:, None]
+    nrm = nv_acc / _norm(nv_acc, axis=1)[:, None]
     return Av, nrm
 
 
@@ -68,10 +93,10 @@ def dihedral_angles(X, hinge):
     nA = np.cross(v2 - v1, v3 - v1)
     nB = np.cross(v3 - v4, v2 - v4)
     e = v3 - v2
-    e_hat = e / np.linalg.norm(e, axis=1)[:, None]
+    e_hat = e / _norm(e, axis=1)[:, None]
     s = np.einsum("ij,ij->i", np.cross(nA, nB), e_hat)
     c = np.einsum("ij,ij->i", nA, nB)
-    return np.arctan2(s, c)
+    return _atan2(s, c)
 
 
 def dihedral_gradients(X, hinge):
@@ -82,7 +107,7 @@ def dihedral_gradients(X, hinge):
     nA = np.cross(v2 - v1, v3 - v1)
     nB = np.cross(v3 - v4, v2 - v4)
     e = v3 - v2
-    L = np.linalg.norm(e, axis=1)
+    L = _norm(e, axis=1)
     e_hat = e / L[:, None]
     a2 = np.einsum("ij,ij->i", nA, nA)
     b2 = np.einsum("ij,ij->i", nB, nB)
@@ -104,8 +129,8 @@ class CapsuleRest:
         self.topo = Topology(tris)
         X0 = np.asarray(X0, dtype=np.float64)
         t = self.topo
-        self.l0 = np.linalg.norm(X0[t.edge[:, 1]] - X0[t.edge[:, 0]], axis=1)
-        tri_area = 0.5 * np.linalg.norm(triangle_vectors(X0, t.tris), axis=1)
+        self.l0 = _norm(X0[t.edge[:, 1]] - X0[t.edge[:, 0]], axis=1)
+        tri_area = 0.5 * _norm(triangle_vectors(X0, t.tris), axis=1)
         self.theta0 = dihedral_angles(X0, t.hinge)
         d = diagnostics(X0, t.tris)
         self.V0 = d["volume"]
@@ -117,7 +142,7 @@ class CapsuleRest:
         Ca = params.get("Ca", 0.01)
         u_ref = params.get("u_ref", 0.02)
         # Ca = rho nu u_ref / k_s0  (Section "Deforming bodies constitutive model")
-        self.ks0 = rho_f * nu * u_ref / Ca if Ca > 0 else 0.0
+        self.ks0 = rho_f * nu * u_ref / Ca if np.real(Ca) > 0 else 0.0
         # Reading S-a: k_s,l = k_s0 T (A_a + A_b) / l0^2 with T = 1
         self.ks = self.ks0 * (tri_area[t.edge_tris[:, 0]] + tri_area[t.edge_tris[:, 1]]) / self.l0 ** 2
         # Eb = k_b / (k_s,l r^2)  ->  k_b = Eb k_s,l r^2 (per hinge = per edge)
@@ -131,7 +156,7 @@ class CapsuleRest:
 def stretch_energy(X, rest):
     """Eq. strainPot summed over edges."""
     e = rest.topo.edge
-    l = np.linalg.norm(X[e[:, 0]] - X[e[:, 1]], axis=1)
+    l = _norm(X[e[:, 0]] - X[e[:, 1]], axis=1)
     return 0.5 * np.sum(rest.ks * (l - rest.l0) ** 2)
 
 
@@ -139,9 +164,9 @@ def stretch_forces(X, rest):
     """Eq. strainFor: F_1 = -k_s,l (l - l0) r_12 / l, F_2 = -F_1, per edge."""
     e = rest.topo.edge
     r12 = X[e[:, 0]] - X[e[:, 1]]
-    l = np.linalg.norm(r12, axis=1)
+    l = _norm(r12, axis=1)
     F1 = -(rest.ks * (l - rest.l0) / l)[:, None] * r12
-    out = np.zeros_like(X)
+    out = np.zeros(X.shape, dtype=F1.dtype)
     np.add.at(out, e[:, 0], F1)
     np.add.at(out, e[:, 1], -F1)
     return out
@@ -161,7 +186,7 @@ def bending_forces(X, rest):
     th = dihedral_angles(X, h)
     g = dihedral_gradients(X, h)                  # (4,H,3)
     coef = -(rest.kb * np.sin(th - rest.theta0))   # (H,)
-    out = np.zeros_like(X)
+    out = np.zeros(X.shape, dtype=np.result_type(coef, g))
     for j in range(4):
         np.add.at(out, h[:, j], coef[:, None] * g[j])
     return out
@@ -199,10 +224,10 @@ def repulsion_forces(Xs, nrms, u_max, cutoff=2.0):
     """Eq. collision between markers of different bodies closer than the
     cutoff (Reading S-e): F_i = u_max dt/(8 sqrt 2) sqrt(dx / d^5) n^-_i, summed
     over the partners j, n^- the inward normal of marker i."""
-    out = [np.zeros_like(X) for X in Xs]
     c = u_max / (8.0 * math.sqrt(2.0))
-    lo = [X.min(axis=0) for X in Xs]
-    hi = [X.max(axis=0) for X in Xs]
+    out = [np.zeros(X.shape, dtype=np.result_type(X, c, nrms[k])) for k, X in enumerate(Xs)]
+    lo = [np.real(X).min(axis=0) for X in Xs]
+    hi = [np.real(X).max(axis=0) for X in Xs]
     for a in range(len(Xs)):
         for b in range(len(Xs)):
             if a == b:
@@ -211,9 +236,10 @@ def repulsion_forces(Xs, nrms, u_max, cutoff=2.0):
             # have no marker pair within it
             if np.any(lo[a] - hi[b] >= cutoff) or np.any(lo[b] - hi[a] >= cutoff):
                 continue
-            d = np.linalg.norm(Xs[a][:, None, :] - Xs[b][None, :, :], axis=2)
-            with np.errstate(divide="ignore"):
-                w = np.where(d < cutoff, c * np.sqrt(1.0 / d ** 5), 0.0)
+            d = _norm(Xs[a][:, None, :] - Xs[b][None, :, :], axis=2)
+            near = np.real(d) < cutoff
+            w = np.zeros(d.shape, dtype=np.result_type(d, c))
+            w[near] = c * np.sqrt(1.0 / d[near] ** 5)
             out[a] += -w.sum(axis=1)[:, None] * nrms[a]
     return out
 
@@ -224,26 +250,28 @@ def diagnostics(X, tris):
     second-moment tensor about the centroid and the Taylor deformation index
     D = (a_max - a_min)/(a_max + a_min) of the equivalent ellipsoid
     (a_i = sqrt(5 lambda_i / V)); Reading R."""
-    X = np.asarray(X, dtype=np.float64)
+    X = np.asarray(X)
     tris = np.asarray(tris, dtype=np.int64)
     o = X.mean(axis=0)
     a, b, c = X[tris[:, 0]] - o, X[tris[:, 1]] - o, X[tris[:, 2]] - o
     v = np.einsum("ij,ij->i", a, np.cross(b, c)) / 6.0
     V = v.sum()
-    S = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1).sum()
+    S = 0.5 * _norm(np.cross(b - a, c - a), axis=1).sum()
     s = a + b + c
     cen_rel = (v[:, None] * s / 4.0).sum(axis=0) / V
     M2 = np.einsum("t,tij->ij", v / 20.0,
                    np.einsum("ti,tj->tij", a, a) + np.einsum("ti,tj->tij", b, b)
                    + np.einsum("ti,tj->tij", c, c) + np.einsum("ti,tj->tij", s, s))
     C = M2 - V * np.outer(cen_rel, cen_rel)
-    lam = np.linalg.eigvalsh(C)
-    ax = np.sqrt(np.maximum(5.0 * lam / V, 0.0))
-    D = (ax.max() - ax.min()) / (ax.max() + ax.min())
+    lam = _eigvalsh(C)
+    q = 5.0 * lam / V
+    ax = np.sqrt(np.where(np.real(q) > 0.0, q, 0.0))
+    hi, lo = ax[np.argmax(np.real(ax))], ax[np.argmin(np.real(ax))]
+    D = (hi - lo) / (hi + lo)
     return dict(volume=V, area=S, centroid=o + cen_rel, second_moment=C, semi_axes=ax, taylor_D=D)
 
 
 def max_stretch(X, rest):
     e = rest.topo.edge
-    l = np.linalg.norm(X[e[:, 0]] - X[e[:, 1]], axis=1)
-    return float(np.max(l / rest.l0))
+    l = _norm(X[e[:, 0]] - X[e[:, 1]], axis=1)
+    return float(np.max(np.real(l / rest.l0)))

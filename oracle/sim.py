@@ -100,7 +100,7 @@ class Simulation:
             U = ib.interpolate_velocity(self.f, st)
             Fl = b.boundary_velocity() - U          # (U_b - U)/dt
             Av, nrm = membrane.vertex_areas_normals(b.x, b.tris, b.x.shape[0])
-            f_ib += ib.spread(lat.N, st, Fl, Av)
+            f_ib = f_ib + ib.spread(lat.N, st, Fl, Av)
             per.append(dict(stencil=st, U=U, F=Fl, Av=Av, nrm=nrm))
         return f_ib, per
 

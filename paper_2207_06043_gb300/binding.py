@@ -81,6 +81,7 @@ def lib():
         "ibl_read_populations": ([vp, vp, i32], i32),
         "ibl_read_capsule": ([vp, i32, P(CapsuleStats), vp], i32),
         "ibl_read_capsule_state": ([vp, i32, vp, vp, vp, vp], i32),
+        "ibl_read_capsules": ([vp, i32, vp, i32], i32),
         "ibl_ensemble_create": ([vp, i32, vp, P(vp)], i32),
         "ibl_num_members": ([vp], i32),
         "ibl_member_read_fields": ([vp, i32, vp, vp, i32], i32),
@@ -93,7 +94,8 @@ def lib():
         "ibl_kernels_per_step": ([vp, P(i32)], i32),
         "ibl_save_state": ([vp, vp, P(sz)], i32),
         "ibl_autotune": ([vp, i32, P(i32), P(i32), P(dbl)], i32),
-        "ibl_adjoint": ([vp, i32, i32, P(Objective), P(dbl), P(dbl), P(dbl)], i32),
+        "ibl_adjoint_flow": ([vp, i32, i32, P(Objective), P(dbl), P(dbl), P(dbl)], i32),
+        "ibl_adjoint": ([vp, i32, i32, P(dbl), P(dbl), P(dbl), P(dbl)], i32),
         "ibl_load_state": ([vp, vp, sz], i32),
         "ibl_kernel_times": ([vp, vp], i32),
         "ibl_last_error": ([vp], C.c_char_p),
@@ -254,16 +256,26 @@ class Solver:
         self._check(self._L.ibl_autotune(self._h, int(steps), C.byref(t), C.byref(b), C.byref(ms)))
         return int(t.value), int(b.value), float(ms.value)
 
-    def adjoint(self, steps, lo, hi, d, ckpt_every=100):
-        """Discrete adjoint of `steps` steps (the context advances by them):
-        J = sum over the fluid nodes of the box [lo, hi) of d . u at the last
-        step, dJ/ds for inlet velocities scaled by (1 + s), and sum_links
-        dJ/dq dq.  Returns (J, dJ/ds, dJ/dr)."""
+    def adjoint_flow(self, steps, lo, hi, d, ckpt_every=100):
+        """Discrete adjoint of `steps` lattice steps without capsules (the
+        context advances by them): J = sum over the fluid nodes of the box
+        [lo, hi) of d . u at the last step, dJ/ds for inlet velocities scaled
+        by (1 + s), and sum_links dJ/dq dq.  Returns (J, dJ/ds, dJ/dr)."""
         ob = Objective((C.c_int32 * 3)(*lo), (C.c_int32 * 3)(*hi), (C.c_double * 3)(*d))
         J, gs, gr = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
-        self._check(self._L.ibl_adjoint(self._h, int(steps), int(ckpt_every), C.byref(ob), C.byref(J),
-                                        C.byref(gs), C.byref(gr)))
+        self._check(self._L.ibl_adjoint_flow(self._h, int(steps), int(ckpt_every), C.byref(ob), C.byref(J),
+                                             C.byref(gs), C.byref(gr)))
         return float(J.value), float(gs.value), float(gr.value)
+
+    def adjoint(self, steps, dJ_dD_dOffset=(1.0, 0.0), ckpt_every=100):
+        """Discrete adjoint of `steps` coupled steps for J = w_D D + w_off
+        offset of capsule 0 after the last step (the context advances by
+        them).  Returns (dJ/dCa, dJ/du_max, dJ/dr_j)."""
+        w = (C.c_double * 2)(float(dJ_dD_dOffset[0]), float(dJ_dD_dOffset[1]))
+        gc, gu, gr = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+        self._check(self._L.ibl_adjoint(self._h, int(steps), int(ckpt_every), w, C.byref(gc), C.byref(gu),
+                                        C.byref(gr)))
+        return float(gc.value), float(gu.value), float(gr.value)
 
     def save_state(self):
         """Snapshot of the dynamic state (bytes)."""
@@ -339,6 +351,15 @@ class Solver:
             d["verts"] = verts.reshape(-1, 3)
         return d
 
+    def read_capsules(self, n, member=0):
+        """FP64 diagnostics of the member's n capsules, computed on the device
+        (one small read): a list of dicts as read_capsule returns."""
+        arr = (CapsuleStats * n)()
+        self._check(self._L.ibl_read_capsules(self._h, int(member), C.cast(arr, C.c_void_p), int(n)))
+        return [dict(centroid=np.array(st.centroid[:]), volume=st.volume, area=st.area, dS=st.dS,
+                     taylor_D=st.taylor_D, max_stretch=st.max_stretch, semi_axes=np.array(st.semi_axes[:]),
+                     velocity=np.array(st.velocity[:]), damaged=bool(st.damaged)) for st in arr]
+
     def _capsule_nv(self, cid, member):
         return self._nv[(member or 0, cid)]
 
@@ -371,3 +392,38 @@ def ensemble(solvers, stream=None):
         for (mm, cid), nv in getattr(s, "_nv", {}).items():
             e._nv[(m, cid)] = nv
     return e
+
+
+def capsule_objective_function():
+    """torch.autograd.Function of the capsule objective: forward(params,
+    build, steps, y_sym, ckpt_every) with params = tensor([Ca, u_max, r_j])
+    builds a context with build(Ca, u_max, r_j) (a Solver holding one soft
+    capsule, set up but not stepped), steps it and returns tensor([D, offset])
+    of capsule 0 (offset = y of the volume centroid - y_sym); backward runs the
+    library's discrete adjoint (ibl_adjoint) from the saved initial state with
+    the incoming gradient as (dJ/dD, dJ/d offset) and returns dJ/d params.
+    The derivative with respect to r_j goes through the dq of the wall links
+    that build() supplies."""
+    import torch
+
+    class CapsuleObjective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params, build, steps, y_sym=0.0, ckpt_every=100):
+            Ca, u_max, r_j = (float(v) for v in params.detach().cpu().tolist())
+            s = build(Ca, u_max, r_j)
+            s.step(0)
+            state = s.save_state()
+            s.step(int(steps))
+            st = s.read_capsule(0)
+            ctx.solver, ctx.state, ctx.steps, ctx.ckpt = s, state, int(steps), int(ckpt_every)
+            return torch.tensor([st["taylor_D"], st["centroid"][1] - y_sym], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            s = ctx.solver
+            s.load_state(ctx.state)
+            g = grad_out.detach().cpu().to(torch.float64).tolist()
+            gc, gu, gr = s.adjoint(ctx.steps, (g[0], g[1]), ckpt_every=ctx.ckpt)
+            return torch.tensor([gc, gu, gr], dtype=torch.float64), None, None, None, None
+
+    return CapsuleObjective

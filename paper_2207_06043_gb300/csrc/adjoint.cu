@@ -214,11 +214,17 @@ __global__ void __launch_bounds__(256) k_adj_links(const MemberDev* __restrict__
 // once they are consumed.  Work list: the aligned 32-node runs that hold a
 // fluid node, one warp per run; interior runs address neighbours by constant
 // offsets, border runs (periodic wrap planes) by coordinates.
+// With capsules, F = F_body + f_ib(n) varies per node: the IB part comes from
+// a tape (w = 1 where the node received spreading), and at those nodes the
+// kernel also returns lambda_F = d f* / d F . lambda*: u depends on F through
+// rho u = sum f e + F/2, and the Guo term directly, so
+//   lambda_F = B / (2 rho) + guo sum_j lambda*_j w_j [3 (e_j - u) + 9 (e_j.u) e_j].
 template <bool BORDER>
 __global__ void __launch_bounds__(256) k_adj_step(const __grid_constant__ MemberDev d, const uint8_t* __restrict__ tag,
                                                   const uint32_t* __restrict__ segs, int n_segs,
                                                   const float4* __restrict__ tape, const float* __restrict__ lam_in,
-                                                  float* __restrict__ lam_out, size_t LS) {
+                                                  float* __restrict__ lam_out, size_t LS,
+                                                  const float4* __restrict__ tape_F, float4* __restrict__ lam_fib) {
     const int si = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (si >= n_segs) return;
     const int n = (int)(segs[si] << 5) + (int)(threadIdx.x & 31);
@@ -237,7 +243,13 @@ __global__ void __launch_bounds__(256) k_adj_step(const __grid_constant__ Member
     }
     const float4 t = tape[n];
     const float rho = t.x, ux = t.y, uy = t.z, uz = t.w;
-    const float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
+    float Fx = d.F[0], Fy = d.F[1], Fz = d.F[2];
+    bool ibn = false;
+    if (tape_F) {
+        const float4 fi = tape_F[n];
+        ibn = fi.w != 0.f;
+        Fx += fi.x; Fy += fi.y; Fz += fi.z;
+    }
     const float om = d.omega, guo = d.guo;
     const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float orho = om * rho;
@@ -248,7 +260,7 @@ __global__ void __launch_bounds__(256) k_adj_step(const __grid_constant__ Member
     // 9 (om rho e.u + guo e.F) sw] to B (beyond -(3 om rho u + 3 guo F)
     // times the same sum).
     float W = wgt(0) * ls[0];
-    float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f;
+    float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f, Cx = 0.f, Cy = 0.f, Cz = 0.f;
 #pragma unroll
     for (int k = 1; k < Q; ++k) {
         if (opp(k) < k) continue;
@@ -262,12 +274,24 @@ __global__ void __launch_bounds__(256) k_adj_step(const __grid_constant__ Member
         if (ex(k)) Bx += ex(k) * c;
         if (ey(k)) By += ey(k) * c;
         if (ez(k)) Bz += ez(k) * c;
+        if (ibn) {
+            // sum_j lambda*_j w_j [3 e_j + 9 (e_j.u) e_j] by pairs
+            const float cc = 3.f * dw + 9.f * eu * sw;
+            if (ex(k)) Cx += ex(k) * cc;
+            if (ey(k)) Cy += ey(k) * cc;
+            if (ez(k)) Cz += ez(k) * cc;
+        }
     }
     A += W * (1.f - usq);
     Bx -= W * (3.f * orho * ux + 3.f * guo * Fx);
     By -= W * (3.f * orho * uy + 3.f * guo * Fy);
     Bz -= W * (3.f * orho * uz + 3.f * guo * Fz);
     const float ir = 1.f / rho;
+    if (ibn) {
+        const float h = 0.5f * ir;
+        lam_fib[n] = make_float4(Bx * h + guo * (Cx - 3.f * ux * W), By * h + guo * (Cy - 3.f * uy * W),
+                                 Bz * h + guo * (Cz - 3.f * uz * W), 0.f);
+    }
     const float Bu = Bx * ux + By * uy + Bz * uz;
     const float base = om * A - Bu * ir, keep = 1.f - om;
     lam_out[n] = keep * ls[0] + base;
@@ -321,7 +345,7 @@ cudaError_t launch_adj_objective(const DevState& d, int parity, const int lo[3],
 
 cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const float* tape_dvdq, const float4* tape_rhou,
                             float* lam_in, float* lam_out, size_t LS, double* grad_s, double* grad_q,
-                            cudaStream_t s) {
+                            cudaStream_t s, const float4* tape_F, float4* lam_fib) {
     if (d.n_face_nodes > 0)
         k_adj_faces<<<(d.n_face_nodes + 255) / 256, 256, 0, s>>>(d.mem, d.fc_node, d.fc_meta, d.face_vel, tape_rho,
                                                                  lam_in, LS, d.n_face_nodes, grad_s);
@@ -330,10 +354,11 @@ cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const floa
                                                             lam_in, LS, d.n_links, grad_q);
     const MemberDev& md = d.h_mem[0];
     if (d.n_segs > 0)
-        k_adj_step<false><<<(d.n_segs + 7) / 8, 256, 0, s>>>(md, d.tag, d.segs, d.n_segs, tape_rhou, lam_in, lam_out, LS);
+        k_adj_step<false><<<(d.n_segs + 7) / 8, 256, 0, s>>>(md, d.tag, d.segs, d.n_segs, tape_rhou, lam_in, lam_out, LS,
+                                                             tape_F, lam_fib);
     if (d.n_bsegs > 0)
         k_adj_step<true><<<(d.n_bsegs + 7) / 8, 256, 0, s>>>(md, d.tag, d.bsegs, d.n_bsegs, tape_rhou, lam_in, lam_out,
-                                                             LS);
+                                                             LS, tape_F, lam_fib);
     if (d.n_links > 0)
         k_adj_clear<<<(d.n_links + 255) / 256, 256, 0, s>>>(md, d.tag, d.l_node, d.l_meta, lam_in, LS, d.n_links);
     return cudaGetLastError();

@@ -80,6 +80,8 @@ struct ibl_ctx {
     float* noalloc = nullptr;          // that device's copy of the static read array
     float* stage = nullptr;            // device staging buffer of host reads, kept and grown
     size_t stage_bytes = 0;
+    double* cap_stats = nullptr;       // CAP_STAT_DOUBLES per capsule (ibl_read_capsules)
+    std::vector<double> h_cap_stats;
     bool timing = false;
     std::vector<cudaEvent_t> tev;
     double ktime[4] = {0, 0, 0, 0};
@@ -87,13 +89,18 @@ struct ibl_ctx {
     std::vector<uint32_t> h_status;
     std::string err;
     // adjoint work buffers and segment graphs, kept between ibl_adjoint calls
-    struct AdjSeg { int mode, parity, len; float* lin; cudaGraphExec_t exec; };
+    struct AdjSeg { int kind, mode, parity, len; float* lin; cudaGraphExec_t exec; };
     struct AdjCache {
+        int kind = -1;   // 0: flow objective (lattice only), 1: capsule objective
         size_t ck_bytes = 0, tape_steps = 0;
         char *ck = nullptr, *snap = nullptr;
         float4* tape_rhou = nullptr;
         float *tape_dvdq = nullptr, *tape_rho = nullptr, *lamA = nullptr, *lamB = nullptr;
         double* acc = nullptr;
+        // capsule objective: IB-force and vertex tapes, per-vertex adjoints
+        float4* tape_F = nullptr;
+        double *tape_x = nullptr, *tape_v = nullptr;
+        AdjCapPtrs cp;
         std::vector<AdjSeg> graphs;
     } adj;
 };
@@ -263,6 +270,108 @@ void sym3_eigen(const double M[6], double ev[3]) {
     std::sort(ev, ev + 3);
 }
 
+// Unit eigenvector of a symmetric 3x3 matrix (xx yy zz xy xz yz) for a simple
+// eigenvalue ev: the longest cross product of two rows of M - ev I.
+V3 sym3_vector(const double M[6], double ev) {
+    const V3 r0 = {M[0] - ev, M[3], M[4]}, r1 = {M[3], M[1] - ev, M[5]}, r2 = {M[4], M[5], M[2] - ev};
+    const V3 c[3] = {vcross(r0, r1), vcross(r0, r2), vcross(r1, r2)};
+    int best = 0;
+    for (int i = 1; i < 3; ++i)
+        if (vdot(c[i], c[i]) > vdot(c[best], c[best])) best = i;
+    const double n = vnorm(c[best]);
+    return {c[best].x / n, c[best].y / n, c[best].z / n};
+}
+
+// Objective of the capsule adjoint, J = wD D + wOff y_c (D the Taylor index,
+// y_c the y of the volume centroid, as ibl_read_capsule computes them from
+// the tetrahedra fanned from the vertex mean o), and dJ/dx in g[3 nv], by
+// reverse mode through the same sums: per triangle (a, b, c relative to o)
+// v = a.(b x c)/6, q = a + b + c, V += v, S1 += v q/4,
+// M2 += v/20 (a a^T + b b^T + c c^T + q q^T); C = M2 - S1 S1^T / V;
+// D from the extreme eigenvalues l of C through a = sqrt(5 l / V), whose
+// derivatives are v v^T (simple eigenvalues).
+double capsule_objective_grad(const double* X, int nv, const int* tris, int nt, double wD, double wOff, double* g) {
+    const MeshSums ms = mesh_sums(X, nv, tris, nt);
+    V3 o = {0, 0, 0};
+    for (int v = 0; v < nv; ++v) { o.x += X[3 * v]; o.y += X[3 * v + 1]; o.z += X[3 * v + 2]; }
+    o.x /= nv; o.y /= nv; o.z /= nv;
+    const double V = ms.V;
+    const double S1[3] = {(ms.cen.x - o.x) * V, (ms.cen.y - o.y) * V, (ms.cen.z - o.z) * V};
+    double ev[3];
+    sym3_eigen(ms.M2, ev);
+    const double a0 = std::sqrt(std::max(5.0 * ev[0] / V, 0.0)), a2 = std::sqrt(std::max(5.0 * ev[2] / V, 0.0));
+    const double D = (a2 - a0) / (a2 + a0);
+    const double J = wD * D + wOff * ms.cen.y;
+    // adjoints of the extreme eigenvalues, then of C (symmetric, full)
+    const double s2 = (a2 + a0) * (a2 + a0);
+    const double dDa2 = 2.0 * a0 / s2, dDa0 = -2.0 * a2 / s2;
+    const double lev2 = wD * dDa2 * a2 / (2.0 * ev[2]), lev0 = wD * dDa0 * a0 / (2.0 * ev[0]);
+    double lV = wD * (dDa2 * (-a2 / (2.0 * V)) + dDa0 * (-a0 / (2.0 * V)));
+    const V3 e2 = sym3_vector(ms.M2, ev[2]), e0 = sym3_vector(ms.M2, ev[0]);
+    const double E2[3] = {e2.x, e2.y, e2.z}, E0[3] = {e0.x, e0.y, e0.z};
+    double lC[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) lC[i][j] = lev2 * E2[i] * E2[j] + lev0 * E0[i] * E0[j];
+    // C = M2 - S1 S1^T / V; y_c = o_y + S1_y / V
+    double lS1[3];
+    for (int i = 0; i < 3; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < 3; ++j) t += lC[i][j] * S1[j];
+        lS1[i] = -2.0 * t / V;
+    }
+    double sCs = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) sCs += S1[i] * lC[i][j] * S1[j];
+    lV += sCs / (V * V);
+    lS1[1] += wOff / V;
+    lV += -wOff * S1[1] / (V * V);
+    double lo[3] = {0.0, wOff, 0.0};
+    for (int i = 0; i < 3 * nv; ++i) g[i] = 0.0;
+    auto quad = [&](const double u[3], double w) {   // w lC u + w lC^T u
+        V3 r;
+        r.x = 2.0 * w * (lC[0][0] * u[0] + lC[0][1] * u[1] + lC[0][2] * u[2]);
+        r.y = 2.0 * w * (lC[1][0] * u[0] + lC[1][1] * u[1] + lC[1][2] * u[2]);
+        r.z = 2.0 * w * (lC[2][0] * u[0] + lC[2][1] * u[1] + lC[2][2] * u[2]);
+        return r;
+    };
+    auto uqu = [&](const double u[3]) {
+        double t = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) t += u[i] * lC[i][j] * u[j];
+        return t;
+    };
+    for (int t = 0; t < nt; ++t) {
+        const int* T = tris + 3 * t;
+        const double a[3] = {X[3 * T[0]] - o.x, X[3 * T[0] + 1] - o.y, X[3 * T[0] + 2] - o.z};
+        const double b[3] = {X[3 * T[1]] - o.x, X[3 * T[1] + 1] - o.y, X[3 * T[1] + 2] - o.z};
+        const double c[3] = {X[3 * T[2]] - o.x, X[3 * T[2] + 1] - o.y, X[3 * T[2] + 2] - o.z};
+        const double q[3] = {a[0] + b[0] + c[0], a[1] + b[1] + c[1], a[2] + b[2] + c[2]};
+        const V3 A = {a[0], a[1], a[2]}, B = {b[0], b[1], b[2]}, Cc = {c[0], c[1], c[2]};
+        const double v = vdot(A, vcross(B, Cc)) / 6.0;
+        const double lv = lV + (lS1[0] * q[0] + lS1[1] * q[1] + lS1[2] * q[2]) / 4.0 +
+                          (uqu(a) + uqu(b) + uqu(c) + uqu(q)) / 20.0;
+        const V3 lq = quad(q, v / 20.0);
+        const double lq3[3] = {v * lS1[0] / 4.0 + lq.x, v * lS1[1] / 4.0 + lq.y, v * lS1[2] / 4.0 + lq.z};
+        const V3 ga = quad(a, v / 20.0), gb = quad(b, v / 20.0), gc = quad(c, v / 20.0);
+        const V3 bc = vcross(B, Cc), ca = vcross(Cc, A), ab = vcross(A, B);
+        const double la[3] = {lq3[0] + ga.x + lv * bc.x / 6.0, lq3[1] + ga.y + lv * bc.y / 6.0,
+                              lq3[2] + ga.z + lv * bc.z / 6.0};
+        const double lb[3] = {lq3[0] + gb.x + lv * ca.x / 6.0, lq3[1] + gb.y + lv * ca.y / 6.0,
+                              lq3[2] + gb.z + lv * ca.z / 6.0};
+        const double lc[3] = {lq3[0] + gc.x + lv * ab.x / 6.0, lq3[1] + gc.y + lv * ab.y / 6.0,
+                              lq3[2] + gc.z + lv * ab.z / 6.0};
+        for (int k = 0; k < 3; ++k) {
+            g[3 * T[0] + k] += la[k];
+            g[3 * T[1] + k] += lb[k];
+            g[3 * T[2] + k] += lc[k];
+            lo[k] -= la[k] + lb[k] + lc[k];
+        }
+    }
+    for (int v = 0; v < nv; ++v)
+        for (int k = 0; k < 3; ++k) g[3 * v + k] += lo[k] / nv;
+    return J;
+}
+
 ibl_status enter(ibl_ctx* ctx) {
     CK(cudaEventRecord(ctx->ev_in, ctx->user_stream));
     CK(cudaStreamWaitEvent(ctx->work, ctx->ev_in, 0));
@@ -298,7 +407,10 @@ void free_adjoint(ibl_ctx* ctx) {
     auto& A = ctx->adj;
     for (auto& g : A.graphs) cudaGraphExecDestroy(g.exec);
     A.graphs.clear();
-    void* ptrs[] = {A.ck, A.snap, A.tape_rhou, A.tape_dvdq, A.tape_rho, A.lamA, A.lamB, A.acc};
+    void* ptrs[] = {A.ck,   A.snap,  A.tape_rhou, A.tape_dvdq, A.tape_rho, A.lamA,   A.lamB,
+                    A.acc,  A.tape_F, A.tape_x,  A.tape_v,   A.cp.lx,    A.cp.lxp, A.cp.lv,
+                    A.cp.lU, A.cp.lF, A.cp.ln,   A.cp.lA,    A.cp.snorm, A.cp.lV,  A.cp.lfib,
+                    A.cp.lmac};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     A = ibl_ctx::AdjCache{};
@@ -726,6 +838,7 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(upload(ctx, D.kb, kb_all));
         CKS(upload(ctx, D.e_cap, e_cap));
         CK(launch_mirror(D, ctx->work));   // derived from x
+        CKS(dev_alloc(ctx, ctx->cap_stats, CAP_STAT_DOUBLES * caps.size()));
         if (any_cells) {
             D.n_cells = cell_off;
             CKS(dev_alloc(ctx, D.cell_count, (size_t)cell_off));
@@ -760,6 +873,20 @@ ibl_status finalize(ibl_ctx* ctx) {
 
 enum { TK_LBM = 0, TK_BFL = 1, TK_IB = 2, TK_STRUCT = 3 };
 
+// What the discrete adjoint needs from one forward step, written while the
+// step runs: (rho, u) and the IB force of every fluid node before the
+// collision, d(value)/dq of every wall link, rho of every face node, and the
+// vertex positions and velocities at the start of the step.  Any pointer may
+// be null.
+struct StepTape {
+    float4* rhou = nullptr;
+    float4* F = nullptr;
+    float* dvdq = nullptr;
+    float* rho = nullptr;
+    double* x = nullptr;
+    double* v = nullptr;
+};
+
 struct Mark {
     int kind;
     cudaEvent_t a, b;
@@ -773,9 +900,13 @@ struct Mark {
 // forces (beside the IB pass); after the markers and the probes, the
 // structure update (beside the lattice step).  The update touches no lattice
 // data and the lattice step no structure data.
-ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks) {
+ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks, const StepTape* tp = nullptr) {
     DevState& D = ctx->dev;
     cudaStream_t s = ctx->work, s2 = ctx->work2, s3 = ctx->work3;
+    if (tp && tp->x && D.n_verts > 0) {
+        CK(cudaMemcpyAsync(tp->x, D.x, sizeof(double) * 3 * (size_t)D.n_verts, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(tp->v, D.vel, sizeof(double) * 3 * (size_t)D.n_verts, cudaMemcpyDeviceToDevice, s));
+    }
     cudaEvent_t e0 = nullptr;
     auto begin = [&](cudaStream_t st) -> ibl_status {
         if (!marks) return IBL_OK;
@@ -825,11 +956,11 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks) {
         CK(launch_update(D, s2));
     }
     CKS(begin(s));
-    CK(launch_lbm(D, parity, s));
+    CK(launch_lbm(D, parity, s, tp ? tp->rhou : nullptr, tp ? tp->F : nullptr));
     CKS(end(TK_LBM, s));
     CKS(begin(s));
-    CK(launch_bfl(D, parity, s));
-    CK(launch_faces(D, parity, s));
+    CK(launch_bfl(D, parity, s, tp ? tp->dvdq : nullptr));
+    CK(launch_faces(D, parity, s, tp ? tp->rho : nullptr));
     CKS(end(TK_BFL, s));
     if (caps && !marks) {
         CK(cudaEventRecord(ctx->ev_join, s2));
@@ -1189,6 +1320,49 @@ ibl_status ibl_read_capsule(ibl_ctx* ctx, int32_t id, ibl_capsule_stats* stats, 
     return read_capsule_member(ctx, 0, id, stats, verts_out);
 }
 
+ibl_status ibl_read_capsules(ibl_ctx* ctx, int32_t member, ibl_capsule_stats* stats, int32_t n) {
+    if (!ctx || !stats) return fail(ctx, IBL_ERR_ARG, "null argument");
+    if (member < 0 || member >= (int)ctx->members.size()) return fail(ctx, IBL_ERR_ARG, "member out of range");
+    CKS(finalize(ctx));
+    const std::vector<int>& ids = ctx->member_caps[member];
+    if (n != (int32_t)ids.size())
+        return fail(ctx, IBL_ERR_ARG, "member " + std::to_string(member) + " holds " + std::to_string(ids.size()) +
+                                          " capsules");
+    if (n == 0) return IBL_OK;
+    const int c0 = ids[0];
+    CKS(enter(ctx));
+    CK(launch_capsule_stats(ctx->dev, c0, n, ctx->cap_stats, ctx->work));
+    ctx->h_cap_stats.resize((size_t)CAP_STAT_DOUBLES * n);
+    CK(cudaMemcpyAsync(ctx->h_cap_stats.data(), ctx->cap_stats + (size_t)c0 * CAP_STAT_DOUBLES,
+                       sizeof(double) * CAP_STAT_DOUBLES * n, cudaMemcpyDeviceToHost, ctx->work));
+    CK(cudaStreamSynchronize(ctx->work));
+    CKS(leave(ctx));
+    const bool damaged = (ctx->h_status[member] & ST_DAMAGED) != 0;
+    for (int i = 0; i < n; ++i) {
+        const double* o = ctx->h_cap_stats.data() + (size_t)CAP_STAT_DOUBLES * i;
+        const CapsuleRestHost& R = ctx->rest[c0 + i];
+        ibl_capsule_stats* st = stats + i;
+        std::memset(st, 0, sizeof(*st));
+        const double V = o[0];
+        const double cr[3] = {o[2] / V, o[3] / V, o[4] / V};
+        for (int a = 0; a < 3; ++a) st->centroid[a] = o[15 + a] + cr[a];
+        st->volume = V;
+        st->area = o[1];
+        st->dS = (o[1] - R.S0) / R.S0;
+        // second moments about the centroid
+        const double M[6] = {o[5] - V * cr[0] * cr[0], o[6] - V * cr[1] * cr[1], o[7] - V * cr[2] * cr[2],
+                             o[8] - V * cr[0] * cr[1], o[9] - V * cr[0] * cr[2], o[10] - V * cr[1] * cr[2]};
+        double ev[3];
+        sym3_eigen(M, ev);
+        for (int a = 0; a < 3; ++a) st->semi_axes[a] = std::sqrt(std::max(5.0 * ev[a] / V, 0.0));
+        st->taylor_D = (st->semi_axes[2] - st->semi_axes[0]) / (st->semi_axes[2] + st->semi_axes[0]);
+        st->max_stretch = R.rigid ? 1.0 : o[14];
+        for (int a = 0; a < 3; ++a) st->velocity[a] = o[11 + a] / R.nv;
+        st->damaged = damaged ? 1 : 0;
+    }
+    return IBL_OK;
+}
+
 ibl_status ibl_read_capsule_state(ibl_ctx* ctx, int32_t id, double* x, double* x_prev, double* vel, double* force) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
     CKS(finalize(ctx));
@@ -1284,14 +1458,15 @@ ibl_status ibl_load_state(ibl_ctx* ctx, const void* buf, size_t bytes) {
     return IBL_OK;
 }
 
-ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const ibl_objective* obj,
-                       double* J_out, double* grad_inlet_scale, double* grad_rj) {
+ibl_status ibl_adjoint_flow(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const ibl_objective* obj,
+                            double* J_out, double* grad_inlet_scale, double* grad_rj) {
     if (!ctx || !obj) return fail(ctx, IBL_ERR_ARG, "null argument");
     if (n_steps < 1 || ckpt_every < 1) return fail(ctx, IBL_ERR_ARG, "n_steps and ckpt_every must be >= 1");
     CKS(finalize(ctx));
     DevState& D = ctx->dev;
     if (D.n_members != 1 || D.n_caps != 0 || ctx->storage != IBL_STORAGE_F32)
-        return fail(ctx, IBL_ERR_STATE, "the adjoint covers one FP32 lattice without capsules");
+        return fail(ctx, IBL_ERR_STATE, "the flow adjoint covers one FP32 lattice without capsules (ibl_adjoint "
+                                        "differentiates a capsule objective)");
     const MemberDev& md = ctx->hmem[0];
     const size_t N = (size_t)md.N, LS = N;
     const int K = std::min(ckpt_every, n_steps);
@@ -1303,9 +1478,10 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
     // checkpoints or a longer segment) and kept in the context
     auto& AC = ctx->adj;
     const size_t ck_need = (size_t)(n_ck - 1) * D.f_bytes;   // no copy when one segment covers the steps
-    if (AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc) {
+    if (AC.kind != 0 || AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc) {
         cudaStreamSynchronize(ctx->work);
         free_adjoint(ctx);
+        AC.kind = 0;
         auto alloc = [&](size_t bytes, void** p) -> ibl_status {
             const cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
             if (e != cudaSuccess) {
@@ -1369,7 +1545,7 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
         };
         auto run_segment = [&](int mode, int parity0, int len, float* lin0) -> ibl_status {
             for (const ibl_ctx::AdjSeg& g : graphs)
-                if (g.mode == mode && g.parity == parity0 && g.len == len && g.lin == lin0) {
+                if (g.kind == 0 && g.mode == mode && g.parity == parity0 && g.len == len && g.lin == lin0) {
                     CK(cudaGraphLaunch(g.exec, s));
                     return IBL_OK;
                 }
@@ -1383,7 +1559,7 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
             const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
             cudaGraphDestroy(gr);
             CK(ei);
-            graphs.push_back({mode, parity0, len, lin0, ex});
+            graphs.push_back({0, mode, parity0, len, lin0, ex});
             CK(cudaGraphLaunch(ex, s));
             return IBL_OK;
         };
@@ -1444,6 +1620,224 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
         return IBL_OK;
     };
     return run();
+}
+
+ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const double* dJ_dD_dOffset,
+                       double* grad_Ca, double* grad_umax, double* grad_rj) {
+    if (!ctx || !dJ_dD_dOffset) return fail(ctx, IBL_ERR_ARG, "null argument");
+    if (n_steps < 1 || ckpt_every < 1) return fail(ctx, IBL_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+    CKS(finalize(ctx));
+    DevState& D = ctx->dev;
+    if (D.n_members != 1 || ctx->storage != IBL_STORAGE_F32 || D.n_caps != 1 || D.any_rigid)
+        return fail(ctx, IBL_ERR_STATE, "the capsule adjoint covers one FP32 lattice holding one soft capsule "
+                                        "(ibl_adjoint_flow differentiates a flow objective without capsules)");
+    const MemberDev& md = ctx->hmem[0];
+    const size_t N = (size_t)md.N, LS = N;
+    const int nv = D.n_verts;
+    const size_t nv3 = 3 * (size_t)nv;
+    const int K = std::min(ckpt_every, n_steps);
+    const int n_ck = (n_steps + K - 1) / K;
+    const std::vector<StateSection> secs = state_sections(ctx);
+    size_t snap_bytes = 0;
+    for (const StateSection& sc : secs) snap_bytes += sc.bytes;
+    // a checkpoint: the populations and the vertex state x, x(t - dt), v
+    const size_t cap_bytes = 3 * nv3 * sizeof(double);
+    const size_t ck_one = D.f_bytes + cap_bytes;
+    const size_t ck_need = (size_t)(n_ck - 1) * ck_one;
+    auto& AC = ctx->adj;
+    if (AC.kind != 1 || AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc) {
+        cudaStreamSynchronize(ctx->work);
+        free_adjoint(ctx);
+        AC.kind = 1;
+        auto alloc = [&](size_t bytes, void** p) -> ibl_status {
+            const cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                *p = nullptr;
+                return fail(ctx, IBL_ERR_OOM, "adjoint buffers: cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+            }
+            return IBL_OK;
+        };
+        AdjCapPtrs& c = AC.cp;
+        ibl_status ast = IBL_OK;
+        struct Req { size_t bytes; void** p; };
+        const Req reqs[] = {
+            {ck_need, (void**)&AC.ck},
+            {snap_bytes, (void**)&AC.snap},
+            {(size_t)K * N * sizeof(float4), (void**)&AC.tape_rhou},
+            {(size_t)K * N * sizeof(float4), (void**)&AC.tape_F},
+            {(size_t)K * D.n_links * sizeof(float), (void**)&AC.tape_dvdq},
+            {(size_t)K * D.n_face_nodes * sizeof(float), (void**)&AC.tape_rho},
+            {(size_t)K * nv3 * sizeof(double), (void**)&AC.tape_x},
+            {(size_t)K * nv3 * sizeof(double), (void**)&AC.tape_v},
+            {Q * LS * sizeof(float), (void**)&AC.lamA},
+            {Q * LS * sizeof(float), (void**)&AC.lamB},
+            {4 * sizeof(double), (void**)&AC.acc},
+            {nv * sizeof(float4), (void**)&c.lx},
+            {nv * sizeof(float4), (void**)&c.lxp},
+            {nv * sizeof(float4), (void**)&c.lv},
+            {nv * sizeof(float4), (void**)&c.lU},
+            {nv * sizeof(float4), (void**)&c.lF},
+            {nv * sizeof(float4), (void**)&c.ln},
+            {nv * sizeof(float), (void**)&c.lA},
+            {nv * sizeof(float), (void**)&c.snorm},
+            {(size_t)D.n_caps * sizeof(double), (void**)&c.lV},
+            {N * sizeof(float4), (void**)&c.lfib},
+            {N * sizeof(float4), (void**)&c.lmac},
+        };
+        for (const Req& r : reqs)
+            if (ast == IBL_OK) ast = alloc(r.bytes, r.p);
+        if (ast != IBL_OK) { free_adjoint(ctx); return ast; }
+        AC.ck_bytes = ck_need;
+        AC.tape_steps = (size_t)K;
+    }
+    AdjCapPtrs cp = AC.cp;
+    cp.acc_ca = AC.acc + 3;
+    char *ck = AC.ck, *snap = AC.snap;
+    float *lamA = AC.lamA, *lamB = AC.lamB;
+    double* acc = AC.acc;   // [1] dJ/ds_u, [2] dJ/dr_j, [3] sum F_sb . lambda_F
+    const MemberHost& M0 = ctx->members[0];
+    const double Ca = M0.caps[0].p.Ca, u_max = M0.desc.u_max;
+    cudaStream_t s = ctx->work;
+    auto tape_of = [&](int k) {
+        StepTape tp;
+        tp.rhou = AC.tape_rhou + (size_t)k * N;
+        tp.F = AC.tape_F + (size_t)k * N;
+        tp.dvdq = AC.tape_dvdq + (size_t)k * D.n_links;
+        tp.rho = AC.tape_rho + (size_t)k * D.n_face_nodes;
+        tp.x = AC.tape_x + (size_t)k * nv3;
+        tp.v = AC.tape_v + (size_t)k * nv3;
+        return tp;
+    };
+    // Segment work, captured once per (mode, start parity, length, adjoint
+    // buffer) as a CUDA graph: mode 0 recomputes the steps from the checkpoint
+    // writing the tape, then runs the adjoint steps backwards; mode 1 runs the
+    // adjoint steps only; mode 2 runs the forward steps writing the tape.
+    auto enqueue_segment = [&](int mode, int parity0, int len, float* lin0) -> ibl_status {
+        if (mode != 1)
+            for (int k = 0; k < len; ++k) {
+                const StepTape tp = tape_of(k);
+                CKS(enqueue_step(ctx, (parity0 + k) & 1, nullptr, &tp));
+            }
+        if (mode != 2) {
+            float* li = lin0;
+            float* lo = lin0 == lamA ? lamB : lamA;
+            for (int k = len - 1; k >= 0; --k) {
+                const StepTape tp = tape_of(k);
+                CK(launch_adj_step(D, tp.rho, tp.dvdq, tp.rhou, li, lo, LS, acc + 1, acc + 2, s, tp.F, cp.lfib));
+                CK(cudaMemcpyAsync(D.x, tp.x, nv3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                CK(launch_mirror(D, s));
+                CK(launch_adj_geometry(D, cp.lV, cp.snorm, s));
+                CK(launch_adj_capsules(D, cp, tp.rhou, tp.F, tp.v, lo, LS, s));
+                std::swap(li, lo);
+            }
+        }
+        return IBL_OK;
+    };
+    auto run_segment = [&](int mode, int parity0, int len, float* lin0) -> ibl_status {
+        for (const ibl_ctx::AdjSeg& g : AC.graphs)
+            if (g.kind == 1 && g.mode == mode && g.parity == parity0 && g.len == len && g.lin == lin0) {
+                CK(cudaGraphLaunch(g.exec, s));
+                return IBL_OK;
+            }
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const ibl_status est = enqueue_segment(mode, parity0, len, lin0);
+        const cudaError_t e = cudaStreamEndCapture(s, &gr);
+        if (est != IBL_OK) { if (gr) cudaGraphDestroy(gr); return est; }
+        CK(e);
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        CK(ei);
+        AC.graphs.push_back({1, mode, parity0, len, lin0, ex});
+        CK(cudaGraphLaunch(ex, s));
+        return IBL_OK;
+    };
+    auto copy_caps = [&](char* base, bool save) -> ibl_status {
+        double* dst[3] = {D.x, D.x_prev, D.vel};
+        for (int i = 0; i < 3; ++i) {
+            char* h = base + D.f_bytes + i * nv3 * sizeof(double);
+            if (save) CK(cudaMemcpyAsync(h, dst[i], nv3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            else CK(cudaMemcpyAsync(dst[i], h, nv3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        if (save) CK(cudaMemcpyAsync(base, D.f, D.f_bytes, cudaMemcpyDeviceToDevice, s));
+        else {
+            CK(cudaMemcpyAsync(D.f, base, D.f_bytes, cudaMemcpyDeviceToDevice, s));
+            CK(launch_mirror(D, s));
+        }
+        return IBL_OK;
+    };
+    CKS(enter(ctx));
+    CK(cudaMemsetAsync(lamA, 0, Q * LS * sizeof(float), s));
+    CK(cudaMemsetAsync(lamB, 0, Q * LS * sizeof(float), s));
+    CK(cudaMemsetAsync(acc, 0, 4 * sizeof(double), s));
+    CK(cudaMemsetAsync(cp.lmac, 0, N * sizeof(float4), s));
+    CK(cudaMemsetAsync(cp.lfib, 0, N * sizeof(float4), s));
+    const long long t0 = ctx->t;
+    // forward sweep: a checkpoint at the start of every segment but the last,
+    // whose tape is recorded directly
+    const int last0 = (n_ck - 1) * K;
+    for (int k = 0; k < last0; ++k) {
+        if (k % K == 0) CKS(copy_caps(ck + (size_t)(k / K) * ck_one, true));
+        const int parity = (int)(ctx->t & 1);
+        CKS(capture_graph(ctx, parity));
+        CK(cudaGraphLaunch(ctx->graph[parity], s));
+        ctx->t += 1;
+    }
+    CKS(run_segment(2, (int)(ctx->t & 1), n_steps - last0, lamA));
+    ctx->t += n_steps - last0;
+    // terminal condition: lambda_x = dJ/dx at the last step (FP64, host)
+    std::vector<double> XT(nv3), G(nv3);
+    CK(cudaMemcpyAsync(XT.data(), D.x, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const std::vector<int>& tris = M0.caps[0].tris;
+    capsule_objective_grad(XT.data(), nv, tris.data(), (int)tris.size() / 3, dJ_dD_dOffset[0], dJ_dD_dOffset[1],
+                           G.data());
+    {
+        std::vector<float4> L4(nv);
+        for (int v = 0; v < nv; ++v)
+            L4[v] = make_float4((float)G[3 * v], (float)G[3 * v + 1], (float)G[3 * v + 2], 0.f);
+        CK(cudaMemcpyAsync(cp.lx, L4.data(), nv * sizeof(float4), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(cp.lxp, 0, nv * sizeof(float4), s));
+        CK(cudaMemsetAsync(cp.lv, 0, nv * sizeof(float4), s));
+        CK(cudaStreamSynchronize(s));
+    }
+    {   // the final state, put back after the reverse sweep
+        size_t off = 0;
+        for (const StateSection& sc : secs) {
+            if (sc.bytes) CK(cudaMemcpyAsync(snap + off, sc.dev, sc.bytes, cudaMemcpyDeviceToDevice, s));
+            off += sc.bytes;
+        }
+    }
+    float* lin = lamA;
+    for (int seg = n_ck - 1; seg >= 0; --seg) {
+        const int s0 = seg * K, s1 = std::min(n_steps, s0 + K);
+        if (seg < n_ck - 1) CKS(copy_caps(ck + (size_t)seg * ck_one, false));
+        CKS(run_segment(seg < n_ck - 1 ? 0 : 1, (int)((t0 + s0) & 1), s1 - s0, lin));
+        if ((s1 - s0) & 1) lin = lin == lamA ? lamB : lamA;
+    }
+    {
+        size_t off = 0;
+        for (const StateSection& sc : secs) {
+            if (sc.bytes) CK(cudaMemcpyAsync(sc.dev, snap + off, sc.bytes, cudaMemcpyDeviceToDevice, s));
+            off += sc.bytes;
+        }
+        CK(launch_mirror(D, s));
+    }
+    ctx->t = t0 + n_steps;
+    double h[4];
+    CK(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CKS(sync_host_state(ctx));
+    CKS(leave(ctx));
+    if (grad_Ca) *grad_Ca = -h[3] / Ca;
+    if (grad_umax) *grad_umax = u_max != 0.0 ? h[1] / u_max : 0.0;
+    if (grad_rj) *grad_rj = h[2];
+    uint32_t any = 0;
+    for (uint32_t st : ctx->h_status) any |= st;
+    if (any & ST_NONFINITE) return fail(ctx, IBL_ERR_NONFINITE, "a capsule vertex became non-finite");
+    if (any & ST_DAMAGED) return fail(ctx, IBL_ERR_DAMAGED, "a capsule edge reached twice its rest length");
+    return IBL_OK;
 }
 
 ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, float* u) {

@@ -5,52 +5,17 @@
 // damage rule.
 #include <climits>
 
-#include "lbm_device.cuh"
+#include "ib_device.cuh"
 
 namespace ibl {
 
 
-constexpr float SUPPORT_SIDE = 2.6f;   // 2 r_w (Section "No-slip conditions for moving immersed boundaries")
-constexpr float ALPHA = 0.3f;          // Eq. intKernel
-constexpr double PIVOT_TOL = 1e-10;    // singular moment matrix -> nearest fluid node
-constexpr unsigned FULL = 0xffffffffu;
-constexpr uint32_t STOP = ST_DAMAGED | ST_NONFINITE;
-
-struct f3 { float x, y, z; };
-__device__ __forceinline__ f3 sub(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ f3 crs(f3 a, f3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
-__device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ f3 scl(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
-
-// Two-float mirror of the FP64 vertex positions, 32 bytes per vertex:
-// (hi, 0) then (lo, 0) with hi = fl32(x) and lo = fl32(x - hi) (x - hi is
-// exact).  The difference of two positions taken as (hi_a - hi_b) +
-// (lo_a - lo_b) in FP32 is the FP64 difference rounded to FP32 within an ulp,
-// with no FP64 arithmetic (GB300's FP64 pipe is narrow).  Written with x by
-// the update kernels, and by k_mirror after x is set from the host.
-__device__ __forceinline__ void mirror_put(float4* __restrict__ xm, int v, double X, double Y, double Z) {
-    const float hx = (float)X, hy = (float)Y, hz = (float)Z;
-    xm[2 * v] = make_float4(hx, hy, hz, 0.f);
-    xm[2 * v + 1] = make_float4((float)(X - (double)hx), (float)(Y - (double)hy), (float)(Z - (double)hz), 0.f);
-}
-
-// x_a - x_b
-__device__ __forceinline__ f3 mirror_diff(const float4* __restrict__ xm, int a, int b) {
-    const float4 ha = xm[2 * a], la = xm[2 * a + 1], hb = xm[2 * b], lb = xm[2 * b + 1];
-    return {(ha.x - hb.x) + (la.x - lb.x), (ha.y - hb.y) + (la.y - lb.y), (ha.z - hb.z) + (la.z - lb.z)};
-}
 
 __global__ void __launch_bounds__(256) k_mirror(const double* __restrict__ x, float4* __restrict__ xm, int n_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v < n_verts) mirror_put(xm, v, x[3 * v], x[3 * v + 1], x[3 * v + 2]);
 }
 
-// Eq. intKernel with r normalised by the support side.
-__device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, float rz) {
-    const float r = sqrtf(rx * rx + ry * ry + rz * rz) * (1.f / SUPPORT_SIDE);
-    const float s = r * (1.f / ALPHA);
-    return (fluid && r <= 1.f) ? expf(-s * s) : 0.f;
-}
 
 
 // ---------------------------------------------------------------------------
@@ -65,21 +30,6 @@ __device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, floa
 // ---------------------------------------------------------------------------
 constexpr int GEO_BLOCKS = 16;
 
-__device__ __forceinline__ double block_sum_d(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < 32) {
-        t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-    }
-    return t;   // valid in thread 0
-}
 
 __global__ void __launch_bounds__(256) k_geom_tri(const CapsuleDev* __restrict__ caps, CapsuleSums* __restrict__ sums,
                                                   const uint32_t* __restrict__ status, const float4* __restrict__ xm,
@@ -114,7 +64,8 @@ __global__ void __launch_bounds__(256) k_geom_tri(const CapsuleDev* __restrict__
 __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__ caps, const int* __restrict__ v_cap,
                                                   CapsuleSums* __restrict__ sums, const uint32_t* __restrict__ status,
                                                   const float4* __restrict__ xm, float4* __restrict__ vacc,
-                                                  float* __restrict__ nrm, float* __restrict__ area, int n_verts) {
+                                                  float* __restrict__ nrm, float* __restrict__ area, int n_verts,
+                                                  float* __restrict__ snorm) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = v < n_verts && !(status[caps[v_cap[min(v, n_verts - 1)]].member] & STOP);
     const int c = live ? v_cap[v] : -1;
@@ -123,6 +74,7 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
     if (live) {
         const float4 a = vacc[v];
         const float inv = rsqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+        if (snorm) snorm[v] = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);   // |S_l| for the adjoint
         nrm[3 * v] = a.x * inv;
         nrm[3 * v + 1] = a.y * inv;
         nrm[3 * v + 2] = a.z * inv;
@@ -167,22 +119,6 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
     }
 }
 
-// Moments (rho, u* = sum g e / rho) of the current populations at the fluid
-// nodes that a marker or probe stencil can reach.  A marker's support lies
-// within 1.5 dx of it per axis (the 3x3x3 block around its nearest node); a
-// probe sits 1.2 dx off its vertex along the unit normal, so its support lies
-// within 1.2 + 1.5 = 2.7 dx of the vertex per axis and within 1.2 + 1.5 sqrt 3
-// < 3.8 dx of it in distance.  Per axis every support coordinate lies in
-// [floor(min) - 2, floor(max) + 3], which is the vertex box
-// [floor(min), floor(max) + 1] grown by SHELL_MARGIN = 2.  Within the box, a
-// node farther than sqrt(r2_hi) + 3.8 from the step's reference point rc, or
-// nearer than sqrt(r2_lo) - 3.8, is within 3.8 of no vertex and is skipped
-// (a 0.05 slack covers the FP32 distances and square roots).  The IB kernels then read one
-// float4 per support node instead of 19 scattered populations.  Overlapping
-// boxes write identical values.
-constexpr int SHELL_MARGIN = 2;
-constexpr float SHELL_REACH = 3.85f;
-constexpr int SHELL_BLOCKS = 32;   // blocks per capsule
 
 // One warp per row (y, z) of a capsule's box, lanes along x over the part of
 // the row inside the outer sphere, less the part inside the inner one.
@@ -274,231 +210,6 @@ __global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ 
         shell_rows<T, false>(d, fm, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
 }
 
-// Offsets (dx, dy, dz) of support node k = (dx+1) + 3 (dy+1) + 9 (dz+1) of
-// the 3x3x3 MLS block, packed two bits per node, so that a run-time k costs a
-// shift and a mask instead of divisions.
-__device__ __forceinline__ int sdx(int k) { return (int)((0x24924924924924ull >> (2 * k)) & 3ull) - 1; }
-__device__ __forceinline__ int sdy(int k) { return (int)((0x2a540a9502a540ull >> (2 * k)) & 3ull) - 1; }
-__device__ __forceinline__ int sdz(int k) { return (int)((0x2aaaa555540000ull >> (2 * k)) & 3ull) - 1; }
-
-// 1/d in FP64 by Newton's iteration r <- r (2 - d r) from the FP32
-// reciprocal (each step doubles the correct bits: 24 -> 48 -> full)
-__device__ __forceinline__ double rcp_r(double d) {
-    double r = (double)__frcp_rn((float)d);
-    r = r * (2.0 - d * r);
-    return r * (2.0 - d * r);
-}
-__device__ __forceinline__ float rcp_r(float d) { return __frcp_rn(d); }
-
-__device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy, int cz) {
-    if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx; else if (cx < 0 || cx >= d.nx) return -1;
-    if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny; else if (cy < 0 || cy >= d.ny) return -1;
-    if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz; else if (cz < 0 || cz >= d.nz) return -1;
-    return (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
-}
-
-// L D L^T of the symmetric moment matrix m (m00 m01 m02 m03 m11 m12 m13 m22 m23
-// m33) in precision R, then the first ROWS rows of its inverse.  Returns the
-// pivots relative to the first one in `rel` (min of d1, d2, d3 over d0) and
-// false when the matrix fails the singularity test.
-template <int ROWS, typename R>
-__device__ __forceinline__ bool ldlt_solve(const float (&m)[10], float (&inv)[4][4], R& rel) {
-    const R a00 = m[0], a10 = m[1], a20 = m[2], a30 = m[3], a11 = m[4], a21 = m[5], a31 = m[6], a22 = m[7],
-            a32 = m[8], a33 = m[9];
-    const R d0 = a00;
-    const R s0 = d0 > R(0) ? d0 : R(1);
-    const R r0 = rcp_r(s0);
-    const R L10 = a10 * r0, L20 = a20 * r0, L30 = a30 * r0;
-    const R d1 = a11 - L10 * L10 * d0;
-    const R s1 = d1 > R(0) ? d1 : R(1);
-    const R r1 = rcp_r(s1);
-    const R L21 = (a21 - L20 * L10 * d0) * r1;
-    const R L31 = (a31 - L30 * L10 * d0) * r1;
-    const R d2 = a22 - L20 * L20 * d0 - L21 * L21 * d1;
-    const R s2 = d2 > R(0) ? d2 : R(1);
-    const R r2 = rcp_r(s2);
-    const R L32 = (a32 - L30 * L20 * d0 - L31 * L21 * d1) * r2;
-    const R d3 = a33 - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
-    const R tol = R(PIVOT_TOL) * s0;
-    rel = fmin(fmin(d1, d2), d3) * r0;
-    if (!(d0 > R(0) && d1 > tol && d2 > tol && d3 > tol)) return false;
-    const R r3 = rcp_r(d3);
-#pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const R y0 = j == 0 ? R(1) : R(0);
-        const R y1 = (j == 1 ? R(1) : R(0)) - L10 * y0;
-        const R y2 = (j == 2 ? R(1) : R(0)) - L20 * y0 - L21 * y1;
-        const R y3 = (j == 3 ? R(1) : R(0)) - L30 * y0 - L31 * y1 - L32 * y2;
-        const R c3 = y3 * r3;
-        const R c2 = y2 * r2 - L32 * c3;
-        const R c1 = y1 * r1 - L21 * c2 - L31 * c3;
-        const R c0 = y0 * r0 - L10 * c1 - L20 * c2 - L30 * c3;
-        inv[j][0] = (float)c0; inv[j][1] = (float)c1; inv[j][2] = (float)c2; inv[j][3] = (float)c3;
-    }
-    return true;
-}
-
-// Pivots this far above the singularity threshold (relative to d0) keep the
-// FP32 solve's error below ~1e-4 of the inverse; closer ones are redone in
-// FP64, which then takes the singularity decision exactly as an FP64 solve.
-constexpr float FP32_PIVOT_FLOOR = 1e-3f;
-
-// ---------------------------------------------------------------------------
-// IB marker and probe stencils, four lanes per stencil, all on the fluid
-// solution at t (moments of the current populations from the shell pass):
-//  s = 0: Eq. uLag on u*, F_l = (U_b - U_l)/dt, Eq. bodyforce spreading with
-//         c_l = A_l into the dense f_ib field (float atomics) and the node's IB
-//         flag; u_v,0 = U_l (the tentative velocity of Eq. verletPos); the
-//         volume penalty k_v (1 - V/V0) A (Eq. volFor, restoring sign) of soft
-//         capsules (0 for rigid ones);
-//  s = 1, 2: the probe at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u +
-//         grad u^T) from the MLS fit (Eqs. hydroForP, hydroForNu), stored for
-//         the update kernels, which add F_p + F_tau.
-// Each lane gathers its support nodes' moments at once (at most GS loads in
-// flight), so that their latencies overlap.
-// ---------------------------------------------------------------------------
-constexpr int PROBE_STRIDE = 8;   // floats per probe record: p, tau xx yy zz xy xz yz, pad
-
-// Both stencils solve their 4x4 system in FP32 unless a pivot falls below
-// FP32_PIVOT_FLOOR of the first, and then redo it in FP64 (GB300's FP64 pipe
-// is narrow).  IBL_MARKER_FAST32=0 makes the marker stencil, which
-// interpolates and spreads, always solve in FP64.
-constexpr bool PROBE_FAST32 = true;
-#ifndef IB_MARKER_THREADS
-#define IB_MARKER_THREADS 128
-#endif
-#ifndef IB_MARKER_MIN_BLOCKS
-#define IB_MARKER_MIN_BLOCKS 8
-#endif
-#ifndef IB_PROBE_THREADS
-#define IB_PROBE_THREADS 128
-#endif
-#ifndef IB_PROBE_MIN_BLOCKS
-#define IB_PROBE_MIN_BLOCKS 8
-#endif
-#ifndef IBL_MARKER_FAST32
-#define IBL_MARKER_FAST32 1
-#endif
-constexpr bool MARKER_FAST32 = IBL_MARKER_FAST32 != 0;
-
-// The stencils run on groups of GL = 4 consecutive lanes: support node k of
-// a point belongs to lane k % 4 (slot k / 4), so each lane gathers at most 7
-// nodes, the moments and the interpolated sums are combined by shuffles within
-// the group, and every lane of the group holds the same solved rows.  A
-// stencil's latency chain is a quarter of the one-lane form and its registers
-// hold 7 weights instead of 27.
-#ifndef IB_GROUP_LANES
-#define IB_GROUP_LANES 4
-#endif
-constexpr int GL = IB_GROUP_LANES;      // lanes per stencil (a power of two, at most 32)
-constexpr int GS = (27 + GL - 1) / GL;  // support nodes per lane
-static_assert(GL >= 4 && GL <= 32 && (GL & (GL - 1)) == 0, "a stencil group needs a lane per axis");
-
-// MLS operator of one point, held by the GL lanes of its group: weights W_k of
-// this lane's support nodes (Eq. intKernel) and the first ROWS rows of A^{-1}
-// (Eq. l2norm, basis [1, x-X, y-Y, z-Z]; A is symmetric, so row j is
-// A^{-1} e_j), the same in every lane of the group.  fallback >= 0: singular
-// system, the whole point goes to support node `fallback`.
-struct MlsG {
-    int bx, by, bz;
-    int base;               // padded index of the base node when the block is interior, else -1
-    float ox, oy, oz;       // base node minus point
-    float W[GS];            // weights of this lane's support nodes (k = lane + 4 slot)
-    float inv[4][4];
-    int fallback;           // -1: regular; 0..26: nearest fluid node; 27: none
-};
-
-// The FP64 solve of a near-singular or FP64-only stencil, out of line so that
-// its registers do not count against the common FP32 path.
-struct Moments { float m[10]; };
-struct Rows { float v[4][4]; int good; };
-
-template <int ROWS>
-__device__ __noinline__ Rows ldlt_solve64(Moments mm) {
-    Rows out;
-    double rel;
-    out.good = ldlt_solve<ROWS, double>(mm.m, out.v, rel) ? 1 : 0;
-    return out;
-}
-
-// P is the point's coordinate along axis min(r, 2): lanes 0, 1, 2 of a group
-// each take the FP64 steps (nearest node, offset) for one axis and the group
-// exchanges the results, so that GB300's narrow FP64 pipe does a third of the
-// work it would if every lane took all three axes.
-template <int ROWS, bool FAST32>
-__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double P, int r,
-                                            unsigned mask, MlsG& M) {
-    const double b = floor(P + 0.5);
-    const int bi = (int)b;
-    const float o = (float)(b - P);
-    M.bx = __shfl_sync(mask, bi, 0, GL); M.by = __shfl_sync(mask, bi, 1, GL); M.bz = __shfl_sync(mask, bi, 2, GL);
-    M.ox = __shfl_sync(mask, o, 0, GL); M.oy = __shfl_sync(mask, o, 1, GL); M.oz = __shfl_sync(mask, o, 2, GL);
-    const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
-                          M.bz <= d.nz - 2;
-    M.base = interior ? (M.bx + d.px) + d.NX * ((M.by + d.py) + d.NY * (M.bz + d.pz)) : -1;
-    float m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    float best = 0.f;
-    int bestk = 27;
-#pragma unroll
-    for (int j = 0; j < GS; ++j) {
-        const int k = r + GL * j;
-        float w = 0.f;
-        if (k < 27) {
-            const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
-            const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
-                                      : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
-            const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
-            const float rx = M.ox + dx, ry = M.oy + dy, rz = M.oz + dz;
-            w = mls_weight(fluid, rx, ry, rz);
-            if (w > best) { best = w; bestk = k; }
-            m[0] += w; m[1] += w * rx; m[2] += w * ry; m[3] += w * rz;
-            m[4] += w * rx * rx; m[5] += w * rx * ry; m[6] += w * rx * rz;
-            m[7] += w * ry * ry; m[8] += w * ry * rz; m[9] += w * rz * rz;
-        }
-        M.W[j] = w;
-    }
-#pragma unroll
-    for (int o = 1; o < GL; o <<= 1) {
-#pragma unroll
-        for (int i = 0; i < 10; ++i) m[i] += __shfl_xor_sync(mask, m[i], o);
-        const float ob = __shfl_xor_sync(mask, best, o);
-        const int ok = __shfl_xor_sync(mask, bestk, o);
-        if (ob > best || (ob == best && ok < bestk)) { best = ob; bestk = ok; }   // first k of the largest weight
-    }
-    bool good = false;
-    if (FAST32) {
-        float rel;
-        good = ldlt_solve<ROWS, float>(m, M.inv, rel) && rel >= FP32_PIVOT_FLOOR;
-    }
-    if (!good) {
-        Moments mm;
-#pragma unroll
-        for (int i = 0; i < 10; ++i) mm.m[i] = m[i];
-        const Rows rr = ldlt_solve64<ROWS>(mm);
-        good = rr.good != 0;
-#pragma unroll
-        for (int a = 0; a < ROWS; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) M.inv[a][b] = rr.v[a][b];
-    }
-    M.fallback = good ? -1 : (best > 0.f ? bestk : 27);
-}
-
-__device__ __forceinline__ float mls_row_g(const MlsG& M, int row, int j, int k) {
-    const float rx = M.ox + sdx(k), ry = M.oy + sdy(k), rz = M.oz + sdz(k);
-    return M.W[j] * (M.inv[row][0] + M.inv[row][1] * rx + M.inv[row][2] * ry + M.inv[row][3] * rz);
-}
-
-__device__ __forceinline__ int mls_node_g(const MemberDev& d, const MlsG& M, int k) {
-    const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
-    return M.base >= 0 ? M.base + dx + d.NX * (dy + d.NY * dz) : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
-}
-
-__device__ __forceinline__ float group_sum(float v, unsigned mask) {
-#pragma unroll
-    for (int o = 1; o < GL; o <<= 1) v += __shfl_xor_sync(mask, v, o);
-    return v;
-}
 
 __global__ void __launch_bounds__(IB_MARKER_THREADS, IB_MARKER_MIN_BLOCKS)
 k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float* __restrict__ fib,
@@ -623,34 +334,6 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
     rec[6] = mu * (acc[6] + acc[8]);
 }
 
-// F_p + F_tau of vertex v from its two probe records (Eqs. hydroForP,
-// hydroForNu): -(p+ - p-) n A + (tau+ - tau-) . n A, plus the volume penalty
-// (Eq. volFor) stored with them.
-__device__ __forceinline__ void hydro_force(const float* __restrict__ probe, const float* __restrict__ nrm,
-                                            const float* __restrict__ area, int v, float& Hx, float& Hy,
-                                            float& Hz) {
-    const float* a = probe + (size_t)2 * v * PROBE_STRIDE;
-    const float* b = a + PROBE_STRIDE;
-    const float nx = nrm[3 * v], ny = nrm[3 * v + 1], nz = nrm[3 * v + 2], A = area[v];
-    const float dp = a[0] - b[0];
-    const float t0 = a[1] - b[1], t1 = a[2] - b[2], t2 = a[3] - b[3], t3 = a[4] - b[4], t4 = a[5] - b[5],
-                t5 = a[6] - b[6];
-    const float kv = a[7];   // volume penalty k_v (1 - V/V0) A of soft capsules
-    Hx = (-dp * nx + t0 * nx + t3 * ny + t4 * nz) * A + kv * nx;
-    Hy = (-dp * ny + t3 * nx + t1 * ny + t5 * nz) * A + kv * ny;
-    Hz = (-dp * nz + t4 * nx + t5 * ny + t2 * nz) * A + kv * nz;
-}
-
-// ---------------------------------------------------------------------------
-// Stretching (Eq. strainFor) and bending of every hinge of soft capsules.
-// Bending is -grad of k_b [1 - cos(theta - theta0)], the potential whose
-// gradient carries the beta_b = k_b sin(theta - theta0)/sin(theta) factor of
-// Eq. bendFor; theta is the signed angle between the outward normals.
-// ---------------------------------------------------------------------------
-// one vector reduction per vertex (the force array is padded to float4)
-__device__ __forceinline__ void add_force(float* F, int v, f3 a) {
-    atomicAdd(reinterpret_cast<float4*>(F) + v, make_float4(a.x, a.y, a.z, 0.f));
-}
 
 __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, const int* __restrict__ e_cap,
                                                const CapsuleDev* __restrict__ caps, const uint32_t* __restrict__ status,
@@ -662,32 +345,16 @@ __global__ void __launch_bounds__(256) k_edges(const int* __restrict__ hinge, co
     const CapsuleDev& C = caps[e_cap[e]];
     if (C.rigid || (status[C.member] & STOP)) return;
     const int4 hg = reinterpret_cast<const int4*>(hinge)[e];
-    const int v1 = hg.x, v2 = hg.y, v3 = hg.z, v4 = hg.w;
+    const int v1 = hg.x, v2 = hg.y, v3i = hg.z, v4 = hg.w;
     // positions relative to v2
-    const f3 a = mirror_diff(xm, v1, v2), c = mirror_diff(xm, v3, v2), dd = mirror_diff(xm, v4, v2);
-    // stretching on the edge (v2, v3): F_2 = -k (l - l0) r_23 / l, r_23 = v2 - v3
-    const f3 r23 = scl(c, -1.f);
-    const float l = sqrtf(dot3(r23, r23));
-    const f3 Fs = scl(r23, -ks[e] * (l - l0[e]) / l);
-    // bending on the hinge (v1, v2, v3, v4)
-    const f3 nA = crs(scl(a, -1.f), sub(c, a));
-    const f3 nB = crs(sub(c, dd), scl(dd, -1.f));
-    const float L = l;
-    const f3 eh = scl(c, 1.f / L);
-    const float th = atan2f(dot3(crs(nA, nB), eh), dot3(nA, nB));
-    const float k = kb[e] * sinf(th - th0[e]);
-    const f3 gA = scl(nA, 1.f / dot3(nA, nA));
-    const f3 gB = scl(nB, 1.f / dot3(nB, nB));
-    const f3 u1 = scl(gA, L);
-    const f3 u4 = scl(gB, L);
-    const float pa = dot3(sub(a, c), eh), pd = dot3(sub(dd, c), eh);
-    const f3 u2 = {pa * gA.x + pd * gB.x, pa * gA.y + pd * gB.y, pa * gA.z + pd * gB.z};
-    const float qa = dot3(a, eh), qd = dot3(dd, eh);
-    const f3 u3 = {-(qa * gA.x + qd * gB.x), -(qa * gA.y + qd * gB.y), -(qa * gA.z + qd * gB.z)};
-    add_force(force, v1, scl(u1, k));
-    add_force(force, v2, {k * u2.x + Fs.x, k * u2.y + Fs.y, k * u2.z + Fs.z});
-    add_force(force, v3, {k * u3.x - Fs.x, k * u3.y - Fs.y, k * u3.z - Fs.z});
-    add_force(force, v4, scl(u4, k));
+    const f3 a = mirror_diff(xm, v1, v2), c = mirror_diff(xm, v3i, v2), dd = mirror_diff(xm, v4, v2);
+    v3<float> F1, F2, F3, F4;
+    hinge_forces<float>({a.x, a.y, a.z}, {c.x, c.y, c.z}, {dd.x, dd.y, dd.z}, ks[e], l0[e], kb[e], th0[e], F1, F2,
+                        F3, F4);
+    add_force(force, v1, {F1.x, F1.y, F1.z});
+    add_force(force, v2, {F2.x, F2.y, F2.z});
+    add_force(force, v3i, {F3.x, F3.y, F3.z});
+    add_force(force, v4, {F4.x, F4.y, F4.z});
 }
 
 // ---------------------------------------------------------------------------
@@ -1025,15 +692,88 @@ __global__ void __launch_bounds__(256) k_damage(const CapsuleDev* __restrict__ c
 }
 
 // ---------------------------------------------------------------------------
+// FP64 diagnostics of every capsule (Section "Transport of an elastic
+// capsule"; Reading R): per triangle, with a, b, c relative to the capsule's
+// first vertex r0, v = a.(b x c)/6 and q = a + b + c: V += v, S += |N|/2,
+// S1 += v q / 4, M2 += v/20 (a a^T + b b^T + c c^T + q q^T); per edge the
+// largest l / l0; per vertex the summed velocity.  out holds per capsule
+// V, S, S1[3], M2[6] (xx yy zz xy xz yz), vel[3], max stretch, r0[3].
+// ---------------------------------------------------------------------------
+constexpr int STAT_DOUBLES = CAP_STAT_DOUBLES;
+constexpr int STAT_BLOCKS = 8;
+
+__global__ void __launch_bounds__(256) k_capsule_stats(const CapsuleDev* __restrict__ caps, const double* __restrict__ x,
+                                                       const double* __restrict__ vel, const int* __restrict__ tri,
+                                                       const int* __restrict__ hinge, const float* __restrict__ l0,
+                                                       int c_begin, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int c = c_begin + blockIdx.x / STAT_BLOCKS, part = blockIdx.x % STAT_BLOCKS;
+    const CapsuleDev& C = caps[c];
+    const int r0 = C.v_begin;
+    const double ox = x[3 * r0], oy = x[3 * r0 + 1], oz = x[3 * r0 + 2];
+    double acc[STAT_DOUBLES];
+    for (int i = 0; i < STAT_DOUBLES; ++i) acc[i] = 0.0;
+    const int stride = STAT_BLOCKS * blockDim.x;
+    for (int t = C.t_begin + part * blockDim.x + threadIdx.x; t < C.t_begin + C.t_count; t += stride) {
+        const int ia = tri[3 * t], ib = tri[3 * t + 1], ic = tri[3 * t + 2];
+        const double a[3] = {x[3 * ia] - ox, x[3 * ia + 1] - oy, x[3 * ia + 2] - oz};
+        const double b[3] = {x[3 * ib] - ox, x[3 * ib + 1] - oy, x[3 * ib + 2] - oz};
+        const double cc[3] = {x[3 * ic] - ox, x[3 * ic + 1] - oy, x[3 * ic + 2] - oz};
+        const double bc[3] = {b[1] * cc[2] - b[2] * cc[1], b[2] * cc[0] - b[0] * cc[2], b[0] * cc[1] - b[1] * cc[0]};
+        const double v = (a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2]) / 6.0;
+        const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {cc[0] - a[0], cc[1] - a[1], cc[2] - a[2]};
+        const double N[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double q[3] = {a[0] + b[0] + cc[0], a[1] + b[1] + cc[1], a[2] + b[2] + cc[2]};
+        acc[0] += v;
+        acc[1] += 0.5 * sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+        for (int k = 0; k < 3; ++k) acc[2 + k] += v * q[k] * 0.25;
+        const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+        for (int m = 0; m < 6; ++m)
+            acc[5 + m] += v * 0.05 * (a[ii[m]] * a[jj[m]] + b[ii[m]] * b[jj[m]] + cc[ii[m]] * cc[jj[m]] +
+                                      q[ii[m]] * q[jj[m]]);
+    }
+    for (int v = C.v_begin + part * blockDim.x + threadIdx.x; v < C.v_begin + C.v_count; v += stride)
+        for (int k = 0; k < 3; ++k) acc[11 + k] += vel[3 * v + k];
+    double mx = 0.0;
+    for (int e = C.e_begin + part * blockDim.x + threadIdx.x; e < C.e_begin + C.e_count; e += stride) {
+        const int4 h = reinterpret_cast<const int4*>(hinge)[e];
+        const double dx = x[3 * h.y] - x[3 * h.z], dy = x[3 * h.y + 1] - x[3 * h.z + 1], dz = x[3 * h.y + 2] - x[3 * h.z + 2];
+        mx = fmax(mx, sqrt(dx * dx + dy * dy + dz * dz) / (double)l0[e]);
+    }
+    double* o = out + (size_t)c * STAT_DOUBLES;
+    for (int i = 0; i < 14; ++i) {
+        const double t = block_sum_d(acc[i], red);
+        if (threadIdx.x == 0) atomicAdd(o + i, t);
+        __syncthreads();
+    }
+    // the largest stretch: non-negative doubles order as their bit patterns
+#pragma unroll
+    for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(o + 14), (unsigned long long)__double_as_longlong(mx));
+    if (part == 0 && threadIdx.x == 0) { o[15] = ox; o[16] = oy; o[17] = oz; }
+}
+
+cudaError_t launch_capsule_stats(const DevState& d, int c_begin, int c_count, double* out, cudaStream_t s) {
+    if (c_count <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(out + (size_t)c_begin * STAT_DOUBLES, 0, sizeof(double) * STAT_DOUBLES * c_count, s);
+    if (e != cudaSuccess) return e;
+    k_capsule_stats<<<c_count * STAT_BLOCKS, 256, 0, s>>>(d.caps, d.x, d.vel, d.tri, d.hinge, d.l0, c_begin, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
-cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) {
+cudaError_t launch_geometry_snorm(const DevState& d, float* snorm, cudaStream_t s) {
     if (d.n_caps == 0) return cudaSuccess;
     k_geom_tri<<<d.n_caps * GEO_BLOCKS, 256, 0, s>>>(d.caps, d.sums, d.status, d.xm, d.tri, d.vacc);
     k_geom_vtx<<<(d.n_verts + 255) / 256, 256, 0, s>>>(d.caps, d.v_cap, d.sums, d.status, d.xm, d.vacc, d.nrm, d.area,
-                                                       d.n_verts);
+                                                       d.n_verts, snorm);
     return cudaGetLastError();
 }
+
+cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) { return launch_geometry_snorm(d, nullptr, s); }
 
 template <typename T>
 static cudaError_t shell_t(const DevState& d, int parity, cudaStream_t s) {

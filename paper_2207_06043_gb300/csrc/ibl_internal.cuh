@@ -196,7 +196,8 @@ constexpr int NEAR_STRIDE = 1 + 3 * NEAR_CAP;   // int4 entries: the count, then
 // from the forward state: (rho, u) of every fluid node before the collision
 // (float4 per padded node), d(value)/dq of every wall link, rho of every face
 // node before the face rule.  Null in ordinary steps.
-cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou = nullptr);
+cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou = nullptr,
+                       float4* tape_F = nullptr);
 cudaError_t launch_faces(const DevState& d, int parity_done, cudaStream_t s, float* tape_rho = nullptr);
 int lbm_max_threads();   // block-size bound the lattice kernel was compiled for
 cudaError_t launch_bfl(const DevState& d, int parity_done, cudaStream_t s, float* tape_dvdq = nullptr);
@@ -209,9 +210,29 @@ cudaError_t launch_adj_objective(const DevState& d, int parity, const int lo[3],
                                  float* lam, size_t LS, double* J, cudaStream_t s);
 cudaError_t launch_adj_step(const DevState& d, const float* tape_rho, const float* tape_dvdq, const float4* tape_rhou,
                             float* lam_in, float* lam_out, size_t LS, double* grad_s, double* grad_q,
-                            cudaStream_t s);
+                            cudaStream_t s, const float4* tape_F = nullptr, float4* lam_fib = nullptr);
 
 cudaError_t launch_geometry(const DevState& d, int full, cudaStream_t s);
+// the same, also recording |S_l| (the length of each vertex's unnormalised
+// normal) when snorm is not null
+cudaError_t launch_geometry_snorm(const DevState& d, float* snorm, cudaStream_t s);
+
+// Capsule adjoint (adjoint_ib.cu): per-vertex adjoint vectors, the per-node
+// lambda_F of the lattice adjoint and the support-node accumulators.
+struct AdjCapPtrs {
+    float4 *lx = nullptr, *lxp = nullptr, *lv = nullptr, *lU = nullptr, *lF = nullptr, *ln = nullptr;
+    float *lA = nullptr, *snorm = nullptr;
+    double* lV = nullptr;
+    float4 *lfib = nullptr, *lmac = nullptr;
+    double* acc_ca = nullptr;
+};
+// geometry of x(t) (already in the vertex arrays) for a reverse step, with the
+// volume adjoint reset
+cudaError_t launch_adj_geometry(const DevState& d, double* lV, float* snorm, cudaStream_t s);
+// the capsule part of a reverse step t (after the lattice part wrote lam and
+// p.lfib), with the lattice tape of step t and the vertex velocities at t
+cudaError_t launch_adj_capsules(const DevState& d, const AdjCapPtrs& p, const float4* tape_rhou, const float4* tape_F,
+                                const double* vel_t, float* lam, size_t LS, cudaStream_t s);
 // IB pass: shell moments, then the marker stencils (interpolation, force,
 // spreading) and the probe stencils (stresses), which are independent of
 // each other (the markers set only the IB bit of fluid tags, the probes read
@@ -225,5 +246,10 @@ cudaError_t launch_repulsion(const DevState& d, cudaStream_t s);
 cudaError_t launch_update(const DevState& d, cudaStream_t s);
 // refresh the two-float mirror of the vertex positions after x is set from the host
 cudaError_t launch_mirror(const DevState& d, cudaStream_t s);
+// FP64 sums of capsules c_begin .. c_begin + c_count - 1 into out (18 doubles
+// per capsule: V, S, S1[3] and M2[6] about the first vertex r0, summed
+// velocity[3], max stretch, r0[3])
+constexpr int CAP_STAT_DOUBLES = 18;
+cudaError_t launch_capsule_stats(const DevState& d, int c_begin, int c_count, double* out, cudaStream_t s);
 
 }  // namespace ibl

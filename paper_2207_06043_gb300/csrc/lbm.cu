@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(LBM_THREADS, BORDER ? 4 : (SINGLE ? LBM_MIN_BL
 k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T* __restrict__ f,
       uint8_t* __restrict__ tag, float* __restrict__ fib, const float* __restrict__ face_vel,
       const uint32_t* __restrict__ status, const uint32_t* __restrict__ nodes, const int* __restrict__ group_mem,
-      int n_groups, int n_blocks, int parity, float4* __restrict__ tape) {
+      int n_groups, int n_blocks, int parity, float4* __restrict__ tape, float4* __restrict__ tape_F) {
     const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int b = blockIdx.x; b < n_blocks; b += gridDim.x) {
         const int gi = b * warps + (threadIdx.x >> 5);
@@ -111,6 +111,7 @@ k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T
             tag[gn] = tg & (uint8_t)~TAG_IB;
             hasF = true;
         }
+        if (tape_F) tape_F[gn] = make_float4(fv.x, fv.y, fv.z, ibn ? 1.f : 0.f);
         if (tape) {
             float rho, ux, uy, uz;
             moments_of(g, rho, ux, uy, uz);
@@ -350,39 +351,39 @@ __global__ void k_read(const MemberDev* __restrict__ mem, const T* __restrict__ 
 }
 
 template <typename T>
-static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s, float4* tape) {
+static cudaError_t lbm_t(const DevState& d, int parity, cudaStream_t s, float4* tape, float4* tape_F) {
     const int grid = d.grid_lbm > 0 ? d.grid_lbm : d.lbm_blocks;
     const bool one = d.n_members == 1;
     if (grid > 0) {
         if (one)
             k_lbm<T, true, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
                                                              d.status, d.nodes, d.group_mem, d.n_groups,
-                                                             d.lbm_blocks, parity, tape);
+                                                             d.lbm_blocks, parity, tape, tape_F);
         else
             k_lbm<T, false, false><<<grid, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib, d.face_vel,
                                                               d.status, d.nodes, d.group_mem, d.n_groups,
-                                                              d.lbm_blocks, parity, tape);
+                                                              d.lbm_blocks, parity, tape, tape_F);
     }
     if (d.lbm_bblocks > 0) {
         if (one)
             k_lbm<T, true, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
                                                                      d.face_vel, d.status, d.bnodes, d.bgroup_mem,
-                                                                     d.n_bgroups, d.lbm_bblocks, parity, tape);
+                                                                     d.n_bgroups, d.lbm_bblocks, parity, tape, tape_F);
         else
             k_lbm<T, false, true><<<d.lbm_bblocks, d.threads, 0, s>>>(d.h_mem[0], d.mem, (T*)d.f, d.tag, d.fib,
                                                                       d.face_vel, d.status, d.bnodes, d.bgroup_mem,
-                                                                      d.n_bgroups, d.lbm_bblocks, parity, tape);
+                                                                      d.n_bgroups, d.lbm_bblocks, parity, tape, tape_F);
     }
     return cudaGetLastError();
 }
 
 int lbm_max_threads() { return LBM_THREADS; }
 
-cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou) {
+cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou, float4* tape_F) {
     switch (d.storage) {
-        case 1: return lbm_t<__half>(d, parity, s, tape_rhou);
-        case 2: return lbm_t<__nv_bfloat16>(d, parity, s, tape_rhou);
-        default: return lbm_t<float>(d, parity, s, tape_rhou);
+        case 1: return lbm_t<__half>(d, parity, s, tape_rhou, tape_F);
+        case 2: return lbm_t<__nv_bfloat16>(d, parity, s, tape_rhou, tape_F);
+        default: return lbm_t<float>(d, parity, s, tape_rhou, tape_F);
     }
 }
 

@@ -110,7 +110,8 @@ def sweep_member(k, seed=SEED):
     (seed, k): a bifurcation with dims from 128..384 x 48..128 x 32..96 in
     multiples of 8, half-angle U[20, 80], occlusion U[0.3, 0.9], Ca
     log-U[1e-3, 1e-1], junction rounding U[0, 10]; one capsule (642 v if
-    d <= 20 lu else 2562 v) near the inlet; 5k steps."""
+    d <= 20 lu else 2562 v) near the inlet, the junction at 0.4 nx or, for a
+    long capsule, d + 12 lu from the inlet; 5k steps."""
     rng = Ms.SplitMix64((seed << 20) + k)
     nx = 8 * rng.randint(16, 48)
     ny = 8 * rng.randint(6, 16)
@@ -122,7 +123,9 @@ def sweep_member(k, seed=SEED):
     D = float(round(0.75 * min(ny, nz)))
     d = occ * D
     u_max = 0.02
-    g = G.bifurcation(nx, ny, nz, D, th, rj, u_max=u_max)
+    # the junction lies past the capsule's start position (it starts whole
+    # inside the main duct, d/2 + 4 from the inlet)
+    g = G.bifurcation(nx, ny, nz, D, th, rj, u_max=u_max, x_junction=max(0.4 * nx, d + 12.0))
     nv = 642 if d <= 20.0 else 2562
     c = (d / 2 + 4.0, g.info["yc"], g.info["zc"])
     V, T = Ms.sphere_mesh(nv, d, c, rng)

@@ -33,7 +33,7 @@ def test_adjoint_gradients_match_the_oracle(steps, ckpt):
     J0, gu0, gq0 = A.gradient(lat, f, steps, A.Objective(lo, hi, d), g.links["dq"].astype(np.float64))
     s = gpu_for(case(g))
     s.step(25)
-    J1, gu1, gq1 = s.adjoint(steps, lo, hi, d, ckpt_every=ckpt)
+    J1, gu1, gq1 = s.adjoint_flow(steps, lo, hi, d, ckpt_every=ckpt)
     assert J1 == pytest.approx(J0, rel=1e-5)
     assert gu1 == pytest.approx(gu0, rel=1e-3)
     assert gq1 == pytest.approx(gq0, rel=1e-3)
@@ -46,7 +46,7 @@ def test_adjoint_leaves_the_forward_state_of_plain_steps():
     a = gpu_for(case(g))
     b = gpu_for(case(g))
     a.step(7)
-    a.adjoint(11, (2, 0, 0), (24, 20, 16), (1.0, 0.0, 0.0), ckpt_every=4)
+    a.adjoint_flow(11, (2, 0, 0), (24, 20, 16), (1.0, 0.0, 0.0), ckpt_every=4)
     b.step(18)
     assert np.array_equal(a.read_populations(), b.read_populations())
 
@@ -59,5 +59,5 @@ def test_adjoint_rejects_capsules_and_16_bit_storage():
     V, T = Ms.sphere_mesh(162, 6.0, (8.0, g.info["yc"], g.info["zc"]), Ms.SplitMix64(1))
     for s in (gpu_for(case(g, capsules=[W._capsule(V, T, Ca=0.05)])), gpu_for(case(g), "f16")):
         with pytest.raises(IBLError) as e:
-            s.adjoint(2, (0, 0, 0), (4, 4, 4), (1.0, 0.0, 0.0))
+            s.adjoint_flow(2, (0, 0, 0), (4, 4, 4), (1.0, 0.0, 0.0))
         assert e.value.status == ERR_STATE

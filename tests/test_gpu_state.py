@@ -64,3 +64,23 @@ def test_snapshot_of_another_set_up_is_rejected():
     with pytest.raises(IBLError) as e:
         b.load_state(blob)
     assert e.value.status == ERR_ARG
+
+
+def test_device_capsule_diagnostics_match_the_host_ones():
+    """ibl_read_capsules (FP64 sums on the device, one read for all capsules)
+    equals ibl_read_capsule (FP64 sums of the downloaded vertices) for every
+    capsule of a context, after some steps."""
+    from paper_2207_06043_gb300 import meshes as Ms
+    from paper_2207_06043_gb300 import workloads as W
+    g = G.periodic_box(40, 24, 20)
+    caps = []
+    for k, ctr in enumerate([(8.0, 10.0, 10.0), (20.0, 12.0, 9.5), (31.0, 11.0, 10.5)]):
+        V, T = Ms.sphere_mesh(642 if k == 1 else 162, 8.0, ctr, Ms.SplitMix64(30 + k))
+        caps.append(W._capsule(V, T, Ca=0.05, vel0=(0.01, 0.002 * k, 0.0)))
+    s = gpu_for(case(g, tau=0.9, capsules=caps))
+    s.step(25)
+    dev = s.read_capsules(3)
+    for k in range(3):
+        host = s.read_capsule(k)
+        for key in ("centroid", "volume", "area", "dS", "taylor_D", "max_stretch", "semi_axes", "velocity"):
+            np.testing.assert_allclose(dev[k][key], host[key], rtol=1e-9, atol=1e-12, err_msg=key)

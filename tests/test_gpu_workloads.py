@@ -142,3 +142,104 @@ def test_throughput_workload_full_size_sampled_step():
             val = L.bouzidi_value(q, fb[ib], f1[ib], f2[ib], fb[i], f1[i], ok1, ok2)
             worst = max(worst, abs(g1[i, nd] - (float(val) - L.W[i])))
     assert worst <= 2e-7, worst
+
+
+def _face_slab_check(geom, face, tau, g1):
+    """The Zou-He rule of one box face on the GPU's own populations: the
+    3-node slab along the face becomes an oracle lattice holding only that
+    face's condition; the populations entering from outside are blanked and
+    refilled by the oracle's rule from the known ones (streamed and wall
+    values as the GPU left them).  Returns (face nodes, largest difference)."""
+    nx, ny, nz = geom.nx, geom.ny, geom.nz
+    ax, side = face // 2, face % 2
+    dims = [nx, ny, nz]
+    sub = list(dims)
+    sub[ax] = 3
+    lo = 0 if side == 0 else dims[ax] - 3
+    zz, yy, xx = np.meshgrid(np.arange(sub[2]), np.arange(sub[1]), np.arange(sub[0]), indexing="ij")
+    cc = [xx.reshape(-1), yy.reshape(-1), zz.reshape(-1)]
+    cc[ax] = cc[ax] + lo
+    full = cc[0] + nx * (cc[1] + ny * cc[2])
+    faces = [None] * 6
+    faces[face] = geom.faces[face]
+    lat = L.Lattice(sub[0], sub[1], sub[2], tau, geom.tag[full], dict(node=[], dir=[], q=[]), faces, geom.periodic)
+    nodes, _ = lat.face_nodes(face)
+    f = g1[:, full].astype(np.float64) + L.W[:, None]
+    unk = np.nonzero(L.E @ L.FACE_NORMALS[face] < 0)[0]
+    for k in unk:
+        f[k, nodes] = np.nan
+    lat.zou_he(f)
+    exp = f[np.ix_(unk, nodes)] - L.W[unk][:, None]
+    got = g1[np.ix_(unk, full[nodes])].astype(np.float64)
+    return nodes.size, float(np.abs(exp - got).max()) if nodes.size else 0.0
+
+
+def test_throughput_workload_full_size_ib_structure_and_faces():
+    """512x192x128, 64 capsules (163,968 markers), in the bench launch shape:
+    one GPU step from its own state after three steps against the oracle's
+    operators applied to that same state (populations, x(t), x(t - dt), vertex
+    velocities):
+      - every vertex's x(t + dt) and velocity: the oracle's marker stencils
+        (u_v,0 = U_l), probe stresses, membrane, volume and repulsion forces
+        and Verlet update (Eqs. uLag .. verletPosC), within 1e-6 lu;
+      - the populations streamed into sampled IB-shell nodes: the oracle's
+        spreading (Eq. bodyforce) of every marker's force and the collision
+        with it, within 2e-7;
+      - every population the Zou-He rule writes at every node of every
+        inlet and outlet face, within 2e-7."""
+    from types import SimpleNamespace
+    from oracle import sim
+    c = W.throughput_case()
+    g = c["geometry"]
+    s = W.make_solver(c)
+    s.set_launch(128, 0)
+    s.step(3)
+    nvs = [len(cap["verts"]) for cap in c["capsules"]]
+    g0 = s.read_populations()
+    st0 = [s.read_capsule_state(k, nv) for k, nv in enumerate(nvs)]
+    s.step(1)
+    g1 = s.read_populations()
+    st1 = [s.read_capsule_state(k, nv) for k, nv in enumerate(nvs)]
+    s.close()
+    # the oracle's coupled operators on the GPU's pre-step state
+    lat = SimpleNamespace(nx=g.nx, ny=g.ny, nz=g.nz, N=g.n_nodes, tau=c["tau"], periodic=g.periodic,
+                          fluid=g.tag == 0)
+    o = sim.Simulation.__new__(sim.Simulation)
+    o.lat, o.u_max, o.t, o.damaged, o.last = lat, c["u_max"], 0, False, {}
+    o.f = g0.astype(np.float64) + L.W[:, None]
+    o.bodies = []
+    for cap, st in zip(c["capsules"], st0):
+        b = sim.Body(cap["verts"], cap["tris"], cap["params"], c["tau"], cap.get("vel0"))
+        b.x, b.x_prev, b.vel = st["x"].copy(), st["x_prev"].copy(), st["vel"].copy()
+        o.bodies.append(b)
+    f_ib, per = o.ib_force()
+    o.update(o.f, per, o.structure(o.f, per))
+    dx = max(float(np.abs(b.x - st["x"]).max()) for b, st in zip(o.bodies, st1))
+    dv = max(float(np.abs(b.vel - st["vel"]).max()) for b, st in zip(o.bodies, st1))
+    # streamed populations of sampled shell nodes whose 19 upstream nodes are fluid
+    nx, ny, nz = g.nx, g.ny, g.nz
+    n = np.arange(g.n_nodes)
+    X, Y, Z = n % nx, (n // nx) % ny, n // (nx * ny)
+    shell = np.nonzero((np.abs(f_ib).sum(axis=1) > 0) & (X > 1) & (X < nx - 2) & (Y > 1) & (Y < ny - 2)
+                       & (Z > 1) & (Z < nz - 2))[0]
+    fluid = g.tag == 0
+    srcs = [shell - (L.E[i, 0] + nx * (L.E[i, 1] + ny * L.E[i, 2])) for i in range(19)]
+    allf = np.all([fluid[sr] for sr in srcs], axis=0)
+    rng = np.random.default_rng(3)
+    pick = rng.choice(shell[allf], 4000, replace=False)
+    worst_ib = 0.0
+    for i in range(19):
+        src = pick - (L.E[i, 0] + nx * (L.E[i, 1] + ny * L.E[i, 2]))
+        fs = L.collide(o.f[:, src], f_ib[src], c["tau"])
+        worst_ib = max(worst_ib, float(np.abs(g1[i, pick] - (fs[i] - L.W[i])).max()))
+    # Zou-He faces
+    face_err = {}
+    for face in range(6):
+        if g.faces[face].kind != 0:
+            face_err[face] = _face_slab_check(g, face, c["tau"], g1)
+    print(f"full-size one step: vertices {dx:.2e}, velocities {dv:.2e}, shell populations {worst_ib:.2e} "
+          f"({len(pick)} nodes), faces {face_err}")
+    assert dx <= 1e-6 and dv <= 1e-6, (dx, dv)
+    assert worst_ib <= 2e-7, worst_ib
+    assert sum(nf for nf, _ in face_err.values()) > 1000
+    assert all(e <= 2e-7 for _, e in face_err.values()), face_err

@@ -95,3 +95,29 @@ def test_adjoint_gradient_matches_central_differences(setup):
     assert gu == pytest.approx(fd_u, rel=1e-6)
     assert gq == pytest.approx(fd_q, rel=1e-6)
     assert abs(gu) > 1e-6 and abs(gq) > 1e-9
+
+
+def _capsule_case():
+    from paper_2207_06043_gb300 import meshes as Ms
+    from paper_2207_06043_gb300 import workloads as W
+    g = G.bifurcation(40, 20, 16, 10.0, 45.0, 3.0, u_max=0.03, with_dq=True)
+    V, T = Ms.sphere_mesh(162, 7.0, (9.0, g.info["yc"] + 0.4, g.info["zc"] - 0.3), Ms.SplitMix64(4))
+    return dict(geometry=g, tau=0.8, u_max=0.03, capsules=[W._capsule(V, T, Ca=0.05, u_ref=0.03)])
+
+
+def test_coupled_capsule_derivative_matches_central_differences():
+    """The derivative of J = D + 0.5 (y_c - y_sym) of a soft capsule after 30
+    coupled steps (IB, membrane, probes, Verlet, lattice with BFL and Zou-He)
+    with respect to Ca, u_max and the junction radius, taken by the complex
+    step through the whole oracle run, against central differences of the
+    oracle with h = 1e-4 relative: agreement to 1e-6 relative."""
+    c = _capsule_case()
+    steps, yc = 30, c["geometry"].info["yc"]
+    J, g_ca, g_um, g_rj = A.coupled_gradient(c, steps, 1.0, 0.5, yc)
+    for kw, p, g, scale in (("dCa", 0.05, g_ca, 1.0), ("ds_u", 1.0, g_um, 1.0 / 0.03), ("ds_q", 1.0, g_rj, 1.0)):
+        h = 1e-4 * p
+        jp = A.coupled_run(c, steps, 1.0, 0.5, yc, **{kw: h})[0]
+        jm = A.coupled_run(c, steps, 1.0, 0.5, yc, **{kw: -h})[0]
+        fd = (jp - jm) / (2 * h) * scale
+        assert abs(fd - g) <= 1e-6 * abs(g), (kw, fd, g)
+    assert g_ca != 0.0 and g_um != 0.0 and g_rj != 0.0

@@ -254,3 +254,50 @@ def test_fixed_sphere_drag_matches_stokes_with_hasimoto_correction():
     assert abs(ratios[-1] - ratios[-2]) < 3e-3 * ratios[-1], ratios
     assert 1.0 < ratios[-1] < 1.15, ratios
     assert abs(o.bodies[0].xc[0] - (c0 + 0.1)) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Explicit stability of the membrane update (Eqs. verletPos .. verletPosC)
+# ---------------------------------------------------------------------------
+def _stiffness_kappa(rest, X0, iters=120):
+    """lambda_max of the Hessian of the stretch + bend energy at rest, over the
+    vertex mass (power iteration on central differences of the forces)."""
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(X0.shape)
+    v /= np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        h = 1e-6
+        Fp = membrane.stretch_forces(X0 + h * v, rest) + membrane.bending_forces(X0 + h * v, rest)
+        Fm = membrane.stretch_forces(X0 - h * v, rest) + membrane.bending_forces(X0 - h * v, rest)
+        Hv = -(Fp - Fm) / (2 * h)
+        lam = float((v * Hv).sum())
+        v = Hv / np.linalg.norm(Hv)
+    return lam / rest.mv
+
+
+def test_membrane_update_is_stable_below_kappa_0_8():
+    """Without fluid (u_v,0 = 0) the Verlet update of Eqs. verletPos ..
+    verletPosC is x' = (1/2 - 5/4 kappa) x + x_prev / 2 for a mode of
+    stiffness lambda over the vertex mass, kappa = lambda / m_v: its roots
+    leave the unit circle through -1 at kappa = 4/5.  A perturbed capsule at
+    kappa_max = 0.7 stays bounded over 400 steps and one at 0.9 grows by
+    orders of magnitude (Ca chosen from the measured kappa_max, which scales
+    as 1/Ca)."""
+    from paper_2207_06043_gb300 import meshes as Ms
+    X0, T = Ms.sphere_mesh(162, 8.0, (0.0, 0.0, 0.0), Ms.SplitMix64(2))
+    base = membrane.CapsuleRest(X0, T, dict(Ca=0.01, Eb=0.001, kv=0.0), 0.8)
+    k_base = _stiffness_kappa(base, X0)
+    amp = {}
+    for target in (0.7, 0.9):
+        rest = membrane.CapsuleRest(X0, T, dict(Ca=0.01 * k_base / target, Eb=0.001, kv=0.0), 0.8)
+        rng = np.random.default_rng(1)
+        x = X0 + 1e-4 * rng.standard_normal(X0.shape)
+        xp = x.copy()
+        for _ in range(400):
+            F = membrane.stretch_forces(x, rest) + membrane.bending_forces(x, rest)
+            x_new, _ = sim.verlet(x, xp, np.zeros_like(x), F, rest.mv)
+            xp, x = x, x_new
+        amp[target] = float(np.abs(x - X0 - (x - X0).mean(axis=0)).max())
+    assert amp[0.7] < 1e-3, amp
+    assert amp[0.9] > 1e2 * amp[0.7], amp
