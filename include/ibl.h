@@ -163,7 +163,8 @@ ibl_status ibl_read_capsule(ibl_ctx* ctx, int32_t id, ibl_capsule_stats* stats,
 /* FP64 diagnostics of all n capsules of member `member` (n must equal the
  * member's capsule count), computed on the device and read back in one copy
  * of 18 doubles per capsule: the same quantities as ibl_read_capsule (volume
- * moments from the tetrahedra fanned from each capsule's first vertex). */
+ * moments from the tetrahedra fanned from each capsule's first vertex; the
+ * largest stretch divides by the FP32 rest lengths of the damage rule). */
 ibl_status ibl_read_capsules(ibl_ctx* ctx, int32_t member, ibl_capsule_stats* stats, int32_t n);
 
 /* Per-vertex state of a capsule of member 0: positions x(t) and x(t-dt),

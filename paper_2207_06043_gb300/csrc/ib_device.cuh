@@ -105,8 +105,8 @@ __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy,
 // m33) in precision R, then the first ROWS rows of its inverse.  Returns the
 // pivots relative to the first one in `rel` (min of d1, d2, d3 over d0) and
 // false when the matrix fails the singularity test.
-template <int ROWS, typename R>
-__device__ __forceinline__ bool ldlt_solve(const float (&m)[10], float (&inv)[4][4], R& rel) {
+template <int ROWS, typename R, typename MT>
+__device__ __forceinline__ bool ldlt_solve(const MT (&m)[10], float (&inv)[4][4], R& rel) {
     const R a00 = m[0], a10 = m[1], a20 = m[2], a30 = m[3], a11 = m[4], a21 = m[5], a31 = m[6], a22 = m[7],
             a32 = m[8], a33 = m[9];
     const R d0 = a00;
@@ -214,11 +214,11 @@ struct MlsG {
 
 // The FP64 solve of a near-singular or FP64-only stencil, out of line so that
 // its registers do not count against the common FP32 path.
-struct Moments { float m[10]; };
+struct Moments64 { double m[10]; };
 struct Rows { float v[4][4]; int good; };
 
 template <int ROWS>
-__device__ __noinline__ Rows ldlt_solve64(Moments mm) {
+__device__ __noinline__ Rows ldlt_solve64(Moments64 mm) {
     Rows out;
     double rel;
     out.good = ldlt_solve<ROWS, double>(mm.m, out.v, rel) ? 1 : 0;
@@ -275,9 +275,30 @@ __device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* _
         good = ldlt_solve<ROWS, float>(m, M.inv, rel) && rel >= FP32_PIVOT_FLOOR;
     }
     if (!good) {
-        Moments mm;
+        // The moments again, summed in FP64 from the same weights and
+        // offsets: the offsets of support nodes in one plane (or on one line)
+        // are equal floats, so the pivots such a support makes vanish stay at
+        // FP64 rounding and the singularity test decides as an FP64 fit does
+        // (FP32 sums leave them near 1e-8 of A_00).  good is the same in the
+        // GL lanes of the group, which alone take part in the sums.
+        const unsigned gmask = mask & (((1u << GL) - 1u) << ((threadIdx.x & 31) & ~(GL - 1)));
+        Moments64 mm;
 #pragma unroll
-        for (int i = 0; i < 10; ++i) mm.m[i] = m[i];
+        for (int i = 0; i < 10; ++i) mm.m[i] = 0.0;
+#pragma unroll
+        for (int j = 0; j < GS; ++j) {
+            const int k = r + GL * j;
+            if (k >= 27) continue;
+            const double w = M.W[j];
+            const double rx = (double)(M.ox + sdx(k)), ry = (double)(M.oy + sdy(k)), rz = (double)(M.oz + sdz(k));
+            mm.m[0] += w; mm.m[1] += w * rx; mm.m[2] += w * ry; mm.m[3] += w * rz;
+            mm.m[4] += w * rx * rx; mm.m[5] += w * rx * ry; mm.m[6] += w * rx * rz;
+            mm.m[7] += w * ry * ry; mm.m[8] += w * ry * rz; mm.m[9] += w * rz * rz;
+        }
+#pragma unroll
+        for (int o = 1; o < GL; o <<= 1)
+#pragma unroll
+            for (int i = 0; i < 10; ++i) mm.m[i] += __shfl_xor_sync(gmask, mm.m[i], o);
         const Rows rr = ldlt_solve64<ROWS>(mm);
         good = rr.good != 0;
 #pragma unroll

@@ -69,7 +69,8 @@ def test_snapshot_of_another_set_up_is_rejected():
 def test_device_capsule_diagnostics_match_the_host_ones():
     """ibl_read_capsules (FP64 sums on the device, one read for all capsules)
     equals ibl_read_capsule (FP64 sums of the downloaded vertices) for every
-    capsule of a context, after some steps."""
+    capsule of a context, after some steps, to FP64 rounding (the largest
+    stretch to the FP32 rounding of the rest lengths)."""
     from paper_2207_06043_gb300 import meshes as Ms
     from paper_2207_06043_gb300 import workloads as W
     g = G.periodic_box(40, 24, 20)
@@ -82,5 +83,7 @@ def test_device_capsule_diagnostics_match_the_host_ones():
     dev = s.read_capsules(3)
     for k in range(3):
         host = s.read_capsule(k)
-        for key in ("centroid", "volume", "area", "dS", "taylor_D", "max_stretch", "semi_axes", "velocity"):
+        for key in ("centroid", "volume", "area", "dS", "taylor_D", "semi_axes", "velocity"):
             np.testing.assert_allclose(dev[k][key], host[key], rtol=1e-9, atol=1e-12, err_msg=key)
+        # the device divides by the FP32 rest lengths that the damage rule uses
+        np.testing.assert_allclose(dev[k]["max_stretch"], host["max_stretch"], rtol=1e-7, err_msg="max_stretch")
