@@ -32,7 +32,7 @@ BYTES_PER_UPDATE = {"f32": 152, "f16": 76, "bf16": 76}
 # with the profile summaries), with the hash of the lattice kernel's sources
 # (lbm.cu, lbm_device.cuh) it was captured from: any change to them makes the
 # figure stale, and the bench then reports null until it is captured again.
-LBM_TRAFFIC = {("throughput", "f32"): (623.4e6, "dabdfdcf9e783efe")}
+LBM_TRAFFIC = {("throughput", "f32"): (623.1e6, "5aa954892ee66c37")}
 LBM_SOURCES = ("lbm.cu", "lbm_device.cuh")
 CPU_SAMPLE_X = 64          # x-slab of the workload the oracle runs on (cpu_baseline)
 REF_SAMPLE_X = 40          # slab of the reference arm (its first layer of capsules)
@@ -294,6 +294,36 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def cpu_survey(args):
+    """--cpu-survey: the FP64 oracle on the host cores over the standard
+    configurations, single-threaded and one independent copy per core at
+    once (throughput): the small bifurcation in full (500 steps), windows of
+    the deformable-capsule, batched-sweep (member 0), adjoint and throughput
+    (its x-slab [0, 64) with 21 capsules) configurations.  No GPU is used."""
+    from paper_2207_06043_gb300 import workloads as W
+    nproc = os.cpu_count() or 1
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = None
+    plan = [("small bifurcation 96x32x32, rigid sphere (full run)", W.bifurcation_small(), 500, 1.0e8),
+            ("deformable capsule 256x96x64", W.deformable_capsule(), args.survey_window, 2.0e9),
+            ("batched sweep member 0", W.sweep_member(0), args.survey_window, 2.0e9),
+            ("adjoint 192x64x48 with capsule", W.adjoint_case(), 2 * args.survey_window, 1.0e9),
+            ("throughput x-slab [0,64), 21 capsules", cpu_sample_case(W.throughput_case()), 3, 2.0e9)]
+    out = {"nproc": nproc, "cpu_model": cpu_model(), "runs": []}
+    for name, case, steps, mem in plan:
+        case["geometry"].sdf = None
+        m1, w1, nf = oracle_throughput(case, steps, 1)
+        procs = nproc if avail is None else max(1, min(nproc, int(avail // mem)))
+        mn, wn, _ = oracle_throughput(case, steps, procs)
+        out["runs"].append({"config": name, "fluid_nodes": nf, "steps": steps, "single_thread_mlups": m1,
+                            "single_thread_s": w1, "all_cores_mlups": mn, "all_cores_procs": procs,
+                            "all_cores_s": wn})
+        print(json.dumps({"progress": out["runs"][-1]}), file=sys.stderr, flush=True)
+    print(json.dumps({"cpu_survey": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,9 +331,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="throughput", choices=sorted(WORKLOADS) + ["sweep"])
+    ap.add_argument("--workload", default="throughput", choices=sorted(WORKLOADS) + ["sweep", "deformable"])
+    ap.add_argument("--traj-out", default=None, help="deformable campaign: write the trajectories here (JSON)")
     ap.add_argument("--members", type=int, default=64, help="lattices of the batched sweep workload")
     ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cpu-survey", action="store_true", help="time the oracle on the host over the configurations")
+    ap.add_argument("--survey-window", type=int, default=20, help="steps of the survey's windows")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
@@ -324,8 +357,16 @@ def main():
     if args.impl == "reference":
         reference_arm(args, rank)
         return
+    if args.cpu_survey:
+        if rank == 0:
+            cpu_survey(args)
+        return
     if args.workload == "sweep":
         sweep_bench(args, rank, world, local)
+        return
+    if args.workload == "deformable":
+        if rank == 0:
+            deformable_campaign(args, local)
         return
 
     import torch
@@ -706,6 +747,89 @@ def sweep_bench(args, rank, world, local):
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def deformable_campaign(args, local):
+    """--workload deformable: the deformable-capsule configuration in full:
+    half-angles 30, 45 and 60 deg x Ca 0.005, 0.01 and 0.05 (256x96x64 duct,
+    D = 48, junction rounding 8 lu, capsule d = 36 of 2562 vertices, Re = 10),
+    each stored as FP32, FP16 and BF16 (FP32 arithmetic), --steps steps
+    (default 20000 here) with the capsule's FP64 diagnostics read every 100
+    steps.  Prints one JSON line: MLUPS over all runs and, per run, the final
+    centroid, branch offset, Taylor D (final and largest), the largest volume
+    drift, and for the 16-bit forms the largest centroid and D deviation from
+    the FP32 run over the trajectory."""
+    import torch
+    from paper_2207_06043_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    torch.zeros(1, device="cuda")
+    steps = args.steps
+    every = 100
+    runs = []
+    traj_all = {}
+    total_upd, total_ms = 0, 0.0
+    stream = torch.cuda.current_stream()
+    for th in (30.0, 45.0, 60.0):
+        for Ca in (0.005, 0.01, 0.05):
+            case = W.deformable_capsule(th, Ca)
+            nf = fluid_updates(case)
+            yc = case["geometry"].info["yc"]
+            per_storage = {}
+            for st in ("f32", "f16", "bf16"):
+                s = W.make_solver(case, storage=st)
+                s.step(0)
+                V0 = s.read_capsules(1)[0]["volume"]
+                traj = []
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                done_total = 0
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(steps // every):
+                    done, _ = s.step(every, allow_damage=True)
+                    done_total += done
+                    c = s.read_capsules(1)[0]
+                    traj.append((done_total, *c["centroid"].tolist(), c["volume"], c["taylor_D"], c["dS"],
+                                 c["max_stretch"]))
+                    if done < every:
+                        break
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                s.close()
+                total_upd += nf * done_total
+                total_ms += ms
+                per_storage[st] = np.array(traj)
+            t32 = per_storage["f32"]
+            rec = {"half_angle": th, "Ca": Ca, "fluid_nodes": nf}
+            for st, t in per_storage.items():
+                last = t[-1]
+                r = {"steps_done": int(last[0]), "centroid": [round(v, 6) for v in last[1:4]],
+                     "branch_offset": round(last[2] - yc, 6), "taylor_D_final": round(last[5], 6),
+                     "taylor_D_max": round(float(t[:, 5].max()), 6),
+                     "volume_drift_max": float(np.abs(t[:, 4] / V0 - 1.0).max()),
+                     "dS_max": round(float(t[:, 6].max()), 6), "max_stretch_max": round(float(t[:, 7].max()), 6)}
+                if st != "f32":
+                    n = min(len(t), len(t32))
+                    r["centroid_dev_vs_f32_max"] = float(np.abs(t[:n, 1:4] - t32[:n, 1:4]).max())
+                    r["taylor_D_dev_vs_f32_max"] = float(np.abs(t[:n, 5] - t32[:n, 5]).max())
+                rec[st] = r
+                traj_all[f"th{th:g}_Ca{Ca:g}_{st}"] = t.tolist()
+            runs.append(rec)
+            print(json.dumps({"progress": rec}), file=sys.stderr, flush=True)
+    if args.traj_out:
+        with open(args.traj_out, "w") as fh:
+            json.dump({"columns": ["step", "cx", "cy", "cz", "volume", "taylor_D", "dS", "max_stretch"],
+                       "runs": traj_all}, fh)
+    out = {"metric": METRIC, "value": total_upd / (total_ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": 1,
+           "steps": steps, "warmup": 0, "ms_per_step": total_ms / (len(runs) * 3 * steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f16/bf16 storage",
+           "data": "synthetic",
+           "config": {"workload": "deformable capsule 256x96x64, D 48, junction rounding 8 lu, d 36 (2562 v), "
+                                  "Re 10; half-angle x Ca x storage campaign", "stats_every": every,
+                      "note": "value and ms_per_step include the FP64 diagnostics read every 100 steps"},
+           "runs": runs}
+    print(json.dumps(out), flush=True)
 
 
 def e2e_run(case, args, chunk=10):

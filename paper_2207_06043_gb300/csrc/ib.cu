@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
 // One warp per row (y, z) of a capsule's box, lanes along x over the part of
 // the row inside the outer sphere, less the part inside the inner one.
 template <typename T, bool LIN>
-__device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restrict__ fm, float4* __restrict__ macro,
+__device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restrict__ fm, const uint8_t* __restrict__ tag,
+                                           float4* __restrict__ macro,
                                            const int lo[3], const int ext[3], bool radial, float r2_out, float r2_in,
                                            float rcx, float rcy, float rcz, int parity) {
     const int lane = threadIdx.x & 31;
@@ -155,15 +156,16 @@ __device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restri
             if (!LIN && (d.per & 1)) wx = ((wx % d.nx) + d.nx) % d.nx;
             const int X = wx + d.px;
             const int node = X + d.NX * (Y + d.NY * Z);
-            // solid nodes are not skipped: their slots are in the array, and
-            // the stencils never read their moments, so the populations'
-            // loads need not wait on the tag
+            // solid nodes get rho = 0, which the stencils read as "solid"
+            // (their gathers then need no tag); the populations' loads are
+            // issued beside the tag's, so they do not wait on it
+            const bool solid = tag[d.node_off + node] & TAG_SOLID;
             float g[Q];
             if (LIN) load_pre_lin<T>(d, fm, node, parity, g);
             else load_pre<T>(d, fm, node, X, Y, Z, parity, g);
             float rho, ux, uy, uz;
             moments_of(g, rho, ux, uy, uz);
-            macro[d.node_off + node] = make_float4(rho, ux, uy, uz);
+            macro[d.node_off + node] = solid ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(rho, ux, uy, uz);
         }
     }
 }
@@ -205,9 +207,9 @@ __global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ 
     // a lattice with no periodic axis reaches every upstream node at a
     // constant offset (the ghost layer absorbs the steps off the box)
     if (d.per == 0)
-        shell_rows<T, true>(d, fm, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
+        shell_rows<T, true>(d, fm, tag, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
     else
-        shell_rows<T, false>(d, fm, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
+        shell_rows<T, false>(d, fm, tag, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
 }
 
 
@@ -234,14 +236,13 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     if (!valid) return;
     const MemberDev& d = mem[m];
     MlsG M;
-    mls_build_g<1, MARKER_FAST32>(d, tag, P, r, mask, M);
-    float p[GS];
     float4 q[GS];
+    mls_build_g<1, MARKER_FAST32>(d, macro, P, r, mask, M, q);
+    float p[GS];
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
         const int k = r + GL * j;
         p[j] = k >= 27 ? 0.f : (M.fallback < 0 ? mls_row_g(M, 0, j, k) : (M.fallback == k ? 1.f : 0.f));
-        q[j] = p[j] != 0.f ? macro[d.node_off + mls_node_g(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float Ux = 0.f, Uy = 0.f, Uz = 0.f;
 #pragma unroll
@@ -296,13 +297,8 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
     const MemberDev& d = mem[m];
     const double sg = s == 1 ? 1.2 : -1.2;
     MlsG M;
-    mls_build_g<4, PROBE_FAST32>(d, tag, xa + sg * na, r, mask, M);
     float4 q[GS];
-#pragma unroll
-    for (int j = 0; j < GS; ++j) {
-        const int k = r + GL * j;
-        q[j] = (k < 27 && M.W[j] > 0.f) ? macro[d.node_off + mls_node_g(d, M, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    mls_build_g<4, PROBE_FAST32>(d, macro, xa + sg * na, r, mask, M, q);
     float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // rho, then grad u row-major
 #pragma unroll
     for (int j = 0; j < GS; ++j) {

@@ -229,9 +229,31 @@ __device__ __noinline__ Rows ldlt_solve64(Moments64 mm) {
 // each take the FP64 steps (nearest node, offset) for one axis and the group
 // exchanges the results, so that GB300's narrow FP64 pipe does a third of the
 // work it would if every lane took all three axes.
-template <int ROWS, bool FAST32>
-__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double P, int r,
-                                            unsigned mask, MlsG& M) {
+// Fluid support nodes are found from the tag array (the adjoint) or, with
+// MAC, from the moments array of the step, where solid nodes hold rho = 0:
+// then the moments of every support node of the lane are gathered at once
+// into q, with no tag gather before them.
+template <bool MAC>
+struct Support;
+template <>
+struct Support<false> {
+    const uint8_t* tag;
+    __device__ __forceinline__ bool fluid(const MemberDev& d, int node, float4&) const {
+        return node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
+    }
+};
+template <>
+struct Support<true> {
+    const float4* macro;
+    __device__ __forceinline__ bool fluid(const MemberDev& d, int node, float4& q) const {
+        q = node >= 0 ? macro[d.node_off + node] : make_float4(0.f, 0.f, 0.f, 0.f);
+        return q.x > 0.f;
+    }
+};
+
+template <int ROWS, bool FAST32, bool MAC>
+__device__ __forceinline__ void mls_build_impl(const MemberDev& d, Support<MAC> sup, double P, int r, unsigned mask,
+                                               MlsG& M, float4 (&q)[GS]) {
     const double b = floor(P + 0.5);
     const int bi = (int)b;
     const float o = (float)(b - P);
@@ -247,11 +269,12 @@ __device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* _
     for (int j = 0; j < GS; ++j) {
         const int k = r + GL * j;
         float w = 0.f;
+        q[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < 27) {
             const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
             const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
                                       : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
-            const bool fluid = node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
+            const bool fluid = sup.fluid(d, node, q[j]);
             const float rx = M.ox + dx, ry = M.oy + dy, rz = M.oz + dz;
             w = mls_weight(fluid, rx, ry, rz);
             if (w > best) { best = w; bestk = k; }
@@ -307,6 +330,19 @@ __device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* _
             for (int b = 0; b < 4; ++b) M.inv[a][b] = rr.v[a][b];
     }
     M.fallback = good ? -1 : (best > 0.f ? bestk : 27);
+}
+
+template <int ROWS, bool FAST32>
+__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double P, int r,
+                                            unsigned mask, MlsG& M) {
+    float4 q[GS];
+    mls_build_impl<ROWS, FAST32, false>(d, Support<false>{tag}, P, r, mask, M, q);
+}
+
+template <int ROWS, bool FAST32>
+__device__ __forceinline__ void mls_build_g(const MemberDev& d, const float4* __restrict__ macro, double P, int r,
+                                            unsigned mask, MlsG& M, float4 (&q)[GS]) {
+    mls_build_impl<ROWS, FAST32, true>(d, Support<true>{macro}, P, r, mask, M, q);
 }
 
 __device__ __forceinline__ float mls_row_g(const MlsG& M, int row, int j, int k) {

@@ -391,6 +391,94 @@ def bifurcation(nx, ny, nz, D, half_angle_deg=45.0, r_j=0.0, u_max=0.02, x_junct
                          u_max=u_max, x_junction=x_junction, yc=yc, zc=zc, levels=levels))
 
 
+def cylinder_sdf(p0, p1, radius):
+    """Circular-section duct whose axis runs from p0 to p1 (flat ends).  Exact
+    distance of a finite cylinder."""
+    p0 = np.asarray(p0, dtype=np.float64)
+    p1 = np.asarray(p1, dtype=np.float64)
+    axis = p1 - p0
+    length = float(np.linalg.norm(axis))
+    a = axis / length
+    centre = 0.5 * (p0 + p1)
+
+    def f(P):
+        r = P - centre[None, :]
+        s = r @ a
+        radial = np.sqrt(np.maximum((r * r).sum(axis=1) - s * s, 0.0)) - radius
+        axial = np.abs(s) - 0.5 * length
+        ro, ao = np.maximum(radial, 0.0), np.maximum(axial, 0.0)
+        return np.sqrt(ro * ro + ao * ao) + np.minimum(np.maximum(radial, axial), 0.0)
+    return f
+
+
+def circular_bifurcation(d=30.0, half_angle_deg=30.0, smooth=False, u_max=0.003, main_len=6.7, branch_len=5.0,
+                         daughter_ratio=0.7, flat_width=None, margin=3, rho_out=1.0):
+    """The paper's bifurcation (Section "Computational set-up and boundary
+    conditions"): a circular main duct of diameter d along +x, main_len * d
+    long, splitting into two circular daughters of diameter daughter_ratio * d
+    and branch_len * d long at +-half_angle in the x-y plane.  smooth=False
+    joins the three ducts as they are (a sharp cusp between the daughters);
+    smooth=True also fills the tip of the solid cusp, up to where it is
+    flat_width wide (default d / 3), leaving a flat wall across the flow that
+    faces the main duct: the flat-topped junction.  The box encloses the ducts with `margin` solid
+    nodes; the inlet (x = 0) carries the circular Poiseuille profile of peak
+    u_max and every daughter end face is a pressure outlet."""
+    th = math.radians(half_angle_deg)
+    R, r = d / 2.0, daughter_ratio * d / 2.0
+    L0, L1 = main_len * d, branch_len * d
+    span_y = 2.0 * (L1 * math.sin(th) + r * math.cos(th)) + 2.0 * margin
+    ny = int(math.ceil(max(d + 2 * margin, span_y))) + 1
+    nz = int(math.ceil(d)) + 2 * margin + 1
+    yc, zc = (ny - 1) / 2.0, (nz - 1) / 2.0
+    xj = L0
+    nx = int(math.ceil(xj + L1 * math.cos(th) + r * math.sin(th))) + 1
+    far = 2.0 * d
+    main = cylinder_sdf((-far, yc, zc), (xj, yc, zc), R)
+    ducts = []
+    for sgn in (1.0, -1.0):
+        direc = np.array([math.cos(th), sgn * math.sin(th), 0.0])
+        start = np.array([xj, yc, zc]) - R * np.array([1.0, 0.0, 0.0])
+        ducts.append(cylinder_sdf(start, start + (L1 + far) * direc, r))
+    # the inner walls of the two daughters (parallel to their axes, which
+    # start on the main axis at xj - R) meet on the main axis at the cusp; the
+    # solid cusp between them is |y - yc| < (x - x_cusp) tan th
+    x_cusp = xj - R + r / math.sin(th)
+    if flat_width is None:
+        flat_width = d / 3.0
+    x_cut = x_cusp + 0.5 * flat_width / math.tan(th)
+
+    def wedge(P):
+        # the solid cusp from its tip to x_cut, within the daughters' height
+        lateral = np.abs(P[:, 1] - yc) - (P[:, 0] - x_cusp) * math.tan(th)
+        return np.maximum.reduce([lateral * math.cos(th), P[:, 0] - x_cut, (x_cusp - 1.0) - P[:, 0],
+                                  np.abs(P[:, 2] - zc) - r])
+
+    def sdf(Pts):
+        dd = main(Pts)
+        for f in ducts:
+            dd = np.minimum(dd, f(Pts))
+        if smooth:
+            dd = np.minimum(dd, wedge(Pts))
+        return dd
+
+    periodic = (False, False, False)
+    tag, links = voxelise(sdf, nx, ny, nz, periodic)
+    faces = [Face() for _ in range(6)]
+    Y, Z = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nz, dtype=np.float64), indexing="xy")
+    rr2 = ((Y.reshape(-1) - yc) ** 2 + (Z.reshape(-1) - zc) ** 2) / (R * R)
+    mask = face_node_mask(tag, nx, ny, nz, 0)
+    vel = np.zeros((ny * nz, 3), dtype=np.float32)
+    vel[:, 0] = np.where(mask & (rr2 < 1.0), u_max * (1.0 - rr2), 0.0).astype(np.float32)
+    faces[0] = Face(FACE_VELOCITY, 1.0, vel)
+    for f in range(1, 6):
+        if face_node_mask(tag, nx, ny, nz, f).any():
+            faces[f] = Face(FACE_PRESSURE, rho_out, None)
+    return Geometry(nx, ny, nz, periodic, tag, links, faces, sdf,
+                    dict(kind="circular_bifurcation", D=d, half_angle=half_angle_deg, smooth=bool(smooth),
+                         u_max=u_max, x_junction=xj, x_cusp=x_cusp, x_cut=x_cut if smooth else None,
+                         yc=yc, zc=zc))
+
+
 def crop_x(geom: Geometry, x1: int) -> Geometry:
     """The slab 0 <= x < x1 of a geometry whose x axis is not periodic: wall
     links that leave the slab are dropped and the fluid nodes of the cut plane

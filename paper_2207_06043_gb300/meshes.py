@@ -136,3 +136,30 @@ def place_capsules(rng: SplitMix64, n: int, diameter: float, x_range, yc, zc, du
         if all(np.linalg.norm(c - o) >= diameter + min_gap for o in centres):
             centres.append(c)
     return np.array(centres)
+
+
+def fibonacci_sphere(n_vertices: int):
+    """Unit sphere through n_vertices points on the Fibonacci spiral, triangulated
+    as their convex hull (every point is a hull vertex), outward CCW: a closed
+    mesh with any vertex count (2 n - 4 triangles)."""
+    from scipy.spatial import ConvexHull
+    n = int(n_vertices)
+    i = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * i / n
+    phi = math.pi * (3.0 - math.sqrt(5.0)) * i
+    s = np.sqrt(1.0 - z * z)
+    P = np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
+    T = ConvexHull(P).simplices.astype(np.int32)
+    # orient outward: the triangle normal points away from the origin
+    a, b, c = P[T[:, 0]], P[T[:, 1]], P[T[:, 2]]
+    flip = np.einsum("ij,ij->i", np.cross(b - a, c - a), a + b + c) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return P, T
+
+
+def sphere_mesh_n(n_vertices: int, diameter: float, centre, rng: SplitMix64):
+    """Fibonacci sphere of n_vertices vertices, scaled to `diameter`, randomly
+    rotated and placed at `centre`."""
+    V, T = fibonacci_sphere(n_vertices)
+    R = random_rotation(rng)
+    return (V @ R.T) * (0.5 * diameter) + np.asarray(centre, dtype=np.float64)[None, :], T

@@ -146,3 +146,66 @@ def make_solver(case, storage="f32", stream=None):
     for c in case["capsules"]:
         s.add_capsule(c["verts"], c["tris"], vel0=c.get("vel0"), **c["params"])
     return s
+
+
+# ----------------------------------------------------------------------------
+# The paper's experiment campaigns (Section "Results and discussion") on its
+# circular-duct bifurcation: d = 30 lu, daughters 0.7 d, main duct 6.7 d,
+# branches 5 d, tau = 0.75, Eb = 0.001, density ratio 1.1, capsules released
+# at 1.16 d from the inlet on the duct axis.  The paper runs at Re = 0.01
+# (u_max = 2.8e-5 lu, some 10^7 steps per passage); these builders take Re as
+# a parameter (default 1, the Stokes-like regime at a cost of about 10^5
+# steps per passage).
+# ----------------------------------------------------------------------------
+PAPER_D = 30.0
+PAPER_TAU = 0.75
+PAPER_N_MARKERS = {1.0 / 3.0: 325, 0.5: 485, 2.0 / 3.0: 645, 5.0 / 6.0: 785}
+
+
+def paper_geometry(half_angle_deg=30.0, smooth=False, Re=1.0):
+    nu = (PAPER_TAU - 0.5) / 3.0
+    u_max = Re * nu / PAPER_D
+    return G.circular_bifurcation(PAPER_D, half_angle_deg, smooth=smooth, u_max=u_max), u_max
+
+
+def _paper_markers(dp_ratio):
+    for k, n in PAPER_N_MARKERS.items():
+        if abs(k - dp_ratio) < 1e-9:
+            return n
+    return int(round(325 + (785 - 325) * (dp_ratio - 1.0 / 3.0) / 0.5))
+
+
+def paper_single_capsule(half_angle_deg=30.0, smooth=False, dp_ratio=2.0 / 3.0, Ca=0.05, Re=1.0, seed=SEED):
+    """One soft capsule of diameter dp_ratio d (n_L markers as the paper lists
+    them: 325, 485, 645, 785 for d_p/d = 1/3, 1/2, 2/3, 5/6) released at
+    1.16 d from the inlet on the axis."""
+    g, u_max = paper_geometry(half_angle_deg, smooth, Re)
+    dp = dp_ratio * PAPER_D
+    V, T = Ms.sphere_mesh_n(_paper_markers(dp_ratio), dp, (1.16 * PAPER_D, g.info["yc"], g.info["zc"]),
+                            Ms.SplitMix64(seed))
+    return dict(name=f"paper bifurcation th={half_angle_deg:g} {'smooth' if smooth else 'sharp'}, d_p/d="
+                     f"{dp_ratio:.3f}, Ca={Ca:g}, Re={Re:g}",
+                geometry=g, tau=PAPER_TAU, u_max=u_max,
+                capsules=[_capsule(V, T, Ca=Ca, u_ref=u_max)], steps=int(40 * PAPER_D / u_max))
+
+
+def paper_train(half_angle_deg=30.0, smooth=False, Ca=0.01, kinds=("soft", "soft", "soft"), Re=1.0, seed=SEED):
+    """Three bodies of d_p = 2/3 d in a row along the axis, centres 0.85 d apart,
+    the last one (nearest the inlet) at 1.16 d: "soft" capsules (645 markers)
+    or "rigid" spheres of diameter d_p / 2 with the same density (325
+    markers), listed from the last to the leading one."""
+    g, u_max = paper_geometry(half_angle_deg, smooth, Re)
+    dp = 2.0 / 3.0 * PAPER_D
+    rng = Ms.SplitMix64(seed)
+    caps = []
+    for k, kind in enumerate(kinds):
+        c = ((1.16 + 0.85 * k) * PAPER_D, g.info["yc"], g.info["zc"])
+        if kind == "soft":
+            V, T = Ms.sphere_mesh_n(645, dp, c, rng)
+            caps.append(_capsule(V, T, Ca=Ca, u_ref=u_max))
+        else:
+            V, T = Ms.sphere_mesh_n(325, 0.5 * dp, c, rng)
+            caps.append(_capsule(V, T, rigid=True))
+    return dict(name=f"paper bifurcation th={half_angle_deg:g} {'smooth' if smooth else 'sharp'}, train "
+                     f"{'/'.join(kinds)}, Ca={Ca:g}, Re={Re:g}",
+                geometry=g, tau=PAPER_TAU, u_max=u_max, capsules=caps, steps=int(40 * PAPER_D / u_max))
