@@ -309,7 +309,7 @@ def cpu_survey(args):
     plan = [("small bifurcation 96x32x32, rigid sphere (full run)", W.bifurcation_small(), 500, 1.0e8),
             ("deformable capsule 256x96x64", W.deformable_capsule(), args.survey_window, 2.0e9),
             ("batched sweep member 0", W.sweep_member(0), args.survey_window, 2.0e9),
-            ("adjoint 192x64x48 with capsule", W.adjoint_case(), 2 * args.survey_window, 1.0e9),
+            ("adjoint 192x64x48 with capsule", W.adjoint_case(), args.survey_window, 1.0e9),
             ("throughput x-slab [0,64), 21 capsules", cpu_sample_case(W.throughput_case()), 3, 2.0e9)]
     out = {"nproc": nproc, "cpu_model": cpu_model(), "runs": []}
     for name, case, steps, mem in plan:
@@ -336,7 +336,7 @@ def main():
     ap.add_argument("--members", type=int, default=64, help="lattices of the batched sweep workload")
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--cpu-survey", action="store_true", help="time the oracle on the host over the configurations")
-    ap.add_argument("--survey-window", type=int, default=20, help="steps of the survey's windows")
+    ap.add_argument("--survey-window", type=int, default=50, help="steps of the survey's windows")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")

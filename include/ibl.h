@@ -327,6 +327,34 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
 #define IBL_NOALLOC_MAX_NODES (1 << 20)
 ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, float* u);
 
+/* Marker-based tagging of a fixed wall (Section "Boundary conditions on fixed
+ * bodies", Eq. qbouzidi): the wall is a triangular mesh verts[3*n_verts]
+ * (FP64, lattice units) / tris[3*n_tris] (vertex indices) whose triangle
+ * centroids are its markers.  On a box of nx*ny*nz nodes (periodic[3]
+ * nonzero: the axis wraps; may be NULL):
+ *   - a node whose cell (the unit cube centred on it: the node floor(c + 1/2)
+ *     per axis) holds a marker is solid; markers off a non-periodic box are
+ *     dropped;
+ *   - tag_in[N] (optional, 0 fluid / 1 solid) marks nodes solid beforehand;
+ *   - every node that is not solid and has a solid node at x + e_i gets the
+ *     wall link (node, i) with q = |x_b - x_L| / |e_i|, x_L the marker of the
+ *     solid cell nearest to x_b, 1/2 when that cell holds no marker, clipped
+ *     to [1e-6, 1] and rounded to FP32 once (distances in FP64).
+ * Outputs go to HOST buffers: tag_out[N] and the links in (node, direction)
+ * order as link_node / link_dir / link_q.  *n_links is the capacity of the
+ * link buffers on entry and the link count on return; with all three link
+ * pointers NULL the call only counts (and fills tag_out).  IBL_ERR_ARG when a
+ * triangle index is out of range, a dimension is < 1, the box exceeds
+ * 2^32/19 nodes, or the link buffers are missing or too small (*n_links then
+ * holds the count).  The work runs on cuda_stream (NULL: the legacy stream)
+ * in temporary device buffers freed before the call returns; the call
+ * synchronises that stream.  Not tied to a context: its output feeds
+ * ibl_set_geometry (with dq = 0). */
+ibl_status ibl_voxelise_markers(const double* verts, int32_t n_verts, const int32_t* tris, int32_t n_tris,
+                                int32_t nx, int32_t ny, int32_t nz, const int32_t* periodic,
+                                const uint8_t* tag_in, uint8_t* tag_out, uint32_t* link_node,
+                                uint32_t* link_dir, float* link_q, int64_t* n_links, void* cuda_stream);
+
 /* Message of the last failed call on ctx (or of the last failed ibl_create /
  * ibl_ensemble_create when ctx is NULL). */
 const char* ibl_last_error(const ibl_ctx* ctx);

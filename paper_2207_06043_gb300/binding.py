@@ -98,6 +98,8 @@ def lib():
         "ibl_adjoint": ([vp, i32, i32, P(dbl), P(dbl), P(dbl), P(dbl)], i32),
         "ibl_load_state": ([vp, vp, sz], i32),
         "ibl_kernel_times": ([vp, vp], i32),
+        "ibl_voxelise_markers": ([vp, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, P(C.c_int64), vp],
+                                 i32),
         "ibl_last_error": ([vp], C.c_char_p),
         "ibl_destroy": ([vp], None),
     }
@@ -138,6 +140,36 @@ def _current_stream():
     except Exception:
         pass
     return None
+
+
+def voxelise_markers(verts, tris, shape, periodic=(False, False, False), tag_in=None):
+    """ibl_voxelise_markers: tag a box of shape (nx, ny, nz) by the markers
+    (triangle centroids) of a fixed wall mesh and measure the BFL q of every
+    wall link to them (Eq. qbouzidi).  Returns (tag u8 (N,), links) with
+    links a LINK-layout structured array (node, dir, q, dq = 0) in (node,
+    direction) order, ready for Solver.set_geometry."""
+    from .geometry import LINK_DTYPE
+    L = lib()
+    V = np.ascontiguousarray(verts, dtype=np.float64)
+    T = np.ascontiguousarray(tris, dtype=np.int32)
+    nx, ny, nz = (int(v) for v in shape)
+    per = np.array([1 if p else 0 for p in periodic], dtype=np.int32)
+    tin = None if tag_in is None else np.ascontiguousarray(tag_in, dtype=np.uint8)
+    tag = np.empty(nx * ny * nz, dtype=np.uint8)
+    n = C.c_int64(0)
+    args = (_ptr(V), V.shape[0], _ptr(T), T.shape[0], nx, ny, nz, _ptr(per), _ptr(tin), _ptr(tag))
+    st = L.ibl_voxelise_markers(*args, None, None, None, C.byref(n), _current_stream())
+    if st != OK:
+        raise IBLError(st, L.ibl_last_error(None).decode())
+    node = np.empty(n.value, dtype=np.uint32)
+    dirs = np.empty(n.value, dtype=np.uint32)
+    q = np.empty(n.value, dtype=np.float32)
+    st = L.ibl_voxelise_markers(*args, _ptr(node), _ptr(dirs), _ptr(q), C.byref(n), _current_stream())
+    if st != OK:
+        raise IBLError(st, L.ibl_last_error(None).decode())
+    links = np.zeros(n.value, dtype=LINK_DTYPE)
+    links["node"], links["dir"], links["q"] = node, dirs, q
+    return tag, links
 
 
 class Solver:

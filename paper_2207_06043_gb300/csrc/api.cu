@@ -1997,6 +1997,17 @@ ibl_status ibl_kernel_times(ibl_ctx* ctx, double* out4) {
     return IBL_OK;
 }
 
+ibl_status ibl_voxelise_markers(const double* verts, int32_t n_verts, const int32_t* tris, int32_t n_tris,
+                                int32_t nx, int32_t ny, int32_t nz, const int32_t* periodic,
+                                const uint8_t* tag_in, uint8_t* tag_out, uint32_t* link_node,
+                                uint32_t* link_dir, float* link_q, int64_t* n_links, void* cuda_stream) {
+    std::string msg;
+    const int r = ibl::voxelise_markers(verts, n_verts, tris, n_tris, nx, ny, nz, periodic, tag_in, tag_out,
+                                        link_node, link_dir, link_q, n_links, (cudaStream_t)cuda_stream, msg);
+    if (r == 0) return IBL_OK;
+    return fail(nullptr, r == -1 ? IBL_ERR_ARG : IBL_ERR_CUDA, msg);
+}
+
 const char* ibl_last_error(const ibl_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
 
 void ibl_destroy(ibl_ctx* ctx) {

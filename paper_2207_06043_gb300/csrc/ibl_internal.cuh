@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 namespace ibl {
 
@@ -251,5 +252,11 @@ cudaError_t launch_mirror(const DevState& d, cudaStream_t s);
 // velocity[3], max stretch, r0[3])
 constexpr int CAP_STAT_DOUBLES = 18;
 cudaError_t launch_capsule_stats(const DevState& d, int c_begin, int c_count, double* out, cudaStream_t s);
+
+// marker-based wall tagging and BFL distances (walls.cu): 0, or -1 (argument)
+// / -3 (CUDA) with msg set; arguments as ibl_voxelise_markers
+int voxelise_markers(const double* verts, int nv, const int32_t* tris, int nt, int nx, int ny, int nz,
+                     const int32_t* periodic, const uint8_t* tag_in, uint8_t* tag_out, uint32_t* link_node,
+                     uint32_t* link_dir, float* link_q, int64_t* n_links, cudaStream_t s, std::string& msg);
 
 }  // namespace ibl

@@ -163,3 +163,35 @@ def sphere_mesh_n(n_vertices: int, diameter: float, centre, rng: SplitMix64):
     V, T = fibonacci_sphere(n_vertices)
     R = random_rotation(rng)
     return (V @ R.T) * (0.5 * diameter) + np.asarray(centre, dtype=np.float64)[None, :], T
+
+
+def tube_mesh(x0: float, x1: float, radius: float, yc: float, zc: float, h: float, periodic_x: bool = False):
+    """Open circular tube of the given radius around the line (y, z) = (yc, zc),
+    from x0 to x1, triangulated with edges of about h: rings of
+    ceil(2 pi radius / h) vertices about h sqrt(3)/2 apart, every other ring
+    turned by half a step.  periodic_x: an even number of ring spacings, so
+    that the ring at x1 repeats the one at x0 shifted by x1 - x0 (a tube that
+    continues across a periodic x axis of that length).  A fixed-wall surface:
+    its triangle centroids are the wall markers."""
+    n_t = max(8, int(math.ceil(2.0 * math.pi * radius / h)))
+    length = float(x1 - x0)
+    n_b = max(2, int(math.ceil(length / (h * math.sqrt(3.0) / 2.0))))
+    if periodic_x and n_b % 2:
+        n_b += 1
+    dxr = length / n_b
+    k = np.arange(n_b + 1)[:, None]
+    j = np.arange(n_t)[None, :]
+    th = 2.0 * math.pi * (j + 0.5 * (k % 2)) / n_t
+    X = np.broadcast_to(x0 + dxr * k, th.shape)
+    V = np.stack([X, yc + radius * np.cos(th), zc + radius * np.sin(th)], axis=-1).reshape(-1, 3)
+    tris = []
+    for r in range(n_b):
+        for t in range(n_t):
+            t2 = (t + 1) % n_t
+            a, b = r * n_t + t, r * n_t + t2
+            c, d = (r + 1) * n_t + t, (r + 1) * n_t + t2
+            if r % 2 == 0:
+                tris += [(a, b, c), (b, d, c)]
+            else:
+                tris += [(a, b, d), (a, d, c)]
+    return V.astype(np.float64), np.array(tris, dtype=np.int32)

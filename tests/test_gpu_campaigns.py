@@ -23,16 +23,23 @@ def _cuda():
 
 
 def test_single_capsules_stretch_more_when_softer():
+    """d_p/d = 2/3 capsules into the sharp junction at theta = pi/6 from the
+    stationary flow: the stiff one (Ca = 0.01) reaches the junction (6.7 d
+    downstream of the inlet); the soft one (Ca = 0.1) stretches more and is
+    damaged, as the paper reports for this size and junction (Table 1)."""
     cases = [W.paper_single_capsule(30.0, False, 2.0 / 3.0, Ca, Re=10.0) for Ca in (0.01, 0.1)]
     res = CP.run(cases, 9000, every=300, warm_steps=3000)
-    peaks = []
+    rows = []
     for c, r in zip(cases, res):
         s = CP.summary(c, r)[0]
-        print(c["name"], s)
-        peaks.append(s["dS_max"])
-        x = r["capsules"][0]["centroid"][:, 0]
-        assert x[-1] > x[0] + 3 * 30.0           # carried past the junction region
-    assert peaks[1] > peaks[0] > 0.0, peaks
+        print(c["name"], s, "steps", r["steps_done"])
+        rows.append((s, r["capsules"][0]["centroid"][:, 0]))
+    (stiff, x_stiff), (soft, x_soft) = rows
+    d = cases[0]["geometry"].info["D"]
+    assert x_stiff.max() > 6.0 * d, x_stiff.max() / d
+    assert x_soft[-1] > x_soft[0] + 0.5 * d
+    assert soft["dS_max"] > stiff["dS_max"] > 0.0, (soft, stiff)
+    assert soft["damaged"]
 
 
 def test_train_with_a_rigid_sphere_runs_and_moves_downstream():

@@ -111,5 +111,9 @@ def test_apex_contact_step_matches_the_oracle():
     print(f"  U {np.round(per[0]['U'][k], 5).tolist()}; forces: pressure {np.round(Fp[k], 5).tolist()}, "
           f"viscous {np.round(Ft[k], 5).tolist()}, stretch {np.round(Fst[k], 5).tolist()}, "
           f"bending {np.round(Fb[k], 5).tolist()}, volume {np.round(Fv[k], 5).tolist()}; m_v {b.rest.mv:.4f}")
+    st = per[0]["stencil"]
+    print(f"  marker stencil of the vertex: {int((st.weight[k] > 0).sum())} fluid support nodes, "
+          f"sum |phi| {np.abs(st.phi[k]).sum():.3f} (a support wholly in the fluid: "
+          f"{np.median(np.abs(st.phi).sum(axis=1)):.3f} median over the vertices)")
     print(f"  CUDA vs oracle from the same state: x {dx:.2e}, velocity {dv:.2e}")
     assert dx <= 1e-5 * max(1.0, move[k]) and dv <= 1e-5 * max(1.0, move[k]), (dx, dv)
