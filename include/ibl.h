@@ -327,6 +327,48 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
 #define IBL_NOALLOC_MAX_NODES (1 << 20)
 ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, float* u);
 
+/* Slab decomposition along x (the lattice's natural data-parallel split): the
+ * owned planes [x0, x1) of a slab, and the ghost planes it also holds, lo
+ * below x0 and hi above x1 - 1 (0 at a non-periodic end of the box; on a
+ * periodic x axis the ghost planes wrap). */
+typedef struct {
+    int32_t x0, x1;
+    int32_t lo, hi;
+} ibl_slab;
+
+/* Host-only planner (no CUDA call): n_slabs owned ranges that tile [0, nx),
+ * balanced by plane_weight[nx] (e.g. fluid nodes per plane; NULL: uniform),
+ * each at least max(halo, 1) planes wide, with lo / hi = halo ghost planes on
+ * every cut side (and on both sides of a periodic axis when n_slabs > 1).
+ * out[n_slabs].  IBL_ERR_ARG when nx < n_slabs * max(halo, 1), n_slabs < 1,
+ * halo < 0 or a weight is negative. */
+ibl_status ibl_slab_plan(int32_t nx, int32_t periodic_x, int32_t n_slabs, int32_t halo, const double* plane_weight,
+                         ibl_slab* out);
+
+/* A context that steps the lattice of `whole` (one lattice, set up but never
+ * stepped or read: geometry, faces, initial state) as n_slabs x-slabs, each a
+ * member of one batched context holding its owned planes plus `halo` ghost
+ * planes per cut side (ibl_slab_plan with fluid-node weights).  A cut face is
+ * no Dirichlet face: after every step each ghost plane is overwritten by the
+ * plane of the slab that owns it (all 19 slots of every node, fluid and
+ * solid), one kernel for all planes.  With halo >= 4 every owned node ends
+ * each step with the populations of the undivided lattice bit for bit: a
+ * node's new values depend on its neighbours' old ones (streaming, 1 plane)
+ * and on post-collision values two planes upstream (the quadratic wall
+ * rule), which depend on slots one plane further.
+ *   - ibl_read_fields / ibl_read_populations return the whole lattice
+ *     (host buffers only: on_device gives IBL_ERR_ARG); the ibl_member_*
+ *     readers return slab m with its ghost planes.
+ *   - `whole` is only read; destroy it separately.  Capsules are not
+ *     supported yet (IBL_ERR_STATE), nor the adjoint on a slab context.
+ *   - IBL_ERR_ARG for an invalid plan (see ibl_slab_plan) or halo < 4;
+ *     IBL_ERR_STATE when whole was stepped or read or holds capsules. */
+ibl_status ibl_slab_group_create(ibl_ctx* whole, int32_t n_slabs, int32_t halo, void* cuda_stream, ibl_ctx** out);
+
+/* The plan of a slab context: *n_slabs on entry is the capacity of out, on
+ * return the slab count (0 for a context that is not cut into slabs). */
+ibl_status ibl_slab_info(const ibl_ctx* ctx, int32_t* n_slabs, ibl_slab* out);
+
 /* Marker-based tagging of a fixed wall (Section "Boundary conditions on fixed
  * bodies", Eq. qbouzidi): the wall is a triangular mesh verts[3*n_verts]
  * (FP64, lattice units) / tris[3*n_tris] (vertex indices) whose triangle

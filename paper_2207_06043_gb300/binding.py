@@ -45,6 +45,10 @@ class CapsuleStats(C.Structure):
                 ("velocity", C.c_double * 3), ("damaged", C.c_int32), ("reserved", C.c_int32)]
 
 
+class Slab(C.Structure):
+    _fields_ = [("x0", C.c_int32), ("x1", C.c_int32), ("lo", C.c_int32), ("hi", C.c_int32)]
+
+
 class Objective(C.Structure):
     _fields_ = [("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3), ("d", C.c_double * 3)]
 
@@ -100,6 +104,9 @@ def lib():
         "ibl_kernel_times": ([vp, vp], i32),
         "ibl_voxelise_markers": ([vp, i32, vp, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, P(C.c_int64), vp],
                                  i32),
+        "ibl_slab_plan": ([i32, i32, i32, i32, vp, P(Slab)], i32),
+        "ibl_slab_group_create": ([vp, i32, i32, vp, P(vp)], i32),
+        "ibl_slab_info": ([vp, P(i32), P(Slab)], i32),
         "ibl_last_error": ([vp], C.c_char_p),
         "ibl_destroy": ([vp], None),
     }
@@ -424,6 +431,38 @@ def ensemble(solvers, stream=None):
         for (mm, cid), nv in getattr(s, "_nv", {}).items():
             e._nv[(m, cid)] = nv
     return e
+
+
+def slab_plan(nx, n_slabs, halo=4, periodic_x=False, plane_weight=None):
+    """ibl_slab_plan (host only): list of (x0, x1, lo, hi) per slab."""
+    L = lib()
+    out = (Slab * int(n_slabs))()
+    w = None if plane_weight is None else np.ascontiguousarray(plane_weight, dtype=np.float64)
+    st = L.ibl_slab_plan(int(nx), 1 if periodic_x else 0, int(n_slabs), int(halo), _ptr(w), out)
+    if st != OK:
+        raise IBLError(st, L.ibl_last_error(None).decode())
+    return [(o.x0, o.x1, o.lo, o.hi) for o in out]
+
+
+def slab_group(whole, n_slabs, halo=4, stream=None):
+    """ibl_slab_group_create: the lattice of `whole` (a Solver set up but not
+    stepped) stepped as n_slabs x-slabs with halo exchange.  Returns a Solver
+    whose read_fields / read_populations give the whole lattice; `whole`
+    stays the caller's."""
+    L = lib()
+    h = C.c_void_p()
+    st = L.ibl_slab_group_create(whole._h, int(n_slabs), int(halo),
+                                 stream if stream is not None else _current_stream(), C.byref(h))
+    if st != OK:
+        raise IBLError(st, L.ibl_last_error(None).decode())
+    g = Solver(*whole.shape, whole.tau, _handle=h)
+    n = C.c_int32(int(n_slabs))
+    out = (Slab * int(n_slabs))()
+    g._check(L.ibl_slab_info(h, C.byref(n), out))
+    g.slabs = [(o.x0, o.x1, o.lo, o.hi) for o in out[:n.value]]
+    g.member_shapes = [(x1 - x0 + lo + hi, whole.shape[1], whole.shape[2]) for x0, x1, lo, hi in g.slabs]
+    g._nv = {}
+    return g
 
 
 def capsule_objective_function():

@@ -83,6 +83,11 @@ struct ibl_ctx {
     double* cap_stats = nullptr;       // CAP_STAT_DOUBLES per capsule (ibl_read_capsules)
     std::vector<double> h_cap_stats;
     bool timing = false;
+    // slab decomposition along x (ibl_slab_group_create): member m is slab m
+    struct Slabs {
+        int S = 0, H = 0, nx = 0, per = 0;
+        std::vector<ibl_slab> sl;
+    } slabs;
     std::vector<cudaEvent_t> tev;
     double ktime[4] = {0, 0, 0, 0};
     std::vector<int> h_counters;
@@ -416,6 +421,118 @@ void free_adjoint(ibl_ctx* ctx) {
     A = ibl_ctx::AdjCache{};
 }
 
+// Owned x-ranges of n slabs, balanced by plane weights (cumulative-weight
+// cuts, then pushed apart so that every slab is at least max(H, 1) planes
+// wide), and the ghost planes of each side.
+bool plan_slabs(int nx, bool per, int S, int H, const double* w, std::vector<ibl_slab>& out, std::string& why) {
+    const int wmin = std::max(H, 1);
+    if (S < 1 || H < 0 || nx < S * wmin) {
+        why = "slab plan: need n_slabs >= 1, halo >= 0 and nx >= n_slabs * max(halo, 1)";
+        return false;
+    }
+    std::vector<double> cum(nx + 1, 0.0);
+    for (int x = 0; x < nx; ++x) {
+        const double v = w ? w[x] : 1.0;
+        if (!(v >= 0.0)) {
+            why = "slab plan: negative plane weight";
+            return false;
+        }
+        cum[x + 1] = cum[x] + v;
+    }
+    if (!(cum[nx] > 0.0))
+        for (int x = 0; x <= nx; ++x) cum[x] = x;   // all weights zero: uniform
+    std::vector<int> cut(S + 1, 0);
+    cut[S] = nx;
+    for (int s = 1; s < S; ++s) {
+        const double target = cum[nx] * s / S;
+        int c = (int)(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
+        c = std::max(c, cut[s - 1] + wmin);
+        c = std::min(c, nx - (S - s) * wmin);
+        cut[s] = c;
+    }
+    out.assign(S, ibl_slab{});
+    for (int s = 0; s < S; ++s) {
+        ibl_slab& b = out[s];
+        b.x0 = cut[s];
+        b.x1 = cut[s + 1];
+        if (S == 1) { b.lo = b.hi = 0; continue; }
+        b.lo = per ? H : std::min(H, b.x0);
+        b.hi = per ? H : std::min(H, nx - b.x1);
+    }
+    return true;
+}
+
+// Slab s of the one-lattice member W: its owned planes and ghost planes as a
+// lattice of its own (non-periodic in x when cut; a cut face is FACE_HALO),
+// with the wall links that start on its planes and end inside them, the face
+// data and the initial state of those planes.
+bool crop_slab(const MemberHost& W, const ibl_slab& b, int S, MemberHost& M, std::string& why) {
+    const auto& d = W.desc;
+    const int nx = d.nx, ny = d.ny, nz = d.nz;
+    const int nxs = (b.x1 - b.x0) + b.lo + b.hi;
+    auto gx_of = [&](int l) { return (((b.x0 - b.lo + l) % nx) + nx) % nx; };
+    M = MemberHost{};
+    M.desc = d;
+    M.desc.nx = nxs;
+    if (S > 1) M.desc.periodic[0] = 0;
+    const size_t Ns = (size_t)nxs * ny * nz;
+    M.tag.assign(Ns, 1);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int l = 0; l < nxs; ++l)
+                M.tag[l + (size_t)nxs * (y + (size_t)ny * z)] = W.tag[gx_of(l) + (size_t)nx * (y + (size_t)ny * z)];
+    // links grouped by the global x of their node
+    std::vector<std::vector<size_t>> by_x(nx);
+    for (size_t i = 0; i < W.links.size(); ++i) by_x[W.links[i].node % (uint32_t)nx].push_back(i);
+    for (int l = 0; l < nxs; ++l)
+        for (size_t i : by_x[gx_of(l)]) {
+            ibl_wall_link L = W.links[i];
+            const int tl = l + ex((int)L.dir);
+            if (tl < 0 || tl >= nxs) continue;   // leaves the slab: only at its outermost planes
+            const uint32_t rest = L.node / (uint32_t)nx;   // y + ny z
+            L.node = (uint32_t)l + (uint32_t)nxs * rest;
+            M.links.push_back(L);
+        }
+    for (int f = 0; f < 6; ++f) {
+        M.face_kind[f] = W.face_kind[f];
+        M.face_rho[f] = W.face_rho[f];
+    }
+    if (S > 1) {
+        if (d.periodic[0] || b.x0 > 0) M.face_kind[0] = FACE_HALO;
+        if (d.periodic[0] || b.x1 < nx) M.face_kind[1] = FACE_HALO;
+    }
+    for (int f = 0; f < 6; ++f) {
+        if (W.face_kind[f] != IBL_FACE_VELOCITY || M.face_kind[f] == FACE_HALO) continue;
+        const std::vector<float>& v = W.face_vel[f];
+        if (f < 2) { M.face_vel[f] = v; continue; }
+        // faces 2/3: x + nx z; faces 4/5: x + nx y
+        const int other = f < 4 ? nz : ny;
+        M.face_vel[f].assign((size_t)3 * nxs * other, 0.f);
+        for (int o = 0; o < other; ++o)
+            for (int l = 0; l < nxs; ++l)
+                for (int c = 0; c < 3; ++c)
+                    M.face_vel[f][3 * (l + (size_t)nxs * o) + c] = v[3 * (gx_of(l) + (size_t)nx * o) + c];
+    }
+    if (!W.init_rho.empty() || !W.init_u.empty()) {
+        if (!W.init_rho.empty()) M.init_rho.assign(Ns, 1.f);
+        if (!W.init_u.empty()) M.init_u.assign(3 * Ns, 0.f);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int l = 0; l < nxs; ++l) {
+                    const size_t ln = l + (size_t)nxs * (y + (size_t)ny * z);
+                    const size_t gn = gx_of(l) + (size_t)nx * (y + (size_t)ny * z);
+                    if (!W.init_rho.empty()) M.init_rho[ln] = W.init_rho[gn];
+                    if (!W.init_u.empty())
+                        for (int c = 0; c < 3; ++c) M.init_u[3 * ln + c] = W.init_u[3 * gn + c];
+                }
+    }
+    if (!W.caps.empty()) {
+        why = "slab groups take no capsules";
+        return false;
+    }
+    return true;
+}
+
 ibl_status validate_member(ibl_ctx* ctx, const MemberHost& M) {
     const auto& d = M.desc;
     const long long N = (long long)d.nx * d.ny * d.nz;
@@ -430,8 +547,8 @@ ibl_status validate_member(ibl_ctx* ctx, const MemberHost& M) {
                 int nf = 0, face = -1;
                 for (int a = 0; a < 3; ++a) {
                     if (d.periodic[a]) continue;
-                    if (c[a] == 0) { ++nf; face = 2 * a; }
-                    if (c[a] == dims[a] - 1) { ++nf; face = 2 * a + 1; }
+                    if (c[a] == 0 && M.face_kind[2 * a] != FACE_HALO) { ++nf; face = 2 * a; }
+                    if (c[a] == dims[a] - 1 && M.face_kind[2 * a + 1] != FACE_HALO) { ++nf; face = 2 * a + 1; }
                 }
                 if (nf > 1)
                     return fail(ctx, IBL_ERR_ARG,
@@ -723,12 +840,14 @@ ibl_status finalize(ibl_ctx* ctx) {
                         bool wrap = false;
                         for (int a = 0; a < 3; ++a) {
                             if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) wrap = true;            // wrap plane
-                            if (!per[a] && face < 0 && c[a] == 1) face = 2 * a;                        // box faces
-                            if (!per[a] && face < 0 && c[a] == dimP[a] - 2) face = 2 * a + 1;
+                            if (!per[a] && face < 0 && c[a] == 1 && md.face_kind[2 * a] != FACE_HALO)
+                                face = 2 * a;                                                          // box faces
+                            if (!per[a] && face < 0 && c[a] == dimP[a] - 2 && md.face_kind[2 * a + 1] != FACE_HALO)
+                                face = 2 * a + 1;
                         }
                         border = border || wrap;
                         (wrap ? bnodes : nodes).push_back((uint32_t)n);
-                        if (face >= 0 && md.face_kind[face] != FACE_NONE) {
+                        if (face >= 0 && (md.face_kind[face] == FACE_VELOCITY || md.face_kind[face] == FACE_PRESSURE)) {
                             fc_node.push_back((uint32_t)n);
                             fc_meta.push_back((uint32_t)face | ((uint32_t)m << 8));
                         }
@@ -847,6 +966,33 @@ ibl_status finalize(ibl_ctx* ctx) {
             CKS(dev_alloc(ctx, D.near, caps.size() * NEAR_STRIDE));
         }
     }
+    // slab decomposition: every ghost plane of every slab, from the slab
+    // that owns its global x
+    if (ctx->slabs.S > 1) {
+        const auto& P = ctx->slabs;
+        std::vector<int4> pairs;
+        for (int m = 0; m < P.S; ++m) {
+            const ibl_slab& a = P.sl[m];
+            const int w = a.x1 - a.x0;
+            for (int l = 0; l < a.lo + w + a.hi; ++l) {
+                if (l >= a.lo && l < a.lo + w) continue;
+                int gx = a.x0 - a.lo + l;
+                gx = ((gx % P.nx) + P.nx) % P.nx;
+                int src = -1;
+                for (int t = 0; t < P.S; ++t)
+                    if (gx >= P.sl[t].x0 && gx < P.sl[t].x1) src = t;
+                if (src < 0 || src == m) return fail(ctx, IBL_ERR_ARG, "slab plan: a ghost plane has no other owner");
+                const ibl_slab& b = P.sl[src];
+                pairs.push_back(make_int4(m, l + ctx->hmem[m].px, src, gx - b.x0 + b.lo + ctx->hmem[src].px));
+            }
+        }
+        for (int m = 1; m < nm; ++m)
+            if (ctx->hmem[m].NY != ctx->hmem[0].NY || ctx->hmem[m].NZ != ctx->hmem[0].NZ)
+                return fail(ctx, IBL_ERR_ARG, "slab members differ in y or z");
+        D.n_halo = (int)pairs.size();
+        CKS(dev_alloc(ctx, D.halo, pairs.size()));
+        CKS(upload(ctx, D.halo, pairs));
+    }
     D.h_mem = ctx->hmem.data();
     CKS(dev_alloc(ctx, D.mem, (size_t)nm));
     CKS(upload(ctx, D.mem, ctx->hmem));
@@ -961,6 +1107,7 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks, cons
     CKS(begin(s));
     CK(launch_bfl(D, parity, s, tp ? tp->dvdq : nullptr));
     CK(launch_faces(D, parity, s, tp ? tp->rho : nullptr));
+    CK(launch_halo(D, s));
     CKS(end(TK_BFL, s));
     if (caps && !marks) {
         CK(cudaEventRecord(ctx->ev_join, s2));
@@ -1045,6 +1192,34 @@ ibl_status read_fields_member(ibl_ctx* ctx, int m, float* rho, float* u, float* 
         CK(cudaStreamSynchronize(ctx->work));
     }
     CKS(leave(ctx));
+    return IBL_OK;
+}
+
+// The whole lattice of a slab context: each slab's owned planes, read from
+// its member into host buffers.
+ibl_status read_fields_slabs(ibl_ctx* ctx, float* rho, float* u, float* g, int on_device) {
+    if (on_device) return fail(ctx, IBL_ERR_ARG, "a slab context reads the whole lattice into host buffers only");
+    const auto& P = ctx->slabs;
+    const int ny = ctx->members[0].desc.ny, nz = ctx->members[0].desc.nz;
+    const size_t Ng = (size_t)P.nx * ny * nz;
+    for (int m = 0; m < P.S; ++m) {
+        const ibl_slab& b = P.sl[m];
+        const int nxs = ctx->members[m].desc.nx;
+        const size_t Ns = (size_t)nxs * ny * nz;
+        std::vector<float> r(rho ? Ns : 0), v(u ? 3 * Ns : 0), q(g ? 19 * Ns : 0);
+        CKS(read_fields_member(ctx, m, rho ? r.data() : nullptr, u ? v.data() : nullptr, g ? q.data() : nullptr, 0));
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = b.x0; x < b.x1; ++x) {
+                    const size_t ln = (x - b.x0 + b.lo) + (size_t)nxs * (y + (size_t)ny * z);
+                    const size_t gn = x + (size_t)P.nx * (y + (size_t)ny * z);
+                    if (rho) rho[gn] = r[ln];
+                    if (u)
+                        for (int c = 0; c < 3; ++c) u[3 * gn + c] = v[3 * ln + c];
+                    if (g)
+                        for (int k = 0; k < 19; ++k) g[k * Ng + gn] = q[k * Ns + ln];
+                }
+    }
     return IBL_OK;
 }
 
@@ -1306,12 +1481,14 @@ ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done) {
 
 ibl_status ibl_read_fields(ibl_ctx* ctx, float* rho, float* u, int32_t on_device) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (ctx->slabs.S > 1) return read_fields_slabs(ctx, rho, u, nullptr, on_device);
     return read_fields_member(ctx, 0, rho, u, nullptr, on_device);
 }
 
 ibl_status ibl_read_populations(ibl_ctx* ctx, float* g, int32_t on_device) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
     if (!g) return fail(ctx, IBL_ERR_ARG, "null output");
+    if (ctx->slabs.S > 1) return read_fields_slabs(ctx, nullptr, nullptr, g, on_device);
     return read_fields_member(ctx, 0, nullptr, nullptr, g, on_device);
 }
 
@@ -1406,6 +1583,63 @@ ibl_status ibl_ensemble_create(ibl_ctx* const* members, int32_t n, void* cuda_st
         return fail(nullptr, IBL_ERR_ARG, "too many members");
     }
     *out = ctx;
+    return IBL_OK;
+}
+
+ibl_status ibl_slab_plan(int32_t nx, int32_t periodic_x, int32_t n_slabs, int32_t halo, const double* plane_weight,
+                         ibl_slab* out) {
+    if (!out) return fail(nullptr, IBL_ERR_ARG, "null output");
+    std::vector<ibl_slab> sl;
+    std::string why;
+    if (!plan_slabs(nx, periodic_x != 0, n_slabs, halo, plane_weight, sl, why)) return fail(nullptr, IBL_ERR_ARG, why);
+    std::copy(sl.begin(), sl.end(), out);
+    return IBL_OK;
+}
+
+ibl_status ibl_slab_group_create(ibl_ctx* whole, int32_t n_slabs, int32_t halo, void* cuda_stream, ibl_ctx** out) {
+    if (!whole || !out) return fail(nullptr, IBL_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (whole->finalized) return fail(nullptr, IBL_ERR_STATE, "the whole lattice must not have been stepped or read");
+    if (whole->members.size() != 1 || whole->slabs.S > 1)
+        return fail(nullptr, IBL_ERR_STATE, "a slab context is cut from one lattice");
+    const MemberHost& W = whole->members[0];
+    if (!W.caps.empty()) return fail(nullptr, IBL_ERR_STATE, "slab groups take no capsules");
+    if (halo < 4) return fail(nullptr, IBL_ERR_ARG, "halo must be at least 4 planes");
+    if (n_slabs > MAX_MEMBERS) return fail(nullptr, IBL_ERR_ARG, "too many slabs");
+    const auto& d = W.desc;
+    if ((long long)W.tag.size() != (long long)d.nx * d.ny * d.nz) return fail(nullptr, IBL_ERR_STATE, "geometry not set");
+    // balance the slabs by fluid nodes per plane
+    std::vector<double> wgt(d.nx, 0.0);
+    for (size_t n = 0; n < W.tag.size(); ++n)
+        if (W.tag[n] == 0) wgt[n % (size_t)d.nx] += 1.0;
+    std::vector<ibl_slab> sl;
+    std::string why;
+    if (!plan_slabs(d.nx, d.periodic[0] != 0, n_slabs, halo, wgt.data(), sl, why)) return fail(nullptr, IBL_ERR_ARG, why);
+    ibl_ctx* ctx = nullptr;
+    ibl_status st = new_ctx(cuda_stream, &ctx);
+    if (st != IBL_OK) return st;
+    ctx->storage = whole->storage;
+    ctx->members.resize(n_slabs);
+    for (int m = 0; m < n_slabs; ++m)
+        if (!crop_slab(W, sl[m], n_slabs, ctx->members[m], why)) {
+            ibl_destroy(ctx);
+            return fail(nullptr, IBL_ERR_ARG, why);
+        }
+    ctx->slabs.S = n_slabs;
+    ctx->slabs.H = halo;
+    ctx->slabs.nx = d.nx;
+    ctx->slabs.per = d.periodic[0] ? 1 : 0;
+    ctx->slabs.sl = sl;
+    *out = ctx;
+    return IBL_OK;
+}
+
+ibl_status ibl_slab_info(const ibl_ctx* ctx, int32_t* n_slabs, ibl_slab* out) {
+    if (!ctx || !n_slabs) return fail(nullptr, IBL_ERR_ARG, "null argument");
+    const int S = ctx->slabs.S > 1 ? ctx->slabs.S : 0;
+    if (out && *n_slabs < S) return fail(nullptr, IBL_ERR_ARG, "slab buffer too small");
+    if (out) std::copy(ctx->slabs.sl.begin(), ctx->slabs.sl.begin() + S, out);
+    *n_slabs = S;
     return IBL_OK;
 }
 

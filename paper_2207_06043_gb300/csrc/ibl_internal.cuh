@@ -39,7 +39,8 @@ constexpr int MAX_MEMBERS = 128;
 
 enum : uint8_t { TAG_SOLID = 1, TAG_IB = 2 };
 enum : uint32_t { ST_DAMAGED = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
-enum { FACE_NONE = 0, FACE_VELOCITY = 1, FACE_PRESSURE = 2 };
+enum { FACE_NONE = 0, FACE_VELOCITY = 1, FACE_PRESSURE = 2,
+       FACE_HALO = 3 };   // a cut face of a slab member: its planes are copied from their owner
 
 // Per-lattice descriptor (a device array per context, passed to every kernel).
 struct MemberDev {
@@ -187,6 +188,10 @@ struct DevState {
     float4* xm = nullptr;            // two-float mirror of x: (hi, 0), (lo, 0) per vertex, x = hi + lo
     int4* near = nullptr;            // NEAR_STRIDE per capsule: count (-1: too many), then grown boxes and spheres
     long long n_cells = 0;
+    // slab decomposition: plane copies (dst member, dst padded x, src member,
+    // src padded x) run after every step; members share NY and NZ
+    int n_halo = 0;
+    int4* halo = nullptr;
 };
 constexpr int CELL_CAP = 32;
 constexpr int NEAR_CAP = 31;          // capsules listed as near one capsule; more: all its markers search
@@ -252,6 +257,9 @@ cudaError_t launch_mirror(const DevState& d, cudaStream_t s);
 // velocity[3], max stretch, r0[3])
 constexpr int CAP_STAT_DOUBLES = 18;
 cudaError_t launch_capsule_stats(const DevState& d, int c_begin, int c_count, double* out, cudaStream_t s);
+// the halo planes of a slab decomposition from their owners (every slot of
+// every padded node of each listed plane)
+cudaError_t launch_halo(const DevState& d, cudaStream_t s);
 
 // marker-based wall tagging and BFL distances (walls.cu): 0, or -1 (argument)
 // / -3 (CUDA) with msg set; arguments as ibl_voxelise_markers

@@ -117,3 +117,60 @@ def test_apex_contact_step_matches_the_oracle():
           f"{np.median(np.abs(st.phi).sum(axis=1)):.3f} median over the vertices)")
     print(f"  CUDA vs oracle from the same state: x {dx:.2e}, velocity {dv:.2e}")
     assert dx <= 1e-5 * max(1.0, move[k]) and dv <= 1e-5 * max(1.0, move[k]), (dx, dv)
+
+
+def test_apex_contact_window_against_the_oracle():
+    """The 40 steps before the jump, from the GPU state, stepped by both
+    paths: the growth of the fluid speed near the tip and of the largest edge
+    stretch must be the same in the FP64 oracle (it is the method's, not the
+    kernels'); the per-step largest stretch agrees within 1e-3 until the
+    jump and both paths jump at the same step."""
+    from helpers import oracle_for
+    c = W.deformable_capsule(30.0, 0.005)
+    cap = c["capsules"][0]
+    nv = len(cap["verts"])
+    s = W.make_solver(c)
+    s.step(START, allow_damage=True)
+    start = s.save_state()
+    t = START
+    hist = []
+    while t < LIMIT:
+        done, _ = s.step(1, allow_damage=True)
+        t += 1
+        hist.append(s.read_capsules(1)[0]["max_stretch"])
+        if done == 0 or hist[-1] >= 2.0 or (len(hist) > 1 and hist[-1] - hist[-2] > 0.05):
+            break
+    if t >= LIMIT:
+        s.close()
+        pytest.skip("no jump")
+    t_jump = t
+    w0 = t_jump - 40
+    s.load_state(start)
+    s.step(w0 - START, allow_damage=True)
+    g0 = s.read_populations()
+    st0 = s.read_capsule_state(0, nv)
+    gpu = []
+    for _ in range(41):
+        done, _ = s.step(1, allow_damage=True)
+        st = s.read_capsules(1)[0]
+        _, u = s.read_fields()
+        gpu.append((st["max_stretch"], float(np.linalg.norm(u, axis=1).max())))
+        if done == 0:
+            break
+    s.close()
+    lat, o = oracle_for(c, f0=g0.astype(np.float64) + L.W[:, None])
+    b = o.bodies[0]
+    b.x, b.x_prev, b.vel = st0["x"].copy(), st0["x_prev"].copy(), st0["vel"].copy()
+    orc = []
+    for _ in range(len(gpu)):
+        o.step(1)
+        _, uo = lat.macroscopic(o.f)
+        orc.append((Mb.max_stretch(b.x, b.rest), float(np.linalg.norm(uo[lat.fluid], axis=1).max())))
+    for k, (a, r) in enumerate(zip(gpu, orc)):
+        print(f"step {w0 + k + 1}: max stretch {a[0]:.5f} / {r[0]:.5f}, max |u| {a[1]:.4e} / {r[1]:.4e}")
+    jump_g = next((k for k, a in enumerate(gpu) if a[0] >= 2.0), None)
+    jump_o = next((k for k, r in enumerate(orc) if r[0] >= 2.0), None)
+    assert jump_g is not None and jump_o is not None, (jump_g, jump_o)
+    assert abs(jump_g - jump_o) <= 1, (jump_g, jump_o)
+    for a, r in zip(gpu[:min(jump_g, jump_o)], orc):
+        assert abs(a[0] - r[0]) <= 1e-3 * r[0], (a, r)
