@@ -13,7 +13,7 @@ from .lattice import Ef
 # 2 r_w = 2.6 dx centred on the marker (Reading M2)
 SUPPORT_SIDE = 2.6
 ALPHA = 0.3            # Eq. intKernel
-PIVOT_TOL = 1e-10      # Reading M4: singular moment matrix -> nearest fluid node
+PIVOT_TOL = 1e-10      # Reading M4: singular moment matrix -> nearest support node
 
 OFFSETS = np.array([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)],
                    dtype=np.int64)   # k = (dx+1) + 3 (dy+1) + 9 (dz+1)
@@ -68,8 +68,15 @@ def stencil(lat, X):
     a = A^{-1} sum_k W_k p_k u^k, A = sum_k W_k p_k p_k^T, so
     U(X) = a_0 gives phi_k = W_k (A^{-1} p_k)_0 and the gradient weights are
     W_k (A^{-1} p_k)_{1..3}.  The support is the 3x3x3 block around the
-    nearest node (round half up), r_k = |X - x^k| / 2.6 (Reading M2).  Solid
-    and out-of-domain nodes get W = 0 (Reading M4).
+    nearest node (round half up), r_k = |X - x^k| / 2.6 (Reading M2).
+    Reading M4: every Eulerian point of the support takes part, a solid one
+    with the state of the wall it lies in (the populations of a solid node
+    are the rest equilibrium: rho = 1, u = 0); only points off a non-periodic
+    box get W = 0, and a support whose moment matrix is singular (possible
+    only for a point at the box edge) falls back to its nearest point.
+    Dropping the solid points instead leaves a point near a wall with a few
+    fluid points that carry large weights, and the explicit direct forcing
+    (Eq. bodyforce) then amplifies the fluid velocity there from step to step.
 
     X may be complex (complex-step derivatives): every discrete decision (the
     nearest node, the support, the singularity test, the fallback node) is
@@ -94,7 +101,6 @@ def stencil(lat, X):
             c = np.clip(c, 0, dims[ax] - 1)
         wrapped.append(c)
     nodes = wrapped[0] + lat.nx * (wrapped[1] + lat.ny * wrapped[2])
-    ok &= lat.fluid[nodes]
     rel = pos - X[:, None, :]
     r2 = (rel * rel).sum(axis=2) / SUPPORT_SIDE ** 2
     Wk = np.where(ok, weight_of_r2(r2), 0.0)
@@ -112,7 +118,7 @@ def stencil(lat, X):
         grad[good] = coef[:, 1:, :]
     bad = ~good
     if bad.any():
-        # nearest fluid support node takes the whole marker (largest W)
+        # the nearest support point takes the whole marker (largest W)
         has = np.real(Wk[bad]).max(axis=1) > 0
         kk = np.argmax(np.real(Wk[bad]), axis=1)
         rows = np.nonzero(bad)[0]

@@ -133,6 +133,15 @@ __device__ __forceinline__ float4 tape_macro(const MemberDev& d, const float4* _
     return make_float4(t.x, t.y - (d.F[0] + fi.x) * h, t.z - (d.F[1] + fi.y) * h, t.w - (d.F[2] + fi.z) * h);
 }
 
+// The moments a stencil reads at a support node: a fluid node's from the
+// tape, a solid node's from the wall it lies in (rho = 1, u = 0; constants).
+__device__ __forceinline__ float4 node_macro(const MemberDev& d, const uint8_t* __restrict__ tag,
+                                             const float4* __restrict__ tape, const float4* __restrict__ tape_F,
+                                             int node) {
+    if (tag[d.node_off + node] & TAG_SOLID) return make_float4(1.f, 0.f, 0.f, 0.f);
+    return tape_macro(d, tape, tape_F, node);
+}
+
 // The MLS product of the header comment for the lanes of one group: lam[j][s]
 // are the row weights of this lane's support slots s (rows < NR), returns
 // d/dP of sum_jk lam_jk phi^j_k (the same in every lane of the group).
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(IB_PROBE_THREADS) k_adj_probes(
         q[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < 27 && M.W[j] > 0.f) {
             node[j] = mls_node_g(d, M, k);
-            q[j] = tape_macro(d, tape, tape_F, node[j]);
+            q[j] = node_macro(d, tag, tape, tape_F, node[j]);
         }
     }
     // forward: rho_P and G[c][jj] = d u_c / d x_jj at the probe
@@ -348,8 +357,9 @@ __global__ void __launch_bounds__(IB_MARKER_THREADS) k_adj_markers(
         q[j] = lf[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ph[j] != 0.f) {
             node[j] = mls_node_g(d, M, k);
-            q[j] = tape_macro(d, tape, tape_F, node[j]);
-            lf[j] = a.lfib[d.node_off + node[j]];
+            q[j] = node_macro(d, tag, tape, tape_F, node[j]);
+            // the forward spreads onto fluid nodes only
+            if (q[j].x > 0.f && !(tag[d.node_off + node[j]] & TAG_SOLID)) lf[j] = a.lfib[d.node_off + node[j]];
         }
     }
     float Ux = 0.f, Uy = 0.f, Uz = 0.f, Lx = 0.f, Ly = 0.f, Lz = 0.f;

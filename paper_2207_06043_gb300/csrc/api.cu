@@ -888,6 +888,29 @@ ibl_status finalize(ibl_ctx* ctx) {
         CKS(upload(ctx, D.group_mem, group_mem));
         CKS(upload(ctx, D.bgroup_mem, bgroup_mem));
     }
+    // the wall links that start on a Zou-He face node: taken by that node's
+    // thread of the walls kernel, before its face rule
+    {
+        std::map<uint64_t, int> face_at;
+        for (size_t i = 0; i < fc_node.size(); ++i)
+            face_at[((uint64_t)(fc_meta[i] >> 8) << 32) | fc_node[i]] = (int)i;
+        std::vector<std::vector<int>> per(fc_node.size());
+        for (size_t l = 0; l < l_node.size(); ++l) {
+            const auto it = face_at.find(((uint64_t)(l_meta[l] >> 8) << 32) | l_node[l]);
+            if (it == face_at.end()) continue;
+            per[it->second].push_back((int)l);
+            l_meta[l] |= LINK_AT_FACE;
+        }
+        std::vector<int> lbeg(fc_node.size() + 1, 0), links;
+        for (size_t i = 0; i < per.size(); ++i) {
+            lbeg[i + 1] = lbeg[i] + (int)per[i].size();
+            links.insert(links.end(), per[i].begin(), per[i].end());
+        }
+        CKS(dev_alloc(ctx, D.fc_lbeg, lbeg.size()));
+        CKS(dev_alloc(ctx, D.fc_links, std::max<size_t>(links.size(), 1)));
+        CKS(upload(ctx, D.fc_lbeg, lbeg));
+        CKS(upload(ctx, D.fc_links, links));
+    }
     CKS(dev_alloc(ctx, D.fc_node, std::max<size_t>(fc_node.size(), 1)));
     CKS(dev_alloc(ctx, D.fc_meta, std::max<size_t>(fc_meta.size(), 1)));
     CKS(upload(ctx, D.fc_node, fc_node));
@@ -1105,8 +1128,7 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks, cons
     CK(launch_lbm(D, parity, s, tp ? tp->rhou : nullptr, tp ? tp->F : nullptr));
     CKS(end(TK_LBM, s));
     CKS(begin(s));
-    CK(launch_bfl(D, parity, s, tp ? tp->dvdq : nullptr));
-    CK(launch_faces(D, parity, s, tp ? tp->rho : nullptr));
+    CK(launch_walls(D, parity, s, tp ? tp->dvdq : nullptr, tp ? tp->rho : nullptr));
     CK(launch_halo(D, s));
     CKS(end(TK_BFL, s));
     if (caps && !marks) {
@@ -1763,8 +1785,8 @@ ibl_status ibl_adjoint_flow(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, c
                     const int parity = (parity0 + k) & 1;
                     if (mode == 2) CK(launch_step_begin(D, s));
                     CK(launch_lbm(D, parity, s, tape_rhou + (size_t)k * N));
-                    CK(launch_bfl(D, parity, s, tape_dvdq + (size_t)k * D.n_links));
-                    CK(launch_faces(D, parity, s, tape_rho + (size_t)k * D.n_face_nodes));
+                    CK(launch_walls(D, parity, s, tape_dvdq + (size_t)k * D.n_links,
+                                    tape_rho + (size_t)k * D.n_face_nodes));
                 }
             if (mode != 2) {
                 float* li = lin0;

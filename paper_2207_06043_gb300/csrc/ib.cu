@@ -156,16 +156,17 @@ __device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restri
             if (!LIN && (d.per & 1)) wx = ((wx % d.nx) + d.nx) % d.nx;
             const int X = wx + d.px;
             const int node = X + d.NX * (Y + d.NY * Z);
-            // solid nodes get rho = 0, which the stencils read as "solid"
-            // (their gathers then need no tag); the populations' loads are
-            // issued beside the tag's, so they do not wait on it
+            // a solid node holds the wall's state, rho = 1 and u = 0, stored
+            // with rho negated so that the marker stencils know not to spread
+            // onto it without a tag gather; the populations' loads are issued
+            // beside the tag's, so they do not wait on it
             const bool solid = tag[d.node_off + node] & TAG_SOLID;
             float g[Q];
             if (LIN) load_pre_lin<T>(d, fm, node, parity, g);
             else load_pre<T>(d, fm, node, X, Y, Z, parity, g);
             float rho, ux, uy, uz;
             moments_of(g, rho, ux, uy, uz);
-            macro[d.node_off + node] = solid ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(rho, ux, uy, uz);
+            macro[d.node_off + node] = solid ? make_float4(-1.f, 0.f, 0.f, 0.f) : make_float4(rho, ux, uy, uz);
         }
     }
 }
@@ -257,7 +258,9 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     const float A = area[l];
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
-        if (p[j] != 0.f) {
+        if (p[j] != 0.f && q[j].x > 0.f) {
+            // a fluid support node (the force a solid one would take acts on
+            // the wall)
             const float c = A * p[j];
             const size_t gi = (size_t)d.node_off + mls_node_g(d, M, r + GL * j);
             // one vector reduction per support node (f_ib is padded to float4)
@@ -307,12 +310,12 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
         if (M.fallback < 0) {
             const float p = mls_row_g(M, 0, j, k), g0 = mls_row_g(M, 1, j, k), g1 = mls_row_g(M, 2, j, k),
                         g2 = mls_row_g(M, 3, j, k);
-            acc[0] += p * q[j].x;
+            acc[0] += p * fabsf(q[j].x);   // a solid node's rho (1) is stored negated
             acc[1] += g0 * q[j].y; acc[2] += g1 * q[j].y; acc[3] += g2 * q[j].y;
             acc[4] += g0 * q[j].z; acc[5] += g1 * q[j].z; acc[6] += g2 * q[j].z;
             acc[7] += g0 * q[j].w; acc[8] += g1 * q[j].w; acc[9] += g2 * q[j].w;
         } else if (M.fallback == k) {
-            acc[0] += q[j].x;
+            acc[0] += fabsf(q[j].x);
         }
     }
 #pragma unroll

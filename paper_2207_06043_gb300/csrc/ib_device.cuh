@@ -229,25 +229,25 @@ __device__ __noinline__ Rows ldlt_solve64(Moments64 mm) {
 // each take the FP64 steps (nearest node, offset) for one axis and the group
 // exchanges the results, so that GB300's narrow FP64 pipe does a third of the
 // work it would if every lane took all three axes.
-// Fluid support nodes are found from the tag array (the adjoint) or, with
-// MAC, from the moments array of the step, where solid nodes hold rho = 0:
-// then the moments of every support node of the lane are gathered at once
-// into q, with no tag gather before them.
+// Every support node inside the box takes part in the fit, a solid one with
+// the wall's state (rho = 1, u = 0); only nodes off a non-periodic box are
+// left out (node < 0).  With MAC the moments of every support node of the
+// lane are gathered at once into q from the moments array of the step,
+// where a solid node holds (-1, 0, 0, 0): its rho negated, so that the
+// spreading can skip it without a tag gather.
 template <bool MAC>
 struct Support;
 template <>
 struct Support<false> {
     const uint8_t* tag;
-    __device__ __forceinline__ bool fluid(const MemberDev& d, int node, float4&) const {
-        return node >= 0 && !(tag[d.node_off + node] & TAG_SOLID);
-    }
+    __device__ __forceinline__ bool fluid(const MemberDev&, int node, float4&) const { return node >= 0; }
 };
 template <>
 struct Support<true> {
     const float4* macro;
     __device__ __forceinline__ bool fluid(const MemberDev& d, int node, float4& q) const {
         q = node >= 0 ? macro[d.node_off + node] : make_float4(0.f, 0.f, 0.f, 0.f);
-        return q.x > 0.f;
+        return node >= 0;
     }
 };
 

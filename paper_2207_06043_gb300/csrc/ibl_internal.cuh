@@ -35,6 +35,7 @@ __host__ __device__ constexpr float wgt(int k) {
 }
 
 constexpr int Q = 19;
+constexpr uint32_t LINK_AT_FACE = 128u;   // l_meta flag: the link starts on a Zou-He face node
 constexpr int MAX_MEMBERS = 128;
 
 enum : uint8_t { TAG_SOLID = 1, TAG_IB = 2 };
@@ -153,10 +154,12 @@ struct DevState {
     int n_face_nodes = 0;            // fluid nodes on a Zou-He face, all members
     uint32_t* fc_node = nullptr;     // padded node
     uint32_t* fc_meta = nullptr;     // face | member << 8
+    int* fc_lbeg = nullptr;          // n_face_nodes + 1: the face node's wall links in fc_links
+    int* fc_links = nullptr;         // link indices (their l_meta carries LINK_AT_FACE)
 
     int n_links = 0;
     uint32_t* l_node = nullptr;      // padded node of the link
-    uint32_t* l_meta = nullptr;      // dir | ok1 << 5 | ok2 << 6 | member << 8
+    uint32_t* l_meta = nullptr;      // dir | ok1 << 5 | ok2 << 6 | LINK_AT_FACE | member << 8
     float* l_q = nullptr;
     float* l_dq = nullptr;           // dq / d(junction radius) per link (adjoint input)
 
@@ -204,9 +207,11 @@ constexpr int NEAR_STRIDE = 1 + 3 * NEAR_CAP;   // int4 entries: the count, then
 // node before the face rule.  Null in ordinary steps.
 cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou = nullptr,
                        float4* tape_F = nullptr);
-cudaError_t launch_faces(const DevState& d, int parity_done, cudaStream_t s, float* tape_rho = nullptr);
 int lbm_max_threads();   // block-size bound the lattice kernel was compiled for
-cudaError_t launch_bfl(const DevState& d, int parity_done, cudaStream_t s, float* tape_dvdq = nullptr);
+// the wall fill (Eq. bbouzidi) and the Zou-He faces (Eq. extbound) of the
+// step just done, in one launch
+cudaError_t launch_walls(const DevState& d, int parity_done, cudaStream_t s, float* tape_dvdq = nullptr,
+                         float* tape_rho = nullptr);
 cudaError_t launch_init_member(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s);
 cudaError_t launch_read(const DevState& d, int member, int parity, float* rho, float* u,
                         float* g, cudaStream_t s);

@@ -130,15 +130,10 @@ k_lbm(const __grid_constant__ MemberDev d0, const MemberDev* __restrict__ mem, T
 // post-collision values of the step just done (parity pp) and writes the slot
 // the next step (parity 1 - pp) reads.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, T* __restrict__ f, const uint32_t* __restrict__ l_node,
-                                             const uint32_t* __restrict__ l_meta, const float* __restrict__ l_q,
-                                             const uint32_t* __restrict__ status, int n_links, int pp,
-                                             float* __restrict__ tape_dvdq) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n_links) return;
-    const uint32_t meta = l_meta[l];
+__device__ __forceinline__ void bfl_link(const MemberDev* __restrict__ mem, T* __restrict__ f,
+                                         const uint32_t* __restrict__ l_node, const float* __restrict__ l_q, int l,
+                                         uint32_t meta, int pp, float* __restrict__ tape_dvdq) {
     const int m = (int)(meta >> 8);
-    if (status[m] & (ST_DAMAGED | ST_NONFINITE)) return;
     const MemberDev& d = mem[m];
     const int i = (int)(meta & 31u);
     const bool ok1 = meta & 32u, ok2 = meta & 64u;
@@ -218,16 +213,10 @@ __global__ void __launch_bounds__(256) k_bfl(const MemberDev* __restrict__ mem, 
 // among the populations the rule reads, and it replaces only those entering
 // through the box face.
 template <typename T>
-__global__ void __launch_bounds__(256) k_faces(const MemberDev* __restrict__ mem, T* __restrict__ f,
-                                               const uint32_t* __restrict__ fc_node,
-                                               const uint32_t* __restrict__ fc_meta,
-                                               const float* __restrict__ face_vel, const uint32_t* __restrict__ status,
-                                               int n_face_nodes, int pp, float* __restrict__ tape_rho) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_face_nodes) return;
-    const uint32_t meta = fc_meta[i];
+__device__ __forceinline__ void face_node(const MemberDev* __restrict__ mem, T* __restrict__ f, int i, uint32_t meta,
+                                          const uint32_t* __restrict__ fc_node, const float* __restrict__ face_vel,
+                                          int pp, float* __restrict__ tape_rho) {
     const int m = (int)(meta >> 8), fc = (int)(meta & 7u);
-    if (status[m] & (ST_DAMAGED | ST_NONFINITE)) return;
     const MemberDev& d = mem[m];
     const int n = (int)fc_node[i];
     int X, Y, Z;
@@ -263,19 +252,54 @@ __global__ void __launch_bounds__(256) k_faces(const MemberDev* __restrict__ mem
     }
 }
 
+// The wall fill and the faces of a step in one launch.  Threads [0, n_face)
+// take one face node each: first the wall links that start on it (in the
+// order they are listed), then the face rule, which reads those values; the
+// other threads take one wall link each and skip the links of face nodes
+// (flag LINK_AT_FACE).  No other thread reads or writes the slots a face
+// node's rule reads: each of them is written by at most one link.
 template <typename T>
-static cudaError_t faces_t(const DevState& d, int pp, cudaStream_t s, float* tape) {
-    if (d.n_face_nodes == 0) return cudaSuccess;
-    k_faces<T><<<(d.n_face_nodes + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.fc_node, d.fc_meta, d.face_vel,
-                                                             d.status, d.n_face_nodes, pp, tape);
+__global__ void __launch_bounds__(256) k_walls(const MemberDev* __restrict__ mem, T* __restrict__ f,
+                                               const uint32_t* __restrict__ l_node, const uint32_t* __restrict__ l_meta,
+                                               const float* __restrict__ l_q, const uint32_t* __restrict__ status,
+                                               int n_links, const uint32_t* __restrict__ fc_node,
+                                               const uint32_t* __restrict__ fc_meta, const int* __restrict__ fc_lbeg,
+                                               const int* __restrict__ fc_links, const float* __restrict__ face_vel,
+                                               int n_face_nodes, int pp, float* __restrict__ tape_dvdq,
+                                               float* __restrict__ tape_rho) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_face_nodes) {
+        const uint32_t meta = fc_meta[t];
+        if (status[meta >> 8] & (ST_DAMAGED | ST_NONFINITE)) return;
+        for (int j = fc_lbeg[t]; j < fc_lbeg[t + 1]; ++j) {
+            const int l = fc_links[j];
+            bfl_link<T>(mem, f, l_node, l_q, l, l_meta[l], pp, tape_dvdq);
+        }
+        face_node<T>(mem, f, t, meta, fc_node, face_vel, pp, tape_rho);
+        return;
+    }
+    const int l = t - n_face_nodes;
+    if (l >= n_links) return;
+    const uint32_t meta = l_meta[l];
+    if ((meta & LINK_AT_FACE) || (status[meta >> 8] & (ST_DAMAGED | ST_NONFINITE))) return;
+    bfl_link<T>(mem, f, l_node, l_q, l, meta, pp, tape_dvdq);
+}
+
+template <typename T>
+static cudaError_t walls_t(const DevState& d, int pp, cudaStream_t s, float* tape_dvdq, float* tape_rho) {
+    const int n = d.n_links + d.n_face_nodes;
+    if (n == 0) return cudaSuccess;
+    k_walls<T><<<(n + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.l_node, d.l_meta, d.l_q, d.status, d.n_links,
+                                               d.fc_node, d.fc_meta, d.fc_lbeg, d.fc_links, d.face_vel,
+                                               d.n_face_nodes, pp, tape_dvdq, tape_rho);
     return cudaGetLastError();
 }
 
-cudaError_t launch_faces(const DevState& d, int pp, cudaStream_t s, float* tape_rho) {
+cudaError_t launch_walls(const DevState& d, int pp, cudaStream_t s, float* tape_dvdq, float* tape_rho) {
     switch (d.storage) {
-        case 1: return faces_t<__half>(d, pp, s, tape_rho);
-        case 2: return faces_t<__nv_bfloat16>(d, pp, s, tape_rho);
-        default: return faces_t<float>(d, pp, s, tape_rho);
+        case 1: return walls_t<__half>(d, pp, s, tape_dvdq, tape_rho);
+        case 2: return walls_t<__nv_bfloat16>(d, pp, s, tape_dvdq, tape_rho);
+        default: return walls_t<float>(d, pp, s, tape_dvdq, tape_rho);
     }
 }
 
@@ -387,21 +411,6 @@ cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* ta
     }
 }
 
-template <typename T>
-static cudaError_t bfl_t(const DevState& d, int pp, cudaStream_t s, float* tape) {
-    if (d.n_links == 0) return cudaSuccess;
-    k_bfl<T><<<(d.n_links + 255) / 256, 256, 0, s>>>(d.mem, (T*)d.f, d.l_node, d.l_meta, d.l_q, d.status, d.n_links, pp,
-                                                     tape);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bfl(const DevState& d, int pp, cudaStream_t s, float* tape_dvdq) {
-    switch (d.storage) {
-        case 1: return bfl_t<__half>(d, pp, s, tape_dvdq);
-        case 2: return bfl_t<__nv_bfloat16>(d, pp, s, tape_dvdq);
-        default: return bfl_t<float>(d, pp, s, tape_dvdq);
-    }
-}
 
 template <typename T>
 static cudaError_t init_t(const DevState& d, int m, const float* rho, const float* u, cudaStream_t s) {
@@ -435,49 +444,6 @@ cudaError_t launch_read(const DevState& d, int m, int parity, float* rho, float*
         case 2: return read_t<__nv_bfloat16>(d, m, parity, rho, u, g, s);
         default: return read_t<float>(d, m, parity, rho, u, g, s);
     }
-}
-
-// ---------------------------------------------------------------------------
-// Halo planes of a slab decomposition along x.  Every step ends with each
-// member's ghost planes overwritten by the planes of the members that own
-// them: all 19 slots of every padded node of the plane (fluid and solid, so
-// that the wall values the bounce-back left in solid slots travel too).  The
-// pair index runs fastest, so that the consecutive ghost planes of one side
-// (consecutive in memory) go to consecutive lanes.
-// ---------------------------------------------------------------------------
-template <typename E>
-__global__ void k_halo(const MemberDev* __restrict__ mem, E* __restrict__ f, const int4* __restrict__ halo, int n_pairs,
-                       int NY, long long n_plane) {
-    const long long total = (long long)n_pairs * n_plane * Q;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(t % n_pairs);
-        const long long r = t / n_pairs;
-        const long long yz = r % n_plane;
-        const int k = (int)(r / n_plane);
-        const int4 h = halo[p];
-        const MemberDev& dd = mem[h.x];
-        const MemberDev& ds = mem[h.z];
-        const long long Y = yz % NY, Z = yz / NY;
-        const long long nd = h.y + (long long)dd.NX * (Y + (long long)NY * Z);
-        const long long ns = h.w + (long long)ds.NX * (Y + (long long)NY * Z);
-        f[dd.f_off + (long long)k * dd.S + nd] = f[ds.f_off + (long long)k * ds.S + ns];
-    }
-}
-
-cudaError_t launch_halo(const DevState& d, cudaStream_t s) {
-    if (d.n_halo == 0) return cudaSuccess;
-    const MemberDev& m0 = d.h_mem[0];
-    const long long n_plane = (long long)m0.NY * m0.NZ;
-    const long long total = (long long)d.n_halo * n_plane * Q;
-    const int threads = 256;
-    const long long want = (total + threads - 1) / threads;
-    const int blocks = (int)std::min<long long>(want, (long long)std::max(d.n_sm, 1) * 16);
-    if (d.storage == 0)
-        k_halo<uint32_t><<<blocks, threads, 0, s>>>(d.mem, (uint32_t*)d.f, d.halo, d.n_halo, m0.NY, n_plane);
-    else
-        k_halo<uint16_t><<<blocks, threads, 0, s>>>(d.mem, (uint16_t*)d.f, d.halo, d.n_halo, m0.NY, n_plane);
-    return cudaGetLastError();
 }
 
 }  // namespace ibl

@@ -1,12 +1,15 @@
-"""A stiff capsule meeting the rounded apex of the deformable-capsule
+"""A stiff capsule carried through the rounded apex of the deformable-capsule
 bifurcation (256x96x64, D = 48, junction rounding 8 lu, d = 36 of 2562
-vertices, half-angle 30 deg, Ca = 0.005), stepped on the GPU until its
-largest edge stretch jumps; the state just before the jump is handed to the
-FP64 oracle's coupled operators (Eqs. uLag .. verletPosC), which must give the
-same x(t + dt) and vertex velocities as one CUDA step from that state.  The
-test prints where the jump happens: the vertex that moves most, its distance
-to the nearest solid node, and the oracle's split of its force into probe
-pressure, probe viscous stress, stretching, bending and volume terms."""
+vertices, half-angle 30 deg, Ca = 0.005).  With solid support nodes dropped
+from the MLS fits, the direct forcing near the wall amplified the fluid
+velocity by about a third per step (0.021 to above 0.5 lu per step in 12
+steps near step 6380, in the FP64 oracle as in the CUDA path) and threw a
+vertex a lattice spacing in one step; with the wall's state in the fits
+(Reading M4) the flow stays bounded.  The tests find the step of closest
+approach to the wall and check there: the largest edge stretch never jumps,
+one CUDA step from that state matches the oracle's coupled operators (Eqs.
+uLag .. verletPosC), and a 40-step window of both paths agrees step by
+step."""
 from types import SimpleNamespace
 
 import numpy as np
@@ -19,8 +22,9 @@ from paper_2207_06043_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-START = 6250          # steps run in one call before stepping one by one
-LIMIT = 7000
+START = 6000          # the search for the closest approach starts here
+STOP = 8000
+CHUNK = 25
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,34 +51,39 @@ def _wall_distance(g, x):
     return float(d.min())
 
 
+def _closest_approach(s, g, nv):
+    """Step from START to STOP in chunks, return (step, distance, state) of
+    the chunk boundary where a vertex is nearest a solid node, and the
+    largest growth of the largest edge stretch over one chunk."""
+    s.step(START, allow_damage=True)
+    best = (None, np.inf, None)
+    prev = s.read_capsules(1)[0]["max_stretch"]
+    worst = 0.0
+    for t in range(START, STOP, CHUNK):
+        x = s.read_capsule(0, with_verts=True)["verts"]
+        front = x[np.argsort(x[:, 0])[-300:]]
+        dist = min(_wall_distance(g, p) for p in front)
+        if dist < best[1]:
+            best = (t, dist, s.save_state())
+        done, _ = s.step(CHUNK, allow_damage=True)
+        assert done == CHUNK, t
+        st = s.read_capsules(1)[0]["max_stretch"]
+        worst = max(worst, st - prev)
+        prev = st
+    return best, worst
+
+
 def test_apex_contact_step_matches_the_oracle():
     c = W.deformable_capsule(30.0, 0.005)
     g = c["geometry"]
     cap = c["capsules"][0]
     nv = len(cap["verts"])
     s = W.make_solver(c)
-    done, _ = s.step(START, allow_damage=True)
-    assert done == START
-    hist = []
-    prev_blob, prev_stretch = None, s.read_capsules(1)[0]["max_stretch"]
-    t = START
-    jump = None
-    while t < LIMIT:
-        blob = s.save_state()
-        done, _ = s.step(1, allow_damage=True)
-        t += 1
-        st = s.read_capsules(1)[0]
-        hist.append((t, st["max_stretch"]))
-        if done == 0 or st["max_stretch"] - prev_stretch > 0.05 or st["max_stretch"] >= 2.0:
-            jump = (t, blob, prev_blob)
-            break
-        prev_blob, prev_stretch = blob, st["max_stretch"]
-    print("max stretch, last steps:", [(a, round(b, 4)) for a, b in hist[-8:]])
-    if jump is None:
-        s.close()
-        pytest.skip(f"no jump of the largest stretch before step {LIMIT}")
-    t_jump, blob, _ = jump
-    # the pre-step state of the jump, then one CUDA step from it
+    (t_c, dist, blob), worst = _closest_approach(s, g, nv)
+    print(f"closest approach at step {t_c}: a vertex {dist:.3f} lu from a solid node; largest growth of the "
+          f"max stretch over {CHUNK} steps {worst:.2e}")
+    assert worst < 0.05, worst
+    # one CUDA step from the state of closest approach
     s.load_state(blob)
     g0 = s.read_populations()
     st0 = s.read_capsule_state(0, nv)
@@ -91,72 +100,40 @@ def test_apex_contact_step_matches_the_oracle():
     o.bodies = [b]
     _, per = o.ib_force()
     Fs = o.structure(o.f, per)
-    x0 = st0["x"]
     o.update(o.f, per, Fs)
     dx = float(np.abs(b.x - st1["x"]).max())
     dv = float(np.abs(b.vel - st1["vel"]).max())
-    # where it happens
-    move = np.linalg.norm(st1["x"] - x0, axis=1)
-    k = int(np.argmax(move))
-    Av, nrm = per[0]["Av"], per[0]["nrm"]
-    Fp, Ft = Mb.hydrodynamic_forces(lat, o.f, x0, Av, nrm)
-    V = Mb.diagnostics(x0, b.tris)["volume"]
-    Fst = Mb.stretch_forces(x0, b.rest)
-    Fb = Mb.bending_forces(x0, b.rest)
-    Fv = Mb.volume_forces(x0, b.rest, V, Av, nrm)
-    print(f"jump at step {t_jump}: vertex {k} moves {move[k]:.3e} lu (median {np.median(move):.3e}); "
-          f"x {np.round(x0[k], 3).tolist()}, n {np.round(nrm[k], 3).tolist()}, "
-          f"wall distance {_wall_distance(g, x0[k]):.3f}, probe+ wall distance "
-          f"{_wall_distance(g, x0[k] + 1.2 * nrm[k]):.3f}")
-    print(f"  U {np.round(per[0]['U'][k], 5).tolist()}; forces: pressure {np.round(Fp[k], 5).tolist()}, "
-          f"viscous {np.round(Ft[k], 5).tolist()}, stretch {np.round(Fst[k], 5).tolist()}, "
-          f"bending {np.round(Fb[k], 5).tolist()}, volume {np.round(Fv[k], 5).tolist()}; m_v {b.rest.mv:.4f}")
     st = per[0]["stencil"]
-    print(f"  marker stencil of the vertex: {int((st.weight[k] > 0).sum())} fluid support nodes, "
-          f"sum |phi| {np.abs(st.phi[k]).sum():.3f} (a support wholly in the fluid: "
-          f"{np.median(np.abs(st.phi).sum(axis=1)):.3f} median over the vertices)")
-    print(f"  CUDA vs oracle from the same state: x {dx:.2e}, velocity {dv:.2e}")
-    assert dx <= 1e-5 * max(1.0, move[k]) and dv <= 1e-5 * max(1.0, move[k]), (dx, dv)
+    solid = (~lat.fluid[st.nodes]).any(axis=1)
+    print(f"step {t_c + 1}: {int(solid.sum())} marker stencils with solid support nodes; "
+          f"CUDA vs oracle: x {dx:.2e}, velocity {dv:.2e}")
+    assert solid.sum() > 0
+    assert dx <= 1e-5 and dv <= 1e-5, (dx, dv)
 
 
 def test_apex_contact_window_against_the_oracle():
-    """The 40 steps before the jump, from the GPU state, stepped by both
-    paths: the growth of the fluid speed near the tip and of the largest edge
-    stretch must be the same in the FP64 oracle (it is the method's, not the
-    kernels'); the per-step largest stretch agrees within 1e-3 until the
-    jump and both paths jump at the same step."""
+    """40 steps around the closest approach, from the GPU state, by both
+    paths: per step the largest stretch and the largest fluid speed agree
+    within 1e-3 relative, and the speed stays below 1.5 times its start."""
     from helpers import oracle_for
     c = W.deformable_capsule(30.0, 0.005)
     cap = c["capsules"][0]
     nv = len(cap["verts"])
     s = W.make_solver(c)
-    s.step(START, allow_damage=True)
-    start = s.save_state()
-    t = START
-    hist = []
-    while t < LIMIT:
-        done, _ = s.step(1, allow_damage=True)
-        t += 1
-        hist.append(s.read_capsules(1)[0]["max_stretch"])
-        if done == 0 or hist[-1] >= 2.0 or (len(hist) > 1 and hist[-1] - hist[-2] > 0.05):
-            break
-    if t >= LIMIT:
-        s.close()
-        pytest.skip("no jump")
-    t_jump = t
-    w0 = t_jump - 40
-    s.load_state(start)
-    s.step(w0 - START, allow_damage=True)
+    (t_c, _, _), _ = _closest_approach(s, c["geometry"], nv)
+    s.close()
+    s = W.make_solver(c)
+    w0 = max(t_c - 20, 1)
+    s.step(w0, allow_damage=True)
     g0 = s.read_populations()
     st0 = s.read_capsule_state(0, nv)
     gpu = []
-    for _ in range(41):
+    for _ in range(40):
         done, _ = s.step(1, allow_damage=True)
+        assert done == 1
         st = s.read_capsules(1)[0]
         _, u = s.read_fields()
         gpu.append((st["max_stretch"], float(np.linalg.norm(u, axis=1).max())))
-        if done == 0:
-            break
     s.close()
     lat, o = oracle_for(c, f0=g0.astype(np.float64) + L.W[:, None])
     b = o.bodies[0]
@@ -168,9 +145,6 @@ def test_apex_contact_window_against_the_oracle():
         orc.append((Mb.max_stretch(b.x, b.rest), float(np.linalg.norm(uo[lat.fluid], axis=1).max())))
     for k, (a, r) in enumerate(zip(gpu, orc)):
         print(f"step {w0 + k + 1}: max stretch {a[0]:.5f} / {r[0]:.5f}, max |u| {a[1]:.4e} / {r[1]:.4e}")
-    jump_g = next((k for k, a in enumerate(gpu) if a[0] >= 2.0), None)
-    jump_o = next((k for k, r in enumerate(orc) if r[0] >= 2.0), None)
-    assert jump_g is not None and jump_o is not None, (jump_g, jump_o)
-    assert abs(jump_g - jump_o) <= 1, (jump_g, jump_o)
-    for a, r in zip(gpu[:min(jump_g, jump_o)], orc):
-        assert abs(a[0] - r[0]) <= 1e-3 * r[0], (a, r)
+    assert max(r[1] for r in orc) < 1.5 * orc[0][1]
+    for a, r in zip(gpu, orc):
+        assert abs(a[0] - r[0]) <= 1e-3 * r[0] and abs(a[1] - r[1]) <= 1e-3 * r[1], (a, r)

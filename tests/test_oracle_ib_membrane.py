@@ -39,34 +39,49 @@ def test_mls_partition_of_unity_and_linear_reproduction():
     assert st.nodes.shape == (200, 27) and (st.weight > 0).all()
 
 
-def test_mls_near_walls_excludes_solid_and_stays_consistent():
+def test_mls_near_walls_keeps_solid_nodes_as_wall_data():
+    """Reading M4: near a wall every point of the 3x3x3 support takes part,
+    the solid ones with the wall's rest state, so the fit keeps the bulk
+    weights (partition of unity, linear reproduction, no fallback), and the
+    velocity interpolated from a uniform flow U0 in the fluid is U0 times the
+    weight of the fluid points alone."""
     g = G.straight_duct(10, 14, 14, 9.0, periodic_x=True)
     lat = L.Lattice(g.nx, g.ny, g.nz, 0.8, g.tag, g.links, g.faces, g.periodic)
     rng = np.random.default_rng(2)
     yc = g.info["yc"]
     X = np.stack([rng.uniform(0, 10, 100), yc + rng.uniform(3.0, 4.4, 100), yc + rng.uniform(-4, 4, 100)], 1)
     st = ib.stencil(lat, X)
-    assert (st.weight[~lat.fluid[st.nodes]] == 0).all()
-    assert (st.weight[lat.fluid[st.nodes]] > 0).sum() > 0
+    solid = ~lat.fluid[st.nodes]
+    assert solid.any(axis=1).sum() > 50              # most points see the wall
+    assert (st.weight > 0).all() and not st.fallback.any()
     pos = np.stack([lat.X, lat.Y, lat.Z], axis=1).astype(float)[st.nodes]
     assert np.allclose(st.phi.sum(1), 1.0, atol=1e-12)
-    ok = ~st.fallback
-    assert ok.sum() > 50
     # periodic x: unwrap node coordinates near the seam before checking x
     dx = (pos[..., 0] - X[:, None, 0] + 5) % 10 - 5
-    assert np.allclose(np.einsum("mk,mk->m", st.phi, dx)[ok], 0.0, atol=1e-11)
-    assert np.allclose(np.einsum("mk,mk->m", st.phi, pos[..., 1])[ok], X[ok, 1], atol=1e-11)
+    assert np.allclose(np.einsum("mk,mk->m", st.phi, dx), 0.0, atol=1e-11)
+    assert np.allclose(np.einsum("mk,mk->m", st.phi, pos[..., 1]), X[:, 1], atol=1e-11)
+    U0 = np.array([0.02, -0.01, 0.005])
+    u = np.where(lat.fluid[:, None], U0[None, :], 0.0)
+    f = lat.init_equilibrium(None, u)
+    f[:, ~lat.fluid] = L.W[:, None]          # solid nodes: the rest state
+    U = ib.interpolate_velocity(f, st)
+    w_fluid = np.where(solid, 0.0, st.phi).sum(axis=1)
+    assert np.allclose(U, w_fluid[:, None] * U0[None, :], atol=1e-12)
+    assert (np.abs(w_fluid - 1.0) > 1e-3).sum() > 20
 
 
-def test_mls_singular_support_falls_back_to_nearest_fluid_node():
+def test_mls_support_off_the_box_falls_back_to_the_nearest_point():
+    """A point beyond a non-periodic box face keeps one plane of its support
+    inside the box: the moment matrix is singular and the nearest point of
+    that plane takes the whole weight (Reading M4)."""
     n = 7
-    tag = np.ones(n ** 3, np.uint8)
-    tag[3 + n * (3 + n * 3)] = 0       # one fluid node in a solid block
+    tag = np.zeros(n ** 3, np.uint8)
     lat = L.Lattice(n, n, n, 0.8, tag, np.zeros(0, G.LINK_DTYPE), [G.Face() for _ in range(6)],
-                    (True, True, True))
-    st = ib.stencil(lat, np.array([[3.2, 2.9, 3.4]]))
+                    (False, True, True))
+    st = ib.stencil(lat, np.array([[-0.8, 3.2, 2.9]]))
+    assert st.fallback[0]
     assert st.phi.sum() == 1.0
-    assert st.nodes[0][np.argmax(st.phi[0])] == 3 + n * (3 + n * 3)
+    assert st.nodes[0][np.argmax(st.phi[0])] == 0 + n * (3 + n * 3)
     assert np.all(st.grad == 0)
 
 
