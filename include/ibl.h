@@ -346,9 +346,9 @@ ibl_status ibl_slab_plan(int32_t nx, int32_t periodic_x, int32_t n_slabs, int32_
                          ibl_slab* out);
 
 /* A context that steps the lattice of `whole` (one lattice, set up but never
- * stepped or read: geometry, faces, initial state) as n_slabs x-slabs, each a
- * member of one batched context holding its owned planes plus `halo` ghost
- * planes per cut side (ibl_slab_plan with fluid-node weights).  A cut face is
+ * stepped or read: geometry, faces, initial state, capsules) as n_slabs
+ * x-slabs, each a member of one batched context holding its owned planes plus
+ * `halo` ghost planes per cut side (ibl_slab_plan with fluid-node weights).  A cut face is
  * no Dirichlet face: after every step each ghost plane is overwritten by the
  * plane of the slab that owns it (all 19 slots of every node, fluid and
  * solid), one kernel for all planes.  With halo >= 4 every owned node ends
@@ -356,13 +356,25 @@ ibl_status ibl_slab_plan(int32_t nx, int32_t periodic_x, int32_t n_slabs, int32_
  * node's new values depend on its neighbours' old ones (streaming, 1 plane)
  * and on post-collision values two planes upstream (the quadratic wall
  * rule), which depend on slots one plane further.
+ *   - Capsules: they belong to one more member, the whole lattice as the
+ *     capsules see it (tags and the IB arrays of the whole box, no
+ *     populations).  Its moments at each capsule's shell nodes come from the
+ *     slab that owns each node; after the marker stencils, the IB force of
+ *     every shell node goes to each slab that holds the node (owner and ghost
+ *     copies); a damage or non-finite flag stops every slab.  The capsule
+ *     calls (ibl_read_capsule, ibl_read_capsules with member 0,
+ *     ibl_read_capsule_state) address these capsules.  Owned populations
+ *     then match the undivided lattice to the rounding of the spreading's
+ *     atomics.
  *   - ibl_read_fields / ibl_read_populations return the whole lattice
  *     (host buffers only: on_device gives IBL_ERR_ARG); the ibl_member_*
- *     readers return slab m with its ghost planes.
- *   - `whole` is only read; destroy it separately.  Capsules are not
- *     supported yet (IBL_ERR_STATE), nor the adjoint on a slab context.
- *   - IBL_ERR_ARG for an invalid plan (see ibl_slab_plan) or halo < 4;
- *     IBL_ERR_STATE when whole was stepped or read or holds capsules. */
+ *     readers return slab m with its ghost planes (the whole-lattice member
+ *     holds no populations: IBL_ERR_ARG).
+ *   - `whole` is only read; destroy it separately.  No adjoint on a slab
+ *     context.
+ *   - IBL_ERR_ARG for an invalid plan (see ibl_slab_plan), halo < 4 or more
+ *     than 127 slabs with capsules; IBL_ERR_STATE when whole was stepped or
+ *     read. */
 ibl_status ibl_slab_group_create(ibl_ctx* whole, int32_t n_slabs, int32_t halo, void* cuda_stream, ibl_ctx** out);
 
 /* The plan of a slab context: *n_slabs on entry is the capacity of out, on

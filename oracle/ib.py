@@ -71,9 +71,10 @@ def stencil(lat, X):
     nearest node (round half up), r_k = |X - x^k| / 2.6 (Reading M2).
     Reading M4: every Eulerian point of the support takes part, a solid one
     with the state of the wall it lies in (the populations of a solid node
-    are the rest equilibrium: rho = 1, u = 0); only points off a non-periodic
-    box get W = 0, and a support whose moment matrix is singular (possible
-    only for a point at the box edge) falls back to its nearest point.
+    are the rest equilibrium: rho = 1, u = 0) and one off a non-periodic box
+    with the state of the nearest box node (its coordinates clamped to the
+    box).  Every support is then the full block, so the moment matrix is
+    never singular; the nearest-point fallback below is a guard only.
     Dropping the solid points instead leaves a point near a wall with a few
     fluid points that carry large weights, and the explicit direct forcing
     (Eq. bodyforce) then amplifies the fluid velocity there from step to step.
@@ -97,7 +98,6 @@ def stencil(lat, X):
         if lat.periodic[ax]:
             c = c % dims[ax]
         else:
-            ok &= (c >= 0) & (c < dims[ax])
             c = np.clip(c, 0, dims[ax] - 1)
         wrapped.append(c)
     nodes = wrapped[0] + lat.nx * (wrapped[1] + lat.ny * wrapped[2])

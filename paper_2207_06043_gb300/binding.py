@@ -461,7 +461,7 @@ def slab_group(whole, n_slabs, halo=4, stream=None):
     g._check(L.ibl_slab_info(h, C.byref(n), out))
     g.slabs = [(o.x0, o.x1, o.lo, o.hi) for o in out[:n.value]]
     g.member_shapes = [(x1 - x0 + lo + hi, whole.shape[1], whole.shape[2]) for x0, x1, lo, hi in g.slabs]
-    g._nv = {}
+    g._nv = dict(getattr(whole, "_nv", {}))
     return g
 
 

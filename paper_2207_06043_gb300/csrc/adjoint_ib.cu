@@ -235,16 +235,12 @@ __global__ void __launch_bounds__(IB_PROBE_THREADS) k_adj_probes(
     for (int j = 0; j < GS; ++j) {
         const int k = r + GL * j;
         if (k >= 27) continue;
-        if (M.fallback < 0) {
-            const float p = mls_row_g(M, 0, j, k), g0 = mls_row_g(M, 1, j, k), g1 = mls_row_g(M, 2, j, k),
-                        g2 = mls_row_g(M, 3, j, k);
-            acc[0] += p * q[j].x;
-            acc[1] += g0 * q[j].y; acc[2] += g1 * q[j].y; acc[3] += g2 * q[j].y;
-            acc[4] += g0 * q[j].z; acc[5] += g1 * q[j].z; acc[6] += g2 * q[j].z;
-            acc[7] += g0 * q[j].w; acc[8] += g1 * q[j].w; acc[9] += g2 * q[j].w;
-        } else if (M.fallback == k) {
-            acc[0] += q[j].x;
-        }
+        const float p = mls_row_g(M, 0, j, k), g0 = mls_row_g(M, 1, j, k), g1 = mls_row_g(M, 2, j, k),
+                    g2 = mls_row_g(M, 3, j, k);
+        acc[0] += p * q[j].x;
+        acc[1] += g0 * q[j].y; acc[2] += g1 * q[j].y; acc[3] += g2 * q[j].y;
+        acc[4] += g0 * q[j].z; acc[5] += g1 * q[j].z; acc[6] += g2 * q[j].z;
+        acc[7] += g0 * q[j].w; acc[8] += g1 * q[j].w; acc[9] += g2 * q[j].w;
     }
 #pragma unroll
     for (int i = 0; i < 10; ++i) acc[i] = group_sum(acc[i], mask);
@@ -295,29 +291,23 @@ __global__ void __launch_bounds__(IB_PROBE_THREADS) k_adj_probes(
         const int k = r + GL * j;
         lam[0][j] = lam[1][j] = lam[2][j] = lam[3][j] = 0.f;
         if (k >= 27 || node[j] < 0) continue;
-        float lr, lux = 0.f, luy = 0.f, luz = 0.f;
-        if (M.fallback < 0) {
-            const float ph = mls_row_g(M, 0, j, k);
-            const float ps[3] = {mls_row_g(M, 1, j, k), mls_row_g(M, 2, j, k), mls_row_g(M, 3, j, k)};
-            lr = ph * lrP;
+        float lux = 0.f, luy = 0.f, luz = 0.f;
+        const float ph = mls_row_g(M, 0, j, k);
+        const float ps[3] = {mls_row_g(M, 1, j, k), mls_row_g(M, 2, j, k), mls_row_g(M, 3, j, k)};
+        const float lr = ph * lrP;
 #pragma unroll
-            for (int jj = 0; jj < 3; ++jj) {
-                lux += ps[jj] * lG[0][jj];
-                luy += ps[jj] * lG[1][jj];
-                luz += ps[jj] * lG[2][jj];
-            }
-            lam[0][j] = lrP * q[j].x;
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj)
-                lam[1 + jj][j] = lG[0][jj] * q[j].y + lG[1][jj] * q[j].z + lG[2][jj] * q[j].w;
-        } else {
-            if (M.fallback != k) continue;
-            lr = lrP;
+        for (int jj = 0; jj < 3; ++jj) {
+            lux += ps[jj] * lG[0][jj];
+            luy += ps[jj] * lG[1][jj];
+            luz += ps[jj] * lG[2][jj];
         }
+        lam[0][j] = lrP * q[j].x;
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj)
+            lam[1 + jj][j] = lG[0][jj] * q[j].y + lG[1][jj] * q[j].z + lG[2][jj] * q[j].w;
         add4(a.lmac + d.node_off + node[j], lr, lux, luy, luz);
     }
-    f3 lP = {0.f, 0.f, 0.f};
-    if (M.fallback < 0) lP = mls_vjp_g<4>(M, lam, r, mask);
+    const f3 lP = mls_vjp_g<4>(M, lam, r, mask);
     if (r == 0) {
         const float sgf = (float)sg;
         add4(a.lx + l, lP.x, lP.y, lP.z);
@@ -352,7 +342,7 @@ __global__ void __launch_bounds__(IB_MARKER_THREADS) k_adj_markers(
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
         const int k = r + GL * j;
-        ph[j] = k >= 27 ? 0.f : (M.fallback < 0 ? mls_row_g(M, 0, j, k) : (M.fallback == k ? 1.f : 0.f));
+        ph[j] = k >= 27 ? 0.f : mls_row_g(M, 0, j, k);
         node[j] = -1;
         q[j] = lf[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ph[j] != 0.f) {
@@ -388,8 +378,7 @@ __global__ void __launch_bounds__(IB_MARKER_THREADS) k_adj_markers(
         add4(a.lmac + d.node_off + node[j], 0.f, ph[j] * lUx, ph[j] * lUy, ph[j] * lUz);
     }
     lAs = group_sum(lAs, mask);
-    f3 lP = {0.f, 0.f, 0.f};
-    if (M.fallback < 0) lP = mls_vjp_g<1>(M, lam, r, mask);
+    const f3 lP = mls_vjp_g<1>(M, lam, r, mask);
     double lVp = 0.0;
     if (r == 0) {
         a.lv[l] = make_float4(lFx, lFy, lFz, 0.f);

@@ -42,6 +42,9 @@ struct MemberHost {
     std::vector<float> face_vel[6];
     std::vector<float> init_rho, init_u;
     std::vector<CapsuleHost> caps;
+    // the whole lattice of a slab context as its capsules see it: tags and
+    // capsules only, no populations, links or faces
+    bool whole_view = false;
 };
 
 // Rest data of one capsule kept on the host for read-out.
@@ -94,10 +97,10 @@ struct ibl_ctx {
     std::vector<uint32_t> h_status;
     std::string err;
     // adjoint work buffers and segment graphs, kept between ibl_adjoint calls
-    struct AdjSeg { int kind, mode, parity, len; float* lin; cudaGraphExec_t exec; };
+    struct AdjSeg { int kind, mode, parity, len; float* lin; int tb; cudaGraphExec_t exec; };
     struct AdjCache {
         int kind = -1;   // 0: flow objective (lattice only), 1: capsule objective
-        size_t ck_bytes = 0, tape_steps = 0;
+        size_t ck_bytes = 0, tape_steps = 0, tape2_steps = 0;
         char *ck = nullptr, *snap = nullptr;
         float4* tape_rhou = nullptr;
         float *tape_dvdq = nullptr, *tape_rho = nullptr, *lamA = nullptr, *lamB = nullptr;
@@ -105,6 +108,18 @@ struct ibl_ctx {
         // capsule objective: IB-force and vertex tapes, per-vertex adjoints
         float4* tape_F = nullptr;
         double *tape_x = nullptr, *tape_v = nullptr;
+        // a second tape, so that the recompute of one segment runs beside the
+        // reverse sweep of the next, and the reverse sweep's own copies of the
+        // geometry buffers it rebuilds at every step
+        float4 *tape2_rhou = nullptr, *tape2_F = nullptr;
+        float *tape2_dvdq = nullptr, *tape2_rho = nullptr;
+        double *tape2_x = nullptr, *tape2_v = nullptr;
+        double* rx = nullptr;
+        float4 *rxm = nullptr, *rvacc = nullptr;
+        float *rnrm = nullptr, *rarea = nullptr;
+        CapsuleSums* rsums = nullptr;
+        cudaStream_t rs = nullptr;
+        cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr}, ev_fwd = nullptr;
         AdjCapPtrs cp;
         std::vector<AdjSeg> graphs;
     } adj;
@@ -415,9 +430,13 @@ void free_adjoint(ibl_ctx* ctx) {
     void* ptrs[] = {A.ck,   A.snap,  A.tape_rhou, A.tape_dvdq, A.tape_rho, A.lamA,   A.lamB,
                     A.acc,  A.tape_F, A.tape_x,  A.tape_v,   A.cp.lx,    A.cp.lxp, A.cp.lv,
                     A.cp.lU, A.cp.lF, A.cp.ln,   A.cp.lA,    A.cp.snorm, A.cp.lV,  A.cp.lfib,
-                    A.cp.lmac};
+                    A.cp.lmac, A.tape2_rhou, A.tape2_F, A.tape2_dvdq, A.tape2_rho, A.tape2_x, A.tape2_v,
+                    A.rx, A.rxm, A.rvacc, A.rnrm, A.rarea, A.rsums};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : {A.ev_rec[0], A.ev_rec[1], A.ev_rev[0], A.ev_rev[1], A.ev_fwd})
+        if (e) cudaEventDestroy(e);
+    if (A.rs) cudaStreamDestroy(A.rs);
     A = ibl_ctx::AdjCache{};
 }
 
@@ -526,10 +545,6 @@ bool crop_slab(const MemberHost& W, const ibl_slab& b, int S, MemberHost& M, std
                         for (int c = 0; c < 3; ++c) M.init_u[3 * ln + c] = W.init_u[3 * gn + c];
                 }
     }
-    if (!W.caps.empty()) {
-        why = "slab groups take no capsules";
-        return false;
-    }
     return true;
 }
 
@@ -611,7 +626,8 @@ ibl_status finalize(ibl_ctx* ctx) {
     CKS(noalloc_scratch(ctx, dev_id, &ctx->noalloc));
     const int nm = (int)ctx->members.size();
     if (nm < 1 || nm > MAX_MEMBERS) return fail(ctx, IBL_ERR_ARG, "member count out of range");
-    for (auto& M : ctx->members) CKS(validate_member(ctx, M));
+    for (auto& M : ctx->members)
+        if (!M.whole_view) CKS(validate_member(ctx, M));
 
     const size_t esize = ctx->storage == IBL_STORAGE_F32 ? 4 : 2;
     DevState& D = ctx->dev;
@@ -645,9 +661,10 @@ ibl_status finalize(ibl_ctx* ctx) {
         if (Np * 19 >= (1LL << 31)) return fail(ctx, IBL_ERR_ARG, "lattice too large for one member");
         md.N = (int)Np;
         md.S = (int)round_up((size_t)Np, 64) + IBL_PLANE_PAD;
-        md.f_off = f_off;
+        md.f_off = M.whole_view ? 0 : f_off;
         md.node_off = node_off;
-        f_off += 19LL * md.S;
+        md.slab_view = M.whole_view ? 1 : 0;
+        if (!M.whole_view) f_off += 19LL * md.S;
         node_off += (long long)round_up((size_t)Np, 256);
         md.omega = (float)(1.0 / d.tau);
         md.guo = (float)(1.0 - 0.5 / d.tau);
@@ -825,6 +842,11 @@ ibl_status finalize(ibl_ctx* ctx) {
             MemberDev& md = ctx->hmem[m];
             md.seg_begin = (int)segs.size();
             md.bseg_begin = (int)bsegs.size();
+            if (ctx->members[m].whole_view) {   // no lattice work
+                md.seg_count = md.bseg_count = 0;
+                base += round_up((size_t)md.N, 256);
+                continue;
+            }
             const int ns = (md.N + 31) / 32;
             const bool per[3] = {(md.per & 1) != 0, (md.per & 2) != 0, (md.per & 4) != 0};
             const int dimP[3] = {md.NX, md.NY, md.NZ};
@@ -1015,6 +1037,25 @@ ibl_status finalize(ibl_ctx* ctx) {
         D.n_halo = (int)pairs.size();
         CKS(dev_alloc(ctx, D.halo, pairs.size()));
         CKS(upload(ctx, D.halo, pairs));
+        if (nm == P.S + 1 && ctx->members[P.S].whole_view) {
+            std::vector<int> of(P.nx, 0);
+            std::vector<int4> tab(P.S);
+            for (int m = 0; m < P.S; ++m) {
+                const ibl_slab& b = P.sl[m];
+                for (int x = b.x0; x < b.x1; ++x) of[x] = m;
+                tab[m] = make_int4(b.x0, b.x1, b.lo, b.hi);
+            }
+            int* d_of = nullptr;
+            int4* d_tab = nullptr;
+            CKS(dev_alloc(ctx, d_of, of.size()));
+            CKS(dev_alloc(ctx, d_tab, tab.size()));
+            CKS(upload(ctx, d_of, of));
+            CKS(upload(ctx, d_tab, tab));
+            D.slab_of = d_of;
+            D.slab_tab = d_tab;
+            D.slab_w = P.S;
+            D.n_slabs = P.S;
+        }
     }
     D.h_mem = ctx->hmem.data();
     CKS(dev_alloc(ctx, D.mem, (size_t)nm));
@@ -1022,6 +1063,7 @@ ibl_status finalize(ibl_ctx* ctx) {
     // initial populations
     for (int mi = 0; mi < nm; ++mi) {
         const MemberHost& M = ctx->members[mi];
+        if (M.whole_view) continue;
         float* drho = nullptr;
         float* du = nullptr;
         if (!M.init_rho.empty()) { CK(cudaMalloc((void**)&drho, sizeof(float) * M.init_rho.size())); }
@@ -1101,6 +1143,7 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks, cons
         CK(launch_shell(D, parity, s));
         CK(launch_markers(D, s));
         CK(launch_probes(D, s));
+        CK(launch_fib_scatter(D, s));
         CKS(end(TK_IB, s));
         CKS(begin(s));
         CK(launch_repulsion(D, s));
@@ -1114,6 +1157,7 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks, cons
         CK(cudaEventRecord(ctx->ev_shell, s));
         CK(launch_markers(D, s));
         CK(cudaEventRecord(ctx->ev_ib, s));
+        CK(launch_fib_scatter(D, s));
         CK(cudaStreamWaitEvent(s3, ctx->ev_shell, 0));
         CK(launch_probes(D, s3));
         CK(cudaEventRecord(ctx->ev_probes, s3));
@@ -1135,6 +1179,7 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks, cons
         CK(cudaEventRecord(ctx->ev_join, s2));
         CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     }
+    if (caps) CK(launch_status_spread(D, s));
     return IBL_OK;
 }
 
@@ -1179,6 +1224,7 @@ MemberHost* member0(ibl_ctx* ctx) { return ctx->members.empty() ? nullptr : &ctx
 
 ibl_status read_fields_member(ibl_ctx* ctx, int m, float* rho, float* u, float* g, int on_device) {
     if (m < 0 || m >= (int)ctx->members.size()) return fail(ctx, IBL_ERR_ARG, "member out of range");
+    if (ctx->members[m].whole_view) return fail(ctx, IBL_ERR_ARG, "the whole-lattice member of a slab context holds no populations");
     CKS(finalize(ctx));
     CKS(enter(ctx));
     const MemberDev& md = ctx->hmem[m];
@@ -1215,6 +1261,14 @@ ibl_status read_fields_member(ibl_ctx* ctx, int m, float* rho, float* u, float* 
     }
     CKS(leave(ctx));
     return IBL_OK;
+}
+
+// The member whose capsules member m's capsule calls address: in a slab
+// context the capsules live in its whole-lattice member.
+int caps_member(const ibl_ctx* ctx, int m) {
+    const int n = (int)ctx->members.size();
+    if (ctx->slabs.S > 1 && m == 0 && n == ctx->slabs.S + 1 && ctx->members[n - 1].whole_view) return n - 1;
+    return m;
 }
 
 // The whole lattice of a slab context: each slab's owned planes, read from
@@ -1516,13 +1570,14 @@ ibl_status ibl_read_populations(ibl_ctx* ctx, float* g, int32_t on_device) {
 
 ibl_status ibl_read_capsule(ibl_ctx* ctx, int32_t id, ibl_capsule_stats* stats, double* verts_out) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
-    return read_capsule_member(ctx, 0, id, stats, verts_out);
+    return read_capsule_member(ctx, caps_member(ctx, 0), id, stats, verts_out);
 }
 
 ibl_status ibl_read_capsules(ibl_ctx* ctx, int32_t member, ibl_capsule_stats* stats, int32_t n) {
     if (!ctx || !stats) return fail(ctx, IBL_ERR_ARG, "null argument");
     if (member < 0 || member >= (int)ctx->members.size()) return fail(ctx, IBL_ERR_ARG, "member out of range");
     CKS(finalize(ctx));
+    member = caps_member(ctx, member);
     const std::vector<int>& ids = ctx->member_caps[member];
     if (n != (int32_t)ids.size())
         return fail(ctx, IBL_ERR_ARG, "member " + std::to_string(member) + " holds " + std::to_string(ids.size()) +
@@ -1565,8 +1620,9 @@ ibl_status ibl_read_capsules(ibl_ctx* ctx, int32_t member, ibl_capsule_stats* st
 ibl_status ibl_read_capsule_state(ibl_ctx* ctx, int32_t id, double* x, double* x_prev, double* vel, double* force) {
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
     CKS(finalize(ctx));
-    if (id < 0 || id >= (int)ctx->member_caps[0].size()) return fail(ctx, IBL_ERR_ARG, "capsule id out of range");
-    const CapsuleRestHost& R = ctx->rest[ctx->member_caps[0][id]];
+    const int cm = caps_member(ctx, 0);
+    if (id < 0 || id >= (int)ctx->member_caps[cm].size()) return fail(ctx, IBL_ERR_ARG, "capsule id out of range");
+    const CapsuleRestHost& R = ctx->rest[ctx->member_caps[cm][id]];
     const size_t n3 = 3 * (size_t)R.nv, off = 3 * (size_t)R.v_begin;
     CKS(enter(ctx));
     std::vector<float> F(4 * (size_t)R.nv);
@@ -1625,9 +1681,8 @@ ibl_status ibl_slab_group_create(ibl_ctx* whole, int32_t n_slabs, int32_t halo, 
     if (whole->members.size() != 1 || whole->slabs.S > 1)
         return fail(nullptr, IBL_ERR_STATE, "a slab context is cut from one lattice");
     const MemberHost& W = whole->members[0];
-    if (!W.caps.empty()) return fail(nullptr, IBL_ERR_STATE, "slab groups take no capsules");
     if (halo < 4) return fail(nullptr, IBL_ERR_ARG, "halo must be at least 4 planes");
-    if (n_slabs > MAX_MEMBERS) return fail(nullptr, IBL_ERR_ARG, "too many slabs");
+    if (n_slabs + (W.caps.empty() ? 0 : 1) > MAX_MEMBERS) return fail(nullptr, IBL_ERR_ARG, "too many slabs");
     const auto& d = W.desc;
     if ((long long)W.tag.size() != (long long)d.nx * d.ny * d.nz) return fail(nullptr, IBL_ERR_STATE, "geometry not set");
     // balance the slabs by fluid nodes per plane
@@ -1647,6 +1702,16 @@ ibl_status ibl_slab_group_create(ibl_ctx* whole, int32_t n_slabs, int32_t halo, 
             ibl_destroy(ctx);
             return fail(nullptr, IBL_ERR_ARG, why);
         }
+    if (!W.caps.empty() && n_slabs > 1) {
+        MemberHost V;
+        V.desc = W.desc;
+        V.tag = W.tag;
+        V.caps = W.caps;
+        V.whole_view = true;
+        ctx->members.push_back(std::move(V));
+    } else if (!W.caps.empty()) {
+        ctx->members[0].caps = W.caps;
+    }
     ctx->slabs.S = n_slabs;
     ctx->slabs.H = halo;
     ctx->slabs.nx = d.nx;
@@ -1815,7 +1880,7 @@ ibl_status ibl_adjoint_flow(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, c
             const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
             cudaGraphDestroy(gr);
             CK(ei);
-            graphs.push_back({0, mode, parity0, len, lin0, ex});
+            graphs.push_back({0, mode, parity0, len, lin0, 0, ex});
             CK(cudaGraphLaunch(ex, s));
             return IBL_OK;
         };
@@ -1901,7 +1966,8 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
     const size_t ck_one = D.f_bytes + cap_bytes;
     const size_t ck_need = (size_t)(n_ck - 1) * ck_one;
     auto& AC = ctx->adj;
-    if (AC.kind != 1 || AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc) {
+    if (AC.kind != 1 || AC.ck_bytes < ck_need || AC.tape_steps < (size_t)K || !AC.acc ||
+        (n_ck > 1 && AC.tape2_steps < (size_t)K)) {
         cudaStreamSynchronize(ctx->work);
         free_adjoint(ctx);
         AC.kind = 1;
@@ -1940,12 +2006,33 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
             {(size_t)D.n_caps * sizeof(double), (void**)&c.lV},
             {N * sizeof(float4), (void**)&c.lfib},
             {N * sizeof(float4), (void**)&c.lmac},
+            {n_ck > 1 ? (size_t)K * N * sizeof(float4) : 0, (void**)&AC.tape2_rhou},
+            {n_ck > 1 ? (size_t)K * N * sizeof(float4) : 0, (void**)&AC.tape2_F},
+            {n_ck > 1 ? (size_t)K * D.n_links * sizeof(float) : 0, (void**)&AC.tape2_dvdq},
+            {n_ck > 1 ? (size_t)K * D.n_face_nodes * sizeof(float) : 0, (void**)&AC.tape2_rho},
+            {n_ck > 1 ? (size_t)K * nv3 * sizeof(double) : 0, (void**)&AC.tape2_x},
+            {n_ck > 1 ? (size_t)K * nv3 * sizeof(double) : 0, (void**)&AC.tape2_v},
+            {nv3 * sizeof(double), (void**)&AC.rx},
+            {2 * (size_t)nv * sizeof(float4), (void**)&AC.rxm},
+            {(size_t)nv * sizeof(float4), (void**)&AC.rvacc},
+            {nv3 * sizeof(float), (void**)&AC.rnrm},
+            {(size_t)nv * sizeof(float), (void**)&AC.rarea},
+            {(size_t)D.n_caps * sizeof(CapsuleSums), (void**)&AC.rsums},
         };
         for (const Req& r : reqs)
             if (ast == IBL_OK) ast = alloc(r.bytes, r.p);
         if (ast != IBL_OK) { free_adjoint(ctx); return ast; }
+        cudaError_t ce = cudaStreamCreateWithFlags(&AC.rs, cudaStreamNonBlocking);
+        for (cudaEvent_t* e : {&AC.ev_rec[0], &AC.ev_rec[1], &AC.ev_rev[0], &AC.ev_rev[1], &AC.ev_fwd})
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(AC.rvacc, 0, (size_t)nv * sizeof(float4), ctx->work);
+        if (ce != cudaSuccess) {
+            free_adjoint(ctx);
+            return fail(ctx, IBL_ERR_CUDA, std::string("adjoint streams: ") + cudaGetErrorString(ce));
+        }
         AC.ck_bytes = ck_need;
         AC.tape_steps = (size_t)K;
+        AC.tape2_steps = n_ck > 1 ? (size_t)K : 0;
     }
     AdjCapPtrs cp = AC.cp;
     cp.acc_ca = AC.acc + 3;
@@ -1955,50 +2042,64 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
     const MemberHost& M0 = ctx->members[0];
     const double Ca = M0.caps[0].p.Ca, u_max = M0.desc.u_max;
     cudaStream_t s = ctx->work;
-    auto tape_of = [&](int k) {
+    // the reverse sweep rebuilds the geometry of every step in its own
+    // buffers, so that the recompute of the previous segment can run on the
+    // forward buffers at the same time
+    DevState Dr = D;
+    Dr.x = AC.rx;
+    Dr.xm = AC.rxm;
+    Dr.vacc = AC.rvacc;
+    Dr.nrm = AC.rnrm;
+    Dr.area = AC.rarea;
+    Dr.sums = AC.rsums;
+    cudaStream_t rs = AC.rs;
+    auto tape_of = [&](int k, int b) {
         StepTape tp;
-        tp.rhou = AC.tape_rhou + (size_t)k * N;
-        tp.F = AC.tape_F + (size_t)k * N;
-        tp.dvdq = AC.tape_dvdq + (size_t)k * D.n_links;
-        tp.rho = AC.tape_rho + (size_t)k * D.n_face_nodes;
-        tp.x = AC.tape_x + (size_t)k * nv3;
-        tp.v = AC.tape_v + (size_t)k * nv3;
+        tp.rhou = (b ? AC.tape2_rhou : AC.tape_rhou) + (size_t)k * N;
+        tp.F = (b ? AC.tape2_F : AC.tape_F) + (size_t)k * N;
+        tp.dvdq = (b ? AC.tape2_dvdq : AC.tape_dvdq) + (size_t)k * D.n_links;
+        tp.rho = (b ? AC.tape2_rho : AC.tape_rho) + (size_t)k * D.n_face_nodes;
+        tp.x = (b ? AC.tape2_x : AC.tape_x) + (size_t)k * nv3;
+        tp.v = (b ? AC.tape2_v : AC.tape_v) + (size_t)k * nv3;
         return tp;
     };
     // Segment work, captured once per (mode, start parity, length, adjoint
-    // buffer) as a CUDA graph: mode 0 recomputes the steps from the checkpoint
-    // writing the tape, then runs the adjoint steps backwards; mode 1 runs the
-    // adjoint steps only; mode 2 runs the forward steps writing the tape.
-    auto enqueue_segment = [&](int mode, int parity0, int len, float* lin0) -> ibl_status {
-        if (mode != 1)
+    // buffer, tape) as a CUDA graph: mode 1 runs the adjoint steps backwards
+    // over a tape; mode 2 runs the forward steps writing the tape.
+    auto enqueue_segment = [&](int mode, int parity0, int len, float* lin0, int b) -> ibl_status {
+        if (mode == 2)
             for (int k = 0; k < len; ++k) {
-                const StepTape tp = tape_of(k);
+                const StepTape tp = tape_of(k, b);
                 CKS(enqueue_step(ctx, (parity0 + k) & 1, nullptr, &tp));
             }
-        if (mode != 2) {
+        if (mode == 1) {
             float* li = lin0;
             float* lo = lin0 == lamA ? lamB : lamA;
             for (int k = len - 1; k >= 0; --k) {
-                const StepTape tp = tape_of(k);
+                const StepTape tp = tape_of(k, b);
                 CK(launch_adj_step(D, tp.rho, tp.dvdq, tp.rhou, li, lo, LS, acc + 1, acc + 2, s, tp.F, cp.lfib));
-                CK(cudaMemcpyAsync(D.x, tp.x, nv3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-                CK(launch_mirror(D, s));
-                CK(launch_adj_geometry(D, cp.lV, cp.snorm, s));
-                CK(launch_adj_capsules(D, cp, tp.rhou, tp.F, tp.v, lo, LS, s));
+                CK(cudaMemcpyAsync(Dr.x, tp.x, nv3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                CK(launch_mirror(Dr, s));
+                CK(launch_adj_geometry(Dr, cp.lV, cp.snorm, s));
+                CK(launch_adj_capsules(Dr, cp, tp.rhou, tp.F, tp.v, lo, LS, s));
                 std::swap(li, lo);
             }
         }
         return IBL_OK;
     };
-    auto run_segment = [&](int mode, int parity0, int len, float* lin0) -> ibl_status {
+    // launch on `on` (a graph is captured on the work stream the first time,
+    // with both streams idle)
+    auto run_segment = [&](int mode, int parity0, int len, float* lin0, int b, cudaStream_t on) -> ibl_status {
         for (const ibl_ctx::AdjSeg& g : AC.graphs)
-            if (g.kind == 1 && g.mode == mode && g.parity == parity0 && g.len == len && g.lin == lin0) {
-                CK(cudaGraphLaunch(g.exec, s));
+            if (g.kind == 1 && g.mode == mode && g.parity == parity0 && g.len == len && g.lin == lin0 && g.tb == b) {
+                CK(cudaGraphLaunch(g.exec, on));
                 return IBL_OK;
             }
+        CK(cudaStreamSynchronize(s));
+        CK(cudaStreamSynchronize(rs));
         cudaGraph_t gr = nullptr;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        const ibl_status est = enqueue_segment(mode, parity0, len, lin0);
+        const ibl_status est = enqueue_segment(mode, parity0, len, lin0, b);
         const cudaError_t e = cudaStreamEndCapture(s, &gr);
         if (est != IBL_OK) { if (gr) cudaGraphDestroy(gr); return est; }
         CK(e);
@@ -2006,8 +2107,8 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
         const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
         cudaGraphDestroy(gr);
         CK(ei);
-        AC.graphs.push_back({1, mode, parity0, len, lin0, ex});
-        CK(cudaGraphLaunch(ex, s));
+        AC.graphs.push_back({1, mode, parity0, len, lin0, b, ex});
+        CK(cudaGraphLaunch(ex, on));
         return IBL_OK;
     };
     auto copy_caps = [&](char* base, bool save) -> ibl_status {
@@ -2041,7 +2142,8 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
         CK(cudaGraphLaunch(ctx->graph[parity], s));
         ctx->t += 1;
     }
-    CKS(run_segment(2, (int)(ctx->t & 1), n_steps - last0, lamA));
+    const int L = n_ck - 1;
+    CKS(run_segment(2, (int)(ctx->t & 1), n_steps - last0, lamA, L & 1, s));
     ctx->t += n_steps - last0;
     // terminal condition: lambda_x = dJ/dx at the last step (FP64, host)
     std::vector<double> XT(nv3), G(nv3);
@@ -2066,13 +2168,27 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
             off += sc.bytes;
         }
     }
+    // reverse sweep on stream rs, segment by segment from the last; the
+    // recompute of segment seg - 1 (on the work stream, into the other tape)
+    // runs beside the reverse of segment seg
+    CK(cudaEventRecord(AC.ev_fwd, s));
     float* lin = lamA;
-    for (int seg = n_ck - 1; seg >= 0; --seg) {
-        const int s0 = seg * K, s1 = std::min(n_steps, s0 + K);
-        if (seg < n_ck - 1) CKS(copy_caps(ck + (size_t)seg * ck_one, false));
-        CKS(run_segment(seg < n_ck - 1 ? 0 : 1, (int)((t0 + s0) & 1), s1 - s0, lin));
+    for (int seg = L; seg >= 0; --seg) {
+        if (seg >= 1) {
+            const int p = seg - 1, b = p & 1;
+            if (seg + 1 <= L) CK(cudaStreamWaitEvent(s, AC.ev_rev[b], 0));   // tape b free again
+            CKS(copy_caps(ck + (size_t)p * ck_one, false));
+            CKS(run_segment(2, (int)((t0 + (long long)p * K) & 1), K, lamA, b, s));
+            CK(cudaEventRecord(AC.ev_rec[b], s));
+        }
+        const int s0 = seg * K, s1 = std::min(n_steps, s0 + K), b = seg & 1;
+        CK(cudaStreamWaitEvent(rs, seg == L ? AC.ev_fwd : AC.ev_rec[b], 0));
+        CKS(run_segment(1, (int)((t0 + s0) & 1), s1 - s0, lin, b, rs));
+        CK(cudaEventRecord(AC.ev_rev[b], rs));
         if ((s1 - s0) & 1) lin = lin == lamA ? lamB : lamA;
     }
+    CK(cudaEventRecord(AC.ev_fwd, rs));
+    CK(cudaStreamWaitEvent(s, AC.ev_fwd, 0));
     {
         size_t off = 0;
         for (const StateSection& sc : secs) {
@@ -2100,6 +2216,8 @@ ibl_status ibl_read_fields_noalloc(ibl_ctx* ctx, int32_t member, float* rho, flo
     if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
     if (!rho && !u) return fail(ctx, IBL_ERR_ARG, "null outputs");
     if (member < 0 || member >= (int)ctx->members.size()) return fail(ctx, IBL_ERR_ARG, "member out of range");
+    if (ctx->members[member].whole_view)
+        return fail(ctx, IBL_ERR_ARG, "the whole-lattice member of a slab context holds no populations");
     const ibl_lattice_desc& dsc = ctx->members[member].desc;
     const size_t Nu = (size_t)dsc.nx * dsc.ny * dsc.nz;
     if (Nu > (size_t)IBL_NOALLOC_MAX_NODES)

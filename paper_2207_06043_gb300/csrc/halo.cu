@@ -50,4 +50,20 @@ cudaError_t launch_halo(const DevState& d, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The flags a step raised on the capsules of a slab context (their member is
+// the whole-lattice view) stop every slab at the next step begin.
+__global__ void k_status_spread(uint32_t* __restrict__ status_new, int n_members, int w) {
+    const int m = threadIdx.x;
+    if (m < n_members && m != w) {
+        const uint32_t f = status_new[w];
+        if (f) atomicOr(status_new + m, f);
+    }
+}
+
+cudaError_t launch_status_spread(const DevState& d, cudaStream_t s) {
+    if (d.slab_w < 0) return cudaSuccess;
+    k_status_spread<<<1, MAX_MEMBERS, 0, s>>>(d.status_new, d.n_members, d.slab_w);
+    return cudaGetLastError();
+}
+
 }  // namespace ibl

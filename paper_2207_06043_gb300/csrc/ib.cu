@@ -171,22 +171,15 @@ __device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restri
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
-                                               const uint8_t* __restrict__ tag,
-                                               const uint32_t* __restrict__ status, const CapsuleDev* __restrict__ caps,
-                                               const CapsuleSums* __restrict__ sums, float4* __restrict__ macro,
-                                               int parity) {
-    const int c = blockIdx.x / SHELL_BLOCKS;
-    const CapsuleDev& C = caps[c];
-    if (status[C.member] & STOP) return;
-    const MemberDev& d = mem[C.member];
+// The capsule's box grown by the shell margin (clipped to the box, or at most
+// one period on a periodic axis) and its radial band: false if empty.
+__device__ __forceinline__ bool shell_box(const MemberDev& d, const CapsuleSums& S, int lo[3], int ext[3],
+                                          bool& radial, float& r2_out, float& r2_in) {
     const int dims[3] = {d.nx, d.ny, d.nz};
-    int lo[3], ext[3];
     bool wide = false;   // a grown box wider than a periodic lattice: no radial test
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int l = sums[c].box_lo[a] - SHELL_MARGIN, h = sums[c].box_hi[a] + SHELL_MARGIN;
+        int l = S.box_lo[a] - SHELL_MARGIN, h = S.box_hi[a] + SHELL_MARGIN;
         if ((d.per >> a) & 1) {
             wide = wide || h > l + dims[a] - 1;
             h = min(h, l + dims[a] - 1);
@@ -197,13 +190,89 @@ __global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ 
         lo[a] = l;
         ext[a] = h - l + 1;
     }
-    if (ext[0] <= 0 || ext[1] <= 0 || ext[2] <= 0) return;
+    if (ext[0] <= 0 || ext[1] <= 0 || ext[2] <= 0) return false;
     // annulus of the vertices about rc, grown by the stencils' reach
-    const float rhi = sqrtf(__int_as_float(sums[c].r2_hi)) + SHELL_REACH;
-    const float rlo = sqrtf(__int_as_float(sums[c].r2_lo)) - SHELL_REACH;
-    const bool radial = !wide && rhi < 1e6f;   // no radial test for a non-finite or over-wide capsule
-    const float r2_out = rhi * rhi, r2_in = (radial && rlo > 0.f) ? rlo * rlo : -1.f;
+    const float rhi = sqrtf(__int_as_float(S.r2_hi)) + SHELL_REACH;
+    const float rlo = sqrtf(__int_as_float(S.r2_lo)) - SHELL_REACH;
+    radial = !wide && rhi < 1e6f;   // no radial test for a non-finite or over-wide capsule
+    r2_out = rhi * rhi;
+    r2_in = (radial && rlo > 0.f) ? rlo * rlo : -1.f;
+    return true;
+}
+
+// fn(x, y, z) for every node of the capsule's shell (user coordinates, wrapped
+// on periodic axes), one warp per row as in shell_rows.
+template <typename F>
+__device__ __forceinline__ void for_shell_nodes(const MemberDev& d, const int lo[3], const int ext[3], bool radial,
+                                                float r2_out, float r2_in, float rcx, float rcy, float rcz, F fn) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = SHELL_BLOCKS * (int)(blockDim.x >> 5);
+    const int rows = ext[1] * ext[2];
+    for (int row = (blockIdx.x % SHELL_BLOCKS) * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); row < rows;
+         row += nwarps) {
+        const int iz = row / ext[1], iy = row - iz * ext[1];
+        int cy = lo[1] + iy, cz = lo[2] + iz;
+        const float qy = (float)cy - rcy, qz = (float)cz - rcz;
+        const float d2 = qy * qy + qz * qz;
+        int x0 = lo[0], x1 = lo[0] + ext[0] - 1;
+        float hin = -1.f;
+        if (radial) {
+            if (d2 > r2_out) continue;
+            const float hw = sqrtf(r2_out - d2);
+            x0 = max(x0, (int)ceilf(rcx - hw));
+            x1 = min(x1, (int)floorf(rcx + hw));
+            if (r2_in > d2) hin = sqrtf(r2_in - d2);
+        }
+        if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny;
+        if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz;
+        for (int cx = x0 + lane; cx <= x1; cx += 32) {
+            if (fabsf((float)cx - rcx) < hin) continue;
+            int wx = cx;
+            if (d.per & 1) wx = ((wx % d.nx) + d.nx) % d.nx;
+            fn(wx, cy, cz);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
+                                               uint8_t* __restrict__ tag,
+                                               const uint32_t* __restrict__ status, const CapsuleDev* __restrict__ caps,
+                                               const CapsuleSums* __restrict__ sums, float4* __restrict__ macro,
+                                               int parity, float* __restrict__ fib, const int* __restrict__ slab_of,
+                                               const int4* __restrict__ slab_tab) {
+    const int c = blockIdx.x / SHELL_BLOCKS;
+    const CapsuleDev& C = caps[c];
+    if (status[C.member] & STOP) return;
+    const MemberDev& d = mem[C.member];
+    int lo[3], ext[3];
+    bool radial;
+    float r2_out, r2_in;
+    if (!shell_box(d, sums[c], lo, ext, radial, r2_out, r2_in)) return;
     const float rcx = sums[c].rcf[0], rcy = sums[c].rcf[1], rcz = sums[c].rcf[2];
+    if (d.slab_view) {
+        // the whole lattice of a slab context: each node's populations from the
+        // slab that owns it (its neighbours are in that slab's ghost planes);
+        // the node's IB force and flag of the previous step are cleared here,
+        // as the lattice kernel does for a lattice of its own
+        for_shell_nodes(d, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, [&](int x, int y, int z) {
+            const long long nW = d.node_off + (x + d.px) + (long long)d.NX * ((y + d.py) + (long long)d.NY * (z + d.pz));
+            const int s = slab_of[x];
+            const MemberDev& ds = mem[s];
+            const int4 t = slab_tab[s];
+            const int X = x - (t.x - t.z) + ds.px, Y = y + ds.py, Z = z + ds.pz;
+            const int n = X + ds.NX * (Y + ds.NY * Z);
+            const bool solid = tag[nW] & TAG_SOLID;
+            float g[Q];
+            load_pre<T>(ds, f + ds.f_off, n, X, Y, Z, parity, g);
+            float rho, ux, uy, uz;
+            moments_of(g, rho, ux, uy, uz);
+            macro[nW] = solid ? make_float4(-1.f, 0.f, 0.f, 0.f) : make_float4(rho, ux, uy, uz);
+            reinterpret_cast<float4*>(fib)[nW] = make_float4(0.f, 0.f, 0.f, 0.f);
+            tag[nW] = solid ? TAG_SOLID : 0;
+        });
+        return;
+    }
     const T* fm = f + d.f_off;
     // a lattice with no periodic axis reaches every upstream node at a
     // constant offset (the ghost layer absorbs the steps off the box)
@@ -213,6 +282,53 @@ __global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ 
         shell_rows<T, false>(d, fm, tag, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
 }
 
+// The IB force the markers spread into the whole-lattice member of a slab
+// context, copied to every slab that holds the node (its owner and the ghost
+// planes of its neighbours), with the node's IB flag, for the slabs' lattice
+// step.
+__global__ void __launch_bounds__(256) k_fib_scatter(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag,
+                                                      float* __restrict__ fib, const uint32_t* __restrict__ status,
+                                                      const CapsuleDev* __restrict__ caps,
+                                                      const CapsuleSums* __restrict__ sums,
+                                                      const int* __restrict__ slab_of,
+                                                      const int4* __restrict__ slab_tab, int n_slabs) {
+    const int c = blockIdx.x / SHELL_BLOCKS;
+    const CapsuleDev& C = caps[c];
+    if (status[C.member] & STOP) return;
+    const MemberDev& d = mem[C.member];
+    int lo[3], ext[3];
+    bool radial;
+    float r2_out, r2_in;
+    if (!shell_box(d, sums[c], lo, ext, radial, r2_out, r2_in)) return;
+    const float rcx = sums[c].rcf[0], rcy = sums[c].rcf[1], rcz = sums[c].rcf[2];
+    for_shell_nodes(d, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, [&](int x, int y, int z) {
+        const long long nW = d.node_off + (x + d.px) + (long long)d.NX * ((y + d.py) + (long long)d.NY * (z + d.pz));
+        if (!(tag[nW] & TAG_IB)) return;
+        const float4 v = reinterpret_cast<const float4*>(fib)[nW];
+        const int own = slab_of[x];
+        int seen0 = -1, seen1 = -1;   // a slab is listed once (two slabs on a periodic axis are both neighbours)
+#pragma unroll
+        for (int ds_ = -1; ds_ <= 1; ++ds_) {
+            int s = own + ds_;
+            if (s < 0 || s >= n_slabs) {
+                if (!(d.per & 1)) continue;
+                s = (s + n_slabs) % n_slabs;
+            }
+            if (s == seen0 || s == seen1) continue;
+            seen1 = seen0;
+            seen0 = s;
+            const int4 t = slab_tab[s];
+            const int nxs = t.y - t.x + t.z + t.w;
+            int lx = x - (t.x - t.z);
+            if (d.per & 1) lx = ((lx % d.nx) + d.nx) % d.nx;
+            if (lx < 0 || lx >= nxs) continue;
+            const MemberDev& ds = mem[s];
+            const long long n = ds.node_off + (lx + ds.px) + (long long)ds.NX * ((y + ds.py) + (long long)ds.NY * (z + ds.pz));
+            reinterpret_cast<float4*>(fib)[n] = v;
+            tag[n] = TAG_IB;
+        }
+    });
+}
 
 __global__ void __launch_bounds__(IB_MARKER_THREADS, IB_MARKER_MIN_BLOCKS)
 k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float* __restrict__ fib,
@@ -243,7 +359,7 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
         const int k = r + GL * j;
-        p[j] = k >= 27 ? 0.f : (M.fallback < 0 ? mls_row_g(M, 0, j, k) : (M.fallback == k ? 1.f : 0.f));
+        p[j] = k >= 27 ? 0.f : mls_row_g(M, 0, j, k);
     }
     float Ux = 0.f, Uy = 0.f, Uz = 0.f;
 #pragma unroll
@@ -307,16 +423,12 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
     for (int j = 0; j < GS; ++j) {
         const int k = r + GL * j;
         if (k >= 27) continue;
-        if (M.fallback < 0) {
-            const float p = mls_row_g(M, 0, j, k), g0 = mls_row_g(M, 1, j, k), g1 = mls_row_g(M, 2, j, k),
-                        g2 = mls_row_g(M, 3, j, k);
-            acc[0] += p * fabsf(q[j].x);   // a solid node's rho (1) is stored negated
-            acc[1] += g0 * q[j].y; acc[2] += g1 * q[j].y; acc[3] += g2 * q[j].y;
-            acc[4] += g0 * q[j].z; acc[5] += g1 * q[j].z; acc[6] += g2 * q[j].z;
-            acc[7] += g0 * q[j].w; acc[8] += g1 * q[j].w; acc[9] += g2 * q[j].w;
-        } else if (M.fallback == k) {
-            acc[0] += fabsf(q[j].x);
-        }
+        const float p = mls_row_g(M, 0, j, k), g0 = mls_row_g(M, 1, j, k), g1 = mls_row_g(M, 2, j, k),
+                    g2 = mls_row_g(M, 3, j, k);
+        acc[0] += p * fabsf(q[j].x);   // a solid node's rho (1) is stored negated
+        acc[1] += g0 * q[j].y; acc[2] += g1 * q[j].y; acc[3] += g2 * q[j].y;
+        acc[4] += g0 * q[j].z; acc[5] += g1 * q[j].z; acc[6] += g2 * q[j].z;
+        acc[7] += g0 * q[j].w; acc[8] += g1 * q[j].w; acc[9] += g2 * q[j].w;
     }
 #pragma unroll
     for (int i = 0; i < 10; ++i) acc[i] = group_sum(acc[i], mask);
@@ -777,7 +889,14 @@ cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) { return lau
 template <typename T>
 static cudaError_t shell_t(const DevState& d, int parity, cudaStream_t s) {
     k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.status, d.caps, d.sums,
-                                                       d.macro, parity);
+                                                       d.macro, parity, d.fib, d.slab_of, d.slab_tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fib_scatter(const DevState& d, cudaStream_t s) {
+    if (d.n_verts == 0 || d.slab_w < 0) return cudaSuccess;
+    k_fib_scatter<<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, d.tag, d.fib, d.status, d.caps, d.sums, d.slab_of,
+                                                          d.slab_tab, d.n_slabs);
     return cudaGetLastError();
 }
 

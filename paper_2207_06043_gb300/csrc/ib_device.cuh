@@ -1,7 +1,8 @@
 // Device helpers of the immersed-boundary kernels and of their adjoint:
 // shared constants, small vector helpers, the two-float position mirror,
-// the MLS stencil (weights, moment matrix, its LDL^T solve) built by groups
-// of GL lanes, the probe-record force and the force accumulation.
+// the MLS stencil (tensor-product weights and the closed-form inverse of the
+// moment matrix) built by groups of GL lanes, the probe-record force and the
+// force accumulation.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -10,7 +11,6 @@ namespace ibl {
 
 constexpr float SUPPORT_SIDE = 2.6f;   // 2 r_w (Section "No-slip conditions for moving immersed boundaries")
 constexpr float ALPHA = 0.3f;          // Eq. intKernel
-constexpr double PIVOT_TOL = 1e-10;    // singular moment matrix -> nearest fluid node
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t STOP = ST_DAMAGED | ST_NONFINITE;
 
@@ -39,12 +39,6 @@ __device__ __forceinline__ f3 mirror_diff(const float4* __restrict__ xm, int a, 
 }
 
 // Eq. intKernel with r normalised by the support side.
-__device__ __forceinline__ float mls_weight(bool fluid, float rx, float ry, float rz) {
-    const float r = sqrtf(rx * rx + ry * ry + rz * rz) * (1.f / SUPPORT_SIDE);
-    const float s = r * (1.f / ALPHA);
-    return (fluid && r <= 1.f) ? expf(-s * s) : 0.f;
-}
-
 __device__ __forceinline__ double block_sum_d(double v, double* red) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -85,67 +79,15 @@ __device__ __forceinline__ int sdx(int k) { return (int)((0x24924924924924ull >>
 __device__ __forceinline__ int sdy(int k) { return (int)((0x2a540a9502a540ull >> (2 * k)) & 3ull) - 1; }
 __device__ __forceinline__ int sdz(int k) { return (int)((0x2aaaa555540000ull >> (2 * k)) & 3ull) - 1; }
 
-// 1/d in FP64 by Newton's iteration r <- r (2 - d r) from the FP32
-// reciprocal (each step doubles the correct bits: 24 -> 48 -> full)
-__device__ __forceinline__ double rcp_r(double d) {
-    double r = (double)__frcp_rn((float)d);
-    r = r * (2.0 - d * r);
-    return r * (2.0 - d * r);
-}
-__device__ __forceinline__ float rcp_r(float d) { return __frcp_rn(d); }
-
+// Support node (cx, cy, cz) of a point: wrapped on a periodic axis, clamped
+// to the box on the others (a point off the box takes the state of the
+// nearest box node, Reading M4).
 __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy, int cz) {
-    if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx; else if (cx < 0 || cx >= d.nx) return -1;
-    if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny; else if (cy < 0 || cy >= d.ny) return -1;
-    if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz; else if (cz < 0 || cz >= d.nz) return -1;
+    if (d.per & 1) cx = ((cx % d.nx) + d.nx) % d.nx; else cx = min(max(cx, 0), d.nx - 1);
+    if (d.per & 2) cy = ((cy % d.ny) + d.ny) % d.ny; else cy = min(max(cy, 0), d.ny - 1);
+    if (d.per & 4) cz = ((cz % d.nz) + d.nz) % d.nz; else cz = min(max(cz, 0), d.nz - 1);
     return (cx + d.px) + d.NX * ((cy + d.py) + d.NY * (cz + d.pz));
 }
-
-// L D L^T of the symmetric moment matrix m (m00 m01 m02 m03 m11 m12 m13 m22 m23
-// m33) in precision R, then the first ROWS rows of its inverse.  Returns the
-// pivots relative to the first one in `rel` (min of d1, d2, d3 over d0) and
-// false when the matrix fails the singularity test.
-template <int ROWS, typename R, typename MT>
-__device__ __forceinline__ bool ldlt_solve(const MT (&m)[10], float (&inv)[4][4], R& rel) {
-    const R a00 = m[0], a10 = m[1], a20 = m[2], a30 = m[3], a11 = m[4], a21 = m[5], a31 = m[6], a22 = m[7],
-            a32 = m[8], a33 = m[9];
-    const R d0 = a00;
-    const R s0 = d0 > R(0) ? d0 : R(1);
-    const R r0 = rcp_r(s0);
-    const R L10 = a10 * r0, L20 = a20 * r0, L30 = a30 * r0;
-    const R d1 = a11 - L10 * L10 * d0;
-    const R s1 = d1 > R(0) ? d1 : R(1);
-    const R r1 = rcp_r(s1);
-    const R L21 = (a21 - L20 * L10 * d0) * r1;
-    const R L31 = (a31 - L30 * L10 * d0) * r1;
-    const R d2 = a22 - L20 * L20 * d0 - L21 * L21 * d1;
-    const R s2 = d2 > R(0) ? d2 : R(1);
-    const R r2 = rcp_r(s2);
-    const R L32 = (a32 - L30 * L20 * d0 - L31 * L21 * d1) * r2;
-    const R d3 = a33 - L30 * L30 * d0 - L31 * L31 * d1 - L32 * L32 * d2;
-    const R tol = R(PIVOT_TOL) * s0;
-    rel = fmin(fmin(d1, d2), d3) * r0;
-    if (!(d0 > R(0) && d1 > tol && d2 > tol && d3 > tol)) return false;
-    const R r3 = rcp_r(d3);
-#pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const R y0 = j == 0 ? R(1) : R(0);
-        const R y1 = (j == 1 ? R(1) : R(0)) - L10 * y0;
-        const R y2 = (j == 2 ? R(1) : R(0)) - L20 * y0 - L21 * y1;
-        const R y3 = (j == 3 ? R(1) : R(0)) - L30 * y0 - L31 * y1 - L32 * y2;
-        const R c3 = y3 * r3;
-        const R c2 = y2 * r2 - L32 * c3;
-        const R c1 = y1 * r1 - L21 * c2 - L31 * c3;
-        const R c0 = y0 * r0 - L10 * c1 - L20 * c2 - L30 * c3;
-        inv[j][0] = (float)c0; inv[j][1] = (float)c1; inv[j][2] = (float)c2; inv[j][3] = (float)c3;
-    }
-    return true;
-}
-
-// Pivots this far above the singularity threshold (relative to d0) keep the
-// FP32 solve's error below ~1e-4 of the inverse; closer ones are redone in
-// FP64, which then takes the singularity decision exactly as an FP64 solve.
-constexpr float FP32_PIVOT_FLOOR = 1e-3f;
 
 // ---------------------------------------------------------------------------
 // IB marker and probe stencils, four lanes per stencil, all on the fluid
@@ -163,11 +105,7 @@ constexpr float FP32_PIVOT_FLOOR = 1e-3f;
 // ---------------------------------------------------------------------------
 constexpr int PROBE_STRIDE = 8;   // floats per probe record: p, tau xx yy zz xy xz yz, pad
 
-// Both stencils solve their 4x4 system in FP32 unless a pivot falls below
-// FP32_PIVOT_FLOOR of the first, and then redo it in FP64 (GB300's FP64 pipe
-// is narrow).  IBL_MARKER_FAST32=0 makes the marker stencil, which
-// interpolates and spreads, always solve in FP64.
-constexpr bool PROBE_FAST32 = true;
+constexpr bool PROBE_FAST32 = true;   // (template argument kept by the callers; the closed form needs no FP64 redo)
 #ifndef IB_MARKER_THREADS
 #define IB_MARKER_THREADS 128
 #endif
@@ -180,15 +118,12 @@ constexpr bool PROBE_FAST32 = true;
 #ifndef IB_PROBE_MIN_BLOCKS
 #define IB_PROBE_MIN_BLOCKS 8
 #endif
-#ifndef IBL_MARKER_FAST32
-#define IBL_MARKER_FAST32 1
-#endif
-constexpr bool MARKER_FAST32 = IBL_MARKER_FAST32 != 0;
+constexpr bool MARKER_FAST32 = true;
 
 // The stencils run on groups of GL = 4 consecutive lanes: support node k of
 // a point belongs to lane k % 4 (slot k / 4), so each lane gathers at most 7
-// nodes, the moments and the interpolated sums are combined by shuffles within
-// the group, and every lane of the group holds the same solved rows.  A
+// nodes, the per-axis weights and the interpolated sums are combined by
+// shuffles within the group, and every lane of the group holds the same rows.  A
 // stencil's latency chain is a quarter of the one-lane form and its registers
 // hold 7 weights instead of 27.
 #ifndef IB_GROUP_LANES
@@ -201,58 +136,39 @@ static_assert(GL >= 4 && GL <= 32 && (GL & (GL - 1)) == 0, "a stencil group need
 // MLS operator of one point, held by the GL lanes of its group: weights W_k of
 // this lane's support nodes (Eq. intKernel) and the first ROWS rows of A^{-1}
 // (Eq. l2norm, basis [1, x-X, y-Y, z-Z]; A is symmetric, so row j is
-// A^{-1} e_j), the same in every lane of the group.  fallback >= 0: singular
-// system, the whole point goes to support node `fallback`.
+// A^{-1} e_j), the same in every lane of the group.
 struct MlsG {
     int bx, by, bz;
     int base;               // padded index of the base node when the block is interior, else -1
     float ox, oy, oz;       // base node minus point
     float W[GS];            // weights of this lane's support nodes (k = lane + 4 slot)
     float inv[4][4];
-    int fallback;           // -1: regular; 0..26: nearest fluid node; 27: none
 };
-
-// The FP64 solve of a near-singular or FP64-only stencil, out of line so that
-// its registers do not count against the common FP32 path.
-struct Moments64 { double m[10]; };
-struct Rows { float v[4][4]; int good; };
-
-template <int ROWS>
-__device__ __noinline__ Rows ldlt_solve64(Moments64 mm) {
-    Rows out;
-    double rel;
-    out.good = ldlt_solve<ROWS, double>(mm.m, out.v, rel) ? 1 : 0;
-    return out;
-}
 
 // P is the point's coordinate along axis min(r, 2): lanes 0, 1, 2 of a group
 // each take the FP64 steps (nearest node, offset) for one axis and the group
 // exchanges the results, so that GB300's narrow FP64 pipe does a third of the
 // work it would if every lane took all three axes.
-// Every support node inside the box takes part in the fit, a solid one with
-// the wall's state (rho = 1, u = 0); only nodes off a non-periodic box are
-// left out (node < 0).  With MAC the moments of every support node of the
-// lane are gathered at once into q from the moments array of the step,
-// where a solid node holds (-1, 0, 0, 0): its rho negated, so that the
-// spreading can skip it without a tag gather.
-template <bool MAC>
-struct Support;
-template <>
-struct Support<false> {
-    const uint8_t* tag;
-    __device__ __forceinline__ bool fluid(const MemberDev&, int node, float4&) const { return node >= 0; }
-};
-template <>
-struct Support<true> {
-    const float4* macro;
-    __device__ __forceinline__ bool fluid(const MemberDev& d, int node, float4& q) const {
-        q = node >= 0 ? macro[d.node_off + node] : make_float4(0.f, 0.f, 0.f, 0.f);
-        return node >= 0;
-    }
-};
-
-template <int ROWS, bool FAST32, bool MAC>
-__device__ __forceinline__ void mls_build_impl(const MemberDev& d, Support<MAC> sup, double P, int r, unsigned mask,
+//
+// Every point of the 3x3x3 block takes part in the fit (Reading M4: a solid
+// one with the wall's state, one off the box with the nearest box node's), and
+// W = exp(-|x_k - X|^2 / (2.6 alpha)^2) (every node of the block lies within
+// r <= 1) is the product of one factor per axis.  The moment matrix of the
+// linear basis is then
+//     A = S [[1, m_x, m_y, m_z], [m_x, m_x^2 + v_x, m_x m_y, m_x m_z], ...]
+// with, per axis a, s0 = sum_j w_a(j), s1 = sum_j w_a(j) r_j and
+// s2 = sum_j w_a(j) r_j^2 over the offsets r_j = o_a - 1, o_a, o_a + 1 of the
+// three nodes, m_a = s1 / s0, v_a = s2 / s0 - m_a^2 and S = s0_x s0_y s0_z.
+// In the basis centred on m, A is diagonal, which gives the rows of A^{-1}
+// below: the same operator as the general 4x4 solve of the oracle, in a few
+// operations per point and with no small pivot.  Lane a (< 3) evaluates the
+// three factors of axis a; the group shares them.
+// With MAC the moments of every support node of the lane are gathered at once
+// into q from the moments array of the step, where a solid node holds
+// (-1, 0, 0, 0): the wall's rho negated, so that the spreading can skip it
+// without a tag gather.
+template <int ROWS, bool MAC>
+__device__ __forceinline__ void mls_build_impl(const MemberDev& d, const void* src, double P, int r, unsigned mask,
                                                MlsG& M, float4 (&q)[GS]) {
     const double b = floor(P + 0.5);
     const int bi = (int)b;
@@ -262,87 +178,74 @@ __device__ __forceinline__ void mls_build_impl(const MemberDev& d, Support<MAC> 
     const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
                           M.bz <= d.nz - 2;
     M.base = interior ? (M.bx + d.px) + d.NX * ((M.by + d.py) + d.NY * (M.bz + d.pz)) : -1;
-    float m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    float best = 0.f;
-    int bestk = 27;
+    // this lane's axis factors exp(-r^2 / (2.6 alpha)^2) at r = o - 1, o, o + 1
+    constexpr float L2 = 1.f / (SUPPORT_SIDE * ALPHA * SUPPORT_SIDE * ALPHA);
+    const float om = o - 1.f, op = o + 1.f;
+    const float wm = expf(-om * om * L2), w0 = expf(-o * o * L2), wp = expf(-op * op * L2);
+    float fa[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        fa[a][0] = __shfl_sync(mask, wm, a, GL);
+        fa[a][1] = __shfl_sync(mask, w0, a, GL);
+        fa[a][2] = __shfl_sync(mask, wp, a, GL);
+    }
+    const float oa[3] = {M.ox, M.oy, M.oz};
+    float m1[3], iv[3], S = 1.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float r0 = oa[a] - 1.f, r1 = oa[a], r2 = oa[a] + 1.f;
+        const float s0 = fa[a][0] + fa[a][1] + fa[a][2];
+        const float s1 = fa[a][0] * r0 + fa[a][1] * r1 + fa[a][2] * r2;
+        const float s2 = fa[a][0] * r0 * r0 + fa[a][1] * r1 * r1 + fa[a][2] * r2 * r2;
+        const float is0 = 1.f / s0;
+        m1[a] = s1 * is0;
+        iv[a] = 1.f / (s2 * is0 - m1[a] * m1[a]);
+        S *= s0;
+    }
+    const float iS = 1.f / S;
+    M.inv[0][0] = (1.f + m1[0] * m1[0] * iv[0] + m1[1] * m1[1] * iv[1] + m1[2] * m1[2] * iv[2]) * iS;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) M.inv[0][1 + a] = -m1[a] * iv[a] * iS;
+    if (ROWS > 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            M.inv[1 + a][0] = -m1[a] * iv[a] * iS;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) M.inv[1 + a][1 + c] = c == a ? iv[a] * iS : 0.f;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
         const int k = r + GL * j;
-        float w = 0.f;
         q[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        M.W[j] = 0.f;
         if (k < 27) {
             const int dx = sdx(k), dy = sdy(k), dz = sdz(k);
-            const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
-                                      : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
-            const bool fluid = sup.fluid(d, node, q[j]);
-            const float rx = M.ox + dx, ry = M.oy + dy, rz = M.oz + dz;
-            w = mls_weight(fluid, rx, ry, rz);
-            if (w > best) { best = w; bestk = k; }
-            m[0] += w; m[1] += w * rx; m[2] += w * ry; m[3] += w * rz;
-            m[4] += w * rx * rx; m[5] += w * rx * ry; m[6] += w * rx * rz;
-            m[7] += w * ry * ry; m[8] += w * ry * rz; m[9] += w * rz * rz;
+            // register selects (the lane's node offsets are not compile-time)
+            const float wx = dx < 0 ? fa[0][0] : (dx == 0 ? fa[0][1] : fa[0][2]);
+            const float wy = dy < 0 ? fa[1][0] : (dy == 0 ? fa[1][1] : fa[1][2]);
+            const float wz = dz < 0 ? fa[2][0] : (dz == 0 ? fa[2][1] : fa[2][2]);
+            M.W[j] = wx * wy * wz;
+            if (MAC) {
+                const int node = interior ? M.base + dx + d.NX * (dy + d.NY * dz)
+                                          : support_index(d, M.bx + dx, M.by + dy, M.bz + dz);
+                q[j] = static_cast<const float4*>(src)[d.node_off + node];
+            }
         }
-        M.W[j] = w;
     }
-#pragma unroll
-    for (int o = 1; o < GL; o <<= 1) {
-#pragma unroll
-        for (int i = 0; i < 10; ++i) m[i] += __shfl_xor_sync(mask, m[i], o);
-        const float ob = __shfl_xor_sync(mask, best, o);
-        const int ok = __shfl_xor_sync(mask, bestk, o);
-        if (ob > best || (ob == best && ok < bestk)) { best = ob; bestk = ok; }   // first k of the largest weight
-    }
-    bool good = false;
-    if (FAST32) {
-        float rel;
-        good = ldlt_solve<ROWS, float>(m, M.inv, rel) && rel >= FP32_PIVOT_FLOOR;
-    }
-    if (!good) {
-        // The moments again, summed in FP64 from the same weights and
-        // offsets: the offsets of support nodes in one plane (or on one line)
-        // are equal floats, so the pivots such a support makes vanish stay at
-        // FP64 rounding and the singularity test decides as an FP64 fit does
-        // (FP32 sums leave them near 1e-8 of A_00).  good is the same in the
-        // GL lanes of the group, which alone take part in the sums.
-        const unsigned gmask = mask & (((1u << GL) - 1u) << ((threadIdx.x & 31) & ~(GL - 1)));
-        Moments64 mm;
-#pragma unroll
-        for (int i = 0; i < 10; ++i) mm.m[i] = 0.0;
-#pragma unroll
-        for (int j = 0; j < GS; ++j) {
-            const int k = r + GL * j;
-            if (k >= 27) continue;
-            const double w = M.W[j];
-            const double rx = (double)(M.ox + sdx(k)), ry = (double)(M.oy + sdy(k)), rz = (double)(M.oz + sdz(k));
-            mm.m[0] += w; mm.m[1] += w * rx; mm.m[2] += w * ry; mm.m[3] += w * rz;
-            mm.m[4] += w * rx * rx; mm.m[5] += w * rx * ry; mm.m[6] += w * rx * rz;
-            mm.m[7] += w * ry * ry; mm.m[8] += w * ry * rz; mm.m[9] += w * rz * rz;
-        }
-#pragma unroll
-        for (int o = 1; o < GL; o <<= 1)
-#pragma unroll
-            for (int i = 0; i < 10; ++i) mm.m[i] += __shfl_xor_sync(gmask, mm.m[i], o);
-        const Rows rr = ldlt_solve64<ROWS>(mm);
-        good = rr.good != 0;
-#pragma unroll
-        for (int a = 0; a < ROWS; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) M.inv[a][b] = rr.v[a][b];
-    }
-    M.fallback = good ? -1 : (best > 0.f ? bestk : 27);
 }
 
 template <int ROWS, bool FAST32>
 __device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double P, int r,
                                             unsigned mask, MlsG& M) {
     float4 q[GS];
-    mls_build_impl<ROWS, FAST32, false>(d, Support<false>{tag}, P, r, mask, M, q);
+    mls_build_impl<ROWS, false>(d, tag, P, r, mask, M, q);
 }
 
 template <int ROWS, bool FAST32>
 __device__ __forceinline__ void mls_build_g(const MemberDev& d, const float4* __restrict__ macro, double P, int r,
                                             unsigned mask, MlsG& M, float4 (&q)[GS]) {
-    mls_build_impl<ROWS, FAST32, true>(d, Support<true>{macro}, P, r, mask, M, q);
+    mls_build_impl<ROWS, true>(d, macro, P, r, mask, M, q);
 }
 
 __device__ __forceinline__ float mls_row_g(const MlsG& M, int row, int j, int k) {

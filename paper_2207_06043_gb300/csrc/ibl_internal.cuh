@@ -67,6 +67,7 @@ struct MemberDev {
     int vert_begin, vert_count;
     long long cell_off;
     int cnx, cny, cnz, has_cells;
+    int slab_view;           // 1: the whole lattice of a slab context, seen by its capsules (no populations)
 };
 
 // Per-capsule descriptor (global memory).
@@ -195,6 +196,12 @@ struct DevState {
     // src padded x) run after every step; members share NY and NZ
     int n_halo = 0;
     int4* halo = nullptr;
+    // capsules of a slab context live in the whole-lattice member slab_w:
+    // its moments are taken from the slab owning each node (slab_of, per
+    // global x) and its IB force is copied to every slab holding the node
+    int slab_w = -1, n_slabs = 0;
+    const int* slab_of = nullptr;
+    const int4* slab_tab = nullptr;     // (x0, x1, lo, hi) per slab
 };
 constexpr int CELL_CAP = 32;
 constexpr int NEAR_CAP = 31;          // capsules listed as near one capsule; more: all its markers search
@@ -265,6 +272,11 @@ cudaError_t launch_capsule_stats(const DevState& d, int c_begin, int c_count, do
 // the halo planes of a slab decomposition from their owners (every slot of
 // every padded node of each listed plane)
 cudaError_t launch_halo(const DevState& d, cudaStream_t s);
+// the IB force spread into the whole-lattice member of a slab context, to the
+// slabs that hold each node (owner and ghost copies), before the lattice step
+cudaError_t launch_fib_scatter(const DevState& d, cudaStream_t s);
+// the stop flags raised on those capsules, to every slab
+cudaError_t launch_status_spread(const DevState& d, cudaStream_t s);
 
 // marker-based wall tagging and BFL distances (walls.cu): 0, or -1 (argument)
 // / -3 (CUDA) with msg set; arguments as ibl_voxelise_markers

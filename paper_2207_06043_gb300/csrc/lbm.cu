@@ -259,7 +259,7 @@ __device__ __forceinline__ void face_node(const MemberDev* __restrict__ mem, T* 
 // (flag LINK_AT_FACE).  No other thread reads or writes the slots a face
 // node's rule reads: each of them is written by at most one link.
 template <typename T>
-__global__ void __launch_bounds__(256) k_walls(const MemberDev* __restrict__ mem, T* __restrict__ f,
+__global__ void __launch_bounds__(256, 6) k_walls(const MemberDev* __restrict__ mem, T* __restrict__ f,
                                                const uint32_t* __restrict__ l_node, const uint32_t* __restrict__ l_meta,
                                                const float* __restrict__ l_q, const uint32_t* __restrict__ status,
                                                int n_links, const uint32_t* __restrict__ fc_node,

@@ -70,19 +70,35 @@ def test_mls_near_walls_keeps_solid_nodes_as_wall_data():
     assert (np.abs(w_fluid - 1.0) > 1e-3).sum() > 20
 
 
-def test_mls_support_off_the_box_falls_back_to_the_nearest_point():
-    """A point beyond a non-periodic box face keeps one plane of its support
-    inside the box: the moment matrix is singular and the nearest point of
-    that plane takes the whole weight (Reading M4)."""
+def test_mls_support_off_the_box_takes_the_nearest_box_node():
+    """A point beyond a non-periodic box face keeps its full support; the
+    points off the box take the state of the nearest box node (Reading M4),
+    so the fit stays regular, and a field that does not vary across the face
+    is reproduced exactly."""
     n = 7
     tag = np.zeros(n ** 3, np.uint8)
     lat = L.Lattice(n, n, n, 0.8, tag, np.zeros(0, G.LINK_DTYPE), [G.Face() for _ in range(6)],
                     (False, True, True))
-    st = ib.stencil(lat, np.array([[-0.8, 3.2, 2.9]]))
-    assert st.fallback[0]
-    assert st.phi.sum() == 1.0
-    assert st.nodes[0][np.argmax(st.phi[0])] == 0 + n * (3 + n * 3)
-    assert np.all(st.grad == 0)
+    X = np.array([[-0.8, 3.2, 2.9], [0.3, 4.4, 2.1], [6.4, 3.0, 3.5]])   # y, z clear of the periodic seam
+    st = ib.stencil(lat, X)
+    assert not st.fallback.any() and (st.weight > 0).all()
+    base = np.floor(X + 0.5).astype(int)
+    cx = np.clip(base[:, None, 0] + ib.OFFSETS[None, :, 0], 0, n - 1)
+    assert np.array_equal(st.nodes % n, cx)
+    assert np.allclose(st.phi.sum(axis=1), 1.0, atol=1e-12)
+    # a field linear in y and z only, constant in x: reproduced exactly
+    u = np.zeros((n ** 3, 3))
+    idx = np.arange(n ** 3)
+    u[:, 0] = 0.01 * (idx // n % n) - 0.02 * (idx // (n * n))
+    f = lat.init_equilibrium(None, u)
+    U = ib.interpolate_velocity(f, st)
+    # periodic y, z: unwrap the support coordinates relative to the point
+    Y = st.nodes // n % n
+    Z = st.nodes // (n * n)
+    dy = (Y - X[:, None, 1] + n / 2) % n - n / 2
+    dz = (Z - X[:, None, 2] + n / 2) % n - n / 2
+    want = np.einsum("mk,mk->m", st.phi, 0.01 * (X[:, None, 1] + dy) - 0.02 * (X[:, None, 2] + dz))
+    assert np.allclose(U[:, 0], want, atol=1e-12)
 
 
 def test_spreading_conserves_total_force_and_is_the_transpose_of_interpolation():
