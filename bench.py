@@ -32,7 +32,7 @@ BYTES_PER_UPDATE = {"f32": 152, "f16": 76, "bf16": 76}
 # with the profile summaries), with the hash of the lattice kernel's sources
 # (lbm.cu, lbm_device.cuh) it was captured from: any change to them makes the
 # figure stale, and the bench then reports null until it is captured again.
-LBM_TRAFFIC = {("throughput", "f32"): (623.1e6, "5aa954892ee66c37")}
+LBM_TRAFFIC = {("throughput", "f32"): (623.0e6, "189b327fc7195800")}
 LBM_SOURCES = ("lbm.cu", "lbm_device.cuh")
 CPU_SAMPLE_X = 64          # x-slab of the workload the oracle runs on (cpu_baseline)
 REF_SAMPLE_X = 40          # slab of the reference arm (its first layer of capsules)
@@ -342,6 +342,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-parity", action="store_true", help="skip the oracle-parity leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched-sweep side measurement")
+    ap.add_argument("--no-slabs", action="store_true", help="skip the slab-decomposition side measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage side measurements")
     ap.add_argument("--sweep-members", type=int, default=64)
     ap.add_argument("--sweep-steps", type=int, default=100)
@@ -457,6 +458,8 @@ def main():
         out["storage_variants"] = storage_variants(case, nf)
     if rank == 0 and not args.no_sweep:
         out["sweep"] = sweep_measure(args.sweep_members, args.sweep_steps, local, dist)
+    if rank == 0 and not args.no_slabs:
+        out["slabs"] = slab_measure(case, nf, out["ms_per_step"])
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(case, args.cpu_steps)
     if rank == 0:
@@ -496,6 +499,40 @@ def oracle_parity(steps=PARITY_STEPS):
         out[st] = {"velocity_rel_l2": float(np.linalg.norm(u[fl] - uo[fl]) / np.linalg.norm(uo[fl])),
                    "centroid_max_abs": float(np.abs(cen - cen_o).max())}
     return out
+
+
+def slab_measure(case, nf, ms_whole, n_slabs=4, steps=50):
+    """The same workload stepped as x-slabs of one context on this GPU (the
+    decomposition a multi-GPU run uses, with its halo copies and the capsules'
+    whole-lattice member): whole-step MLUPS against the undivided context, and
+    the bytes the ghost-plane copies move per step (what each cut sends to its
+    neighbours on several GPUs)."""
+    import torch
+    from paper_2207_06043_gb300 import binding as B
+    from paper_2207_06043_gb300 import workloads as W
+    whole = W.make_solver(case)
+    grp = B.slab_group(whole, n_slabs)
+    whole.close()
+    grp.step(5)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    grp.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    g = case["geometry"]
+    ghost_planes = sum(lo + hi for _, _, lo, hi in grp.slabs)
+    ny_p = g.ny + (0 if g.periodic[1] else 2)
+    nz_p = g.nz + (0 if g.periodic[2] else 2)
+    halo_bytes = ghost_planes * ny_p * nz_p * 19 * 4 * 2   # every slot of every padded node, read + written
+    grp.close()
+    return {"slabs": n_slabs, "plan": [list(x) for x in grp.slabs], "value": nf / (ms * 1e-3) / 1e6,
+            "unit": "MLUPS", "ms_per_step": ms, "steps": steps, "overhead_vs_whole": ms / ms_whole - 1.0,
+            "halo_bytes_per_step": int(halo_bytes),
+            "note": "one GPU; each ghost plane copied from its owner after every step (all 19 slots of every node)"}
 
 
 def sweep_measure(n_members, steps, local, dist):
