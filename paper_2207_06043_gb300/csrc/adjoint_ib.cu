@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(IB_PROBE_THREADS) k_adj_probes(
     const double sg = s == 1 ? 1.2 : -1.2;
     const float sigma = s == 1 ? 1.f : -1.f;
     MlsG M;
-    mls_build_g<4, PROBE_FAST32>(d, tag, xa + sg * na, r, mask, M);
+    float xh, xl, ph, pl;   // the forward probe point, formed as the forward kernel forms it
+    split_of(xa, xh, xl);
+    probe_of(xh, xl, __fmul_rn(s == 1 ? 1.2f : -1.2f, na), ph, pl);
+    mls_build_g<4, PROBE_FAST32>(d, tag, ph, pl, r, mask, M);
     float4 q[GS];
     int node[GS];
 #pragma unroll
@@ -335,7 +338,9 @@ __global__ void __launch_bounds__(IB_MARKER_THREADS) k_adj_markers(
     if (!valid) return;
     const MemberDev& d = mem[C.member];
     MlsG M;
-    mls_build_g<4, MARKER_FAST32>(d, tag, P, r, mask, M);
+    float Ph, Pl;
+    split_of(P, Ph, Pl);
+    mls_build_g<4, MARKER_FAST32>(d, tag, Ph, Pl, r, mask, M);
     float ph[GS];
     float4 q[GS], lf[GS];
     int node[GS];

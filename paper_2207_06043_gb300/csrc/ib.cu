@@ -333,17 +333,18 @@ __global__ void __launch_bounds__(256) k_fib_scatter(const MemberDev* __restrict
 __global__ void __launch_bounds__(IB_MARKER_THREADS, IB_MARKER_MIN_BLOCKS)
 k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float* __restrict__ fib,
              const uint32_t* __restrict__ status, const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps,
-             const CapsuleSums* __restrict__ sums, const double* __restrict__ x, const double* __restrict__ vel,
+             const CapsuleSums* __restrict__ sums, const float4* __restrict__ xm, const double* __restrict__ vel,
              const float* __restrict__ area, float* __restrict__ uv0, float* __restrict__ probe, int n_verts,
              const float4* __restrict__ macro) {
     // four lanes per marker
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = t & (GL - 1);
     const int l = min(t / GL, n_verts - 1);
-    const int ax = min(r, 2);   // the axis this lane converts from FP64
-    // the marker's coordinate and velocity along ax, fetched beside its
-    // capsule's flags
-    const double P = x[3 * l + ax];
+    const int ax = min(r, 2);   // the axis this lane takes the nearest node of
+    // the marker's coordinate (two-float mirror) and velocity along ax,
+    // fetched beside its capsule's flags
+    const float4 mh = xm[2 * l], ml = xm[2 * l + 1];
+    const float Ph = ax == 0 ? mh.x : (ax == 1 ? mh.y : mh.z), Pl = ax == 0 ? ml.x : (ax == 1 ? ml.y : ml.z);
     const float Vb = (float)vel[3 * l + ax];
     const int cap = v_cap[l];
     const CapsuleDev& C = caps[cap];
@@ -354,7 +355,7 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
     const MemberDev& d = mem[m];
     MlsG M;
     float4 q[GS];
-    mls_build_g<1, MARKER_FAST32>(d, macro, P, r, mask, M, q);
+    mls_build_g<1, MARKER_FAST32>(d, macro, Ph, Pl, r, mask, M, q);
     float p[GS];
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
@@ -396,7 +397,7 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
 
 __global__ void __launch_bounds__(IB_PROBE_THREADS, IB_PROBE_MIN_BLOCKS)
 k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, const uint32_t* __restrict__ status,
-            const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps, const double* __restrict__ x,
+            const int* __restrict__ v_cap, const CapsuleDev* __restrict__ caps, const float4* __restrict__ xm,
             const float* __restrict__ nrm, float* __restrict__ probe, int n_verts,
             const float4* __restrict__ macro) {
     // four lanes per probe, two probes per marker: x + 1.2 n (s = 1), x - 1.2 n (s = 2)
@@ -405,19 +406,22 @@ k_ib_probes(const MemberDev* __restrict__ mem, const uint8_t* __restrict__ tag, 
     const int sid = t / GL;
     const int l = min(sid >> 1, n_verts - 1);
     const int s = 1 + (sid & 1);
-    const int ax = min(r, 2);   // the axis this lane converts from FP64
-    // the probe's coordinate along ax, fetched beside its capsule's flags
+    const int ax = min(r, 2);   // the axis this lane takes the nearest node of
+    // the vertex coordinate (two-float mirror) and the normal along ax,
+    // fetched beside its capsule's flags
     const float na = nrm[3 * l + ax];
-    const double xa = x[3 * l + ax];
+    const float4 mh = xm[2 * l], ml = xm[2 * l + 1];
+    const float xh = ax == 0 ? mh.x : (ax == 1 ? mh.y : mh.z), xl = ax == 0 ? ml.x : (ax == 1 ? ml.y : ml.z);
     const int m = caps[v_cap[l]].member;
     const bool valid = (sid >> 1) < n_verts && !(status[m] & STOP);
     const unsigned mask = __ballot_sync(FULL, valid);
     if (!valid) return;
     const MemberDev& d = mem[m];
-    const double sg = s == 1 ? 1.2 : -1.2;
+    float ph, pl;
+    probe_of(xh, xl, __fmul_rn(s == 1 ? 1.2f : -1.2f, na), ph, pl);
     MlsG M;
     float4 q[GS];
-    mls_build_g<4, PROBE_FAST32>(d, macro, xa + sg * na, r, mask, M, q);
+    mls_build_g<4, PROBE_FAST32>(d, macro, ph, pl, r, mask, M, q);
     float acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // rho, then grad u row-major
 #pragma unroll
     for (int j = 0; j < GS; ++j) {
@@ -913,7 +917,7 @@ cudaError_t launch_markers(const DevState& d, cudaStream_t s) {
     if (d.n_verts == 0) return cudaSuccess;
     const long long mt = (long long)GL * d.n_verts;
     k_ib_markers<<<(unsigned)((mt + IB_MARKER_THREADS - 1) / IB_MARKER_THREADS), IB_MARKER_THREADS, 0, s>>>(
-        d.mem, d.tag, d.fib, d.status, d.v_cap, d.caps, d.sums, d.x, d.vel, d.area, d.uv0, d.probe, d.n_verts,
+        d.mem, d.tag, d.fib, d.status, d.v_cap, d.caps, d.sums, d.xm, d.vel, d.area, d.uv0, d.probe, d.n_verts,
         d.macro);
     return cudaGetLastError();
 }
@@ -922,7 +926,7 @@ cudaError_t launch_probes(const DevState& d, cudaStream_t s) {
     if (d.n_verts == 0) return cudaSuccess;
     const long long pt = 2LL * GL * d.n_verts;
     k_ib_probes<<<(unsigned)((pt + IB_PROBE_THREADS - 1) / IB_PROBE_THREADS), IB_PROBE_THREADS, 0, s>>>(
-        d.mem, d.tag, d.status, d.v_cap, d.caps, d.x, d.nrm, d.probe, d.n_verts, d.macro);
+        d.mem, d.tag, d.status, d.v_cap, d.caps, d.xm, d.nrm, d.probe, d.n_verts, d.macro);
     return cudaGetLastError();
 }
 

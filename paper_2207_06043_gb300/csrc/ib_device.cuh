@@ -145,10 +145,9 @@ struct MlsG {
     float inv[4][4];
 };
 
-// P is the point's coordinate along axis min(r, 2): lanes 0, 1, 2 of a group
-// each take the FP64 steps (nearest node, offset) for one axis and the group
-// exchanges the results, so that GB300's narrow FP64 pipe does a third of the
-// work it would if every lane took all three axes.
+// (h, l) is the point's coordinate along axis min(r, 2): lanes 0, 1, 2 of a
+// group each take the nearest-node step of one axis and the group exchanges
+// the results.
 //
 // Every point of the 3x3x3 block takes part in the fit (Reading M4: a solid
 // one with the wall's state, one off the box with the nearest box node's), and
@@ -167,12 +166,46 @@ struct MlsG {
 // into q from the moments array of the step, where a solid node holds
 // (-1, 0, 0, 0): the wall's rho negated, so that the spreading can skip it
 // without a tag gather.
+// The sum a + b of two floats as the unevaluated pair (p, e), p = fl(a + b)
+// and e its rounding error, exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& p, float& e) {
+    p = __fadd_rn(a, b);
+    const float z = __fsub_rn(p, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(p, z)), __fsub_rn(b, z));
+}
+
+// The nearest node b = floor(x + 1/2) of a coordinate given as the
+// unevaluated float sum x = h + l with |l| <= ulp(h) (the two-float mirror of
+// an FP64 position), exactly as the FP64 floor, and the offset b - x rounded
+// once: h + 1/2 is exact for |h| < 2^22; only when it is an integer does the
+// sign of l decide; b - h is exact (Sterbenz).  No FP64 arithmetic (GB300's
+// FP64 pipe is narrow).
+__device__ __forceinline__ void nearest_of(float h, float l, int& bi, float& o) {
+    const float t = __fadd_rn(h, 0.5f);
+    float b = floorf(t);
+    if (t == b && l < 0.f) b -= 1.f;
+    bi = (int)b;
+    o = __fsub_rn(__fsub_rn(b, h), l);
+}
+
+// (h, l) of an FP64 coordinate, as the mirror holds it (mirror_put)
+__device__ __forceinline__ void split_of(double x, float& h, float& l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// A probe point x + s n along one axis (s = +-1.2, Section "No-slip
+// conditions ..."), from the mirror (h, l) of x: the pair of h + (l + s n).
+__device__ __forceinline__ void probe_of(float h, float l, float sn, float& ph, float& pl) {
+    two_sum(h, __fadd_rn(l, sn), ph, pl);
+}
+
 template <int ROWS, bool MAC>
-__device__ __forceinline__ void mls_build_impl(const MemberDev& d, const void* src, double P, int r, unsigned mask,
-                                               MlsG& M, float4 (&q)[GS]) {
-    const double b = floor(P + 0.5);
-    const int bi = (int)b;
-    const float o = (float)(b - P);
+__device__ __forceinline__ void mls_build_impl(const MemberDev& d, const void* src, float h, float l, int r,
+                                               unsigned mask, MlsG& M, float4 (&q)[GS]) {
+    int bi;
+    float o;
+    nearest_of(h, l, bi, o);
     M.bx = __shfl_sync(mask, bi, 0, GL); M.by = __shfl_sync(mask, bi, 1, GL); M.bz = __shfl_sync(mask, bi, 2, GL);
     M.ox = __shfl_sync(mask, o, 0, GL); M.oy = __shfl_sync(mask, o, 1, GL); M.oz = __shfl_sync(mask, o, 2, GL);
     const bool interior = M.bx >= 1 && M.bx <= d.nx - 2 && M.by >= 1 && M.by <= d.ny - 2 && M.bz >= 1 &&
@@ -235,17 +268,18 @@ __device__ __forceinline__ void mls_build_impl(const MemberDev& d, const void* s
     }
 }
 
+// the lane's coordinate along axis min(r, 2) as the pair (h, l)
 template <int ROWS, bool FAST32>
-__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, double P, int r,
-                                            unsigned mask, MlsG& M) {
+__device__ __forceinline__ void mls_build_g(const MemberDev& d, const uint8_t* __restrict__ tag, float h, float l,
+                                            int r, unsigned mask, MlsG& M) {
     float4 q[GS];
-    mls_build_impl<ROWS, false>(d, tag, P, r, mask, M, q);
+    mls_build_impl<ROWS, false>(d, tag, h, l, r, mask, M, q);
 }
 
 template <int ROWS, bool FAST32>
-__device__ __forceinline__ void mls_build_g(const MemberDev& d, const float4* __restrict__ macro, double P, int r,
-                                            unsigned mask, MlsG& M, float4 (&q)[GS]) {
-    mls_build_impl<ROWS, true>(d, macro, P, r, mask, M, q);
+__device__ __forceinline__ void mls_build_g(const MemberDev& d, const float4* __restrict__ macro, float h, float l,
+                                            int r, unsigned mask, MlsG& M, float4 (&q)[GS]) {
+    mls_build_impl<ROWS, true>(d, macro, h, l, r, mask, M, q);
 }
 
 __device__ __forceinline__ float mls_row_g(const MlsG& M, int row, int j, int k) {
