@@ -342,14 +342,18 @@ class Solver:
 
     # -- read-out -----------------------------------------------------------------
     def read_fields(self, member=None, out=None):
-        """rho (N,), u (N,3) as float32 numpy arrays (or into device tensors
-        out=(rho, u))."""
+        """rho (N,), u (N,3) as float32 numpy arrays, or into out=(rho, u):
+        device tensors, or host buffers (numpy arrays or CPU tensors; pinned
+        tensors make the copy a direct DMA)."""
         if out is not None:
             rho, u = out
+            dev = int(bool(getattr(rho, "is_cuda", False)))
+            if dev != int(bool(getattr(u, "is_cuda", False))):
+                raise ValueError("rho and u must both be on the device or both on the host")
             if member is None:
-                self._check(self._L.ibl_read_fields(self._h, _ptr(rho), _ptr(u), 1))
+                self._check(self._L.ibl_read_fields(self._h, _ptr(rho), _ptr(u), dev))
             else:
-                self._check(self._L.ibl_member_read_fields(self._h, int(member), _ptr(rho), _ptr(u), 1))
+                self._check(self._L.ibl_member_read_fields(self._h, int(member), _ptr(rho), _ptr(u), dev))
             return rho, u
         n = self.member_nodes(member)
         rho = np.empty(n, dtype=np.float32)

@@ -40,7 +40,7 @@ def build(verbose: bool = False, extra=(), out_dir=OUT_DIR) -> str:
     lib = os.path.join(out_dir, "libibl.so")
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra), out_dir), SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

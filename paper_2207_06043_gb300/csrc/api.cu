@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -146,6 +147,26 @@ ibl_status fail(ibl_ctx* ctx, ibl_status st, const std::string& msg) {
         if (s_ != IBL_OK) return s_;                \
     } while (0)
 
+// fn(begin, end) over [0, n) in up to hardware_concurrency chunks of at least
+// min_chunk items, on host threads (the calling thread takes the first chunk).
+template <typename F>
+void parallel_chunks(size_t n, size_t min_chunk, F fn) {
+    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t T = std::min(hw, std::max<size_t>(1, n / std::max<size_t>(min_chunk, 1)));
+    if (T <= 1) {
+        fn((size_t)0, n);
+        return;
+    }
+    const size_t step = (n + T - 1) / T;
+    std::vector<std::thread> th;
+    for (size_t t = 1; t < T; ++t) {
+        const size_t b = t * step, e = std::min(n, b + step);
+        if (b < e) th.emplace_back([&fn, b, e] { fn(b, e); });
+    }
+    fn((size_t)0, std::min(n, step));
+    for (std::thread& x : th) x.join();
+}
+
 template <typename T>
 ibl_status dev_alloc(ibl_ctx* ctx, T*& p, size_t count) {
     p = nullptr;
@@ -187,41 +208,55 @@ inline double vnorm(V3 a) { return std::sqrt(vdot(a, a)); }
 // vertices are set up in a millisecond.
 bool build_hinges(const std::vector<int>& tris, int nv, std::vector<int>& hinge, std::vector<int>& tri_a,
                   std::vector<int>& tri_b, std::string& why) {
-    struct Half { long long key; int t, wing; };
+    // half-edges u -> v (with their triangle and the triangle's third vertex)
+    // bucketed by u; every edge u < v pairs with v -> u.  Edges come out in
+    // ascending (u, v) order.
     const int nt = (int)tris.size() / 3;
-    std::vector<Half> half;
-    half.reserve(3 * (size_t)nt);
+    struct Half { int v, t, wing; };
+    std::vector<int> start(nv + 1, 0);
     for (int t = 0; t < nt; ++t) {
         const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
         if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv || a == b || b == c || a == c) {
             why = "triangle " + std::to_string(t) + " has an invalid vertex index";
             return false;
         }
-        const int uvw[3][3] = {{a, b, c}, {b, c, a}, {c, a, b}};
-        for (auto& r : uvw) half.push_back({(long long)r[0] * nv + r[1], t, r[2]});
+        ++start[a + 1]; ++start[b + 1]; ++start[c + 1];
     }
-    std::sort(half.begin(), half.end(), [](const Half& x, const Half& y) { return x.key < y.key; });
-    for (size_t i = 1; i < half.size(); ++i)
-        if (half[i].key == half[i - 1].key) {
-            why = "edge used twice in the same direction (mesh not consistently oriented)";
-            return false;
-        }
+    for (int v = 0; v < nv; ++v) start[v + 1] += start[v];
+    std::vector<Half> half(3 * (size_t)nt);
+    std::vector<int> at(start.begin(), start.end() - 1);
+    for (int t = 0; t < nt; ++t) {
+        const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        const int uvw[3][3] = {{a, b, c}, {b, c, a}, {c, a, b}};
+        for (auto& r : uvw) half[at[r[0]]++] = {r[1], t, r[2]};
+    }
+    for (int u = 0; u < nv; ++u) {
+        auto b = half.begin() + start[u], e = half.begin() + start[u + 1];
+        std::sort(b, e, [](const Half& x, const Half& y) { return x.v < y.v; });
+        for (auto it = b; it + 1 < e; ++it)
+            if (it->v == (it + 1)->v) {
+                why = "edge used twice in the same direction (mesh not consistently oriented)";
+                return false;
+            }
+    }
     hinge.clear(); tri_a.clear(); tri_b.clear();
     size_t paired = 0;
-    for (const Half& h : half) {
-        const int u = (int)(h.key / nv), v = (int)(h.key % nv);
-        if (u > v) continue;
-        const long long rk = (long long)v * nv + u;
-        auto it = std::lower_bound(half.begin(), half.end(), rk, [](const Half& x, long long k) { return x.key < k; });
-        if (it == half.end() || it->key != rk) { why = "mesh is not closed"; return false; }
-        hinge.push_back(h.wing);
-        hinge.push_back(u);
-        hinge.push_back(v);
-        hinge.push_back(it->wing);
-        tri_a.push_back(h.t);
-        tri_b.push_back(it->t);
-        ++paired;
-    }
+    for (int u = 0; u < nv; ++u)
+        for (int i = start[u]; i < start[u + 1]; ++i) {
+            const Half& h = half[i];
+            if (u > h.v) continue;
+            const Half* back = nullptr;
+            for (int k = start[h.v]; k < start[h.v + 1]; ++k)
+                if (half[k].v == u) { back = &half[k]; break; }
+            if (!back) { why = "mesh is not closed"; return false; }
+            hinge.push_back(h.wing);
+            hinge.push_back(u);
+            hinge.push_back(h.v);
+            hinge.push_back(back->wing);
+            tri_a.push_back(h.t);
+            tri_b.push_back(back->t);
+            ++paired;
+        }
     if (2 * paired != half.size()) { why = "mesh is not closed"; return false; }
     return true;
 }
@@ -687,13 +722,16 @@ ibl_status finalize(ibl_ctx* ctx) {
         // padded tags (ghost layer solid)
         const size_t base = tag_all.size();
         tag_all.resize(base + round_up((size_t)Np, 256), TAG_SOLID);
-        for (int z = 0; z < d.nz; ++z)
-            for (int y = 0; y < d.ny; ++y)
-                for (int x = 0; x < d.nx; ++x) {
-                    const long long un = x + (long long)d.nx * (y + (long long)d.ny * z);
-                    const long long pn = (x + md.px) + (long long)md.NX * ((y + md.py) + (long long)md.NY * (z + md.pz));
-                    tag_all[base + pn] = M.tag[un] ? TAG_SOLID : 0;
-                }
+        parallel_chunks((size_t)d.nz, 4, [&](size_t z0, size_t z1) {
+            for (int z = (int)z0; z < (int)z1; ++z)
+                for (int y = 0; y < d.ny; ++y)
+                    for (int x = 0; x < d.nx; ++x) {
+                        const long long un = x + (long long)d.nx * (y + (long long)d.ny * z);
+                        const long long pn =
+                            (x + md.px) + (long long)md.NX * ((y + md.py) + (long long)md.NY * (z + md.pz));
+                        tag_all[base + pn] = M.tag[un] ? TAG_SOLID : 0;
+                    }
+        });
         // links
         md.link_begin = link_off;
         const int dims[3] = {d.nx, d.ny, d.nz};
@@ -713,26 +751,49 @@ ibl_status finalize(ibl_ctx* ctx) {
         // of the wall pass then touch consecutive nodes of one population
         // plane along a wall
         struct LinkRec { uint32_t node, meta; float q, dq; };
-        std::vector<LinkRec> recs;
-        recs.reserve(M.links.size());
-        for (size_t li = 0; li < M.links.size(); ++li) {
-            const ibl_wall_link& L = M.links[li];
+        const size_t nl = M.links.size();
+        std::vector<LinkRec> made(nl);
+        // per link: 0 valid, 1 out of range, 2 starts at a solid node, 3 does
+        // not end at a solid node inside the box; the first bad link is reported
+        std::vector<uint8_t> bad(nl, 0);
+        parallel_chunks(nl, 16384, [&](size_t l0, size_t l1) {
             const long long Nu = (long long)d.nx * d.ny * d.nz;
-            if ((long long)L.node >= Nu || L.dir < 1 || L.dir > 18 || !(L.q > 0.f && L.q <= 1.f))
-                return fail(ctx, IBL_ERR_ARG, "wall link " + std::to_string(li) + " out of range");
-            int c[3] = {(int)(L.node % d.nx), (int)((L.node / d.nx) % d.ny), (int)(L.node / ((long long)d.nx * d.ny))};
-            int s0[3], m1[3], m2[3];
-            if (!fluid_at(c)) return fail(ctx, IBL_ERR_ARG, "wall link " + std::to_string(li) + " starts at a solid node");
-            if (!shift(c, 1, L.dir, s0) || fluid_at(s0))
-                return fail(ctx, IBL_ERR_ARG, "wall link " + std::to_string(li) + " does not end at a solid node inside the box");
-            const bool ok1 = shift(c, -1, L.dir, m1) && fluid_at(m1);
-            const bool ok2 = shift(c, -2, L.dir, m2) && fluid_at(m2);
-            const long long pn = (c[0] + md.px) + (long long)md.NX * ((c[1] + md.py) + (long long)md.NY * (c[2] + md.pz));
-            recs.push_back({(uint32_t)pn, L.dir | (ok1 ? 32u : 0u) | (ok2 ? 64u : 0u) | ((uint32_t)mi << 8), L.q, L.dq});
-        }
-        std::sort(recs.begin(), recs.end(), [](const LinkRec& a, const LinkRec& b) {
-            return (a.meta & 31u) != (b.meta & 31u) ? (a.meta & 31u) < (b.meta & 31u) : a.node < b.node;
+            for (size_t li = l0; li < l1; ++li) {
+                const ibl_wall_link& L = M.links[li];
+                if ((long long)L.node >= Nu || L.dir < 1 || L.dir > 18 || !(L.q > 0.f && L.q <= 1.f)) { bad[li] = 1; continue; }
+                int c[3] = {(int)(L.node % d.nx), (int)((L.node / d.nx) % d.ny), (int)(L.node / ((long long)d.nx * d.ny))};
+                int s0[3], m1[3], m2[3];
+                if (!fluid_at(c)) { bad[li] = 2; continue; }
+                if (!shift(c, 1, L.dir, s0) || fluid_at(s0)) { bad[li] = 3; continue; }
+                const bool ok1 = shift(c, -1, L.dir, m1) && fluid_at(m1);
+                const bool ok2 = shift(c, -2, L.dir, m2) && fluid_at(m2);
+                const long long pn =
+                    (c[0] + md.px) + (long long)md.NX * ((c[1] + md.py) + (long long)md.NY * (c[2] + md.pz));
+                made[li] = {(uint32_t)pn, L.dir | (ok1 ? 32u : 0u) | (ok2 ? 64u : 0u) | ((uint32_t)mi << 8), L.q, L.dq};
+            }
         });
+        for (size_t li = 0; li < nl; ++li)
+            if (bad[li])
+                return fail(ctx, IBL_ERR_ARG, "wall link " + std::to_string(li) +
+                                                  (bad[li] == 1 ? " out of range"
+                                                   : bad[li] == 2 ? " starts at a solid node"
+                                                                  : " does not end at a solid node inside the box"));
+        // (direction, node) order: a stable counting sort by direction, then
+        // each direction's run sorted by node unless it already is
+        std::vector<LinkRec> recs(nl);
+        {
+            size_t cnt[20] = {0};
+            for (const LinkRec& r : made) ++cnt[(r.meta & 31u) + 1];
+            for (int k = 1; k < 20; ++k) cnt[k] += cnt[k - 1];
+            size_t at[19];
+            for (int k = 0; k < 19; ++k) at[k] = cnt[k];
+            for (const LinkRec& r : made) recs[at[r.meta & 31u]++] = r;
+            for (int k = 1; k < 19; ++k) {
+                auto b = recs.begin() + cnt[k], e = recs.begin() + cnt[k + 1];
+                if (!std::is_sorted(b, e, [](const LinkRec& x, const LinkRec& y) { return x.node < y.node; }))
+                    std::sort(b, e, [](const LinkRec& x, const LinkRec& y) { return x.node < y.node; });
+            }
+        }
         for (const LinkRec& r : recs) {
             l_node.push_back(r.node);
             l_meta.push_back(r.meta);
@@ -746,25 +807,72 @@ ibl_status finalize(ibl_ctx* ctx) {
         md.cap_count = (int)M.caps.size();
         md.vert_begin = vert_off;
         const double nu = (d.tau - 0.5) / 3.0;
-        for (const CapsuleHost& ch : M.caps) {
-            const int nv = (int)ch.X.size() / 3, nt = (int)ch.tris.size() / 3;
+        // per capsule, on host threads: hinges, FP64 sums, rest lengths,
+        // spring and bending constants and rest angles
+        struct CapPre {
             std::vector<int> hinge, ta, tb;
+            MeshSums ms;
+            double radius = 0.0;
+            std::vector<double> l0;
+            std::vector<float> ks, kb, th0;
             std::string why;
-            if (!build_hinges(ch.tris, nv, hinge, ta, tb, why)) return fail(ctx, IBL_ERR_ARG, "capsule mesh: " + why);
-            const int ne = (int)hinge.size() / 4;
-            const double* X = ch.X.data();
-            MeshSums ms = mesh_sums(X, nv, ch.tris.data(), nt);
-            if (!(ms.V > 0)) return fail(ctx, IBL_ERR_ARG, "capsule mesh encloses no volume (triangles must be outward CCW)");
-            std::vector<double> tri_area(nt);
-            for (int t = 0; t < nt; ++t) {
-                const int* T = &ch.tris[3 * t];
-                const V3 a = {X[3 * T[0]], X[3 * T[0] + 1], X[3 * T[0] + 2]};
-                const V3 b = {X[3 * T[1]], X[3 * T[1] + 1], X[3 * T[1] + 2]};
-                const V3 c = {X[3 * T[2]], X[3 * T[2] + 1], X[3 * T[2] + 2]};
-                tri_area[t] = 0.5 * vnorm(vcross(vsub(b, a), vsub(c, a)));
+        };
+        std::vector<CapPre> pre(M.caps.size());
+        parallel_chunks(M.caps.size(), 1, [&](size_t c0, size_t c1) {
+            for (size_t ci = c0; ci < c1; ++ci) {
+                const CapsuleHost& ch = M.caps[ci];
+                CapPre& P = pre[ci];
+                const int nv = (int)ch.X.size() / 3, nt = (int)ch.tris.size() / 3;
+                if (!build_hinges(ch.tris, nv, P.hinge, P.ta, P.tb, P.why)) {
+                    P.why = "capsule mesh: " + P.why;
+                    continue;
+                }
+                const double* X = ch.X.data();
+                P.ms = mesh_sums(X, nv, ch.tris.data(), nt);
+                if (!(P.ms.V > 0)) {
+                    P.why = "capsule mesh encloses no volume (triangles must be outward CCW)";
+                    continue;
+                }
+                std::vector<double> tri_area(nt);
+                for (int t = 0; t < nt; ++t) {
+                    const int* T = &ch.tris[3 * t];
+                    const V3 a = {X[3 * T[0]], X[3 * T[0] + 1], X[3 * T[0] + 2]};
+                    const V3 b = {X[3 * T[1]], X[3 * T[1] + 1], X[3 * T[1] + 2]};
+                    const V3 c = {X[3 * T[2]], X[3 * T[2] + 1], X[3 * T[2] + 2]};
+                    tri_area[t] = 0.5 * vnorm(vcross(vsub(b, a), vsub(c, a)));
+                }
+                P.radius = std::cbrt(3.0 * P.ms.V / (4.0 * M_PI));
+                const double ks0 = ch.p.Ca > 0 ? nu * ch.p.u_ref / ch.p.Ca : 0.0;   // Ca = rho nu u_ref / k_s0
+                const int ne = (int)P.hinge.size() / 4;
+                P.l0.resize(ne);
+                P.ks.resize(ne);
+                P.kb.resize(ne);
+                P.th0.resize(ne);
+                for (int e = 0; e < ne; ++e) {
+                    const int* h = &P.hinge[4 * e];
+                    const V3 p1 = {X[3 * h[0]], X[3 * h[0] + 1], X[3 * h[0] + 2]};
+                    const V3 p2 = {X[3 * h[1]], X[3 * h[1] + 1], X[3 * h[1] + 2]};
+                    const V3 p3 = {X[3 * h[2]], X[3 * h[2] + 1], X[3 * h[2] + 2]};
+                    const V3 p4 = {X[3 * h[3]], X[3 * h[3] + 1], X[3 * h[3] + 2]};
+                    const double l0 = vnorm(vsub(p3, p2));
+                    const double ks = ks0 * (tri_area[P.ta[e]] + tri_area[P.tb[e]]) / (l0 * l0);   // T = 1
+                    const double kb = ch.p.Eb * ks * P.radius * P.radius;                         // Eb = k_b/(k_s,l r^2)
+                    P.l0[e] = l0;
+                    P.ks[e] = (float)ks;
+                    P.kb[e] = (float)kb;
+                    P.th0[e] = (float)signed_dihedral(p1, p2, p3, p4);
+                }
             }
-            const double radius = std::cbrt(3.0 * ms.V / (4.0 * M_PI));
-            const double ks0 = ch.p.Ca > 0 ? nu * ch.p.u_ref / ch.p.Ca : 0.0;   // Ca = rho nu u_ref / k_s0
+        });
+        for (size_t ci = 0; ci < M.caps.size(); ++ci) {
+            const CapsuleHost& ch = M.caps[ci];
+            const CapPre& P = pre[ci];
+            if (!P.why.empty()) return fail(ctx, IBL_ERR_ARG, P.why);
+            const int nv = (int)ch.X.size() / 3, nt = (int)ch.tris.size() / 3;
+            const int ne = (int)P.hinge.size() / 4;
+            const double* X = ch.X.data();
+            const MeshSums& ms = P.ms;
+            const double radius = P.radius;
             CapsuleDev cd{};
             cd.member = mi;
             cd.rigid = ch.p.rigid ? 1 : 0;
@@ -780,25 +888,19 @@ ibl_status finalize(ibl_ctx* ctx) {
             CapsuleRestHost rh;
             rh.member = mi; rh.v_begin = vert_off; rh.nv = nv; rh.t_begin = tri_off; rh.nt = nt;
             rh.e_begin = edge_off; rh.ne = ne; rh.S0 = ms.S; rh.V0 = ms.V; rh.rigid = cd.rigid;
+            rh.l0 = P.l0;
+            rh.edges.reserve(2 * (size_t)ne);
             for (int e = 0; e < ne; ++e) {
-                const int* h = &hinge[4 * e];
-                const V3 p1 = {X[3 * h[0]], X[3 * h[0] + 1], X[3 * h[0] + 2]};
-                const V3 p2 = {X[3 * h[1]], X[3 * h[1] + 1], X[3 * h[1] + 2]};
-                const V3 p3 = {X[3 * h[2]], X[3 * h[2] + 1], X[3 * h[2] + 2]};
-                const V3 p4 = {X[3 * h[3]], X[3 * h[3] + 1], X[3 * h[3] + 2]};
-                const double l0 = vnorm(vsub(p3, p2));
-                const double ks = ks0 * (tri_area[ta[e]] + tri_area[tb[e]]) / (l0 * l0);   // T = 1
-                const double kb = ch.p.Eb * ks * radius * radius;                           // Eb = k_b/(k_s,l r^2)
+                const int* h = &P.hinge[4 * e];
                 for (int j = 0; j < 4; ++j) hinge_all.push_back(vert_off + h[j]);
-                l0_all.push_back((float)l0);
-                ks_all.push_back((float)ks);
-                kb_all.push_back((float)kb);
-                th0_all.push_back((float)signed_dihedral(p1, p2, p3, p4));
+                l0_all.push_back((float)P.l0[e]);
                 e_cap.push_back(cap_off);
-                rh.l0.push_back(l0);
                 rh.edges.push_back(h[1]);
                 rh.edges.push_back(h[2]);
             }
+            ks_all.insert(ks_all.end(), P.ks.begin(), P.ks.end());
+            kb_all.insert(kb_all.end(), P.kb.begin(), P.kb.end());
+            th0_all.insert(th0_all.end(), P.th0.begin(), P.th0.end());
             for (int t = 0; t < nt; ++t)
                 for (int j = 0; j < 3; ++j) tri_all.push_back(vert_off + ch.tris[3 * t + j]);
             for (int v = 0; v < nv; ++v) {
@@ -850,33 +952,58 @@ ibl_status finalize(ibl_ctx* ctx) {
             const int ns = (md.N + 31) / 32;
             const bool per[3] = {(md.per & 1) != 0, (md.per & 2) != 0, (md.per & 4) != 0};
             const int dimP[3] = {md.NX, md.NY, md.NZ};
-            int c[3] = {0, 0, 0};   // coordinates of node n, kept by counters (no divisions)
-            for (int j = 0; j < ns; ++j) {
-                bool any = false, border = false;
-                for (int t = 0; t < 32; ++t) {
-                    const long long n = 32LL * j + t;
-                    if (n >= md.N) break;
-                    if (!(tag_all[base + n] & TAG_SOLID)) {
-                        any = true;
-                        int face = -1;
-                        bool wrap = false;
-                        for (int a = 0; a < 3; ++a) {
-                            if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) wrap = true;            // wrap plane
-                            if (!per[a] && face < 0 && c[a] == 1 && md.face_kind[2 * a] != FACE_HALO)
-                                face = 2 * a;                                                          // box faces
-                            if (!per[a] && face < 0 && c[a] == dimP[a] - 2 && md.face_kind[2 * a + 1] != FACE_HALO)
-                                face = 2 * a + 1;
+            // runs of segments scanned on host threads into lists of their
+            // own, joined in segment order (the same lists as one scan)
+            struct Part { std::vector<uint32_t> segs, bsegs, nodes, bnodes, fc_node, fc_meta; };
+            const size_t n_parts = std::min<size_t>(64, std::max<size_t>(1, (size_t)ns / 2048));
+            std::vector<Part> part(n_parts);
+            const size_t per_part = ((size_t)ns + n_parts - 1) / n_parts;
+            parallel_chunks(n_parts, 1, [&](size_t p0, size_t p1) {
+                for (size_t pi = p0; pi < p1; ++pi) {
+                    Part& P = part[pi];
+                    const int j0 = (int)std::min((size_t)ns, pi * per_part);
+                    const int j1 = (int)std::min((size_t)ns, (pi + 1) * per_part);
+                    const long long n0 = 32LL * j0;
+                    // coordinates of node n, kept by counters (no divisions)
+                    int c[3] = {(int)(n0 % md.NX), (int)((n0 / md.NX) % md.NY), (int)(n0 / ((long long)md.NX * md.NY))};
+                    for (int j = j0; j < j1; ++j) {
+                        bool any = false, border = false;
+                        for (int t = 0; t < 32; ++t) {
+                            const long long n = 32LL * j + t;
+                            if (n >= md.N) break;
+                            if (!(tag_all[base + n] & TAG_SOLID)) {
+                                any = true;
+                                int face = -1;
+                                bool wrap = false;
+                                for (int a = 0; a < 3; ++a) {
+                                    if (per[a] && (c[a] == 0 || c[a] == dimP[a] - 1)) wrap = true;    // wrap plane
+                                    if (!per[a] && face < 0 && c[a] == 1 && md.face_kind[2 * a] != FACE_HALO)
+                                        face = 2 * a;                                                  // box faces
+                                    if (!per[a] && face < 0 && c[a] == dimP[a] - 2 &&
+                                        md.face_kind[2 * a + 1] != FACE_HALO)
+                                        face = 2 * a + 1;
+                                }
+                                border = border || wrap;
+                                (wrap ? P.bnodes : P.nodes).push_back((uint32_t)n);
+                                if (face >= 0 &&
+                                    (md.face_kind[face] == FACE_VELOCITY || md.face_kind[face] == FACE_PRESSURE)) {
+                                    P.fc_node.push_back((uint32_t)n);
+                                    P.fc_meta.push_back((uint32_t)face | ((uint32_t)m << 8));
+                                }
+                            }
+                            if (++c[0] == md.NX) { c[0] = 0; if (++c[1] == md.NY) { c[1] = 0; ++c[2]; } }
                         }
-                        border = border || wrap;
-                        (wrap ? bnodes : nodes).push_back((uint32_t)n);
-                        if (face >= 0 && (md.face_kind[face] == FACE_VELOCITY || md.face_kind[face] == FACE_PRESSURE)) {
-                            fc_node.push_back((uint32_t)n);
-                            fc_meta.push_back((uint32_t)face | ((uint32_t)m << 8));
-                        }
+                        if (any) (border ? P.bsegs : P.segs).push_back((uint32_t)j);
                     }
-                    if (++c[0] == md.NX) { c[0] = 0; if (++c[1] == md.NY) { c[1] = 0; ++c[2]; } }
                 }
-                if (any) (border ? bsegs : segs).push_back((uint32_t)j);
+            });
+            for (const Part& P : part) {
+                segs.insert(segs.end(), P.segs.begin(), P.segs.end());
+                bsegs.insert(bsegs.end(), P.bsegs.begin(), P.bsegs.end());
+                nodes.insert(nodes.end(), P.nodes.begin(), P.nodes.end());
+                bnodes.insert(bnodes.end(), P.bnodes.begin(), P.bnodes.end());
+                fc_node.insert(fc_node.end(), P.fc_node.begin(), P.fc_node.end());
+                fc_meta.insert(fc_meta.end(), P.fc_meta.begin(), P.fc_meta.end());
             }
             // close the member's node lists on a whole group of 32
             for (auto* lst : {&nodes, &bnodes}) {
