@@ -234,8 +234,11 @@ __device__ __forceinline__ void for_shell_nodes(const MemberDev& d, const int lo
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
+// LIN_ONLY: every lattice of the context has no periodic axis and none is a
+// slab context's whole view, so only the constant-offset path is compiled,
+// in 48 registers with 5 resident blocks per SM instead of 80 and 3.
+template <typename T, bool LIN_ONLY>
+__global__ void __launch_bounds__(256, LIN_ONLY ? 5 : 3) k_shell(const MemberDev* __restrict__ mem, const T* __restrict__ f,
                                                uint8_t* __restrict__ tag,
                                                const uint32_t* __restrict__ status, const CapsuleDev* __restrict__ caps,
                                                const CapsuleSums* __restrict__ sums, float4* __restrict__ macro,
@@ -250,6 +253,10 @@ __global__ void __launch_bounds__(256, 3) k_shell(const MemberDev* __restrict__ 
     float r2_out, r2_in;
     if (!shell_box(d, sums[c], lo, ext, radial, r2_out, r2_in)) return;
     const float rcx = sums[c].rcf[0], rcy = sums[c].rcf[1], rcz = sums[c].rcf[2];
+    if (LIN_ONLY) {
+        shell_rows<T, true>(d, f + d.f_off, tag, macro, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, parity);
+        return;
+    }
     if (d.slab_view) {
         // the whole lattice of a slab context: each node's populations from the
         // slab that owns it (its neighbours are in that slab's ghost planes);
@@ -892,8 +899,14 @@ cudaError_t launch_geometry(const DevState& d, int, cudaStream_t s) { return lau
 
 template <typename T>
 static cudaError_t shell_t(const DevState& d, int parity, cudaStream_t s) {
-    k_shell<T><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.status, d.caps, d.sums,
-                                                       d.macro, parity, d.fib, d.slab_of, d.slab_tab);
+    bool lin = d.h_mem != nullptr;
+    for (int m = 0; lin && m < d.n_members; ++m) lin = d.h_mem[m].per == 0 && !d.h_mem[m].slab_view;
+    if (lin)
+        k_shell<T, true><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.status, d.caps,
+                                                                 d.sums, d.macro, parity, d.fib, d.slab_of, d.slab_tab);
+    else
+        k_shell<T, false><<<d.n_caps * SHELL_BLOCKS, 256, 0, s>>>(d.mem, (const T*)d.f, d.tag, d.status, d.caps,
+                                                                  d.sums, d.macro, parity, d.fib, d.slab_of, d.slab_tab);
     return cudaGetLastError();
 }
 
