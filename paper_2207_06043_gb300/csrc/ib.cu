@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_geom_vtx(const CapsuleDev* __restrict__
 // One warp per row (y, z) of a capsule's box, lanes along x over the part of
 // the row inside the outer sphere, less the part inside the inner one.
 template <typename T, bool LIN>
-__device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restrict__ fm, const uint8_t* __restrict__ tag,
+__device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restrict__ fm, uint8_t* __restrict__ tag,
                                            float4* __restrict__ macro,
                                            const int lo[3], const int ext[3], bool radial, float r2_out, float r2_in,
                                            float rcx, float rcy, float rcz, int parity) {
@@ -159,8 +159,11 @@ __device__ __forceinline__ void shell_rows(const MemberDev& d, const T* __restri
             // a solid node holds the wall's state, rho = 1 and u = 0, stored
             // with rho negated so that the marker stencils know not to spread
             // onto it without a tag gather; the populations' loads are issued
-            // beside the tag's, so they do not wait on it
+            // beside the tag's, so they do not wait on it.  A fluid node takes
+            // the IB flag: the marker stencils spread onto band nodes only,
+            // and the lattice step adds the node's f_ib and clears both
             const bool solid = tag[d.node_off + node] & TAG_SOLID;
+            if (!solid) tag[d.node_off + node] = TAG_IB;
             float g[Q];
             if (LIN) load_pre_lin<T>(d, fm, node, parity, g);
             else load_pre<T>(d, fm, node, X, Y, Z, parity, g);
@@ -260,8 +263,9 @@ __global__ void __launch_bounds__(256, LIN_ONLY ? 5 : 3) k_shell(const MemberDev
     if (d.slab_view) {
         // the whole lattice of a slab context: each node's populations from the
         // slab that owns it (its neighbours are in that slab's ghost planes);
-        // the node's IB force and flag of the previous step are cleared here,
-        // as the lattice kernel does for a lattice of its own
+        // the node's IB force of the previous step is cleared here, as the
+        // lattice kernel does for a lattice of its own, and a fluid node
+        // takes the IB flag
         for_shell_nodes(d, lo, ext, radial, r2_out, r2_in, rcx, rcy, rcz, [&](int x, int y, int z) {
             const long long nW = d.node_off + (x + d.px) + (long long)d.NX * ((y + d.py) + (long long)d.NY * (z + d.pz));
             const int s = slab_of[x];
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(256, LIN_ONLY ? 5 : 3) k_shell(const MemberDev
             moments_of(g, rho, ux, uy, uz);
             macro[nW] = solid ? make_float4(-1.f, 0.f, 0.f, 0.f) : make_float4(rho, ux, uy, uz);
             reinterpret_cast<float4*>(fib)[nW] = make_float4(0.f, 0.f, 0.f, 0.f);
-            tag[nW] = solid ? TAG_SOLID : 0;
+            tag[nW] = solid ? TAG_SOLID : TAG_IB;
         });
         return;
     }
@@ -389,7 +393,10 @@ k_ib_markers(const MemberDev* __restrict__ mem, uint8_t* __restrict__ tag, float
             const size_t gi = (size_t)d.node_off + mls_node_g(d, M, r + GL * j);
             // one vector reduction per support node (f_ib is padded to float4)
             atomicAdd(reinterpret_cast<float4*>(fib) + gi, make_float4(c * Fx, c * Fy, c * Fz, 0.f));
-            tag[gi] = TAG_IB;   // fluid node: its tag byte was 0 or TAG_IB
+            // the shell pass flagged the fluid nodes of the capsule's band; a
+            // block that leaves the box (its points clamped onto the box's
+            // faces) or wraps a periodic seam flags its nodes itself
+            if (M.base < 0) tag[gi] = TAG_IB;
         }
     }
     if (r == 0) {

@@ -93,8 +93,8 @@ __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy,
 // IB marker and probe stencils, four lanes per stencil, all on the fluid
 // solution at t (moments of the current populations from the shell pass):
 //  s = 0: Eq. uLag on u*, F_l = (U_b - U_l)/dt, Eq. bodyforce spreading with
-//         c_l = A_l into the dense f_ib field (float atomics) and the node's IB
-//         flag; u_v,0 = U_l (the tentative velocity of Eq. verletPos); the
+//         c_l = A_l into the dense f_ib field (float atomics; the shell pass
+//         flags the band's fluid nodes); u_v,0 = U_l (the tentative velocity of Eq. verletPos); the
 //         volume penalty k_v (1 - V/V0) A (Eq. volFor, restoring sign) of soft
 //         capsules (0 for rigid ones);
 //  s = 1, 2: the probe at x +- 1.2 n: p = rho/3 and tau = rho nu (grad u +
