@@ -104,6 +104,7 @@ __device__ __forceinline__ int support_index(const MemberDev& d, int cx, int cy,
 // flight), so that their latencies overlap.
 // ---------------------------------------------------------------------------
 constexpr int PROBE_STRIDE = 8;   // floats per probe record: p, tau xx yy zz xy xz yz, pad
+static_assert(PROBE_STRIDE == 8, "hydro_force reads each probe record as two float4");
 
 constexpr bool PROBE_FAST32 = true;   // (template argument kept by the callers; the closed form needs no FP64 redo)
 #ifndef IB_MARKER_THREADS
@@ -304,13 +305,14 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask) {
 __device__ __forceinline__ void hydro_force(const float* __restrict__ probe, const float* __restrict__ nrm,
                                             const float* __restrict__ area, int v, float& Hx, float& Hy,
                                             float& Hz) {
-    const float* a = probe + (size_t)2 * v * PROBE_STRIDE;
-    const float* b = a + PROBE_STRIDE;
+    // the two 32-byte records of the vertex (16-byte aligned) in four vector loads
+    const float4* r = reinterpret_cast<const float4*>(probe + (size_t)2 * v * PROBE_STRIDE);
+    const float4 a0 = r[0], a1 = r[1], b0 = r[2], b1 = r[3];
     const float nx = nrm[3 * v], ny = nrm[3 * v + 1], nz = nrm[3 * v + 2], A = area[v];
-    const float dp = a[0] - b[0];
-    const float t0 = a[1] - b[1], t1 = a[2] - b[2], t2 = a[3] - b[3], t3 = a[4] - b[4], t4 = a[5] - b[5],
-                t5 = a[6] - b[6];
-    const float kv = a[7];   // volume penalty k_v (1 - V/V0) A of soft capsules
+    const float dp = a0.x - b0.x;
+    const float t0 = a0.y - b0.y, t1 = a0.z - b0.z, t2 = a0.w - b0.w, t3 = a1.x - b1.x, t4 = a1.y - b1.y,
+                t5 = a1.z - b1.z;
+    const float kv = a1.w;   // volume penalty k_v (1 - V/V0) A of soft capsules
     Hx = (-dp * nx + t0 * nx + t3 * ny + t4 * nz) * A + kv * nx;
     Hy = (-dp * ny + t3 * nx + t1 * ny + t5 * nz) * A + kv * ny;
     Hz = (-dp * nz + t4 * nx + t5 * ny + t2 * nz) * A + kv * nz;
