@@ -118,11 +118,17 @@ __device__ __forceinline__ void face_node(const MemberDev* __restrict__ mem, T* 
     node_coords(d, n, X, Y, Z);
     T* fm = f + d.f_off;
     const int parity = 1 - pp;
-    float g[Q];
-    load_pre<T>(d, fm, n, X, Y, Z, parity, g);
     const int nx = fc == 0 ? -1 : (fc == 1 ? 1 : 0);
     const int ny = fc == 2 ? -1 : (fc == 3 ? 1 : 0);
     const int nz = fc == 4 ? -1 : (fc == 5 ? 1 : 0);
+    // the populations the rule reads: those not entering from outside
+    // (e.n >= 0); the entering ones it replaces without reading
+    float g[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+        g[k] = ex(k) * nx + ey(k) * ny + ez(k) * nz < 0
+                   ? 0.f
+                   : Store<T>::ld(fm + pre_slot(d, n, X, Y, Z, parity, k), d.ld_scale);
     if (tape_rho) {
         // rho of the face rule: (1 + Sg) / (1 + u.n) on a velocity face, the
         // imposed density on a pressure face
