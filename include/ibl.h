@@ -146,10 +146,12 @@ ibl_status ibl_add_capsule(ibl_ctx* ctx, const double* verts, int32_t nv,
 ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done);
 
 /* Macroscopic fields of member 0: rho[N], u[3N] (either may be NULL), with
- * rho u = sum f e + F_body/2; solid nodes read 0.  With host buffers the
- * values pass through a device staging buffer that the context allocates on
- * the first such read (cudaMalloc), keeps, and grows when a later read needs
- * more; ibl_destroy frees it. */
+ * rho u = sum f e + F_body/2; solid nodes read 0.  Host buffers that are
+ * page-locked (cudaHostAlloc / cudaMallocHost, or a pinned torch tensor) are
+ * written by the read kernel directly.  Other host buffers take the values
+ * through a device staging buffer that the context allocates on the first
+ * such read (cudaMalloc), keeps, and grows when a later read needs more;
+ * ibl_destroy frees it. */
 ibl_status ibl_read_fields(ibl_ctx* ctx, float* rho, float* u, int32_t on_device);
 
 /* Populations f_i - w_i of member 0 in FP32, layout [19][N], as they stand
@@ -306,8 +308,9 @@ ibl_status ibl_adjoint(ibl_ctx* ctx, int32_t n_steps, int32_t ckpt_every, const 
  * layout as ibl_member_read_fields with on_device = 0.  The paper has no
  * counterpart: this is a service entry for callers that may not allocate
  * device memory (a caching allocator owns the device, or the call runs in a
- * memory-capped phase).  ibl_read_fields with host buffers allocates device
- * staging buffers on every call; this one stages through a fixed static
+ * memory-capped phase).  ibl_read_fields with pageable host buffers
+ * allocates a device staging buffer on its first call; this one stages
+ * through a fixed static
  * device array of 4 * IBL_NOALLOC_MAX_NODES floats (16 MiB) built into the
  * library and calls no cudaMalloc / cudaFree.
  *   - Lattices of more than IBL_NOALLOC_MAX_NODES nodes are rejected with

@@ -1358,8 +1358,27 @@ ibl_status read_fields_member(ibl_ctx* ctx, int m, float* rho, float* u, float* 
     const size_t Nu = (size_t)md.nx * md.ny * md.nz;
     const int cnt = ctx->h_counters[m];
     const int parity = cnt & 1;
+    // page-locked host buffers that the device can address (every
+    // page-locked allocation, with unified addressing) take the read kernel's
+    // output directly: no staging buffer, no copy
+    auto mapped = [](void* p, void** dp) -> bool {
+        *dp = nullptr;
+        if (!p) return true;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        *dp = a.devicePointer;
+        return a.type == cudaMemoryTypeHost && a.devicePointer != nullptr;
+    };
+    void *mr = nullptr, *mu = nullptr, *mg = nullptr;
+    const bool direct = !on_device && mapped(rho, &mr) && mapped(u, &mu) && mapped(g, &mg);
     if (on_device) {
         CK(launch_read(ctx->dev, m, parity, rho, u, g, ctx->work));
+    } else if (direct) {
+        CK(launch_read(ctx->dev, m, parity, (float*)mr, (float*)mu, (float*)mg, ctx->work));
+        CK(cudaStreamSynchronize(ctx->work));
     } else {
         // one device staging buffer per context, allocated by the first host
         // read and grown when a larger one is needed

@@ -87,3 +87,26 @@ def test_device_capsule_diagnostics_match_the_host_ones():
             np.testing.assert_allclose(dev[k][key], host[key], rtol=1e-9, atol=1e-12, err_msg=key)
         # the device divides by the FP32 rest lengths that the damage rule uses
         np.testing.assert_allclose(dev[k]["max_stretch"], host["max_stretch"], rtol=1e-7, err_msg="max_stretch")
+
+
+def test_field_reads_into_pageable_pinned_and_device_buffers_agree():
+    """ibl_read_fields into pageable numpy arrays (staged through the
+    context's device buffer), into page-locked tensors (written by the read
+    kernel directly) and into device tensors: the same values bit for bit."""
+    import torch
+    c = case(G.bifurcation(40, 20, 16, 10.0, 30.0, 2.0))
+    s = gpu_for(c)
+    s.step(7)
+    r0, u0 = s.read_fields()
+    n = r0.shape[0]
+    rp = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    up = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+    s.read_fields(out=(rp, up))
+    rd = torch.empty(n, dtype=torch.float32, device="cuda")
+    ud = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    s.read_fields(out=(rd, ud))
+    assert np.array_equal(r0, rp.numpy()) and np.array_equal(u0, up.numpy())
+    assert np.array_equal(r0, rd.cpu().numpy()) and np.array_equal(u0, ud.cpu().numpy())
+    assert np.abs(u0).max() > 0
+    with pytest.raises(ValueError):
+        s.read_fields(out=(rp, ud))
