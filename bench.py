@@ -253,13 +253,14 @@ def cpu_baseline(case, steps, all_cores=True):
     return out
 
 
-def workload_config(case, storage, world, threads, blocks_per_sm):
+def workload_config(case, storage, world, threads, blocks_per_sm, staged=False):
     """The `config` object of the bench line for a throughput-family case."""
     return {"workload": case["name"], "fluid_nodes": fluid_updates(case), "box_nodes": case["geometry"].n_nodes,
             "capsules": len(case["capsules"]), "markers": sum(len(c["verts"]) for c in case["capsules"]),
             "storage": storage, "l2": "inputs larger than L2 (distributions ~1 GB)",
             "parallelism": "replicas" if world > 1 else "1 GPU",
-            "launch": {"threads": threads, "blocks_per_sm": blocks_per_sm}}
+            "launch": {"threads": threads, "blocks_per_sm": blocks_per_sm,
+                       "lattice_kernel": "staged (bulk copies)" if staged else "register gathers"}}
 
 
 def reference_arm(args, rank):
@@ -350,6 +351,8 @@ def main():
     ap.add_argument("--adjoint-ckpt", type=int, default=100)
     ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--staged", action="store_true",
+                    help="step the lattice with the staged (bulk-copy) kernel instead of the register-gather one")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -384,6 +387,7 @@ def main():
     nf = fluid_updates(case)
     s = W.make_solver(case, storage=args.storage)
     s.set_launch(args.threads, args.blocks_per_sm)
+    s.set_lattice_path(args.staged)
     s.step(args.warmup)
 
     # timed region, twice: in timing mode (CUDA events between the phases,
@@ -437,7 +441,7 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_best / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-           "config": workload_config(case, args.storage, world, args.threads, args.blocks_per_sm),
+           "config": workload_config(case, args.storage, world, args.threads, args.blocks_per_sm, args.staged),
            "roofline": roof,
            "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes,
                              "achieved": step_bytes / (ms_best / args.steps * 1e-3) / 1e9, "peak": peak,
@@ -455,7 +459,7 @@ def main():
     if rank == 0 and not args.no_adjoint:
         out["adjoint"] = adjoint_measure(args, case)
     if rank == 0 and not args.no_variants and args.storage == "f32":
-        out["storage_variants"] = storage_variants(case, nf)
+        out["storage_variants"] = storage_variants(case, nf, staged=args.staged)
     if rank == 0 and not args.no_sweep:
         out["sweep"] = sweep_measure(args.sweep_members, args.sweep_steps, local, dist)
     if rank == 0 and not args.no_slabs:
@@ -542,7 +546,7 @@ def sweep_measure(n_members, steps, local, dist):
     return sweep_run(members, steps, max(3, steps // 10), local, dist)
 
 
-def storage_variants(case, nf, steps=100):
+def storage_variants(case, nf, steps=100, staged=False):
     """The same workload with f - w stored as FP16 (scaled by 2^12) or BF16,
     FP32 arithmetic: whole-step MLUPS (graph replay) and the lattice kernel's
     fraction of the HBM roofline at 76 B per fluid-node update."""
@@ -553,6 +557,7 @@ def storage_variants(case, nf, steps=100):
     stream = torch.cuda.current_stream()
     for st in ("f16", "bf16"):
         s = W.make_solver(case, storage=st)
+        s.set_lattice_path(staged)
         s.step(5)
         s.enable_timing(True)
         s.step(steps)
@@ -891,6 +896,7 @@ def e2e_run(case, args, chunk=10):
     t0 = time.perf_counter()
     s = W.make_solver(case, storage=args.storage)
     s.set_launch(args.threads, args.blocks_per_sm)
+    s.set_lattice_path(args.staged)
     s.step(0)                               # set-up: uploads, work lists, initial state
     torch.cuda.synchronize()
     t1 = time.perf_counter()

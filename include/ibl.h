@@ -54,7 +54,7 @@ typedef enum {
     IBL_ERR_CUDA = -3,       /* a CUDA runtime call failed                      */
     IBL_ERR_DAMAGED = -4,    /* a capsule edge reached twice its rest length   */
     IBL_ERR_NONFINITE = -5,  /* a vertex position became NaN/Inf               */
-    IBL_ERR_TIMEOUT = -6,    /* reserved: a bounded device wait gave up        */
+    IBL_ERR_TIMEOUT = -6,    /* a bounded device wait gave up (staged step)    */
     IBL_ERR_STATE = -7       /* call not allowed in the context's current state */
 } ibl_status;
 
@@ -142,7 +142,8 @@ ibl_status ibl_add_capsule(ibl_ctx* ctx, const double* verts, int32_t nv,
 /* Advance n_steps time steps.  steps_done (may be NULL) receives the steps
  * member 0 completed.  Returns IBL_ERR_DAMAGED when a capsule broke (the state
  * stays readable and the damaged lattice stops stepping), IBL_ERR_NONFINITE
- * when a vertex left the finite range. */
+ * when a vertex left the finite range, IBL_ERR_TIMEOUT when a wait of the
+ * staged lattice kernel gave up (see ibl_set_lattice_path). */
 ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done);
 
 /* Macroscopic fields of member 0: rho[N], u[3N] (either may be NULL), with
@@ -193,6 +194,28 @@ ibl_status ibl_member_steps(const ibl_ctx* ctx, int32_t member, int32_t* steps_d
  * fluid nodes) and blocks per SM of a persistent grid (0 = one block per
  * threads/32 groups).  Used by the autotuner; takes effect at the next step. */
 ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm);
+
+/* Which form of the lattice step (Eq. evoleq with Eqs. eqfunc and forcing:
+ * BGK collision and AA-pattern stream) runs over the interior fluid nodes.
+ * staged = 0 (the default): the register-gather kernel, every lane loading
+ * its node's 19 populations.  staged = 1: in a context holding ONE lattice,
+ * every run of consecutive interior fluid nodes is cut into chunks of at
+ * most 128 nodes, and each chunk's populations and tags are fetched into
+ * shared memory by bulk copies (one per population span, 16-byte aligned)
+ * several chunks ahead of its collision; wrap-plane nodes, batched contexts
+ * and steps that record an adjoint tape keep the register kernel.  Both
+ * compute the same values in the same order (bit-identical populations).
+ * The staged form is measured slower on GB300 (0.26 against 0.12 ms on the
+ * 512x192x128 duct with 64 capsules) and is kept as an alternative.
+ * Takes effect at the next step.  IBL_ERR_ARG unless staged is 0 or 1.  A
+ * staged step whose bounded wait for a copy gives up (about one second)
+ * makes ibl_step return IBL_ERR_TIMEOUT. */
+ibl_status ibl_set_lattice_path(ibl_ctx* ctx, int32_t staged);
+
+/* The form the next regular step of a set-up context uses: 1 staged, 0
+ * register gathers, -1 when the context is not set up yet (no step, read
+ * or save has run). */
+int32_t ibl_lattice_path(const ibl_ctx* ctx);
 
 /* Autotuner of the lattice kernel's launch shape: times `steps` steps of the
  * context for each block size (32, 64, 128 threads) and persistent-grid

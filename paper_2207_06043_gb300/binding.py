@@ -94,6 +94,8 @@ def lib():
         "ibl_member_steps": ([vp, i32, P(i32)], i32),
         "ibl_read_fields_noalloc": ([vp, i32, vp, vp], i32),
         "ibl_set_launch": ([vp, i32, i32], i32),
+        "ibl_set_lattice_path": ([vp, i32], i32),
+        "ibl_lattice_path": ([vp], i32),
         "ibl_enable_timing": ([vp, i32], i32),
         "ibl_kernels_per_step": ([vp, P(i32)], i32),
         "ibl_save_state": ([vp, vp, P(sz)], i32),
@@ -284,6 +286,16 @@ class Solver:
 
     def set_launch(self, threads, blocks_per_sm=0):
         self._check(self._L.ibl_set_launch(self._h, int(threads), int(blocks_per_sm)))
+
+    def set_lattice_path(self, staged=True):
+        """Staged (bulk-copy) lattice kernel where the context allows it, or
+        the register-gather kernel everywhere."""
+        self._check(self._L.ibl_set_lattice_path(self._h, 1 if staged else 0))
+
+    def lattice_path(self):
+        """1 when the next regular step runs the staged lattice kernel, 0 for
+        register gathers, -1 before the context is set up."""
+        return int(self._L.ibl_lattice_path(self._h))
 
     def enable_timing(self, on=True):
         self._check(self._L.ibl_enable_timing(self._h, 1 if on else 0))

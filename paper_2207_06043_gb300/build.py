@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libibl.so")
-SOURCES = ["lbm.cu", "bfl.cu", "ib.cu", "adjoint.cu", "adjoint_ib.cu", "walls.cu", "halo.cu", "api.cu"]
+SOURCES = ["lbm.cu", "lbm_bulk.cu", "bfl.cu", "ib.cu", "adjoint.cu", "adjoint_ib.cu", "walls.cu", "halo.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

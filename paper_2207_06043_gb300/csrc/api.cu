@@ -79,6 +79,7 @@ struct ibl_ctx {
     bool use_graphs = true;
     int threads = 128;   // lattice kernel block size (the compiled bound)
     int blocks_per_sm = 0;
+    int lattice_path = 0;   // 1: staged lattice kernel where available, 0: register gathers
     int n_sm = 0;
     int device = -1;                   // CUDA device current when the context was created
     float* noalloc = nullptr;          // that device's copy of the static read array
@@ -1031,6 +1032,21 @@ ibl_status finalize(ibl_ctx* ctx) {
     CKS(dev_alloc(ctx, D.bnodes, std::max<size_t>(bnodes.size(), 1)));
     CKS(upload(ctx, D.nodes, nodes));
     CKS(upload(ctx, D.bnodes, bnodes));
+    // chunks of the staged lattice kernel (one lattice): every run of
+    // consecutive interior fluid nodes cut into pieces of at most
+    // lbm_chunk_nodes() nodes
+    if (nm == 1 && D.n_groups > 0) {
+        std::vector<uint2> ch;
+        const uint32_t cap = (uint32_t)lbm_chunk_nodes();
+        for (size_t i = 0; i < nodes.size() && nodes[i] != NO_NODE; ++i) {
+            const uint32_t n = nodes[i];
+            if (ch.empty() || n != ch.back().x + ch.back().y || ch.back().y == cap) ch.push_back(make_uint2(n, 1u));
+            else ch.back().y += 1;
+        }
+        D.n_chunks = (int)ch.size();
+        CKS(dev_alloc(ctx, D.chunks, ch.size()));
+        CKS(upload(ctx, D.chunks, ch));
+    }
     if (nm > 1) {
         CKS(dev_alloc(ctx, D.group_mem, std::max<size_t>(group_mem.size(), 1)));
         CKS(dev_alloc(ctx, D.bgroup_mem, std::max<size_t>(bgroup_mem.size(), 1)));
@@ -1202,6 +1218,14 @@ ibl_status finalize(ibl_ctx* ctx) {
         if (drho) cudaFree(drho);
         if (du) cudaFree(du);
     }
+    // staged lattice kernel: its shared-memory attribute and residency
+    D.lattice_path = ctx->lattice_path;
+    D.bulk_blocks_per_sm = 0;
+    if (D.chunks && lbm_bulk_layout_ok(D)) {
+        int nb = 0;
+        CK(lbm_bulk_prepare(D.storage, nb));
+        D.bulk_blocks_per_sm = nb;
+    }
     ctx->h_counters.assign(nm, 0);
     ctx->h_status.assign(nm, 0);
     CK(cudaStreamSynchronize(ctx->work));
@@ -1296,7 +1320,17 @@ ibl_status enqueue_step(ibl_ctx* ctx, int parity, std::vector<Mark>* marks, cons
         CK(launch_update(D, s2));
     }
     CKS(begin(s));
-    CK(launch_lbm(D, parity, s, tp ? tp->rhou : nullptr, tp ? tp->F : nullptr));
+    if (!tp && D.lattice_path == 1 && D.chunks && D.bulk_blocks_per_sm > 0) {
+        // staged kernel over the interior chunks, the register kernel over
+        // the wrap-plane nodes only
+        CK(launch_lbm_bulk(D, parity, s));
+        DevState Db = D;
+        Db.lbm_blocks = 0;
+        Db.grid_lbm = 0;
+        CK(launch_lbm(Db, parity, s));
+    } else {
+        CK(launch_lbm(D, parity, s, tp ? tp->rhou : nullptr, tp ? tp->F : nullptr));
+    }
     CKS(end(TK_LBM, s));
     CKS(begin(s));
     CK(launch_walls(D, parity, s, tp ? tp->dvdq : nullptr, tp ? tp->rho : nullptr));
@@ -1698,6 +1732,7 @@ ibl_status ibl_step(ibl_ctx* ctx, int32_t n_steps, int32_t* steps_done) {
     if (any & ST_NONFINITE) return fail(ctx, IBL_ERR_NONFINITE, "a capsule vertex became non-finite");
     if (any & ST_DAMAGED) return fail(ctx, IBL_ERR_DAMAGED, "a capsule edge reached twice its rest length");
     if (any & ST_OVERFLOW) return fail(ctx, IBL_ERR_ARG, "repulsion cell list overflow (markers too dense)");
+    if (any & ST_TIMEOUT) return fail(ctx, IBL_ERR_TIMEOUT, "a bounded wait of the staged lattice kernel gave up");
     return IBL_OK;
 }
 
@@ -2431,6 +2466,24 @@ ibl_status ibl_set_launch(ibl_ctx* ctx, int32_t threads, int32_t blocks_per_sm) 
         drop_graphs(ctx);
     }
     return IBL_OK;
+}
+
+ibl_status ibl_set_lattice_path(ibl_ctx* ctx, int32_t staged) {
+    if (!ctx) return fail(nullptr, IBL_ERR_ARG, "null context");
+    if (staged != 0 && staged != 1) return fail(ctx, IBL_ERR_ARG, "staged must be 0 or 1");
+    ctx->lattice_path = staged;
+    if (ctx->finalized) {
+        CK(cudaStreamSynchronize(ctx->work));
+        ctx->dev.lattice_path = staged;
+        drop_graphs(ctx);
+    }
+    return IBL_OK;
+}
+
+int32_t ibl_lattice_path(const ibl_ctx* ctx) {
+    if (!ctx || !ctx->finalized) return -1;
+    const DevState& D = ctx->dev;
+    return (D.lattice_path == 1 && D.chunks && D.bulk_blocks_per_sm > 0) ? 1 : 0;
 }
 
 ibl_status ibl_autotune(ibl_ctx* ctx, int32_t steps, int32_t* threads_out, int32_t* blocks_per_sm_out,

@@ -39,7 +39,8 @@ constexpr uint32_t LINK_AT_FACE = 128u;   // l_meta flag: the link starts on a Z
 constexpr int MAX_MEMBERS = 128;
 
 enum : uint8_t { TAG_SOLID = 1, TAG_IB = 2 };
-enum : uint32_t { ST_DAMAGED = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4 };
+enum : uint32_t { ST_DAMAGED = 1, ST_NONFINITE = 2, ST_OVERFLOW = 4,
+                  ST_TIMEOUT = 8 };   // a bounded device wait gave up
 enum { FACE_NONE = 0, FACE_VELOCITY = 1, FACE_PRESSURE = 2,
        FACE_HALO = 3 };   // a cut face of a slab member: its planes are copied from their owner
 
@@ -140,6 +141,14 @@ struct DevState {
     int* group_mem = nullptr;        // member of each group (batched contexts; null with one member)
     int* bgroup_mem = nullptr;
     int lbm_blocks = 0, lbm_bblocks = 0;   // ceil(groups / (threads / 32))
+    // staged lattice kernel (single-lattice contexts): the interior fluid
+    // nodes as chunks (first node, nodes) of consecutive nodes, at most
+    // lbm_chunk_nodes() each; resident blocks per SM of that kernel (0: not
+    // available)
+    int n_chunks = 0;
+    uint2* chunks = nullptr;
+    int bulk_blocks_per_sm = 0;
+    int lattice_path = 0;            // 1: staged kernel where available, 0: register gathers
     int grid_lbm = 0;                // persistent grid of the interior kernel (0: default)
     int n_sm = 0;                    // multiprocessors of the device
 
@@ -215,6 +224,13 @@ constexpr int NEAR_STRIDE = 1 + 3 * NEAR_CAP;   // int4 entries: the count, then
 cudaError_t launch_lbm(const DevState& d, int parity, cudaStream_t s, float4* tape_rhou = nullptr,
                        float4* tape_F = nullptr);
 int lbm_max_threads();   // block-size bound the lattice kernel was compiled for
+// the staged lattice kernel (lbm_bulk.cu): whether the context's layout
+// allows it, its set-up (shared-memory attribute; resident blocks per SM) and
+// its launch over the interior groups of a single lattice
+bool lbm_bulk_layout_ok(const DevState& d);
+cudaError_t lbm_bulk_prepare(int storage, int& blocks_per_sm);
+int lbm_chunk_nodes();
+cudaError_t launch_lbm_bulk(const DevState& d, int parity, cudaStream_t s);
 // the wall fill (Eq. bbouzidi) and the Zou-He faces (Eq. extbound) of the
 // step just done, in one launch
 cudaError_t launch_walls(const DevState& d, int parity_done, cudaStream_t s, float* tape_dvdq = nullptr,
