@@ -589,25 +589,37 @@ ibl_status validate_member(ibl_ctx* ctx, const MemberHost& M) {
     const long long N = (long long)d.nx * d.ny * d.nz;
     if ((long long)M.tag.size() != N) return fail(ctx, IBL_ERR_STATE, "geometry not set");
     const int dims[3] = {d.nx, d.ny, d.nz};
-    long long n = 0;   // x fastest, coordinates kept by the loops (no divisions)
+    // only nodes on a non-periodic box face can break the rule: every row
+    // (fixed y, z) on a y or z face is scanned whole, every other row at its
+    // two x ends, in node order (the first bad node is the one reported)
+    auto check = [&](int x, int y, int z) -> ibl_status {
+        const long long n = x + (long long)d.nx * (y + (long long)d.ny * z);
+        if (M.tag[n] != 0) return IBL_OK;
+        const int c[3] = {x, y, z};
+        int nf = 0, face = -1;
+        for (int a = 0; a < 3; ++a) {
+            if (d.periodic[a]) continue;
+            if (c[a] == 0 && M.face_kind[2 * a] != FACE_HALO) { ++nf; face = 2 * a; }
+            if (c[a] == dims[a] - 1 && M.face_kind[2 * a + 1] != FACE_HALO) { ++nf; face = 2 * a + 1; }
+        }
+        if (nf > 1)
+            return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on an edge of the box (two faces)");
+        if (nf == 1 && M.face_kind[face] == IBL_FACE_NONE)
+            return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on face " + std::to_string(face) +
+                                              " which has no velocity or pressure condition");
+        return IBL_OK;
+    };
     for (int z = 0; z < d.nz; ++z)
-        for (int y = 0; y < d.ny; ++y)
-            for (int x = 0; x < d.nx; ++x, ++n) {
-                if (M.tag[n] != 0) continue;
-                const int c[3] = {x, y, z};
-                int nf = 0, face = -1;
-                for (int a = 0; a < 3; ++a) {
-                    if (d.periodic[a]) continue;
-                    if (c[a] == 0 && M.face_kind[2 * a] != FACE_HALO) { ++nf; face = 2 * a; }
-                    if (c[a] == dims[a] - 1 && M.face_kind[2 * a + 1] != FACE_HALO) { ++nf; face = 2 * a + 1; }
-                }
-                if (nf > 1)
-                    return fail(ctx, IBL_ERR_ARG,
-                                "fluid node " + std::to_string(n) + " lies on an edge of the box (two faces)");
-                if (nf == 1 && M.face_kind[face] == IBL_FACE_NONE)
-                    return fail(ctx, IBL_ERR_ARG, "fluid node " + std::to_string(n) + " lies on face " +
-                                                      std::to_string(face) + " which has no velocity or pressure condition");
+        for (int y = 0; y < d.ny; ++y) {
+            const bool row_on_face = (!d.periodic[1] && (y == 0 || y == d.ny - 1)) ||
+                                     (!d.periodic[2] && (z == 0 || z == d.nz - 1));
+            if (row_on_face) {
+                for (int x = 0; x < d.nx; ++x) CKS(check(x, y, z));
+            } else if (!d.periodic[0]) {
+                CKS(check(0, y, z));
+                if (d.nx > 1) CKS(check(d.nx - 1, y, z));
             }
+        }
     return IBL_OK;
 }
 
@@ -646,6 +658,38 @@ ibl_status noalloc_scratch(ibl_ctx* ctx, int dev, float** out) {
         g_noalloc_ptr[dev] = (float*)p;
     }
     *out = g_noalloc_ptr[dev];
+    return IBL_OK;
+}
+
+// Chunks of the staged lattice kernel (a context of one lattice): every run
+// of consecutive interior fluid nodes of the work list cut into pieces of at
+// most lbm_chunk_nodes() nodes.  Built when that kernel is first asked for.
+ibl_status build_chunks(ibl_ctx* ctx, const std::vector<uint32_t>& nodes) {
+    DevState& D = ctx->dev;
+    if (ctx->members.size() != 1 || D.n_groups == 0 || D.chunks) return IBL_OK;
+    std::vector<uint2> ch;
+    const uint32_t cap = (uint32_t)lbm_chunk_nodes();
+    for (size_t i = 0; i < nodes.size() && nodes[i] != NO_NODE; ++i) {
+        const uint32_t n = nodes[i];
+        if (ch.empty() || n != ch.back().x + ch.back().y || ch.back().y == cap) ch.push_back(make_uint2(n, 1u));
+        else ch.back().y += 1;
+    }
+    D.n_chunks = (int)ch.size();
+    CKS(dev_alloc(ctx, D.chunks, ch.size()));
+    CKS(upload(ctx, D.chunks, ch));
+    return IBL_OK;
+}
+
+// the staged kernel's shared-memory attribute and residency (0 blocks: the
+// layout does not allow it and the register kernel runs)
+ibl_status prepare_staged(ibl_ctx* ctx) {
+    DevState& D = ctx->dev;
+    D.bulk_blocks_per_sm = 0;
+    if (D.chunks && lbm_bulk_layout_ok(D)) {
+        int nb = 0;
+        CK(lbm_bulk_prepare(D.storage, nb));
+        D.bulk_blocks_per_sm = nb;
+    }
     return IBL_OK;
 }
 
@@ -779,27 +823,67 @@ ibl_status finalize(ibl_ctx* ctx) {
                                                   (bad[li] == 1 ? " out of range"
                                                    : bad[li] == 2 ? " starts at a solid node"
                                                                   : " does not end at a solid node inside the box"));
-        // (direction, node) order: a stable counting sort by direction, then
-        // each direction's run sorted by node unless it already is
-        std::vector<LinkRec> recs(nl);
+        // (direction, node) order: a stable counting sort by direction over
+        // fixed pieces of the list (per-piece counts, then each piece scattered
+        // by a host thread to its offsets in the member's part of the link
+        // arrays), then each direction's run sorted by node unless it already is
         {
-            size_t cnt[20] = {0};
-            for (const LinkRec& r : made) ++cnt[(r.meta & 31u) + 1];
-            for (int k = 1; k < 20; ++k) cnt[k] += cnt[k - 1];
-            size_t at[19];
-            for (int k = 0; k < 19; ++k) at[k] = cnt[k];
-            for (const LinkRec& r : made) recs[at[r.meta & 31u]++] = r;
-            for (int k = 1; k < 19; ++k) {
-                auto b = recs.begin() + cnt[k], e = recs.begin() + cnt[k + 1];
-                if (!std::is_sorted(b, e, [](const LinkRec& x, const LinkRec& y) { return x.node < y.node; }))
-                    std::sort(b, e, [](const LinkRec& x, const LinkRec& y) { return x.node < y.node; });
+            const size_t P = std::max<size_t>(1, std::min<size_t>(64, nl / 65536));
+            const size_t step = (nl + P - 1) / P;
+            std::vector<size_t> cnt(P * 20, 0);
+            parallel_chunks(P, 1, [&](size_t p0, size_t p1) {
+                for (size_t pi = p0; pi < p1; ++pi)
+                    for (size_t li = pi * step; li < std::min(nl, (pi + 1) * step); ++li)
+                        ++cnt[pi * 20 + (made[li].meta & 31u)];
+            });
+            // start of every (direction, piece) block: directions outer, pieces inner
+            std::vector<size_t> at(P * 20, 0), dir_begin(20, 0);
+            size_t run = 0;
+            for (int k = 0; k < 20; ++k) {
+                dir_begin[k] = run;
+                for (size_t pi = 0; pi < P; ++pi) {
+                    at[pi * 20 + k] = run;
+                    run += cnt[pi * 20 + k];
+                }
             }
-        }
-        for (const LinkRec& r : recs) {
-            l_node.push_back(r.node);
-            l_meta.push_back(r.meta);
-            l_q.push_back(r.q);
-            l_dq.push_back(r.dq);
+            const size_t o = l_node.size();
+            l_node.resize(o + nl);
+            l_meta.resize(o + nl);
+            l_q.resize(o + nl);
+            l_dq.resize(o + nl);
+            parallel_chunks(P, 1, [&](size_t p0, size_t p1) {
+                for (size_t pi = p0; pi < p1; ++pi) {
+                    size_t* pos = &at[pi * 20];
+                    for (size_t li = pi * step; li < std::min(nl, (pi + 1) * step); ++li) {
+                        const LinkRec& r = made[li];
+                        const size_t j = o + pos[r.meta & 31u]++;
+                        l_node[j] = r.node;
+                        l_meta[j] = r.meta;
+                        l_q[j] = r.q;
+                        l_dq[j] = r.dq;
+                    }
+                }
+            });
+            parallel_chunks(19, 1, [&](size_t k0, size_t k1) {
+                for (size_t k = std::max<size_t>(k0, 1); k < k1; ++k) {
+                    const size_t b = o + dir_begin[k], e = o + dir_begin[k + 1];
+                    bool sorted = true;
+                    for (size_t j = b + 1; j < e && sorted; ++j) sorted = l_node[j - 1] <= l_node[j];
+                    if (sorted) continue;
+                    std::vector<size_t> idx(e - b);
+                    for (size_t j = 0; j < idx.size(); ++j) idx[j] = b + j;
+                    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return l_node[x] < l_node[y]; });
+                    std::vector<uint32_t> nn(idx.size()), mm(idx.size());
+                    std::vector<float> qq(idx.size()), dd(idx.size());
+                    for (size_t j = 0; j < idx.size(); ++j) {
+                        nn[j] = l_node[idx[j]]; mm[j] = l_meta[idx[j]]; qq[j] = l_q[idx[j]]; dd[j] = l_dq[idx[j]];
+                    }
+                    std::copy(nn.begin(), nn.end(), l_node.begin() + b);
+                    std::copy(mm.begin(), mm.end(), l_meta.begin() + b);
+                    std::copy(qq.begin(), qq.end(), l_q.begin() + b);
+                    std::copy(dd.begin(), dd.end(), l_dq.begin() + b);
+                }
+            });
         }
         md.link_count = (int)M.links.size();
         link_off += md.link_count;
@@ -1032,21 +1116,8 @@ ibl_status finalize(ibl_ctx* ctx) {
     CKS(dev_alloc(ctx, D.bnodes, std::max<size_t>(bnodes.size(), 1)));
     CKS(upload(ctx, D.nodes, nodes));
     CKS(upload(ctx, D.bnodes, bnodes));
-    // chunks of the staged lattice kernel (one lattice): every run of
-    // consecutive interior fluid nodes cut into pieces of at most
-    // lbm_chunk_nodes() nodes
-    if (nm == 1 && D.n_groups > 0) {
-        std::vector<uint2> ch;
-        const uint32_t cap = (uint32_t)lbm_chunk_nodes();
-        for (size_t i = 0; i < nodes.size() && nodes[i] != NO_NODE; ++i) {
-            const uint32_t n = nodes[i];
-            if (ch.empty() || n != ch.back().x + ch.back().y || ch.back().y == cap) ch.push_back(make_uint2(n, 1u));
-            else ch.back().y += 1;
-        }
-        D.n_chunks = (int)ch.size();
-        CKS(dev_alloc(ctx, D.chunks, ch.size()));
-        CKS(upload(ctx, D.chunks, ch));
-    }
+    // the staged lattice kernel's chunks, when that kernel is asked for
+    if (ctx->lattice_path == 1) CKS(build_chunks(ctx, nodes));
     if (nm > 1) {
         CKS(dev_alloc(ctx, D.group_mem, std::max<size_t>(group_mem.size(), 1)));
         CKS(dev_alloc(ctx, D.bgroup_mem, std::max<size_t>(bgroup_mem.size(), 1)));
@@ -1056,14 +1127,25 @@ ibl_status finalize(ibl_ctx* ctx) {
     // the wall links that start on a Zou-He face node: taken by that node's
     // thread of the walls kernel, before its face rule
     {
-        std::map<uint64_t, int> face_at;
-        for (size_t i = 0; i < fc_node.size(); ++i)
-            face_at[((uint64_t)(fc_meta[i] >> 8) << 32) | fc_node[i]] = (int)i;
+        // face nodes of each member: a bit per padded node (the members'
+        // node ranges are disjoint in node_off), then the face node's index by
+        // binary search in its member's ascending part of the face list
+        std::vector<uint64_t> is_face(((size_t)node_off + 63) / 64, 0);
+        std::vector<size_t> fc_begin(nm + 1, fc_node.size());
+        for (size_t i = fc_node.size(); i-- > 0;) fc_begin[fc_meta[i] >> 8] = i;
+        for (int m = nm - 1; m >= 0; --m) fc_begin[m] = std::min(fc_begin[m], fc_begin[m + 1]);
+        for (size_t i = 0; i < fc_node.size(); ++i) {
+            const size_t g = (size_t)ctx->hmem[fc_meta[i] >> 8].node_off + fc_node[i];
+            is_face[g >> 6] |= 1ull << (g & 63);
+        }
         std::vector<std::vector<int>> per(fc_node.size());
         for (size_t l = 0; l < l_node.size(); ++l) {
-            const auto it = face_at.find(((uint64_t)(l_meta[l] >> 8) << 32) | l_node[l]);
-            if (it == face_at.end()) continue;
-            per[it->second].push_back((int)l);
+            const int m = (int)(l_meta[l] >> 8);
+            const size_t g = (size_t)ctx->hmem[m].node_off + l_node[l];
+            if (!((is_face[g >> 6] >> (g & 63)) & 1ull)) continue;
+            const auto b = fc_node.begin() + fc_begin[m], e = fc_node.begin() + fc_begin[m + 1];
+            const auto it = std::lower_bound(b, e, l_node[l]);
+            per[it - fc_node.begin()].push_back((int)l);
             l_meta[l] |= LINK_AT_FACE;
         }
         std::vector<int> lbeg(fc_node.size() + 1, 0), links;
@@ -1218,14 +1300,8 @@ ibl_status finalize(ibl_ctx* ctx) {
         if (drho) cudaFree(drho);
         if (du) cudaFree(du);
     }
-    // staged lattice kernel: its shared-memory attribute and residency
     D.lattice_path = ctx->lattice_path;
-    D.bulk_blocks_per_sm = 0;
-    if (D.chunks && lbm_bulk_layout_ok(D)) {
-        int nb = 0;
-        CK(lbm_bulk_prepare(D.storage, nb));
-        D.bulk_blocks_per_sm = nb;
-    }
+    if (D.chunks) CKS(prepare_staged(ctx));
     ctx->h_counters.assign(nm, 0);
     ctx->h_status.assign(nm, 0);
     CK(cudaStreamSynchronize(ctx->work));
@@ -1629,8 +1705,17 @@ ibl_status ibl_set_geometry(ibl_ctx* ctx, const uint8_t* cell_tag, const ibl_wal
     MemberHost& M = ctx->members[0];
     const size_t N = M.tag.size();
     if (!cell_tag || (n_links && !links)) return fail(ctx, IBL_ERR_ARG, "null geometry array");
-    for (size_t n = 0; n < N; ++n)
-        if (cell_tag[n] > 1) return fail(ctx, IBL_ERR_ARG, "cell_tag values must be 0 (fluid) or 1 (solid)");
+    {
+        // eight tags per word: any bit but the lowest of a byte is set
+        size_t n = 0;
+        for (; n + 8 <= N; n += 8) {
+            uint64_t w;
+            std::memcpy(&w, cell_tag + n, 8);
+            if (w & 0xfefefefefefefefeull) break;
+        }
+        for (; n < N; ++n)
+            if (cell_tag[n] > 1) return fail(ctx, IBL_ERR_ARG, "cell_tag values must be 0 (fluid) or 1 (solid)");
+    }
     M.tag.assign(cell_tag, cell_tag + N);
     M.links.assign(links, links + n_links);
     return IBL_OK;
@@ -2474,7 +2559,16 @@ ibl_status ibl_set_lattice_path(ibl_ctx* ctx, int32_t staged) {
     ctx->lattice_path = staged;
     if (ctx->finalized) {
         CK(cudaStreamSynchronize(ctx->work));
-        ctx->dev.lattice_path = staged;
+        DevState& D = ctx->dev;
+        if (staged && !D.chunks && ctx->members.size() == 1 && D.n_groups > 0) {
+            // the chunks come from the interior work list on the device
+            std::vector<uint32_t> nodes((size_t)D.n_groups * 32);
+            CK(cudaMemcpy(nodes.data(), D.nodes, nodes.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            CKS(build_chunks(ctx, nodes));
+            CK(cudaStreamSynchronize(ctx->work));
+            CKS(prepare_staged(ctx));
+        }
+        D.lattice_path = staged;
         drop_graphs(ctx);
     }
     return IBL_OK;
