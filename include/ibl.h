@@ -134,7 +134,10 @@ ibl_status ibl_set_outlet_pressure(ibl_ctx* ctx, int32_t face, double rho_out);
 ibl_status ibl_init_equilibrium(ibl_ctx* ctx, const float* rho, const float* u);
 
 /* Add a closed triangular mesh (verts[3*nv] FP64, tris[3*nt] outward CCW)
- * whose vertices are the Lagrangian markers.  vel0[3] may be NULL. */
+ * whose vertices are the Lagrangian markers.  vel0[3] may be NULL.
+ * IBL_ERR_ARG here for a vertex index out of range or repeated within a
+ * triangle; a mesh that is not closed or not consistently oriented is
+ * reported (IBL_ERR_ARG, naming the capsule) when the context is set up. */
 ibl_status ibl_add_capsule(ibl_ctx* ctx, const double* verts, int32_t nv,
                            const int32_t* tris, int32_t nt, const double* vel0,
                            const ibl_capsule_params* params, int32_t* id_out);

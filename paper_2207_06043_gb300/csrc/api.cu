@@ -909,13 +909,13 @@ ibl_status finalize(ibl_ctx* ctx) {
                 CapPre& P = pre[ci];
                 const int nv = (int)ch.X.size() / 3, nt = (int)ch.tris.size() / 3;
                 if (!build_hinges(ch.tris, nv, P.hinge, P.ta, P.tb, P.why)) {
-                    P.why = "capsule mesh: " + P.why;
+                    P.why = "capsule " + std::to_string(ci) + " mesh: " + P.why;
                     continue;
                 }
                 const double* X = ch.X.data();
                 P.ms = mesh_sums(X, nv, ch.tris.data(), nt);
                 if (!(P.ms.V > 0)) {
-                    P.why = "capsule mesh encloses no volume (triangles must be outward CCW)";
+                    P.why = "capsule " + std::to_string(ci) + " mesh encloses no volume (triangles must be outward CCW)";
                     continue;
                 }
                 std::vector<double> tri_area(nt);
@@ -1772,9 +1772,13 @@ ibl_status ibl_add_capsule(ibl_ctx* ctx, const double* verts, int32_t nv, const 
     ch.tris.assign(tris, tris + 3 * (size_t)nt);
     if (vel0) for (int a = 0; a < 3; ++a) ch.vel0[a] = vel0[a];
     ch.p = *params;
-    std::vector<int> h, ta, tb;
-    std::string why;
-    if (!build_hinges(ch.tris, nv, h, ta, tb, why)) return fail(ctx, IBL_ERR_ARG, "capsule mesh: " + why);
+    // the cheap check here; closure and orientation when the context is set
+    // up, where the hinges are built on host threads
+    for (int t = 0; t < nt; ++t) {
+        const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv || a == b || b == c || a == c)
+            return fail(ctx, IBL_ERR_ARG, "capsule mesh: triangle " + std::to_string(t) + " has an invalid vertex index");
+    }
     M->caps.push_back(std::move(ch));
     if (id_out) *id_out = (int32_t)M->caps.size() - 1;
     return IBL_OK;

@@ -88,3 +88,40 @@ def test_valid_duct_sets_up():
     done, _ = s.step(2)
     assert done == 2
     s.close()
+
+
+def _capsule_in_duct(tris_edit):
+    from paper_2207_06043_gb300 import meshes as Ms
+    g = G.straight_duct(24, 16, 16, 12.0, u_max=0.02)
+    V, T = Ms.sphere_mesh(162, 6.0, (8.0, g.info["yc"], g.info["zc"]), Ms.SplitMix64(2))
+    s = Solver.from_geometry(g, 0.8, u_max=0.02)
+    return s, V, tris_edit(np.array(T, np.int32))
+
+
+def test_capsule_index_errors_are_reported_when_added():
+    def bad(T):
+        T[3, 1] = T[3, 0]            # a triangle with a repeated vertex
+        return T
+    s, V, T = _capsule_in_duct(bad)
+    with pytest.raises(IBLError) as e:
+        s.add_capsule(V, T)
+    assert e.value.status == ERR_ARG and "triangle 3 has an invalid vertex index" in str(e.value)
+    T[3, 1] = len(V)                 # out of range
+    with pytest.raises(IBLError):
+        s.add_capsule(V, T)
+    s.close()
+
+
+@pytest.mark.parametrize("edit,words", [
+    (lambda T: T[1:], "not closed"),                                     # a triangle missing
+    (lambda T: np.concatenate([T[:1, ::-1], T[1:]]), "same direction"),  # one triangle flipped
+])
+def test_open_or_misoriented_capsule_is_reported_at_set_up(edit, words):
+    s, V, T = _capsule_in_duct(edit)
+    s.add_capsule(V, T)              # accepted here
+    s.add_capsule(V + 0.0, T)        # a second one, so the message must name the first
+    with pytest.raises(IBLError) as e:
+        s.step(1)
+    msg = str(e.value)
+    assert e.value.status == ERR_ARG and "capsule 0 mesh" in msg and words in msg, msg
+    s.close()
