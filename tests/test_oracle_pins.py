@@ -1,6 +1,7 @@
 """Pins of oracle parts that the other CPU tests leave open: the rigid-body
 Newton-Euler update, the viscous probe stress, the mass balance of the Zou-He
-faces in a steady duct, and the duct flow at D = 24.  Each expected value is
+faces in a steady duct, the duct flow at D = 24, and the momentum exchange of
+a free rigid sphere with the fluid.  Each expected value is
 worked out here by hand from the closed form, not by calling the oracle's own
 formula (no GPU)."""
 import math
@@ -301,3 +302,55 @@ def test_membrane_update_is_stable_below_kappa_0_8():
         amp[target] = float(np.abs(x - X0 - (x - X0).mean(axis=0)).max())
     assert amp[0.7] < 1e-3, amp
     assert amp[0.9] > 1e2 * amp[0.7], amp
+
+
+# ---------------------------------------------------------------------------
+# Free rigid sphere in quiescent fluid (Section "Rigid structures transport",
+# Eq. angularVelRig, with the probe stresses of Eqs. hydroForP, hydroForNu)
+# ---------------------------------------------------------------------------
+def _free_sphere_momenta(steps_marks, flip_hydro=False, monkeypatch=None):
+    from paper_2207_06043_gb300 import meshes as Ms
+    if flip_hydro:
+        orig = membrane.hydrodynamic_forces
+        monkeypatch.setattr(membrane, "hydrodynamic_forces", lambda *a, **k: tuple(-x for x in orig(*a, **k)))
+    g = G.periodic_box(20, 20, 20)
+    lat = L.Lattice(g.nx, g.ny, g.nz, 0.8, g.tag, g.links, g.faces, g.periodic)
+    o = sim.Simulation(lat, u_max=0.01)
+    V, T = Ms.sphere_mesh(162, 8.0, (10.0, 10.2, 9.9), Ms.SplitMix64(4))
+    vel0 = np.array([0.005, 0.001, 0.0])
+    o.add_body(V, T, dict(rigid=1, density_ratio=1.1), vel0=vel0)
+    b = o.bodies[0]
+    out, done = [], 0
+    for n in steps_marks:
+        o.step(n - done)
+        done = n
+        fluid = np.einsum("kn,ka->a", o.f, L.Ef)      # sum_i f_i e_i over every node
+        out.append((fluid, b.rest.mass * b.u1.copy(), b.u1.copy()))
+    return vel0, out
+
+
+def test_free_rigid_sphere_keeps_its_total_momentum_after_the_start_up(monkeypatch):
+    """A rigid sphere (d = 8, density ratio 1.1) released at u0 in fluid at
+    rest, periodic box.  The direct forcing drags the fluid inside and around
+    the sphere to the sphere's velocity within the first steps, and the
+    sphere's own force is the probe traction, not the reaction to that forcing,
+    so the start-up adds momentum (here 1.42 -> 3.60 in 20 steps).  After it
+    the exchange balances: the sphere slows down, the fluid takes up what it
+    loses, the total stays within 5 % over 100 steps (3.6 % measured) and along
+    u0.  With the sign of the probe forces on the sphere reversed, the sphere
+    is pushed along its motion and the total keeps growing (2.7 times from
+    step 20 to step 60, 33 times its value at release)."""
+    marks = (20, 60, 120)
+    vel0, res = _free_sphere_momenta(marks)
+    tot = [f + p for f, p, _ in res]
+    drift = np.linalg.norm(tot[-1] - tot[0]) / np.linalg.norm(tot[0])
+    assert drift < 0.05, drift
+    speeds = [np.linalg.norm(u) for _, _, u in res]
+    assert speeds[0] > speeds[1] > speeds[2] > 0, speeds          # the drag slows the sphere
+    assert res[2][0] @ vel0 > res[0][0] @ vel0 > 0                   # the fluid takes the momentum up
+    cosang = tot[-1] @ vel0 / (np.linalg.norm(tot[-1]) * np.linalg.norm(vel0))
+    assert cosang > 1 - 1e-6, cosang                                  # along u0, no cross-stream drift
+    # a planted sign error in the sphere's hydrodynamic force
+    _, bad = _free_sphere_momenta((20, 60), flip_hydro=True, monkeypatch=monkeypatch)
+    grow = np.linalg.norm(bad[1][0] + bad[1][1]) / np.linalg.norm(bad[0][0] + bad[0][1])
+    assert grow > 2.0, grow
