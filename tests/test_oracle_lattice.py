@@ -96,6 +96,26 @@ def test_periodic_box_mass_and_momentum():
     assert np.allclose(p - p0, 10 * lat.N * F, atol=1e-12)
 
 
+def test_periodic_box_momentum_gain_equals_a_varying_ib_force():
+    """Guo forcing (Eq. forcing) with a force field that differs from node to
+    node, as the spread IB force does: mass is kept and every step adds
+    exactly sum_k f_ib^k to the momentum (Sigma F_i e_i = (1 - 1/2tau) F plus
+    the F/2 carried by the equilibrium through rho u = sum f e + F/2)."""
+    g = G.periodic_box(6, 5, 4)
+    lat = L.Lattice(g.nx, g.ny, g.nz, 0.7, g.tag, g.links, g.faces, g.periodic)
+    r = _rng(12)
+    f = lat.init_equilibrium(1 + 0.01 * r.standard_normal(lat.N), 0.01 * r.standard_normal((lat.N, 3)))
+    m0 = f.sum()
+    p = (L.Ef.T @ f).sum(axis=1)
+    for s in range(5):
+        fib = 1e-4 * r.standard_normal((lat.N, 3))
+        f = lat.step(f, fib)
+        p_new = (L.Ef.T @ f).sum(axis=1)
+        assert np.allclose(p_new - p, fib.sum(axis=0), rtol=0, atol=1e-13), s
+        p = p_new
+    assert abs(f.sum() - m0) < 1e-11
+
+
 def test_shear_wave_decay_rate():
     """u_y = U sin(k x) in a periodic box decays as exp(-nu k^2 t), nu = (tau - 1/2)/3."""
     nx = 32
