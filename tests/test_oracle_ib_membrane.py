@@ -266,3 +266,25 @@ def test_hydrodynamic_pressure_force_from_linear_density():
     exp = -(beta / 3.0 * 2.4 * nrm[:, 0] * Av)[:, None] * nrm
     assert np.allclose(Fp, exp, atol=1e-14)
     assert np.abs(Ft).max() < 1e-14
+
+
+# -- damage rule (Section "Transport of an elastic capsule") ---------------------
+
+def test_largest_stretch_of_a_scaled_mesh_is_the_scale_and_two_stops_the_run():
+    """Every edge of a mesh scaled by s about any point is s times its rest
+    length, so the largest stretch is s (to rounding); an edge at twice its
+    rest length is the damage of the paper's rule and stops the run at the
+    step that finds it (the lattice is not stepped further)."""
+    X, T = meshes.sphere_mesh(162, 8.0, (6.0, 6.0, 6.0), meshes.SplitMix64(3))
+    rest = Mb.CapsuleRest(X, T, dict(Ca=0.05), 0.8)
+    c = X.mean(axis=0)
+    for s in (1.0, 1.25, 1.999):
+        assert abs(Mb.max_stretch(c + s * (X - c), rest) - s) < 1e-12, s
+    lat = _box_lattice(12)
+    o = sim.Simulation(lat, u_max=0.01)
+    o.add_body(X, T, dict(Ca=0.05))
+    assert o.step(1) == 1 and not o.damaged
+    o.bodies[0].x = c + 2.0 * (o.bodies[0].x - c)
+    o.bodies[0].x_prev = o.bodies[0].x.copy()
+    assert o.step(3) == 1 and o.damaged          # found at the end of that step
+    assert o.step(5) == 0                         # nothing more runs
