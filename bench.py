@@ -426,13 +426,15 @@ def main():
     peak, peak_kind = load_peaks()
     lbm_ms = kt["lattice"] / args.steps
     achieved = bpu * nf / (lbm_ms * 1e-3) / 1e9
-    traffic = lbm_traffic(args.workload, args.storage)
+    # the captured traffic belongs to the register-gather kernel
+    traffic = None if args.staged else lbm_traffic(args.workload, args.storage)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
             "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches, "
                                f"lattice sources {lbm_source_hash()}" if traffic else
                                f"not captured for the lattice sources {lbm_source_hash()}"),
-            "kernel": "k_lbm (fused collide+stream, AA pattern)",
+            "kernel": ("k_lbm_tile (staged by bulk copies)" if args.staged else "k_lbm") +
+                      " (fused collide+stream, AA pattern)",
             "peak_source": f"{peak_kind} hbm_gbs", "ms_per_launch": lbm_ms,
             "algorithmic_bytes_per_launch": bpu * nf}
     s.close()
