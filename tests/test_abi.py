@@ -55,3 +55,29 @@ def test_product_path_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         binding.lib()
+
+
+def _header_arities():
+    """Parameter count of every function prototype in include/ibl.h (comments
+    stripped; `(void)` counts as none)."""
+    import re
+    txt = open(binding.HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"(?:ibl_status|int32_t|void|const char\s*\*)\s+(ibl_\w+)\s*\(([^)]*)\)\s*;", txt):
+        params = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header_arity(lib):
+    """Every declared call is bound with as many arguments as its prototype
+    has, and the binding binds nothing the header does not declare."""
+    ar = _header_arities()
+    assert set(ar) == set(binding.header_functions())
+    for name, n in ar.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+    bound = {k for k in vars(lib) if k.startswith("ibl_")}     # the functions the binding set up
+    assert bound and bound <= set(ar), bound - set(ar)
